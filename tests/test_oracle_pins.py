@@ -1,0 +1,420 @@
+"""Pins of the FP64 oracle against facts the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: closed forms
+(chord lengths, ramp magnitudes, corner values), brute force on tiny inputs (per-pixel
+clipping, dense least squares), invariants (adjoint identity, CGLS monotonicity,
+Armijo sufficient decrease) and library routines (partition for the order statistic).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import eptv_oracle as O
+from paper_1009_2288_b300 import inputs as I
+
+
+def _box_chord(nx, ny, dx, dy, sx, sy, ux, uy):
+    """Length of the line s + t u (t >= 0) inside the image rectangle (slab clipping)."""
+    lo = [-nx * dx / 2, -ny * dy / 2]
+    hi = [nx * dx / 2, ny * dy / 2]
+    t0, t1 = 0.0, math.inf
+    for s, u, a, b in ((sx, ux, lo[0], hi[0]), (sy, uy, lo[1], hi[1])):
+        if u == 0.0:
+            if not (a < s < b):
+                return 0.0
+            continue
+        ta, tb = (a - s) / u, (b - s) / u
+        t0, t1 = max(t0, min(ta, tb)), min(t1, max(ta, tb))
+    return max(0.0, t1 - t0)
+
+
+def _pixel_clip(x0, x1, y0, y1, sx, sy, ux, uy):
+    """Liang-Barsky clip of the line against one pixel rectangle."""
+    t0, t1 = -math.inf, math.inf
+    for s, u, a, b in ((sx, ux, x0, x1), (sy, uy, y0, y1)):
+        if u == 0.0:
+            if not (a <= s <= b):
+                return 0.0
+            continue
+        ta, tb = (a - s) / u, (b - s) / u
+        t0, t1 = max(t0, min(ta, tb)), min(t1, max(ta, tb))
+    t0 = max(t0, 0.0)
+    return max(0.0, t1 - t0)
+
+
+# ---------------------------------------------------------------- geometry (Sec. 3)
+
+def test_geometry_sources_and_fan_angles():
+    g = I.FanGeometry(32, 32, 1.0, 1.0, 7, 9, 0.01, 0.0, 541.0, 949.075, I.ARC)
+    sx, sy, ux, uy = O.rays(g)
+    assert np.allclose(np.hypot(sx, sy), 541.0, rtol=0, atol=1e-12)
+    assert np.allclose(np.hypot(ux, uy), 1.0, atol=1e-15)
+    for v in range(g.n_views):
+        th = 2 * np.pi * v / g.n_views
+        for k in range(g.n_bins):
+            r = v * g.n_bins + k
+            # angle between the ray and the central ray -(cos th, sin th), signed (+ = ccw)
+            cx, cy = -math.cos(th), -math.sin(th)
+            beta = math.atan2(cx * uy[r] - cy * ux[r], cx * ux[r] + cy * uy[r])
+            assert beta == pytest.approx((k - 4) * 0.01, abs=1e-14)
+    # central bin (offset 0, odd count) passes through the isocentre
+    for v in range(g.n_views):
+        r = v * g.n_bins + 4
+        assert abs(sx[r] * uy[r] - sy[r] * ux[r]) < 1e-12
+
+
+def test_geometry_flat_detector_and_offset():
+    g = I.FanGeometry(16, 16, 1.0, 1.0, 3, 6, 0.002, 0.25, 1000.0, 1500.0, I.FLAT)
+    sx, sy, ux, uy = O.rays(g)
+    for k in range(6):
+        cx, cy = -1.0, 0.0                       # view 0
+        tanb = (cx * uy[k] - cy * ux[k]) / (cx * ux[k] + cy * uy[k])
+        assert tanb == pytest.approx((k - 2.5 + 0.25) * 0.002, abs=1e-15)
+
+
+def test_oracle_rays_agree_with_data_generator_rays():
+    g = I.c1_geometry()
+    a = O.rays(g)
+    b = I.fan_rays(g)
+    for u, w in zip(a, b):
+        assert np.allclose(u, w, rtol=0, atol=1e-12)
+
+
+# ---------------------------------------------------------------- P (Eq. 1, Siddon)
+
+@pytest.mark.parametrize("nx,ny,dx,dy", [(8, 8, 1.0, 1.0), (7, 5, 0.8, 1.3), (64, 48, 2.0, 2.0)])
+def test_row_sum_is_chord_through_image(nx, ny, dx, dy):
+    """sum_j p_ij = length of ray i inside the image square (closed form)."""
+    rng = np.random.Generator(np.random.PCG64(5))
+    ones = np.ones(nx * ny)
+    for _ in range(200):
+        ang = rng.uniform(0, 2 * np.pi)
+        sx, sy = 3 * nx * dx * math.cos(ang), 3 * ny * dy * math.sin(ang)
+        tgt = (rng.uniform(-0.6, 0.6) * nx * dx, rng.uniform(-0.6, 0.6) * ny * dy)
+        ux, uy = tgt[0] - sx, tgt[1] - sy
+        n = math.hypot(ux, uy)
+        ux, uy = ux / n, uy / n
+        got = O.project_rays(nx, ny, dx, dy, [sx], [sy], [ux], [uy], ones)[0]
+        want = _box_chord(nx, ny, dx, dy, sx, sy, ux, uy)
+        assert got == pytest.approx(want, rel=1e-12, abs=1e-12)
+
+
+def test_axis_aligned_rays_give_pixel_pitch():
+    nx, ny, dx, dy = 6, 4, 0.7, 1.1
+    x0, y0 = -nx * dx / 2, -ny * dy / 2
+    for j in range(ny):   # horizontal rays through pixel-row centres
+        pix, ln = O.ray_row(nx, ny, dx, dy, -100.0, y0 + (j + 0.5) * dy, 1.0, 0.0)
+        assert sorted(pix.tolist()) == [j * nx + i for i in range(nx)]
+        assert np.allclose(ln, dx, rtol=0, atol=1e-12)
+    for i in range(nx):   # vertical rays, pointing down
+        pix, ln = O.ray_row(nx, ny, dx, dy, x0 + (i + 0.5) * dx, 100.0, 0.0, -1.0)
+        assert sorted(pix.tolist()) == [j * nx + i for j in range(ny)]
+        assert np.allclose(ln, dy, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("nx,ny,dx,dy", [(4, 4, 1.0, 1.0), (5, 3, 0.8, 1.3)])
+def test_brute_force_pixel_clipping(nx, ny, dx, dy):
+    """Every p_ij equals the clip of ray i against pixel j alone."""
+    rng = np.random.Generator(np.random.PCG64(11))
+    x0, y0 = -nx * dx / 2, -ny * dy / 2
+    for _ in range(300):
+        ang = rng.uniform(0, 2 * np.pi)
+        sx, sy = 10 * math.cos(ang), 10 * math.sin(ang)
+        tx, ty = rng.uniform(x0, -x0), rng.uniform(y0, -y0)
+        ux, uy = tx - sx, ty - sy
+        n = math.hypot(ux, uy)
+        ux, uy = ux / n, uy / n
+        pix, ln = O.ray_row(nx, ny, dx, dy, sx, sy, ux, uy)
+        dense = np.zeros(nx * ny)
+        np.add.at(dense, pix, ln)
+        want = np.array([_pixel_clip(x0 + i * dx, x0 + (i + 1) * dx, y0 + j * dy,
+                                     y0 + (j + 1) * dy, sx, sy, ux, uy)
+                         for j in range(ny) for i in range(nx)])
+        assert np.allclose(dense, want, rtol=0, atol=1e-12)
+
+
+def test_disk_projection_converges_to_chord():
+    """P 1_disk -> 2 sqrt(R^2 - d^2) for a finely rasterised uniform disk."""
+    R = 40.0
+    n, d = 256, 0.5
+    g = I.FanGeometry(n, n, d, d, 3, 64, 0.0016, 0.25, 500.0, 800.0, I.ARC)
+    disk = I.rasterize([I.Ellipse(0, 0, R, R, 0.0, 1.0)], g, ss=8)
+    y = O.Operator(g).project(disk).ravel()
+    sx, sy, ux, uy = O.rays(g)
+    dist = np.abs(sx * uy - sy * ux)
+    want = 2 * np.sqrt(np.maximum(R * R - dist * dist, 0.0))
+    inner = dist < 0.9 * R
+    assert np.max(np.abs(y - want)[inner]) < 0.02 * 2 * R
+    assert np.mean(np.abs(y - want)[inner]) < 0.002 * 2 * R
+
+
+# ---------------------------------------------------------------- P^T (adjoint, Eq. A3)
+
+def test_adjoint_identity_fp64():
+    g = I.c1_geometry()
+    op = O.Operator(g)
+    for seed in range(3):
+        x = I.random_image(g, 100 + seed, "normal")
+        y = I.random_sino(g, 200 + seed)
+        px = op.project(x)
+        lhs, rhs = float(np.sum(px * y)), float(np.sum(x * op.backproject(y)))
+        assert abs(lhs - rhs) / (np.linalg.norm(px) * np.linalg.norm(y)) < 1e-13
+
+
+def test_backprojection_is_dense_transpose():
+    g = I.FanGeometry(6, 5, 1.0, 1.2, 4, 7, 0.03, 0.25, 30.0, 60.0, I.ARC)
+    op = O.Operator(g)
+    P = np.stack([op.project(np.eye(30)[j].reshape(5, 6)).ravel() for j in range(30)], 1)
+    PT = np.stack([op.backproject(np.eye(28)[i].reshape(4, 7)).ravel() for i in range(28)], 1)
+    assert np.array_equal(PT, P.T)
+    assert np.count_nonzero(P) > 20
+
+
+# ---------------------------------------------------------------- CGLS (App. I)
+
+def _tiny():
+    g = I.FanGeometry(16, 16, 1.0, 1.0, 12, 32, 0.045, 0.25, 60.0, 100.0, I.ARC)
+    return g, O.Operator(g)
+
+
+def test_cgls_residual_non_increasing():
+    g, op = _tiny()
+    rng = np.random.Generator(np.random.PCG64(3))
+    y = op.project(rng.uniform(0, 1, (16, 16))) + 0.01 * rng.standard_normal((12, 32))
+    log = []
+    O.cgls(op, y, np.zeros((16, 16)), 40, log)
+    rr = [e["rr"] for e in log]
+    assert all(b <= a * (1 + 1e-12) for a, b in zip(rr, rr[1:]))
+
+
+def test_cgls_first_step_is_exact_line_search():
+    g, op = _tiny()
+    rng = np.random.Generator(np.random.PCG64(4))
+    P = np.stack([op.project(np.eye(256)[j].reshape(16, 16)).ravel() for j in range(256)], 1)
+    y = rng.standard_normal(12 * 32)
+    u0 = rng.uniform(0, 1, 256)
+    r0 = y - P @ u0
+    s0 = P.T @ r0
+    q = P @ s0
+    a_star = float(q @ r0) / float(q @ q)    # argmin_a |P (u0 + a s0) - y|
+    u1 = O.cgls(op, y.reshape(12, 32), u0.reshape(16, 16), 1).ravel()
+    assert np.allclose(u1, u0 + a_star * s0, rtol=1e-12, atol=1e-12)
+
+
+def test_cgls_converges_to_min_norm_least_squares():
+    g, op = _tiny()
+    rng = np.random.Generator(np.random.PCG64(6))
+    P = np.stack([op.project(np.eye(256)[j].reshape(16, 16)).ravel() for j in range(256)], 1)
+    y = rng.standard_normal(12 * 32)
+    u0 = rng.uniform(0, 1, 256)
+    want = u0 + np.linalg.lstsq(P, y - P @ u0, rcond=None)[0]
+    got = O.cgls(op, y.reshape(12, 32), u0.reshape(16, 16), 400).ravel()
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) < 1e-6
+
+
+# ------------------------------------------------------ EPTV stencil (Eqs. A2, A3, 5, 9)
+
+def test_half_edge_magnitude_on_ramp():
+    """For f = a i + b j, interior T = sqrt(eps^2 + a^2 + b^2) (pins the 1/2 factors)."""
+    a, b, eps = 0.3, -0.7, 1e-3
+    j, i = np.mgrid[0:9, 0:11]
+    f = a * i + b * j + 5.0
+    Dx, Tx, Dy, Ty = O.half_edges(f, eps)
+    want = math.sqrt(eps * eps + a * a + b * b)
+    assert np.allclose(Tx[1:-1, 1:-1], want, rtol=1e-14)
+    assert np.allclose(Ty[1:-1, 1:-1], want, rtol=1e-14)
+    assert np.allclose(Dx[:, 1:-1], a) and np.allclose(Dy[1:-1, :], b)
+
+
+def test_half_edge_magnitude_zero_boundary_corner():
+    """A single pixel h at (0, 0), zero outside: hand-computed magnitudes."""
+    h, eps = 2.0, 1e-3
+    f = np.zeros((4, 5))
+    f[0, 0] = h
+    Dx, Tx, Dy, Ty = O.half_edges(f, eps)
+    # x half-edge between the outside and pixel (0,0): D = h, cross terms +-h/2
+    assert Dx[0, 0] == h
+    assert Tx[0, 0] == pytest.approx(math.sqrt(eps ** 2 + h * h + 0.25 * h * h))
+    # x half-edge between (0,0) and (1,0): D = -h, same cross terms
+    assert Dx[0, 1] == -h
+    assert Tx[0, 1] == pytest.approx(math.sqrt(eps ** 2 + 1.25 * h * h))
+    # x half-edge between (0,1) and (1,1): D = 0, upper-neighbour average h/2 below it
+    assert Tx[1, 1] == pytest.approx(math.sqrt(eps ** 2 + 0.5 * 0.25 * h * h))
+    # far away: T = eps
+    assert Tx[3, 4] == pytest.approx(eps) and Ty[3, 4] == pytest.approx(eps)
+
+
+def _lagged_energy_terms(f, eps):
+    """Primary differences and frozen cross-term sums C_e per half-edge, by loops."""
+    ny, nx = f.shape
+
+    def F(i, j):
+        return f[j, i] if (0 <= i < nx and 0 <= j < ny) else 0.0
+    ex, ey = [], []
+    for j in range(ny):
+        for e in range(nx + 1):            # between pixels e-1 and e
+            i = e - 1
+            m = [0.5 * (F(i, l) + F(i + 1, l)) for l in (j - 1, j, j + 1)]
+            ex.append(((i, j), (i + 1, j), 0.5 * (m[2] - m[1]) ** 2 + 0.5 * (m[1] - m[0]) ** 2))
+    for e in range(ny + 1):
+        for i in range(nx):
+            j = e - 1
+            m = [0.5 * (F(l, j) + F(l, j + 1)) for l in (i - 1, i, i + 1)]
+            ey.append(((i, j), (i, j + 1), 0.5 * (m[2] - m[1]) ** 2 + 0.5 * (m[1] - m[0]) ** 2))
+    return ex, ey
+
+
+def test_a2_equals_derivative_of_lagged_energy():
+    """Eq. (A2) is the gradient of sum_e w_e sqrt(eps^2 + D_e(f)^2 + C_e) with w and the
+    cross terms C_e frozen at f (lagged diffusivity), checked by central differences."""
+    rng = np.random.Generator(np.random.PCG64(8))
+    ny, nx, eps, lam = 5, 6, 1e-2, 3.0
+    f = rng.uniform(0, 1, (ny, nx))
+    v = rng.uniform(0, 1, (ny, nx))
+    _, Tx, _, Ty = O.half_edges(f, eps)
+    sigma = float(np.median(np.concatenate([Tx.ravel(), Ty.ravel()])))
+    g, wx, wy, _ = O.p2_gradient(f, v, lam, eps, sigma)
+    ex, ey = _lagged_energy_terms(f, eps)
+    w = np.concatenate([wx.ravel(), wy.ravel()])
+
+    def F(fp, i, j):
+        return fp[j, i] if (0 <= i < nx and 0 <= j < ny) else 0.0
+
+    def energy(fp):
+        E = 0.5 * lam * float(np.sum((fp - v) ** 2))
+        for k, (a, b, C) in enumerate(ex + ey):
+            D = F(fp, *b) - F(fp, *a)
+            E += w[k] * math.sqrt(eps * eps + D * D + C)
+        return E
+
+    h = 1e-6
+    fd = np.zeros_like(f)
+    for j in range(ny):
+        for i in range(nx):
+            fp, fm = f.copy(), f.copy()
+            fp[j, i] += h
+            fm[j, i] -= h
+            fd[j, i] = (energy(fp) - energy(fm)) / (2 * h)
+    assert np.allclose(g, fd, rtol=1e-6, atol=1e-7)
+    # and the cross terms frozen at f reproduce the A3 magnitude itself
+    T_loop = np.array([math.sqrt(eps ** 2 + (F(f, *b) - F(f, *a)) ** 2 + C) for a, b, C in ex + ey])
+    assert np.allclose(T_loop, np.concatenate([Tx.ravel(), Ty.ravel()]), rtol=1e-14)
+
+
+def test_constant_image_interior_gradient_is_fidelity_only():
+    f = np.full((12, 12), 0.02)
+    v = np.random.Generator(np.random.PCG64(1)).uniform(0, 0.03, (12, 12))
+    g, _, _, _ = O.p2_gradient(f, v, 7.0, 1e-5, 1e-3)
+    assert np.allclose(g[2:-2, 2:-2], 7.0 * (f - v)[2:-2, 2:-2], rtol=0, atol=1e-15)
+
+
+def test_tv_special_case_step_is_textbook_sign_gradient():
+    """w = 1, eps -> 0, step along x: delta J = -1 left of the jump, +1 right of it."""
+    f = np.zeros((10, 12))
+    f[:, 6:] = 1.0
+    g, _, _, _ = O.p2_gradient(f, f, 1.0, 1e-12, 1.0, mode=O.ONE)
+    assert np.allclose(g[3:7, 5], -1.0, atol=1e-9)
+    assert np.allclose(g[3:7, 6], 1.0, atol=1e-9)
+    assert np.allclose(g[3:7, 2:4], 0.0, atol=1e-9)
+
+
+def test_weights_in_unit_interval_and_value_at_sigma():
+    rng = np.random.Generator(np.random.PCG64(2))
+    T = rng.uniform(1e-6, 1.0, 1000)
+    w = O.edge_weights(T, 0.3)
+    assert np.all(w > 0) and np.all(w <= 1)
+    assert O.edge_weights(np.array([0.3]), 0.3)[0] == pytest.approx(math.exp(-1.0), rel=1e-15)
+
+
+# ---------------------------------------------------------------- sigma (Sec. 2.1)
+
+@pytest.mark.parametrize("q", [0.9, 0.95, 0.5, 0.0, 1.0])
+def test_sigma_is_order_statistic(q):
+    rng = np.random.Generator(np.random.PCG64(9))
+    f = rng.uniform(0, 0.03, (17, 23))
+    _, Tx, _, Ty = O.half_edges(f, 1e-5)
+    pool = np.concatenate([Tx.ravel(), Ty.ravel()])
+    n = pool.size
+    k = min(max(math.ceil(q * n), 1), n)
+    s = O.select_sigma(Tx, Ty, q)
+    assert s == np.partition(pool, k - 1)[k - 1]
+    assert np.count_nonzero(pool <= s) >= k and np.count_nonzero(pool < s) < k
+
+
+# ---------------------------------------------------------------- (P2) GD + Armijo
+
+def test_armijo_sufficient_decrease_every_step():
+    rng = np.random.Generator(np.random.PCG64(12))
+    v = rng.uniform(0, 0.03, (20, 20))
+    p = I.EptvParams(n_gd=12)
+    f = v.copy()
+    _, Tvx, _, Tvy = O.half_edges(v, p.eps)
+    sigma = O.select_sigma(Tvx, Tvy, p.sigma_q)
+    fo, st = O.p2_solve(v, p, p.t_init_eff)
+    assert st.sigma == sigma
+    for t in st.steps:
+        g, wx, wy, E0 = O.p2_gradient(f, v, p.lam, p.eps, sigma)
+        if t > 0:
+            E1 = O.p2_energy_frozen(f - t * g, v, p.lam, p.eps, wx, wy)
+            assert E1 <= E0 - p.armijo_c * t * float(np.sum(g * g))
+            # the step before it (twice as long) was rejected unless it was the first trial
+            f = f - t * g
+    assert np.allclose(f, fo)
+
+
+def test_plain_tv_p2_energy_monotone():
+    rng = np.random.Generator(np.random.PCG64(13))
+    v = rng.uniform(0, 0.03, (24, 24))
+    p = I.EptvParams(n_gd=15, weights_mode=O.ONE)
+    _, st = O.p2_solve(v, p, p.t_init_eff)
+    E = st.energies
+    assert all(b <= a for a, b in zip(E, E[1:]))
+    assert E[-1] < E[0]
+
+
+# ---------------------------------------------------------------- outer loop, Eq. (2)
+
+def test_report_energy_of_zero_image_closed_form():
+    g = I.FanGeometry(8, 6, 1.0, 1.0, 3, 5, 0.05, 0.25, 30.0, 50.0, I.ARC)
+    op = O.Operator(g)
+    y = I.random_sino(g, 3)
+    p = I.EptvParams(mu=2.5, eps=1e-3)
+    sigma = 4e-3
+    n_edges = 6 * 9 + 7 * 8
+    want = 0.5 * 2.5 * float(np.sum(y * y)) + n_edges * 1e-3 * math.exp(-(1e-3 / sigma) ** 2)
+    assert O.report_energy(op, np.zeros((6, 8)), y, p, sigma) == pytest.approx(want, rel=1e-14)
+
+
+def test_reconstruct_positive_and_better_than_zero(c1_case):
+    op = O.Operator(c1_case.geom)
+    p = I.EptvParams(n_outer=4)
+    f = O.reconstruct(op, c1_case.y, p)
+    assert np.all(f >= 0)
+    e = np.sum((f - c1_case.f_true) ** 2) / np.sum(c1_case.f_true ** 2)
+    assert e < 0.05
+
+
+def test_prior_edge_weights_hand_example():
+    w = np.array([[0.2, 0.6], [1.0, 0.4]])
+    wx, wy = O.prior_edge_weights(w)
+    assert np.allclose(wx, [[0.2, 0.4, 0.6], [1.0, 0.7, 0.4]])
+    assert np.allclose(wy, [[0.2, 0.6], [0.6, 0.5], [1.0, 0.4]])
+
+
+# ---------------------------------------------------------------- synthetic inputs
+
+def test_analytic_disk_line_integrals():
+    g = I.c1_geometry()
+    sx, sy, ux, uy = I.fan_rays(g)
+    p = I.line_integrals([I.Ellipse(10.0, -5.0, 30.0, 30.0, 0.3, 0.02)], sx, sy, ux, uy)
+    d = np.abs((sx - 10.0) * uy - (sy + 5.0) * ux)
+    want = 0.02 * 2 * np.sqrt(np.maximum(900.0 - d * d, 0.0))
+    assert np.allclose(p, want, rtol=0, atol=1e-10)     # near-tangent rays amplify rounding
+
+
+def test_overwrite_painting_along_ray():
+    # disk 0.02 radius 50 with a concentric 0.03 disk radius 20 painted over it
+    els = [I.Ellipse(0, 0, 50, 50, 0, 0.02), I.Ellipse(0, 0, 20, 20, 0, 0.03)]
+    p = I.line_integrals(els, np.array([-200.0]), np.array([0.0]), np.array([1.0]), np.array([0.0]))
+    assert p[0] == pytest.approx(0.02 * 60 + 0.03 * 40, rel=1e-14)

@@ -1,0 +1,418 @@
+#!/usr/bin/env python
+"""EPTV reconstruction benchmark on B300: outer iterations per second.
+
+Workload: the 512x512 (0.8 mm) fan-beam reconstruction with 40 views x 888 bins of the
+paper's GE-like scanner (Sec. 3), a seeded 30-ellipse phantom with a ring of 8
+low-contrast discs, Poisson noise I0 = 5e4, 100 EPTV iterations (M = 3 CGLS iterations,
+10 GD iterations per (P2), Armijo steps).  One step = one full 100-iteration
+reconstruction through the C ABI.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank reconstructs its own
+slice (replicas, no collective on the data path) and `value` is the whole-job rate.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "EPTV iterations/s (512x512, 40 views x 888 bins, 100 iterations)"
+UNIT = "iterations/s"
+WORKLOAD = "eptv_512x512_40v_888b"
+N_OUTER = 100
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tte", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return out
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        out.update(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=max(mx) if mx else None,
+                   reasons=reasons, samples=len(rows))
+        return out
+
+
+def nnz_of(g):
+    """Number of nonzeros of P: for each ray, the number of pixels it crosses, counted from
+    the closed-form entry and exit points of its chord through the image rectangle."""
+    import numpy as np
+    from paper_1009_2288_b300 import inputs as I
+    sx, sy, ux, uy = I.fan_rays(g)
+    x0, y0 = -g.nx * g.dx / 2, -g.ny * g.dy / 2
+    with np.errstate(divide="ignore", invalid="ignore"):
+        tx = np.sort(np.stack([(x0 - sx) / ux, (-x0 - sx) / ux]), axis=0)
+        ty = np.sort(np.stack([(y0 - sy) / uy, (-y0 - sy) / uy]), axis=0)
+    t0 = np.maximum(tx[0], ty[0])
+    t1 = np.minimum(tx[1], ty[1])
+    hit = t1 > t0
+
+    def interior(s, u, o, d, n):
+        a, b = (s + t0 * u - o) / d, (s + t1 * u - o) / d
+        lo, hi = np.minimum(a, b), np.maximum(a, b)
+        first = np.maximum(np.floor(lo) + 1, 1)
+        last = np.minimum(np.ceil(hi) - 1, n - 1)
+        return np.maximum(last - first + 1, 0)
+    cnt = interior(sx, ux, x0, g.dx, g.nx) + interior(sy, uy, y0, g.dy, g.ny) + 1
+    return int(np.sum(np.where(hit, cnt, 0)))
+
+
+def source_sha(files):
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def load_counters(kernel, files):
+    """DRAM bytes per launch from the committed ncu summary, if taken on this source."""
+    path = os.path.join(ROOT, "profiles", "counters.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        data = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    ent = data.get(kernel)
+    if not ent or ent.get("source_sha") != source_sha(files):
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d.get("hbm_gbs", 6400.0), "measured"
+    return 6400.0, "fallback"
+
+
+def cpu_baseline(case, steps=2):
+    """The FP64 oracle as it stands, on the host: `steps` outer iterations of the same
+    workload (a bounded sample of the 100)."""
+    import numpy as np
+    from oracle import eptv_oracle as O
+    from paper_1009_2288_b300 import inputs as I
+    p = I.EptvParams(n_outer=steps)
+    op = O.Operator(case.geom)
+    t0 = time.perf_counter()
+    O.reconstruct(op, case.y, p)
+    dt = time.perf_counter() - t0
+    return {"value": steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} of the {N_OUTER} outer iterations of {WORKLOAD} "
+                      f"(single-threaded C Siddon + numpy FP64), {dt:.1f} s"}
+
+
+def run_reference(args, world, rank):
+    """Reference arm: the FP64 oracle timed on the host cores, same workload and metric,
+    each step = one outer iteration (a bounded sample of the 100)."""
+    if rank != 0:
+        return
+    import numpy as np
+    from oracle import eptv_oracle as O
+    from paper_1009_2288_b300 import inputs as I
+    case = I.make_c2(with_truth=False)
+    op = O.Operator(case.geom)
+    p = I.EptvParams(n_outer=1)
+    f = np.zeros((case.geom.ny, case.geom.nx))
+    t_prev = p.t_init_eff
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        v = O.cgls(op, case.y, f, p.cgls_iters)
+        f, st = O.p2_solve(v, p, t_prev)
+        t_prev = st.t_prev
+        f = np.maximum(f, 0.0)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    ms = 1e3 * statistics.mean(times)
+    value = 1e3 / ms
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "step": "one outer iteration (sample of 100)",
+                   "image": "512x512 @ 0.8 mm", "views": 40, "bins": 888, "M": 3, "n_gd": 10},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} outer iterations of {WORKLOAD}, one per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def time_kernel(fn, n=50):
+    import torch
+    for _ in range(5):
+        fn()
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(n):
+        fn()
+    e.record()
+    torch.cuda.synchronize()
+    return s.elapsed_time(e) / n * 1e-3     # seconds per launch
+
+
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+    from paper_1009_2288_b300 import eptv as E
+    from paper_1009_2288_b300 import inputs as I
+    from paper_1009_2288_b300 import build as B
+
+    B.build()
+    E.load()
+    dev = torch.device("cuda", local)
+    case = I.make_c2(seed=2 + rank, with_truth=False)
+    g = case.geom
+    geo = E.Geometry(g)
+    p = I.EptvParams(n_outer=N_OUTER)
+    y_host = torch.from_numpy(case.y.astype(np.float32).reshape(-1)).pin_memory()
+    y_dev = y_host.to(dev)
+    f_dev = torch.zeros(g.n_pix, device=dev)
+    f_host = torch.empty(g.n_pix, dtype=torch.float32).pin_memory()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        f_dev.zero_()
+        return E.eptv_reconstruct(geo, p, y_dev, f_dev, report=True)
+
+    for _ in range(args.warmup):
+        rep = step()
+    torch.cuda.synchronize()
+    launches = rep.n_launches
+
+    # device-resident timing, one event pair per step, L2 flushed between steps
+    clocks = Clocks(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        f_dev.zero_()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        E.eptv_reconstruct(geo, p, y_dev, f_dev, report=False)
+        e.record(stream)
+        e.synchronize()
+        times.append(s.elapsed_time(e))
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    ms = max_over_ranks(statistics.mean(times), world)
+    value = world * N_OUTER * 1e3 / ms
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the region
+    e2e_times = []
+    barrier(world)
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        flush.zero_()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        y_dev.copy_(y_host, non_blocking=True)
+        f_dev.zero_()
+        E.eptv_reconstruct(geo, p, y_dev, f_dev, report=False)
+        f_host.copy_(f_dev, non_blocking=True)
+        e.record(stream)
+        e.synchronize()
+        e2e_times.append(s.elapsed_time(e))
+    barrier(world)
+    e2e_ms = max_over_ranks(statistics.mean(e2e_times), world)
+
+    # dominant kernels timed live: projector (with transposed image) and back projector
+    fT = torch.empty_like(f_dev)
+    E.eptv_transpose(geo, f_dev, fT)
+    ybuf = torch.empty(g.n_rays, device=dev)
+    ximg = torch.empty_like(f_dev)
+    t_k1 = time_kernel(lambda: E.eptv_project_t(geo, f_dev, fT, ybuf))
+    t_k2 = time_kernel(lambda: E.eptv_backproject(geo, y_dev, ximg))
+    per_outer = {"k1_project": (p.cgls_iters + 1) * t_k1, "k2_backproject": p.cgls_iters * t_k2}
+    dom = max(per_outer, key=per_outer.get)
+    nnz = nnz_of(g)
+    vec = 4 * (g.n_pix + g.n_rays)
+    t_dom = t_k1 if dom == "k1_project" else t_k2
+    algo_bytes = 8 * nnz + vec          # CSR SpMV equivalent: value + column index per nonzero
+    peak, peak_kind = measured_peaks()
+    achieved = algo_bytes / t_dom / 1e9
+    src = {"k1_project": ["paper_1009_2288_b300/csrc/project.cu"],
+           "k2_backproject": ["paper_1009_2288_b300/csrc/backproject.cu"]}[dom] + \
+        ["paper_1009_2288_b300/csrc/eptv_internal.cuh", "paper_1009_2288_b300/csrc/kernels.cuh"]
+    traffic = load_counters(dom, src)
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                "algorithmic_bytes_per_launch": algo_bytes, "nnz": nnz,
+                "launch_us": {"k1_project": t_k1 * 1e6, "k2_backproject": t_k2 * 1e6}}
+
+    # time to the FP64 oracle's final reported energy (stored by tests/golden/make_oracle_energy.py)
+    tte = None
+    gold = os.path.join(ROOT, "tests", "golden", "c2_oracle_energy.json")
+    if not args.no_tte and rank == 0 and os.path.exists(gold):
+        ref = json.load(open(gold))
+        sig, e_star = ref["sigma_ref"], ref["e_report_final"]
+        pk = I.EptvParams(n_outer=1)
+        f_dev.zero_()
+        k_star = None
+        energies = []
+        for k in range(1, N_OUTER + 1):
+            rep = E.eptv_reconstruct(geo, pk, y_dev, f_dev, report=True)
+            pk.t_init = rep.t_prev
+            ek = E.eptv_report_energy(geo, p, sig, f_dev, y_dev)
+            energies.append(ek)
+            if k_star is None and ek <= e_star * (1 + 1e-3):
+                k_star = k
+                break
+        if k_star is not None:
+            pt = I.EptvParams(n_outer=k_star)
+            ts = []
+            for _ in range(3):
+                f_dev.zero_()
+                s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                s.record(stream)
+                E.eptv_reconstruct(geo, pt, y_dev, f_dev, report=False)
+                e.record(stream)
+                e.synchronize()
+                ts.append(s.elapsed_time(e))
+            tte = {"seconds": min(ts) * 1e-3, "iterations": k_star,
+                   "oracle_iterations": int(next((i + 1 for i, v in enumerate(ref["e_report_per_iteration"])
+                                                  if v <= e_star * (1 + 1e-3)), ref["n_outer"])),
+                   "target": e_star, "criterion": "E_report <= 1.001 x oracle final"}
+        else:
+            tte = {"seconds": None, "iterations": None, "target": e_star,
+                   "last_energy": energies[-1] if energies else None}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(case)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "step": f"one {N_OUTER}-iteration reconstruction",
+                   "image": "512x512 @ 0.8 mm", "views": 40, "bins": 888, "M": p.cgls_iters,
+                   "n_gd": p.n_gd, "max_trials": p.max_trials, "l2": "flushed (256 MB write) between steps",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "e2e": {"value": world * N_OUTER * 1e3 / e2e_ms, "unit": UNIT,
+                "h2d_bytes_per_step": 4 * g.n_rays, "d2h_bytes_per_step": 4 * g.n_pix,
+                "ms_per_step": e2e_ms},
+        "gpu_launches": int(launches) * args.steps,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "time_to_oracle_energy": tte,
+        "clocks": clk,
+        "paper_context": {"workload": "NCAT 512^2, 40 views, 50 iterations (Table 2)",
+                          "iterations_per_s": 50 / 5.5, "hardware": "Tesla C1060"},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup()
+    try:
+        if args.impl == "reference":
+            run_reference(args, world, rank)
+        else:
+            run_ours(args, world, rank, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

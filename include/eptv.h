@@ -1,0 +1,235 @@
+/*
+ * eptv.h -- C ABI of the B300 (sm_103a) EPTV reconstruction library (libeptv.so).
+ *
+ * Method: Tian, Jia, Yuan, Pan, Jiang, "GPU-based low dose CT reconstruction via
+ * edge-preserving total variation regularization".  The library computes
+ *   E(f) = mu/2 |P f - y|^2 + J(f),  f >= 0                              (Eq. 2)
+ *   J(f) = sum_e w_e T_e(f),  w_e = exp(-(T_e / sigma)^2)            (Eqs. 4, 5)
+ * with P the fan-beam system matrix whose element p_ij is the length of ray i inside
+ * pixel j (Eq. 1, Sec. 2.1), T_e the half-point magnitude of Eq. (A3), and the
+ * two-step iteration of Sec. 2.2: (P1) CGLS on |P f - y|^2 (App. I), (P2) gradient
+ * descent with Armijo line search on lambda/2 |f - v|^2 + J(f) with the weights
+ * recomputed every descent iteration (Eqs. 8, 9, A2), then the positivity clamp.
+ *
+ * Conventions
+ *   image   float32, row-major [ny][nx] (x fastest); pixel (i, j) covers
+ *           [x0 + i dx, x0 + (i+1) dx] x [y0 + j dy, y0 + (j+1) dy] mm with
+ *           x0 = -nx dx / 2, y0 = -ny dy / 2; values in 1/mm.
+ *   sinogram float32, [n_views][n_bins] (bins fastest); values are line integrals.
+ *   view v  angle theta_v = angles[v] (radians) or 2 pi v / n_views; source at
+ *           sid (cos theta_v, sin theta_v) mm; central ray towards the isocentre.
+ *   bin k   fan angle beta_k = k' dbeta (arc detector) or atan(k' dbeta) (flat),
+ *           k' = k - (n_bins - 1)/2 + bin_offset, measured counter-clockwise from the
+ *           central ray.
+ *
+ * Memory and streams
+ *   Every d_* pointer is device memory owned by the caller (e.g. a torch tensor), 4-byte
+ *   aligned at least, and must stay valid until the stream has run the call.  Pointers
+ *   named h_* are host memory.  `stream` is a cudaStream_t (NULL = legacy default
+ *   stream).  Calls are asynchronous on `stream` unless they return host results
+ *   (documented per call), in which case they synchronise that stream before returning.
+ *   A geometry handle owns device workspace (ray tables, solver vectors, reduction
+ *   partials); calls that use the same handle must be issued on one stream or otherwise
+ *   serialised.  The library never falls back to the CPU.
+ *
+ * Errors
+ *   Every int-returning call returns 0 (EPTV_OK) or a negative code; the message of the
+ *   last failure on the calling thread is available from eptv_last_error().  Argument
+ *   errors are detected before any work is queued.
+ */
+#ifndef EPTV_H
+#define EPTV_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define EPTV_OK               0
+#define EPTV_ERR_ARG         -1   /* invalid argument (null pointer, bad size, ...)      */
+#define EPTV_ERR_CUDA        -2   /* a CUDA runtime call failed                          */
+#define EPTV_ERR_NONFINITE   -3   /* a reduction met a NaN or infinity                   */
+#define EPTV_ERR_TIMEOUT     -4   /* a bounded device wait ran out                       */
+#define EPTV_ERR_NOMEM       -5   /* device allocation failed                            */
+#define EPTV_WARN_LINESEARCH  1   /* reported in stats: some Armijo searches found no step */
+
+#define EPTV_DETECTOR_ARC   0
+#define EPTV_DETECTOR_FLAT  1
+
+#define EPTV_WEIGHTS_EPTV   0     /* w = exp(-(T/sigma)^2), Eq. (5)                        */
+#define EPTV_WEIGHTS_ONE    1     /* w = 1: plain TV, the special case of Sec. 4           */
+#define EPTV_WEIGHTS_PRIOR  2     /* w from a per-pixel prior map for the first prior_iters */
+
+#define EPTV_STEP_ARMIJO    0
+#define EPTV_STEP_FIXED     1
+
+/* Scan geometry (Sec. 3: fan beam, arc detector). */
+typedef struct {
+    int nx, ny;              /* image size in pixels, 1..8192 each                     */
+    double dx, dy;           /* pixel pitch, mm                                        */
+    int n_views;             /* number of projection angles, >= 1                      */
+    const double *angles;    /* host, n_views radians, or NULL for 2 pi v / n_views    */
+    int n_bins;              /* detector bins per view, >= 1                           */
+    double dbeta;            /* arc: angular pitch (rad); flat: pitch / sdd             */
+    double bin_offset;       /* detector offset in bins (0.25 keeps rays off the grid)  */
+    double sid, sdd;         /* source-isocentre and source-detector distances, mm     */
+    int detector;            /* EPTV_DETECTOR_ARC or EPTV_DETECTOR_FLAT                */
+} eptv_geometry_desc;
+
+/* Solver parameters.  The paper fixes none of these numerically except the sigma
+ * percentile (90-95%, Sec. 2.1); eptv_default_params() gives this library's defaults. */
+typedef struct {
+    int n_outer;             /* outer iterations NI (Sec. 2.2)                          */
+    int cgls_iters;          /* M, CGLS iterations per (P1), App. I                     */
+    int n_gd;                /* gradient-descent iterations per (P2)                    */
+    double lambda;           /* lambda of (P2), Eq. (8)                                 */
+    double mu;               /* mu of Eq. (2); used only by the reported energy         */
+    double sigma_q;          /* sigma = ceil(q n)-th smallest half-edge magnitude of v  */
+    double sigma_floor;      /* lower bound on sigma                                    */
+    double eps;              /* smoothing inside the A3 magnitude, 1/mm                 */
+    int step_rule;           /* EPTV_STEP_ARMIJO or EPTV_STEP_FIXED                     */
+    double t_fixed;          /* step of EPTV_STEP_FIXED                                 */
+    double armijo_c;         /* sufficient-decrease constant                            */
+    double armijo_shrink;    /* trial step ratio, in (0, 1)                             */
+    double armijo_grow;      /* first trial = min(grow * previous step, t_max)          */
+    int max_trials;          /* trial steps evaluated per GD iteration, 1..16           */
+    double t_max;            /* <= 0: 1/lambda                                          */
+    double t_init;           /* first "previous step"; <= 0: 1/lambda                   */
+    int weights_mode;        /* EPTV_WEIGHTS_*                                          */
+    int prior_iters;         /* outer iterations that use the prior map (PRIOR mode)    */
+} eptv_params;
+
+/* Result of one (P2) solve. */
+typedef struct {
+    double sigma;            /* sigma used (Sec. 2.1)                                   */
+    double energy_first;     /* lambda/2|f-v|^2 + J(f) at the first GD iterate          */
+    double energy_last;      /* same, frozen weights, after the last accepted step      */
+    double t_prev;           /* last accepted step (carried to the next solve)          */
+    int n_accepted;          /* GD iterations with a step > 0                           */
+    int n_fail;              /* GD iterations whose Armijo search found no step         */
+    int status;              /* EPTV_OK or EPTV_WARN_LINESEARCH                         */
+} eptv_stats;
+
+/* Result of a reconstruction. */
+typedef struct {
+    int n_outer;             /* iterations run                                          */
+    double sigma_last;       /* sigma of the last (P2) solve                            */
+    double t_prev;           /* last accepted Armijo step                               */
+    int n_fail;              /* Armijo searches without a step, all iterations          */
+    int status;              /* EPTV_OK or EPTV_WARN_LINESEARCH                         */
+    long long n_launches;    /* kernels the call ran (graph replays counted per node)    */
+} eptv_report;
+
+typedef struct eptv_geometry eptv_geometry;
+
+/* Fills *p with the library defaults.  Never fails. */
+void eptv_default_params(eptv_params *p);
+
+/* Builds the ray tables of a scan (host FP64, stored FP32 on the current device) and
+ * allocates the solver workspace on the current device.  Sec. 3 geometry.
+ * Returns EPTV_ERR_ARG for a bad descriptor, EPTV_ERR_NOMEM / EPTV_ERR_CUDA on device
+ * failures.  *out receives the handle; release it with eptv_destroy_geometry. */
+int eptv_create_geometry(const eptv_geometry_desc *desc, eptv_geometry **out);
+
+/* Frees the handle and its device memory (synchronises the device first).  NULL is a
+ * no-op. */
+void eptv_destroy_geometry(eptv_geometry *g);
+
+/* y = P f  (Eq. 1).  d_f: image [ny][nx]; d_y: sinogram [n_views][n_bins], overwritten.
+ * p_ij is the exact Siddon intersection length (Sec. 2.1), evaluated on the fly by a
+ * ray-driven gather kernel. */
+int eptv_project(const eptv_geometry *g, const float *d_f, float *d_y, void *stream);
+
+/* y = P f with a caller-supplied transposed copy d_fT ([nx][ny], may be NULL) of the
+ * image: rays that cross columns faster than rows march over d_fT, which keeps the 32
+ * lanes of a warp on one cache line.  Launches exactly one kernel (eptv_project adds a
+ * transpose into the handle's scratch first). */
+int eptv_project_t(const eptv_geometry *g, const float *d_f, const float *d_fT, float *d_y,
+                   void *stream);
+
+/* d_fT[i][j] = d_f[j][i] for the handle's image size (d_fT is [nx][ny]). */
+int eptv_transpose(const eptv_geometry *g, const float *d_f, float *d_fT, void *stream);
+
+/* f = P^T y, the exact transpose of eptv_project (adjoint identity <Px, y> = <x, P^T y>,
+ * Eq. A3 of App. III), evaluated by a scatter-free pixel-driven gather that recomputes
+ * each p_ij with the same arithmetic as the projector.  d_f is overwritten. */
+int eptv_backproject(const eptv_geometry *g, const float *d_y, float *d_f, void *stream);
+
+/* M CGLS iterations (App. I) for min |P u - y|^2 started at the content of d_u, which
+ * is overwritten with u^(M).  d_y: sinogram.  Uses the handle's workspace. */
+int eptv_cgls(const eptv_geometry *g, int M, const float *d_y, float *d_u, void *stream);
+
+/* sigma of (P2) (Sec. 2.1): the ceil(q n)-th smallest of the n = (nx+1) ny + nx (ny+1)
+ * half-edge magnitudes T of Eq. (A3) of d_v (zero outside the image), floored at
+ * p->sigma_floor.  Synchronises `stream`; *h_sigma receives the value. */
+int eptv_sigma(const eptv_geometry *g, const eptv_params *p, const float *d_v,
+               double *h_sigma, void *stream);
+
+/* One fused evaluation of the (P2) gradient (Eq. 9 with Eq. A2) at f:
+ *   d_g = lambda (f - v) + dJ/df,  weights w_e from Eq. (5) with the given sigma (or 1,
+ * per p->weights_mode; PRIOR mode is not accepted here).  If h_energy is not NULL the
+ * call synchronises and returns lambda/2 |f - v|^2 + J(f) there (FP64 reduction). */
+int eptv_tv_gradient(const eptv_geometry *g, const eptv_params *p, double sigma,
+                     const float *d_f, const float *d_v, float *d_g, double *h_energy,
+                     void *stream);
+
+/* One (P2) solve (Sec. 2.2, step 2): sigma from d_v, then p->n_gd gradient-descent
+ * iterations from f = v with Armijo steps (or fixed steps), weights recomputed every
+ * iteration, followed by the positivity clamp of step 3.  d_f receives the result.
+ * *t_prev_io (host, may be NULL = p->t_init) is the previous accepted step; it is updated.
+ * d_weights_opt (may be NULL): receives the final half-edge weights, [2][ny+1][nx+1]
+ * (plane 0: x half-edge between pixels (i-1, j) and (i, j) at [0][j][i]; plane 1: y
+ * half-edge between (i, j-1) and (i, j) at [1][j][i]).  If out_opt is not NULL the call
+ * synchronises and fills it. */
+int eptv_tv_step(const eptv_geometry *g, const eptv_params *p, const float *d_v, float *d_f,
+                 double *t_prev_io, float *d_weights_opt, eptv_stats *out_opt, void *stream);
+
+/* The EPTV algorithm (Sec. 2.2): d_f holds the start image (zero for f^(0) = 0, or a
+ * warm start, clamped to >= 0) and receives f^(n_outer).  d_y: sinogram.
+ * d_wprior_opt (may be NULL): per-pixel weight map [ny][nx] used as edge weights
+ * (mean of the two pixels beside each half-edge) for the first p->prior_iters
+ * iterations when p->weights_mode == EPTV_WEIGHTS_PRIOR.  One outer iteration is
+ * captured once into a CUDA graph (cached in the handle) and replayed.  If rep_opt is
+ * not NULL the call synchronises and fills it. */
+int eptv_reconstruct(const eptv_geometry *g, const eptv_params *p, const float *d_y,
+                     float *d_f, const float *d_wprior_opt, eptv_report *rep_opt,
+                     void *stream);
+
+/* Reported energy E(f) = mu/2 |P f - y|^2 + J(f; w(f; sigma_ref)) (Eq. 2).
+ * Synchronises; *h_energy receives the value. */
+int eptv_report_energy(const eptv_geometry *g, const eptv_params *p, double sigma_ref,
+                       const float *d_f, const float *d_y, double *h_energy, void *stream);
+
+/* Per-iteration log of the last eptv_reconstruct on this handle: the step taken by every
+ * GD iteration (0 where the Armijo search found none), laid out [n_outer][n_gd], and the
+ * sigma of every (P2) solve.  Copies min(count, cap) values into each non-NULL host array
+ * and the layout into *n_outer / *n_gd (either may be NULL).  Synchronises the device. */
+int eptv_get_log(const eptv_geometry *g, double *h_steps, int steps_cap, double *h_sigmas,
+                 int sigmas_cap, int *n_outer, int *n_gd);
+
+/* Exact k-th smallest (1-based) of n non-negative finite floats by radix selection on
+ * their bit patterns (the order statistic behind sigma).  d_vals: n floats; d_out: one
+ * float.  Uses a small workspace of the handle g.  k must be in [1, n]. */
+int eptv_select_kth(const eptv_geometry *g, const float *d_vals, long n, long k,
+                    float *d_out, void *stream);
+
+/* Batched reconstruction of n independent slices (any mix of sizes) with one set of
+ * parameters: every kernel of one outer iteration covers all slices in a single launch,
+ * and one outer iteration of the whole batch is captured into one CUDA graph.
+ * d_y[i], d_f[i] as in eptv_reconstruct for slice i (handle geoms[i]).  The batch
+ * workspace is owned by geoms[0].  reps (host, may be NULL) receives n reports. */
+int eptv_reconstruct_batched(int n, eptv_geometry *const *geoms, const eptv_params *p,
+                             const float *const *d_y, float *const *d_f,
+                             eptv_report *reps, void *stream);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *eptv_last_error(void);
+
+/* Library version string. */
+const char *eptv_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EPTV_H */

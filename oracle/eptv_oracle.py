@@ -252,6 +252,7 @@ class P2Stats:
     energies: list = dataclasses.field(default_factory=list)
     fails: int = 0
     t_prev: float = 0.0
+    trials: list = dataclasses.field(default_factory=list)   # per GD iteration: [(t, rho)]
 
 
 def _weights(mode, Tx, Ty, sigma, prior):
@@ -307,12 +308,16 @@ def p2_solve(v, p, t_prev: float, f_init=None, prior=None, mode=None):
         t0 = min(p.armijo_grow * t_prev, p.t_max_eff)
         accepted = None
         t = t0
+        tried = []
         for m in range(p.max_trials):
             t = t0 * p.armijo_shrink ** m
             E1 = p2_energy_frozen(f - t * g, v, p.lam, p.eps, wx, wy)
+            # rho = achieved decrease / (t |g|^2); Armijo accepts rho >= c
+            tried.append((t, (E0 - E1) / (t * gg) if gg > 0 else math.inf))
             if E1 <= E0 - p.armijo_c * t * gg:
                 accepted = t
                 break
+        st.trials.append(tried)
         if accepted is None:
             st.fails += 1
             st.steps.append(0.0)
@@ -337,6 +342,7 @@ def report_energy(op: Operator, f, y, p, sigma_ref: float) -> float:
 class ReconLog:
     sigmas: list = dataclasses.field(default_factory=list)
     steps: list = dataclasses.field(default_factory=list)
+    trials: list = dataclasses.field(default_factory=list)
     fails: int = 0
     energies: list = dataclasses.field(default_factory=list)
     t_prev: float = 0.0
@@ -365,6 +371,7 @@ def reconstruct(op: Operator, y, p, f0=None, prior_w=None, n_outer=None,
         if log is not None:
             log.sigmas.append(st.sigma)
             log.steps.append(st.steps)
+            log.trials.append(st.trials)
             log.fails += st.fails
             if sigma_ref is not None:
                 log.energies.append(report_energy(op, f, y, p, sigma_ref))

@@ -1,0 +1,140 @@
+// K2: f = P^T y, the exact transpose of the projector, as a scatter-free pixel-driven
+// gather (the paper rejects the ray-driven scatter for its write conflicts, Sec. 2.3).
+//
+// Each thread owns 4 adjacent pixels of one row (float4 output).  For every view it
+// bounds the fan angles of its 4-pixel strip from the strip's corners (tan-space
+// min/max, then atan), visits the bins whose rays can cross the strip, and recomputes
+// each p_ij with the canonical plane parameters of eptv_internal.cuh -- the same FP32
+// operations as the projector, so <P x, y> = <x, P^T y> holds up to summation order.
+// The strip's 5 column planes and 2 row planes are shared by its 4 pixels.
+// Optionally also writes the transposed image (for the projector's shallow rays) and
+// reduces |f|^2 (FP32 per warp, FP64 across warps and blocks).
+#include "eptv_internal.cuh"
+#include "kernels.cuh"
+
+namespace eptv {
+
+__global__ void __launch_bounds__(128)
+k2_backproject(const SliceDev *__restrict__ sls, TileMap map, BackArgs a,
+               unsigned int *__restrict__ counters, double *__restrict__ partials)
+{
+    __shared__ float tr[kTileH][kTileW + 1];
+    __shared__ double rsm[4];
+    __shared__ int last_flag;
+
+    int local;
+    const int si = find_slice(map, blockIdx.x, &local);
+    const SliceDev &S = sls[si];
+    const int nx = S.nx, ny = S.ny, nb = S.nb;
+    const int tiles_x = (nx + kTileW - 1) / kTileW;
+    const int tyb = local / tiles_x, txb = local - tyb * tiles_x;
+    const int lx = threadIdx.x & 7, ly = threadIdx.x >> 3;
+    const int i0 = txb * kTileW + lx * 4, j = tyb * kTileH + ly;
+
+    const float *sino = a.in_override ? a.in_override : S.r;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+
+    if (j < ny && i0 < nx) {
+        float X[5];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) X[q] = grid_line((float)(i0 + q), S.dx, S.x0);
+        const float Y0 = grid_line((float)j, S.dy, S.y0);
+        const float Y1 = grid_line((float)(j + 1), S.dy, S.y0);
+        const int ne = min(4, nx - i0);
+        const float Xe = grid_line((float)(i0 + ne), S.dx, S.x0);
+        const float inv_db = S.inv_dbeta, kc = S.kc;
+        const bool arc = S.detector == EPTV_DETECTOR_ARC;
+
+        for (int v = 0; v < S.nv; ++v) {
+            const ViewRec V = S.view[v];
+            // tan of the fan angle of each corner as seen from the source
+            float tmin = 3.0e38f, tmax = -3.0e38f;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const float px = (c & 1) ? Xe : X[0];
+                const float py = (c & 2) ? Y1 : Y0;
+                const float wx = px - V.sx, wy = py - V.sy;
+                const float num = V.cx * wy - V.cy * wx;
+                const float den = V.cx * wx + V.cy * wy;
+                const float tt = __fdividef(num, den);
+                tmin = fminf(tmin, tt);
+                tmax = fmaxf(tmax, tt);
+            }
+            float ulo, uhi;
+            if (arc) { ulo = atanf(tmin) * inv_db + kc; uhi = atanf(tmax) * inv_db + kc; }
+            else { ulo = tmin * inv_db + kc; uhi = tmax * inv_db + kc; }
+            const int klo = max(0, (int)ceilf(ulo - 0.01f));
+            const int khi = min(nb - 1, (int)floorf(uhi + 0.01f));
+            const RayRec *rr = S.ray + (size_t)v * nb;
+            const float *sv = sino + (size_t)v * nb;
+            for (int k = klo; k <= khi; ++k) {
+                const RayRec R = rr[k];
+                const float yv = __ldg(sv + k);
+                const float ta = cross_t(Y0, R.py, R.iy), tb = cross_t(Y1, R.py, R.iy);
+                const float rlo = fminf(ta, tb), rhi = fmaxf(ta, tb);
+                float tx[5];
+#pragma unroll
+                for (int q = 0; q < 5; ++q) tx[q] = cross_t(X[q], R.px, R.ix);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float lo = fminf(tx[q], tx[q + 1]), hi = fmaxf(tx[q], tx[q + 1]);
+                    acc[q] = fmaf(seg_len(lo, hi, rlo, rhi), yv, acc[q]);
+                }
+            }
+        }
+    }
+
+    // output
+    float *out;
+    float *outT = nullptr;
+    if (a.out_override) out = a.out_override;
+    else if (a.out == 0) { out = S.s; if (a.write_T) outT = S.sT; }
+    else if (a.out == 1) out = S.t;
+    else { out = S.u; if (a.write_T) outT = S.uT; }
+
+    float sq = 0.0f;
+    if (j < ny && i0 < nx) {
+        float *p = out + (size_t)j * nx + i0;
+        if (i0 + 3 < nx && ((nx & 3) == 0) && ((((uintptr_t)p) & 15) == 0)) {
+            *reinterpret_cast<float4 *>(p) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+        } else {
+            for (int q = 0; q < 4; ++q) if (i0 + q < nx) p[q] = acc[q];
+        }
+        for (int q = 0; q < 4; ++q) if (i0 + q < nx) sq = fmaf(acc[q], acc[q], sq);
+    }
+    if (outT) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) tr[ly][lx * 4 + q] = acc[q];
+        __syncthreads();
+        const int ii = threadIdx.x >> 2, jj0 = (threadIdx.x & 3) * 4;
+        const int gi = txb * kTileW + ii;
+        if (gi < nx) {
+            for (int q = 0; q < 4; ++q) {
+                const int gj = tyb * kTileH + jj0 + q;
+                if (gj < ny) outT[(size_t)gi * ny + gj] = tr[jj0 + q][ii];
+            }
+        }
+    }
+    if (a.fin == FIN_NONE) return;
+
+    const int b0 = __ldg(map.start + si);
+    const int nblk = __ldg(map.start + si + 1) - b0;
+    float vals[1] = {sq};
+    block_sum_to<1, 128>(vals, partials + (size_t)blockIdx.x * 2, rsm);
+    if (threadIdx.x == 0) partials[(size_t)blockIdx.x * 2 + 1] = 0.0;
+    if (!last_block_of_slice(counters + si, nblk, &last_flag)) return;
+    if (threadIdx.x < 32) {
+        double tot[2];
+        sum_partials<2>(partials, b0, nblk, tot);
+        if (threadIdx.x == 0) finalize(S.sc, a.fin, tot[0], tot[1]);
+    }
+}
+
+void launch_backproject(const Batch &B, const BackArgs &a, cudaStream_t st) {
+    const int nblk = B.blocks(FAM_K2);
+    if (nblk == 0) return;
+    ++g_launch_count;
+    k2_backproject<<<nblk, 128, 0, st>>>(B.d_sd, B.map(FAM_K2), a, B.d_counters, B.d_partials);
+}
+
+}  // namespace eptv

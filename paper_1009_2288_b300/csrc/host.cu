@@ -1,0 +1,803 @@
+// Host side of the EPTV library: geometry handles (FP64 ray tables stored in FP32),
+// device workspace, the launch sequence of one outer iteration (Sec. 2.2 steps 1-3),
+// CUDA-graph capture and the extern "C" entry points declared in eptv.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdarg>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "eptv_internal.cuh"
+#include "kernels.cuh"
+
+namespace eptv {
+
+static thread_local std::string g_last_error;
+
+static int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+#define CU(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(EPTV_ERR_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                        __FILE__, __LINE__);                                              \
+    } while (0)
+
+// Device allocation that is released together with its owner.
+struct DevMem {
+    std::vector<void *> ptrs;
+    template <class T>
+    int alloc(T **p, size_t count) {
+        void *q = nullptr;
+        if (count == 0) count = 1;
+        cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(EPTV_ERR_NOMEM, "cudaMalloc of %zu bytes failed: %s", count * sizeof(T),
+                        cudaGetErrorString(e));
+        }
+        ptrs.push_back(q);
+        *p = static_cast<T *>(q);
+        return 0;
+    }
+    void release() {
+        for (void *p : ptrs) cudaFree(p);
+        ptrs.clear();
+    }
+};
+
+struct GraphCache {
+    cudaGraphExec_t exec = nullptr;
+    int key[6] = {-1, -1, -1, -1, -1, -1};
+    long long kernels = 0;     // kernel nodes in the captured outer iteration
+    void reset() {
+        if (exec) cudaGraphExecDestroy(exec);
+        exec = nullptr;
+        kernels = 0;
+        for (int &k : key) k = -1;
+    }
+};
+
+// Batch over several handles (cached in the first handle).
+struct BatchCache {
+    std::vector<const void *> members;
+    Batch B;
+    DevMem mem;
+    GraphCache graph;
+    void reset() {
+        graph.reset();
+        mem.release();
+        members.clear();
+        B = Batch{};
+    }
+};
+
+}  // namespace eptv
+
+using namespace eptv;
+
+struct eptv_geometry {
+    eptv_geometry_desc desc;
+    std::vector<double> angles;
+    int device = 0;
+    DevMem mem;
+    SliceDev sd{};          // host copy of this slice's descriptor (workspace pointers)
+    Batch B;                // single-slice batch
+    float *y_int = nullptr; // internal copy of the data
+    int *d_map_custom = nullptr;   // [2] TileMap for generic selection
+    cudaStream_t cap = nullptr;    // capture stream
+    GraphCache graph;
+    BatchCache batch;
+    double *d_log = nullptr;       // per-iteration log of the last reconstruction
+    size_t log_cap = 0;            // doubles allocated
+    int log_outer = 0, log_gd = 0; // layout of the last reconstruction's log
+};
+
+namespace eptv {
+
+static void fill_params(const eptv_params *p, ParamsDev *d) {
+    memset(d, 0, sizeof *d);
+    d->lambda = p->lambda;
+    d->mu = p->mu;
+    d->sigma_q = p->sigma_q;
+    d->sigma_floor = p->sigma_floor;
+    d->eps = p->eps;
+    d->t_fixed = p->t_fixed;
+    d->armijo_c = p->armijo_c;
+    d->armijo_shrink = p->armijo_shrink;
+    d->armijo_grow = p->armijo_grow;
+    d->t_max = p->t_max;
+    d->t_init = p->t_init;
+    d->n_outer = p->n_outer;
+    d->cgls_iters = p->cgls_iters;
+    d->n_gd = p->n_gd;
+    d->step_rule = p->step_rule;
+    d->max_trials = p->max_trials;
+    d->weights_mode = p->weights_mode;
+    d->prior_iters = p->prior_iters;
+}
+
+static int check_params(const eptv_params *p) {
+    if (!p) return fail(EPTV_ERR_ARG, "params is NULL");
+    if (p->n_outer < 0 || p->cgls_iters < 0 || p->n_gd < 0)
+        return fail(EPTV_ERR_ARG, "negative iteration count");
+    if (!(p->lambda > 0.0) || !std::isfinite(p->lambda)) return fail(EPTV_ERR_ARG, "lambda must be > 0");
+    if (!(p->eps > 0.0) || !std::isfinite(p->eps)) return fail(EPTV_ERR_ARG, "eps must be > 0");
+    if (!(p->sigma_q >= 0.0 && p->sigma_q <= 1.0)) return fail(EPTV_ERR_ARG, "sigma_q must be in [0, 1]");
+    if (p->step_rule != EPTV_STEP_ARMIJO && p->step_rule != EPTV_STEP_FIXED)
+        return fail(EPTV_ERR_ARG, "bad step_rule %d", p->step_rule);
+    if (p->step_rule == EPTV_STEP_ARMIJO) {
+        if (p->max_trials < 1 || p->max_trials > kMaxTrials)
+            return fail(EPTV_ERR_ARG, "max_trials must be in [1, %d]", kMaxTrials);
+        if (!(p->armijo_shrink > 0.0 && p->armijo_shrink < 1.0))
+            return fail(EPTV_ERR_ARG, "armijo_shrink must be in (0, 1)");
+        if (!(p->armijo_grow > 0.0)) return fail(EPTV_ERR_ARG, "armijo_grow must be > 0");
+        if (!(p->armijo_c >= 0.0 && p->armijo_c < 1.0)) return fail(EPTV_ERR_ARG, "armijo_c must be in [0, 1)");
+    } else if (!std::isfinite(p->t_fixed)) {
+        return fail(EPTV_ERR_ARG, "t_fixed must be finite");
+    }
+    if (p->weights_mode < 0 || p->weights_mode > 2) return fail(EPTV_ERR_ARG, "bad weights_mode");
+    return 0;
+}
+
+static double t_init_of(const eptv_params *p) { return p->t_init > 0.0 ? p->t_init : 1.0 / p->lambda; }
+
+// Blocks per slice of every kernel family.
+static void family_blocks(const SliceDev &s, int out[FAM_COUNT]) {
+    out[FAM_K1] = s.nv * ((s.nb + 31) / 32);
+    out[FAM_K2] = ((s.nx + kTileW - 1) / kTileW) * ((s.ny + kTileH - 1) / kTileH);
+    out[FAM_IMG] = ((s.nx + 31) / 32) * ((s.ny + 31) / 32);
+    out[FAM_SINO] = (s.n_rays + 1023) / 1024;
+    out[FAM_EDGE] = (s.n_edges + 2047) / 2048;
+}
+
+// Allocate the batch bookkeeping (maps, counters, partials, histograms, params) for the
+// given slice descriptors and upload them.
+static int build_batch(Batch &B, DevMem &mem, const std::vector<SliceDev> &sds) {
+    B.n = (int)sds.size();
+    B.h_sd = sds;
+    B.h_start.assign((size_t)FAM_COUNT * (B.n + 1), 0);
+    int maxblk = 0;
+    for (int f = 0; f < FAM_COUNT; ++f) {
+        int acc = 0;
+        for (int i = 0; i < B.n; ++i) {
+            int fb[FAM_COUNT];
+            family_blocks(sds[i], fb);
+            B.h_start[f * (B.n + 1) + i] = acc;
+            acc += fb[f];
+        }
+        B.h_start[f * (B.n + 1) + B.n] = acc;
+        maxblk = std::max(maxblk, acc);
+    }
+    int rc;
+    if ((rc = mem.alloc(&B.d_sd, B.n))) return rc;
+    if ((rc = mem.alloc(&B.d_start, B.h_start.size()))) return rc;
+    if ((rc = mem.alloc(&B.d_counters, B.n))) return rc;
+    if ((rc = mem.alloc(&B.d_partials, (size_t)maxblk * kPartialStride))) return rc;
+    if ((rc = mem.alloc(&B.d_hist, (size_t)B.n * kHistBins))) return rc;
+    if ((rc = mem.alloc(&B.d_params, 1))) return rc;
+    CU(cudaMemcpy(B.d_sd, B.h_sd.data(), sizeof(SliceDev) * B.n, cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(B.d_start, B.h_start.data(), sizeof(int) * B.h_start.size(), cudaMemcpyHostToDevice));
+    CU(cudaMemset(B.d_counters, 0, sizeof(unsigned int) * B.n));
+    CU(cudaMemset(B.d_hist, 0, sizeof(unsigned int) * (size_t)B.n * kHistBins));
+    return 0;
+}
+
+static int upload_sd(Batch &B, cudaStream_t st) {
+    CU(cudaMemcpyAsync(B.d_sd, B.h_sd.data(), sizeof(SliceDev) * B.n, cudaMemcpyHostToDevice, st));
+    return 0;
+}
+
+static int upload_params(const Batch &B, const eptv_params *p, cudaStream_t st) {
+    ParamsDev pd;
+    fill_params(p, &pd);
+    CU(cudaMemcpyAsync(B.d_params, &pd, sizeof pd, cudaMemcpyHostToDevice, st));
+    return 0;
+}
+
+static int n_trials_of(const eptv_params *p) {
+    return p->step_rule == EPTV_STEP_FIXED ? 1 : p->max_trials;
+}
+
+// ---------------------------------------------------------------- launch sequences
+
+// (P1): M CGLS iterations from u (App. I).  r = y - P u; s = P^T r; then M times
+// q = P s, a; r -= a q; [t = P^T r, b; s = t + b s]; u += a s.
+static void enqueue_cgls(const Batch &B, int M, bool have_uT, cudaStream_t st) {
+    ProjArgs pr{};
+    pr.img = IMG_U; pr.out = SINO_R; pr.resid = 1; pr.fin = FIN_NONE; pr.no_T = have_uT ? 0 : 1;
+    launch_project(B, pr, st);
+    BackArgs bs{};
+    bs.out = 0; bs.write_T = 1; bs.fin = FIN_GAMMA0;
+    launch_backproject(B, bs, st);
+    for (int m = 0; m < M; ++m) {
+        ProjArgs pq{};
+        pq.img = IMG_S; pq.out = SINO_Q; pq.resid = 0; pq.fin = FIN_QQ_TO_A;
+        launch_project(B, pq, st);
+        const bool more = (m + 1 < M);
+        if (more) {
+            launch_cgls_update_r(B, st);
+            BackArgs bt{};
+            bt.out = 1; bt.write_T = 0; bt.fin = FIN_B;
+            launch_backproject(B, bt, st);
+        }
+        launch_cgls_update_us(B, more ? 1 : 0, st);
+    }
+}
+
+// (P2) + clamp on v = u: sigma, n_gd fused GD iterations, apply + clamp into u, u^T.
+static void enqueue_p2(const Batch &B, const eptv_params *p, const float *v_override,
+                       float *out_override, cudaStream_t st) {
+    launch_sigma(B, v_override, st);
+    for (int n = 0; n < p->n_gd; ++n) {
+        GdArgs ga{};
+        ga.first = (n == 0);
+        ga.last = (n == p->n_gd - 1);
+        ga.n_trials = n_trials_of(p);
+        ga.v = v_override;
+        ga.write_f = 1;
+        launch_gd_iter(B, ga, n, st);
+    }
+    launch_gd_finish(B, p->n_gd, v_override, out_override, st);
+}
+
+static void enqueue_outer(const Batch &B, const eptv_params *p, cudaStream_t st) {
+    enqueue_cgls(B, p->cgls_iters, true, st);
+    enqueue_p2(B, p, nullptr, nullptr, st);
+}
+
+// Capture one outer iteration of batch B into a graph (cached per structural key).
+static int outer_graph(const Batch &B, GraphCache &gc, cudaStream_t cap, const eptv_params *p) {
+    const int key[6] = {p->cgls_iters, p->n_gd, n_trials_of(p), p->step_rule, B.n, 1};
+    if (gc.exec && memcmp(key, gc.key, sizeof key) == 0) return 0;
+    gc.reset();
+    cudaGraph_t graph = nullptr;
+    CU(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+    const long long c0 = g_launch_count;
+    enqueue_outer(B, p, cap);
+    const long long captured = g_launch_count - c0;
+    g_launch_count = c0;      // captured launches run only when the graph is replayed
+    cudaError_t le = cudaGetLastError();
+    cudaError_t ee = cudaStreamEndCapture(cap, &graph);
+    if (le != cudaSuccess || ee != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return fail(EPTV_ERR_CUDA, "graph capture failed: %s / %s", cudaGetErrorString(le),
+                    cudaGetErrorString(ee));
+    }
+    cudaError_t ie = cudaGraphInstantiate(&gc.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {
+        gc.exec = nullptr;
+        return fail(EPTV_ERR_CUDA, "cudaGraphInstantiate failed: %s", cudaGetErrorString(ie));
+    }
+    memcpy(gc.key, key, sizeof key);
+    gc.kernels = captured;
+    return 0;
+}
+
+static int launch_check() {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(EPTV_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(e));
+    return 0;
+}
+
+static int read_scalars(const SliceDev &sd, double *out, cudaStream_t st) {
+    CU(cudaMemcpyAsync(out, sd.sc, sizeof(double) * kScalarStride, cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    return 0;
+}
+
+// ---------------------------------------------------------------- geometry handle
+
+static int check_desc(const eptv_geometry_desc *d) {
+    if (!d) return fail(EPTV_ERR_ARG, "desc is NULL");
+    if (d->nx < 1 || d->ny < 1 || d->nx > 8192 || d->ny > 8192)
+        return fail(EPTV_ERR_ARG, "image size %dx%d outside 1..8192", d->nx, d->ny);
+    if (!(d->dx > 0) || !(d->dy > 0) || !std::isfinite(d->dx) || !std::isfinite(d->dy))
+        return fail(EPTV_ERR_ARG, "pixel pitch must be > 0");
+    if (d->n_views < 1 || d->n_bins < 1 || (long long)d->n_views * d->n_bins > (1LL << 28))
+        return fail(EPTV_ERR_ARG, "bad view/bin count %d x %d", d->n_views, d->n_bins);
+    if (!(d->dbeta > 0) || !std::isfinite(d->dbeta)) return fail(EPTV_ERR_ARG, "dbeta must be > 0");
+    if (!std::isfinite(d->bin_offset)) return fail(EPTV_ERR_ARG, "bin_offset must be finite");
+    if (d->detector != EPTV_DETECTOR_ARC && d->detector != EPTV_DETECTOR_FLAT)
+        return fail(EPTV_ERR_ARG, "bad detector %d", d->detector);
+    const double half_diag = 0.5 * std::hypot(d->nx * d->dx, d->ny * d->dy);
+    if (!(d->sid > half_diag * 1.0001)) return fail(EPTV_ERR_ARG, "source inside the image circle (sid %g <= %g)", d->sid, half_diag);
+    if (!(d->sdd > d->sid)) return fail(EPTV_ERR_ARG, "sdd must exceed sid");
+    const double kmax = std::max(std::fabs(-(d->n_bins - 1) / 2.0 + d->bin_offset),
+                                 std::fabs((d->n_bins - 1) / 2.0 + d->bin_offset));
+    if (d->detector == EPTV_DETECTOR_ARC && kmax * d->dbeta >= 1.5)
+        return fail(EPTV_ERR_ARG, "fan wider than +-1.5 rad");
+    if (d->angles)
+        for (int v = 0; v < d->n_views; ++v)
+            if (!std::isfinite(d->angles[v])) return fail(EPTV_ERR_ARG, "angle %d not finite", v);
+    return 0;
+}
+
+static float inv_or_big(double c) {
+    if (std::fabs(c) < 1e-30) return c < 0 ? -1e30f : 1e30f;
+    return (float)(1.0 / c);
+}
+
+}  // namespace eptv
+
+extern "C" {
+
+void eptv_default_params(eptv_params *p) {
+    if (!p) return;
+    memset(p, 0, sizeof *p);
+    p->n_outer = 50;
+    p->cgls_iters = 3;
+    p->n_gd = 10;
+    p->lambda = 2000.0;
+    p->mu = 1.0;
+    p->sigma_q = 0.9;
+    p->sigma_floor = 1e-12;
+    p->eps = 1e-5;
+    p->step_rule = EPTV_STEP_ARMIJO;
+    p->t_fixed = 1e-4;
+    p->armijo_c = 1e-4;
+    p->armijo_shrink = 0.5;
+    p->armijo_grow = 2.0;
+    p->max_trials = 8;
+    p->t_max = 0.0;
+    p->t_init = 0.0;
+    p->weights_mode = EPTV_WEIGHTS_EPTV;
+    p->prior_iters = 0;
+}
+
+const char *eptv_last_error(void) { return g_last_error.c_str(); }
+
+const char *eptv_version(void) { return "eptv-b300 0.1 (sm_103a)"; }
+
+int eptv_create_geometry(const eptv_geometry_desc *desc, eptv_geometry **out) {
+    if (!out) return fail(EPTV_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    int rc = check_desc(desc);
+    if (rc) return rc;
+    eptv_geometry *g = new eptv_geometry();
+    g->desc = *desc;
+    if (desc->angles) {
+        g->angles.assign(desc->angles, desc->angles + desc->n_views);
+        g->desc.angles = g->angles.data();
+    }
+    cudaGetDevice(&g->device);
+    const int nx = desc->nx, ny = desc->ny, nv = desc->n_views, nb = desc->n_bins;
+    const long long n_pix = (long long)nx * ny, n_rays = (long long)nv * nb;
+    const long long n_edges = (long long)(nx + 1) * ny + (long long)nx * (ny + 1);
+
+    // ray and view tables in FP64, stored FP32
+    std::vector<RayRec> rays((size_t)n_rays);
+    std::vector<ViewRec> views((size_t)nv);
+    for (int v = 0; v < nv; ++v) {
+        const double th = desc->angles ? desc->angles[v] : 2.0 * M_PI * v / nv;
+        const double c = std::cos(th), s = std::sin(th);
+        const double Sx = desc->sid * c, Sy = desc->sid * s;
+        const double cx = -c, cy = -s;
+        views[v] = ViewRec{(float)Sx, (float)Sy, (float)cx, (float)cy};
+        for (int k = 0; k < nb; ++k) {
+            const double kk = k - (nb - 1) / 2.0 + desc->bin_offset;
+            const double beta = desc->detector == EPTV_DETECTOR_ARC ? kk * desc->dbeta
+                                                                   : std::atan(kk * desc->dbeta);
+            const double cb = std::cos(beta), sb = std::sin(beta);
+            const double dx = cx * cb - cy * sb, dy = cx * sb + cy * cb;
+            const double proj = Sx * dx + Sy * dy;
+            const double Px = Sx - proj * dx, Py = Sy - proj * dy;   // closest point to the isocentre
+            rays[(size_t)v * nb + k] = RayRec{(float)Px, (float)Py, inv_or_big(dx), inv_or_big(dy)};
+        }
+    }
+
+    SliceDev &sd = g->sd;
+    memset(&sd, 0, sizeof sd);
+    sd.nx = nx; sd.ny = ny; sd.nv = nv; sd.nb = nb;
+    sd.dx = (float)desc->dx; sd.dy = (float)desc->dy;
+    sd.x0 = (float)(-0.5 * nx * desc->dx); sd.y0 = (float)(-0.5 * ny * desc->dy);
+    sd.kc = (float)((nb - 1) / 2.0 - desc->bin_offset);
+    sd.inv_dbeta = (float)(1.0 / desc->dbeta);
+    sd.detector = desc->detector;
+    sd.n_pix = (int)n_pix;
+    sd.n_rays = (int)n_rays;
+    sd.n_edges = (int)n_edges;
+    sd.sel_rank = 1;
+
+    DevMem &m = g->mem;
+    RayRec *d_ray;
+    ViewRec *d_view;
+    float *img[9];
+    float *sino[2];
+    double *sc;
+    if ((rc = m.alloc(&d_ray, n_rays)) || (rc = m.alloc(&d_view, nv))) goto bad;
+    for (int i = 0; i < 9; ++i) if ((rc = m.alloc(&img[i], n_pix))) goto bad;
+    for (int i = 0; i < 2; ++i) if ((rc = m.alloc(&sino[i], n_rays))) goto bad;
+    if ((rc = m.alloc(&g->y_int, n_rays))) goto bad;
+    if ((rc = m.alloc(&sd.tv_scr, n_edges))) goto bad;
+    if ((rc = m.alloc(&sc, kScalarStride))) goto bad;
+    if ((rc = m.alloc(&g->d_map_custom, 2))) goto bad;
+    if (cudaMemcpy(d_ray, rays.data(), sizeof(RayRec) * n_rays, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(d_view, views.data(), sizeof(ViewRec) * nv, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(sc, 0, sizeof(double) * kScalarStride) != cudaSuccess) {
+        rc = fail(EPTV_ERR_CUDA, "upload of the geometry tables failed: %s", cudaGetErrorString(cudaGetLastError()));
+        goto bad;
+    }
+    sd.ray = d_ray; sd.view = d_view;
+    sd.u = img[0]; sd.uT = img[1]; sd.s = img[2]; sd.sT = img[3]; sd.t = img[4];
+    sd.fa = img[5]; sd.fb = img[6]; sd.ga = img[7]; sd.gb = img[8];
+    sd.r = sino[0]; sd.q = sino[1];
+    sd.y = g->y_int;
+    sd.sc = sc;
+    if ((rc = build_batch(g->B, m, std::vector<SliceDev>{sd}))) goto bad;
+    if (cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        rc = fail(EPTV_ERR_CUDA, "cudaStreamCreate failed");
+        goto bad;
+    }
+    *out = g;
+    return 0;
+bad:
+    g->mem.release();
+    delete g;
+    return rc;
+}
+
+void eptv_destroy_geometry(eptv_geometry *g) {
+    if (!g) return;
+    cudaDeviceSynchronize();
+    g->graph.reset();
+    g->batch.reset();
+    if (g->d_log) cudaFree(g->d_log);
+    if (g->cap) cudaStreamDestroy(g->cap);
+    g->mem.release();
+    delete g;
+}
+
+int eptv_project_t(const eptv_geometry *gc, const float *d_f, const float *d_fT, float *d_y,
+                   void *stream) {
+    if (!gc || !d_f || !d_y) return fail(EPTV_ERR_ARG, "NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    ProjArgs a{};
+    a.img_override = d_f;
+    a.imgT_override = d_fT;
+    a.out_override = d_y;
+    a.fin = FIN_NONE;
+    launch_project(gc->B, a, st);
+    return launch_check();
+}
+
+int eptv_transpose(const eptv_geometry *gc, const float *d_f, float *d_fT, void *stream) {
+    if (!gc || !d_f || !d_fT) return fail(EPTV_ERR_ARG, "NULL argument");
+    launch_transpose(gc->B, d_f, d_fT, (cudaStream_t)stream);
+    return launch_check();
+}
+
+int eptv_project(const eptv_geometry *gc, const float *d_f, float *d_y, void *stream) {
+    if (!gc || !d_f || !d_y) return fail(EPTV_ERR_ARG, "NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    // the transposed copy lives in the handle's scratch image t (not used across calls)
+    launch_transpose(gc->B, d_f, gc->sd.t, st);
+    int rc = launch_check();
+    if (rc) return rc;
+    return eptv_project_t(gc, d_f, gc->sd.t, d_y, stream);
+}
+
+int eptv_backproject(const eptv_geometry *gc, const float *d_y, float *d_f, void *stream) {
+    if (!gc || !d_f || !d_y) return fail(EPTV_ERR_ARG, "NULL argument");
+    BackArgs a{};
+    a.in_override = d_y;
+    a.out_override = d_f;
+    a.fin = FIN_NONE;
+    launch_backproject(gc->B, a, (cudaStream_t)stream);
+    return launch_check();
+}
+
+int eptv_cgls(const eptv_geometry *gc, int M, const float *d_y, float *d_u, void *stream) {
+    if (!gc || !d_y || !d_u) return fail(EPTV_ERR_ARG, "NULL argument");
+    if (M < 0) return fail(EPTV_ERR_ARG, "M < 0");
+    eptv_geometry *g = const_cast<eptv_geometry *>(gc);
+    cudaStream_t st = (cudaStream_t)stream;
+    const SliceDev &sd = g->sd;
+    CU(cudaMemcpyAsync(g->y_int, d_y, sizeof(float) * sd.n_rays, cudaMemcpyDeviceToDevice, st));
+    CU(cudaMemcpyAsync(sd.u, d_u, sizeof(float) * sd.n_pix, cudaMemcpyDeviceToDevice, st));
+    enqueue_cgls(g->B, M, false, st);
+    int rc = launch_check();
+    if (rc) return rc;
+    CU(cudaMemcpyAsync(d_u, sd.u, sizeof(float) * sd.n_pix, cudaMemcpyDeviceToDevice, st));
+    return 0;
+}
+
+int eptv_sigma(const eptv_geometry *gc, const eptv_params *p, const float *d_v, double *h_sigma,
+               void *stream) {
+    if (!gc || !d_v || !h_sigma) return fail(EPTV_ERR_ARG, "NULL argument");
+    int rc = check_params(p);
+    if (rc) return rc;
+    eptv_geometry *g = const_cast<eptv_geometry *>(gc);
+    cudaStream_t st = (cudaStream_t)stream;
+    SliceDev &sd = g->B.h_sd[0];
+    sd.sel_rank = std::min<long long>(std::max<long long>((long long)std::ceil(p->sigma_q * sd.n_edges), 1), sd.n_edges);
+    if ((rc = upload_sd(g->B, st)) || (rc = upload_params(g->B, p, st))) return rc;
+    launch_sigma(g->B, d_v, st);
+    if ((rc = launch_check())) return rc;
+    double sc[kScalarStride];
+    if ((rc = read_scalars(sd, sc, st))) return rc;
+    if (sc[SC_NONFINITE] != 0.0) return fail(EPTV_ERR_NONFINITE, "non-finite half-edge magnitude");
+    *h_sigma = sc[SC_SIGMA];
+    return 0;
+}
+
+int eptv_tv_gradient(const eptv_geometry *gc, const eptv_params *p, double sigma, const float *d_f,
+                     const float *d_v, float *d_g, double *h_energy, void *stream) {
+    if (!gc || !d_f || !d_v || !d_g) return fail(EPTV_ERR_ARG, "NULL argument");
+    int rc = check_params(p);
+    if (rc) return rc;
+    if (p->weights_mode == EPTV_WEIGHTS_PRIOR) return fail(EPTV_ERR_ARG, "PRIOR weights not accepted here");
+    if (!(sigma > 0.0)) return fail(EPTV_ERR_ARG, "sigma must be > 0");
+    eptv_geometry *g = const_cast<eptv_geometry *>(gc);
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = upload_params(g->B, p, st))) return rc;
+    launch_set_scalar(g->B, SC_SIGMA, sigma, st);
+    GdArgs ga{};
+    ga.first = 1;
+    ga.fprev = d_f;
+    ga.v = d_v;
+    ga.gout = d_g;
+    ga.fout = g->sd.fa;
+    ga.write_f = 0;
+    ga.n_trials = 0;
+    ga.energy_only_fin = 1;
+    launch_gd_iter(g->B, ga, 0, st);
+    if ((rc = launch_check())) return rc;
+    if (h_energy) {
+        double sc[kScalarStride];
+        if ((rc = read_scalars(g->sd, sc, st))) return rc;
+        *h_energy = sc[SC_E_FIRST];
+    }
+    return 0;
+}
+
+int eptv_tv_step(const eptv_geometry *gc, const eptv_params *p, const float *d_v, float *d_f,
+                 double *t_prev_io, float *d_weights_opt, eptv_stats *out_opt, void *stream) {
+    if (!gc || !d_v || !d_f) return fail(EPTV_ERR_ARG, "NULL argument");
+    int rc = check_params(p);
+    if (rc) return rc;
+    if (p->weights_mode == EPTV_WEIGHTS_PRIOR) return fail(EPTV_ERR_ARG, "PRIOR weights need eptv_reconstruct");
+    eptv_geometry *g = const_cast<eptv_geometry *>(gc);
+    cudaStream_t st = (cudaStream_t)stream;
+    SliceDev &sd = g->B.h_sd[0];
+    sd.sel_rank = std::min<long long>(std::max<long long>((long long)std::ceil(p->sigma_q * sd.n_edges), 1), sd.n_edges);
+    sd.wout = d_weights_opt;
+    rc = upload_sd(g->B, st);
+    sd.wout = nullptr;
+    if (rc || (rc = upload_params(g->B, p, st))) return rc;
+    launch_set_scalar(g->B, SC_TPREV, t_prev_io ? *t_prev_io : t_init_of(p), st);
+    launch_set_scalar(g->B, SC_NFAIL_P2, 0.0, st);
+    launch_set_scalar(g->B, SC_NACC_P2, 0.0, st);
+    launch_set_scalar(g->B, SC_NONFINITE, 0.0, st);
+    enqueue_p2(g->B, p, d_v, d_f, st);
+    if ((rc = launch_check())) return rc;
+    if ((rc = upload_sd(g->B, st))) return rc;     // clear the weights pointer for later calls
+    if (t_prev_io || out_opt) {
+        double sc[kScalarStride];
+        if ((rc = read_scalars(sd, sc, st))) return rc;
+        if (sc[SC_NONFINITE] != 0.0) return fail(EPTV_ERR_NONFINITE, "non-finite value in the TV step");
+        if (t_prev_io) *t_prev_io = sc[SC_TPREV];
+        if (out_opt) {
+            out_opt->sigma = sc[SC_SIGMA];
+            out_opt->energy_first = sc[SC_E_FIRST];
+            out_opt->energy_last = sc[SC_E_LAST];
+            out_opt->t_prev = sc[SC_TPREV];
+            out_opt->n_accepted = (int)sc[SC_NACC_P2];
+            out_opt->n_fail = (int)sc[SC_NFAIL_P2];
+            out_opt->status = out_opt->n_fail ? EPTV_WARN_LINESEARCH : EPTV_OK;
+        }
+    }
+    return 0;
+}
+
+// Shared by the single and batched reconstructions: runs n_outer graph replays over B.
+static int run_outer(Batch &B, GraphCache &gc, cudaStream_t cap, const eptv_params *p,
+                     cudaStream_t st) {
+    int rc;
+    if ((rc = upload_sd(B, st)) || (rc = upload_params(B, p, st))) return rc;
+    // f^(0): clamp the start image, build its transpose, reset the per-slice state
+    launch_gd_finish(B, 0, nullptr, nullptr, st);
+    launch_set_scalar(B, SC_OUTER, 0.0, st);
+    launch_set_scalar(B, SC_TPREV, t_init_of(p), st);
+    launch_set_scalar(B, SC_NFAIL, 0.0, st);
+    launch_set_scalar(B, SC_NONFINITE, 0.0, st);
+    if ((rc = launch_check())) return rc;
+    if (p->n_outer == 0) return 0;
+    if ((rc = outer_graph(B, gc, cap, p))) return rc;
+    for (int k = 0; k < p->n_outer; ++k) CU(cudaGraphLaunch(gc.exec, st));
+    g_launch_count += gc.kernels * p->n_outer;
+    return 0;
+}
+
+int eptv_reconstruct(const eptv_geometry *gc, const eptv_params *p, const float *d_y, float *d_f,
+                     const float *d_wprior_opt, eptv_report *rep_opt, void *stream) {
+    if (!gc || !d_y || !d_f) return fail(EPTV_ERR_ARG, "NULL argument");
+    int rc = check_params(p);
+    if (rc) return rc;
+    if (p->weights_mode == EPTV_WEIGHTS_PRIOR && !d_wprior_opt)
+        return fail(EPTV_ERR_ARG, "PRIOR weights mode needs d_wprior_opt");
+    eptv_geometry *g = const_cast<eptv_geometry *>(gc);
+    cudaStream_t st = (cudaStream_t)stream;
+    SliceDev &sd = g->B.h_sd[0];
+    sd.sel_rank = std::min<long long>(std::max<long long>((long long)std::ceil(p->sigma_q * sd.n_edges), 1), sd.n_edges);
+    sd.wprior = (p->weights_mode == EPTV_WEIGHTS_PRIOR) ? d_wprior_opt : nullptr;
+    {
+        const size_t need = (size_t)p->n_outer * (p->n_gd + 1);
+        if (need > g->log_cap) {
+            CU(cudaStreamSynchronize(st));
+            if (g->d_log) cudaFree(g->d_log);
+            g->d_log = nullptr;
+            g->log_cap = 0;
+            CU(cudaMalloc(&g->d_log, need * sizeof(double)));
+            g->log_cap = need;
+        }
+        g->log_outer = p->n_outer;
+        g->log_gd = p->n_gd;
+        sd.log = g->d_log;
+        sd.log_outer = p->n_outer;
+        sd.log_gd = p->n_gd;
+        if (need) CU(cudaMemsetAsync(g->d_log, 0, need * sizeof(double), st));
+    }
+    CU(cudaMemcpyAsync(g->y_int, d_y, sizeof(float) * sd.n_rays, cudaMemcpyDeviceToDevice, st));
+    CU(cudaMemcpyAsync(sd.u, d_f, sizeof(float) * sd.n_pix, cudaMemcpyDeviceToDevice, st));
+    const long long l0 = g_launch_count;
+    if ((rc = run_outer(g->B, g->graph, g->cap, p, st))) return rc;
+    const long long nl = g_launch_count - l0;
+    CU(cudaMemcpyAsync(d_f, sd.u, sizeof(float) * sd.n_pix, cudaMemcpyDeviceToDevice, st));
+    if (rep_opt) {
+        rep_opt->n_launches = nl;
+        double sc[kScalarStride];
+        if ((rc = read_scalars(sd, sc, st))) return rc;
+        if (sc[SC_NONFINITE] != 0.0) return fail(EPTV_ERR_NONFINITE, "non-finite value during the reconstruction");
+        rep_opt->n_outer = p->n_outer;
+        rep_opt->sigma_last = sc[SC_SIGMA];
+        rep_opt->t_prev = sc[SC_TPREV];
+        rep_opt->n_fail = (int)sc[SC_NFAIL];
+        rep_opt->status = rep_opt->n_fail ? EPTV_WARN_LINESEARCH : EPTV_OK;
+    }
+    return 0;
+}
+
+int eptv_report_energy(const eptv_geometry *gc, const eptv_params *p, double sigma_ref,
+                       const float *d_f, const float *d_y, double *h_energy, void *stream) {
+    if (!gc || !d_f || !d_y || !h_energy) return fail(EPTV_ERR_ARG, "NULL argument");
+    int rc = check_params(p);
+    if (rc) return rc;
+    if (!(sigma_ref > 0.0)) return fail(EPTV_ERR_ARG, "sigma_ref must be > 0");
+    eptv_geometry *g = const_cast<eptv_geometry *>(gc);
+    cudaStream_t st = (cudaStream_t)stream;
+    eptv_params pe = *p;
+    if (pe.weights_mode == EPTV_WEIGHTS_PRIOR) pe.weights_mode = EPTV_WEIGHTS_EPTV;
+    if ((rc = upload_params(g->B, &pe, st))) return rc;
+    launch_set_scalar(g->B, SC_NONFINITE, 0.0, st);
+    ProjArgs a{};
+    a.img_override = d_f;
+    a.imgT_override = nullptr;
+    a.out_override = g->sd.q;
+    a.y_override = d_y;
+    a.resid = 1;
+    a.fin = FIN_NORM;
+    launch_project(g->B, a, st);
+    launch_set_scalar(g->B, SC_SIGMA, sigma_ref, st);
+    GdArgs ga{};
+    ga.first = 1;
+    ga.fprev = d_f;
+    ga.v = d_f;
+    ga.gout = g->sd.ga;
+    ga.fout = g->sd.fa;
+    ga.write_f = 0;
+    ga.n_trials = 0;
+    ga.energy_only_fin = 1;
+    launch_gd_iter(g->B, ga, 0, st);
+    if ((rc = launch_check())) return rc;
+    double sc[kScalarStride];
+    if ((rc = read_scalars(g->sd, sc, st))) return rc;
+    if (sc[SC_NONFINITE] != 0.0) return fail(EPTV_ERR_NONFINITE, "non-finite energy");
+    *h_energy = 0.5 * p->mu * sc[SC_NORM] + sc[SC_E_FIRST];
+    return 0;
+}
+
+int eptv_get_log(const eptv_geometry *gc, double *h_steps, int steps_cap, double *h_sigmas,
+                 int sigmas_cap, int *n_outer, int *n_gd) {
+    if (!gc) return fail(EPTV_ERR_ARG, "NULL handle");
+    if (n_outer) *n_outer = gc->log_outer;
+    if (n_gd) *n_gd = gc->log_gd;
+    if (!gc->d_log || gc->log_outer == 0) return 0;
+    CU(cudaDeviceSynchronize());
+    const size_t ns = (size_t)gc->log_outer * gc->log_gd;
+    if (h_steps && steps_cap > 0)
+        CU(cudaMemcpy(h_steps, gc->d_log, sizeof(double) * std::min<size_t>(ns, (size_t)steps_cap),
+                      cudaMemcpyDeviceToHost));
+    if (h_sigmas && sigmas_cap > 0)
+        CU(cudaMemcpy(h_sigmas, gc->d_log + ns,
+                      sizeof(double) * std::min<size_t>((size_t)gc->log_outer, (size_t)sigmas_cap),
+                      cudaMemcpyDeviceToHost));
+    return 0;
+}
+
+int eptv_select_kth(const eptv_geometry *gc, const float *d_vals, long n, long k, float *d_out,
+                    void *stream) {
+    if (!gc || !d_vals || !d_out) return fail(EPTV_ERR_ARG, "NULL argument");
+    if (n < 1 || k < 1 || k > n) return fail(EPTV_ERR_ARG, "need 1 <= k <= n (k=%ld, n=%ld)", k, n);
+    if (n > (1L << 40)) return fail(EPTV_ERR_ARG, "n too large");
+    eptv_geometry *g = const_cast<eptv_geometry *>(gc);
+    cudaStream_t st = (cudaStream_t)stream;
+    const long long nblk = (n + 2047) / 2048;
+    if (nblk > (1LL << 30)) return fail(EPTV_ERR_ARG, "n too large");
+    // a one-slice map over nblk blocks (kept in the handle; stream-ordered upload)
+    static thread_local int hmap[2];
+    hmap[0] = 0;
+    hmap[1] = (int)nblk;
+    CU(cudaMemcpyAsync(g->d_map_custom, hmap, sizeof hmap, cudaMemcpyHostToDevice, st));
+    TileMap m{g->d_map_custom, 1};
+    launch_select_generic(g->B, m, (int)nblk, d_vals, (long long)n, (long long)k, d_out, st);
+    return launch_check();
+}
+
+int eptv_reconstruct_batched(int n, eptv_geometry *const *geoms, const eptv_params *p,
+                             const float *const *d_y, float *const *d_f, eptv_report *reps,
+                             void *stream) {
+    if (n < 1 || !geoms || !d_y || !d_f) return fail(EPTV_ERR_ARG, "bad batch arguments");
+    int rc = check_params(p);
+    if (rc) return rc;
+    if (p->weights_mode == EPTV_WEIGHTS_PRIOR) return fail(EPTV_ERR_ARG, "PRIOR weights not supported in batches");
+    for (int i = 0; i < n; ++i) {
+        if (!geoms[i] || !d_y[i] || !d_f[i]) return fail(EPTV_ERR_ARG, "NULL entry %d", i);
+        for (int j = 0; j < i; ++j)
+            if (geoms[j] == geoms[i]) return fail(EPTV_ERR_ARG, "handle %d repeated in the batch", i);
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    eptv_geometry *g0 = geoms[0];
+    BatchCache &bc = g0->batch;
+    std::vector<const void *> members(geoms, geoms + n);
+    if (bc.members != members) {
+        cudaStreamSynchronize(st);
+        bc.reset();
+        std::vector<SliceDev> sds;
+        for (int i = 0; i < n; ++i) sds.push_back(geoms[i]->sd);
+        if ((rc = build_batch(bc.B, bc.mem, sds))) { bc.reset(); return rc; }
+        bc.members = members;
+    }
+    for (int i = 0; i < n; ++i) {
+        SliceDev &sd = bc.B.h_sd[i];
+        sd.sel_rank = std::min<long long>(std::max<long long>((long long)std::ceil(p->sigma_q * sd.n_edges), 1), sd.n_edges);
+        sd.wprior = nullptr;
+        CU(cudaMemcpyAsync(geoms[i]->y_int, d_y[i], sizeof(float) * sd.n_rays, cudaMemcpyDeviceToDevice, st));
+        CU(cudaMemcpyAsync(sd.u, d_f[i], sizeof(float) * sd.n_pix, cudaMemcpyDeviceToDevice, st));
+    }
+    const long long l0 = g_launch_count;
+    if ((rc = run_outer(bc.B, bc.graph, g0->cap, p, st))) return rc;
+    const long long nl = g_launch_count - l0;
+    for (int i = 0; i < n; ++i)
+        CU(cudaMemcpyAsync(d_f[i], bc.B.h_sd[i].u, sizeof(float) * bc.B.h_sd[i].n_pix,
+                           cudaMemcpyDeviceToDevice, st));
+    if (reps) {
+        CU(cudaStreamSynchronize(st));
+        for (int i = 0; i < n; ++i) {
+            double sc[kScalarStride];
+            if ((rc = read_scalars(bc.B.h_sd[i], sc, st))) return rc;
+            if (sc[SC_NONFINITE] != 0.0) return fail(EPTV_ERR_NONFINITE, "non-finite value in slice %d", i);
+            reps[i].n_outer = p->n_outer;
+            reps[i].n_launches = nl;
+            reps[i].sigma_last = sc[SC_SIGMA];
+            reps[i].t_prev = sc[SC_TPREV];
+            reps[i].n_fail = (int)sc[SC_NFAIL];
+            reps[i].status = reps[i].n_fail ? EPTV_WARN_LINESEARCH : EPTV_OK;
+        }
+    }
+    return 0;
+}
+
+}  // extern "C"

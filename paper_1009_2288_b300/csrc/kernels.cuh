@@ -1,0 +1,119 @@
+// Kernel-family declarations, launch arguments and the batch container shared by the
+// host orchestration (solver.cu, capi.cu) and the kernel files.
+#pragma once
+
+#include <vector>
+
+#include "eptv_internal.cuh"
+
+namespace eptv {
+
+// Kernel families: each has its own blocks-per-slice map.
+enum Family {
+    FAM_K1 = 0,   // projector: n_views * ceil(n_bins / 32) blocks
+    FAM_K2,       // back projector / TV stencils: ceil(nx / 32) * ceil(ny / 16) blocks
+    FAM_IMG,      // image elementwise with transpose: ceil(nx / 32) * ceil(ny / 32) blocks
+    FAM_SINO,     // sinogram elementwise: ceil(n_rays / 1024) blocks
+    FAM_EDGE,     // half-edge arrays: ceil(n_edges / 2048) blocks
+    FAM_COUNT
+};
+
+constexpr int kK1Seg = 8;          // warps (row segments) per projector block
+constexpr int kTileW = 32, kTileH = 16;
+constexpr int kHistBins = 4096;    // radix-select histogram (12 bits per pass)
+constexpr int kMaxTrials = 16;
+constexpr int kPartialStride = kMaxTrials + 8;   // doubles per block in the partials array
+
+// Finalisers run by the last block of a reduction.
+enum Fin {
+    FIN_NONE = 0,
+    FIN_NORM,        // sc[SC_NORM] = sum0, sc[SC_NORM2] = sum1
+    FIN_QQ_TO_A,     // qq = sum0; a = gamma / qq
+    FIN_GAMMA0,      // gamma = sum0
+    FIN_B,           // b = sum0 / gamma; gamma = sum0
+};
+
+enum ImgSel { IMG_U = 0, IMG_S = 1 };
+enum SinoSel { SINO_R = 0, SINO_Q = 1 };
+
+struct ProjArgs {
+    int img;                    // ImgSel
+    int out;                    // SinoSel
+    int resid;                  // out = y - P img
+    int fin;                    // Fin
+    const float *img_override;  // single-slice calls with caller buffers
+    const float *imgT_override;
+    float *out_override;
+    const float *y_override;    // data for resid mode (default: S.y)
+    int no_T;                   // ignore the slice's transposed copy
+};
+
+struct BackArgs {
+    int out;                    // 0: s (+ sT), 1: t, 2: u
+    int write_T;                // also write the transposed image
+    int fin;
+    const float *in_override;   // sinogram input (default: r)
+    float *out_override;
+};
+
+struct Batch {
+    int n = 0;
+    SliceDev *d_sd = nullptr;
+    std::vector<SliceDev> h_sd;
+    int *d_start = nullptr;         // [FAM_COUNT][n + 1]
+    std::vector<int> h_start;
+    unsigned int *d_counters = nullptr;   // [n]
+    double *d_partials = nullptr;         // [max blocks][kPartialStride]
+    unsigned int *d_hist = nullptr;       // [n][kHistBins]
+    ParamsDev *d_params = nullptr;
+    TileMap map(int fam) const { return TileMap{d_start + fam * (n + 1), n}; }
+    int blocks(int fam) const { return h_start[fam * (n + 1) + n]; }
+};
+
+__device__ __forceinline__ void finalize(double *sc, int fin, double s0, double s1) {
+    if (!isfinite(s0) || !isfinite(s1)) sc[SC_NONFINITE] = 1.0;
+    switch (fin) {
+    case FIN_NORM: sc[SC_NORM] = s0; sc[SC_NORM2] = s1; break;
+    case FIN_QQ_TO_A: sc[SC_QQ] = s0; sc[SC_A] = (s0 > 0.0) ? sc[SC_GAMMA] / s0 : 0.0; break;
+    case FIN_GAMMA0: sc[SC_GAMMA] = s0; break;
+    case FIN_B: {
+        const double g = sc[SC_GAMMA];
+        sc[SC_B] = (g > 0.0) ? s0 / g : 0.0;
+        sc[SC_GAMMA] = s0;
+        break;
+    }
+    default: break;
+    }
+}
+
+struct GdArgs {
+    int first;               // 1: the iterate is v itself (no previous step to apply)
+    int last;                // 1: write the final edge weights (if S.wout is set)
+    int n_trials;            // Armijo trial steps evaluated (1 for fixed steps, 0: gradient only)
+    int energy_only_fin;     // store the energy in SC_E_FIRST, take no step decision
+    const float *fprev;      // previous iterate (null: slice ping-pong / v)
+    const float *gprev;      // previous gradient (null: slice ping-pong)
+    const float *v;          // (P2) input (null: S.u)
+    float *fout, *gout;      // outputs (null: slice ping-pong)
+    int write_f;             // store the iterate
+};
+
+// Kernel launches issued by this thread (graph captures included); read by the host
+// code to report how many kernels a call ran.
+extern thread_local long long g_launch_count;
+
+// Launchers (stream-ordered, no host synchronisation).
+void launch_project(const Batch &B, const ProjArgs &a, cudaStream_t st);
+void launch_backproject(const Batch &B, const BackArgs &a, cudaStream_t st);
+void launch_cgls_update_r(const Batch &B, cudaStream_t st);                 // r -= a q
+void launch_cgls_update_us(const Batch &B, int update_s, cudaStream_t st);  // u += a s; s = t + b s
+void launch_sigma(const Batch &B, const float *v_override, cudaStream_t st);
+void launch_gd_iter(const Batch &B, const GdArgs &ga, int iter, cudaStream_t st);
+void launch_gd_finish(const Batch &B, int n_gd, const float *f0_override, float *out_override,
+                      cudaStream_t st);
+void launch_select_generic(const Batch &B, const TileMap &m, int nblk, const float *vals,
+                           long long n, long long k, float *out, cudaStream_t st);
+void launch_set_scalar(const Batch &B, int which, double value, cudaStream_t st);
+void launch_transpose(const Batch &B, const float *src, float *dst, cudaStream_t st);
+
+}  // namespace eptv

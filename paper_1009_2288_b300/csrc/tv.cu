@@ -1,0 +1,581 @@
+// K4/K5: the (P2) step -- edge-preserving TV descent (Sec. 2.2, Eqs. 5, 9, A2, A3).
+//
+// K5 sigma: the ceil(q n)-th smallest half-edge magnitude T of v (Sec. 2.1), found
+//    exactly by a 3-pass radix selection over the FP32 bit patterns (12 + 12 + 8 bits):
+//    pass 0 computes every T (fused stencil) and histograms the top 12 bits; each pass's
+//    last block scans the histogram and narrows the prefix.
+// K4 one gradient-descent iteration, fused: apply the previous step f = f' - t' g'
+//    on the fly, stage f (tile + 2-pixel halo) and v in shared memory, compute T, the
+//    weights w = exp(-T^2/sigma^2) and w D / T at every half-edge, the gradient
+//    g = lambda (f - v) + dJ/df (Eq. A2) on the tile + 1 halo, and for all Armijo trial
+//    steps t_m at once the energy change of f - t_m g with the weights frozen:
+//      fidelity: lambda (-t <g, f-v> + t^2/2 |g|^2)  (two global sums),
+//      TV:       sum_e w_e (T_e(f - t g) - T_e(f)), each term in the cancellation-free
+//                form t (t b_e - 2 a_e) / (T'_e + T_e).
+//    The last block takes the Armijo decision in FP64 and stores the step; the next
+//    kernel applies it.  One launch per GD iteration, no host round trip.
+// K4u apply the last step, clamp f >= 0 (step 3 of the algorithm), write f and f^T.
+#include "eptv_internal.cuh"
+#include "kernels.cuh"
+
+namespace eptv {
+
+// ------------------------------------------------------------------ half-edge stencil
+
+// T^2 of the x half-edge between pixels a=(i-1,j) and b=(i,j) given the six values
+// around it: a_d, b_d (row j-1), a, b (row j), a_u, b_u (row j+1).  Eq. (A3).
+__device__ __forceinline__ float edge_T2(float eps2, float a, float b, float a_u, float b_u,
+                                         float a_d, float b_d, float *D) {
+    const float d = b - a;
+    const float mc = 0.5f * (a + b), mu = 0.5f * (a_u + b_u), md = 0.5f * (a_d + b_d);
+    const float cu = mu - mc, cd = mc - md;
+    *D = d;
+    return eps2 + d * d + 0.5f * cu * cu + 0.5f * cd * cd;
+}
+
+__device__ __forceinline__ float img_at(const float *f, int nx, int ny, int i, int j) {
+    return (i >= 0 && i < nx && j >= 0 && j < ny) ? __ldg(f + (size_t)j * nx + i) : 0.0f;
+}
+
+// Half-edge e of the slice (x-edges first: e = j (nx+1) + i, between (i-1, j) and
+// (i, j); then y-edges: X + j nx + i, between (i, j-1) and (i, j)).
+__device__ __forceinline__ float half_edge_T(const float *f, int nx, int ny, float eps2, int e) {
+    const int X = (nx + 1) * ny;
+    float D;
+    if (e < X) {
+        const int j = e / (nx + 1), i = e - j * (nx + 1);
+        return sqrtf(edge_T2(eps2, img_at(f, nx, ny, i - 1, j), img_at(f, nx, ny, i, j),
+                             img_at(f, nx, ny, i - 1, j + 1), img_at(f, nx, ny, i, j + 1),
+                             img_at(f, nx, ny, i - 1, j - 1), img_at(f, nx, ny, i, j - 1), &D));
+    }
+    e -= X;
+    const int j = e / nx, i = e - j * nx;
+    return sqrtf(edge_T2(eps2, img_at(f, nx, ny, i, j - 1), img_at(f, nx, ny, i, j),
+                         img_at(f, nx, ny, i + 1, j - 1), img_at(f, nx, ny, i + 1, j),
+                         img_at(f, nx, ny, i - 1, j - 1), img_at(f, nx, ny, i - 1, j), &D));
+}
+
+// ------------------------------------------------------------------ radix selection
+
+__device__ __forceinline__ unsigned int sel_key(float x) {
+    unsigned int b = __float_as_uint(x);
+    return (b == 0x80000000u) ? 0u : b;     // -0 -> +0
+}
+
+struct SelCtx {
+    const float *vals;
+    long long n;
+    double *sc;
+    unsigned int *hist;
+    unsigned int *counter;
+    int n_blocks, b0;
+};
+
+// Histogram one pass: keys with the required prefix add to bucket (key >> shift) & mask.
+__device__ __forceinline__ void sel_hist_add(unsigned int *sh, unsigned int key, int pass,
+                                             unsigned int prefix) {
+    if (pass == 0) atomicAdd(&sh[key >> 20], 1u);
+    else if (pass == 1) { if ((key >> 20) == prefix) atomicAdd(&sh[(key >> 8) & 0xFFFu], 1u); }
+    else { if ((key >> 8) == prefix) atomicAdd(&sh[key & 0xFFu], 1u); }
+}
+
+// Last block: find the bucket holding the remaining rank, narrow the prefix.
+// Returns the selected key after pass 2 (in all threads), else 0.
+__device__ unsigned int sel_scan(unsigned int *hist, double *sc, int pass, long long rank0,
+                                 unsigned int *s_cnt /* 256 */, long long *s_res) {
+    const int nbins = (pass == 2) ? 256 : kHistBins;
+    const int per = nbins / 256;
+    const int t = threadIdx.x;
+    unsigned int local = 0;
+    for (int q = 0; q < per; ++q) local += __ldcg(hist + t * per + q);
+    s_cnt[t] = local;
+    __syncthreads();
+    if (t == 0) {
+        long long rank = (pass == 0) ? rank0 : (long long)sc[SC_SEL_RANK];
+        unsigned int prefix = (pass == 0) ? 0u : (unsigned int)sc[SC_SEL_PREFIX];
+        long long cum = 0;
+        int tb = 0;
+        for (; tb < 255; ++tb) { if (cum + s_cnt[tb] >= rank) break; cum += s_cnt[tb]; }
+        int b = tb * per;
+        for (int q = 0; q < per; ++q, ++b) {
+            const unsigned int c = __ldcg(hist + b);
+            if (cum + c >= rank || q == per - 1) break;
+            cum += c;
+        }
+        rank -= cum;
+        if (pass == 0) prefix = (unsigned int)b;
+        else if (pass == 1) prefix = (prefix << 12) | (unsigned int)b;
+        else prefix = (prefix << 8) | (unsigned int)b;
+        sc[SC_SEL_RANK] = (double)rank;
+        sc[SC_SEL_PREFIX] = (double)prefix;
+        *s_res = (long long)prefix;
+    }
+    __syncthreads();
+    for (int q = 0; q < per; ++q) hist[t * per + q] = 0u;     // re-arm for the next pass
+    return (pass == 2) ? (unsigned int)(*s_res) : 0u;
+}
+
+// Pass 0 of sigma: T of every half-edge of v -> scratch, histogram of the top 12 bits.
+__global__ void __launch_bounds__(256)
+k5_sigma_edges(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__restrict__ P,
+               const float *v_override, unsigned int *__restrict__ hist_all,
+               unsigned int *__restrict__ counters)
+{
+    __shared__ unsigned int sh[kHistBins];
+    __shared__ unsigned int s_cnt[256];
+    __shared__ long long s_res;
+    __shared__ int last_flag;
+    int local;
+    const int si = find_slice(map, blockIdx.x, &local);
+    const SliceDev &S = sls[si];
+    for (int b = threadIdx.x; b < kHistBins; b += 256) sh[b] = 0u;
+    __syncthreads();
+    const float *v = v_override ? v_override : S.u;
+    const float eps2 = (float)(P->eps * P->eps);
+    const int e0 = local * 2048;
+    for (int q = 0; q < 8; ++q) {
+        const int e = e0 + q * 256 + threadIdx.x;
+        if (e < S.n_edges) {
+            const float T = half_edge_T(v, S.nx, S.ny, eps2, e);
+            S.tv_scr[e] = T;
+            if (!isfinite(T)) S.sc[SC_NONFINITE] = 1.0;
+            sel_hist_add(sh, sel_key(T), 0, 0u);
+        }
+    }
+    __syncthreads();
+    unsigned int *hist = hist_all + (size_t)si * kHistBins;
+    for (int b = threadIdx.x; b < kHistBins; b += 256) {
+        const unsigned int c = sh[b];
+        if (c) atomicAdd(hist + b, c);
+    }
+    const int b0 = __ldg(map.start + si);
+    const int nblk = __ldg(map.start + si + 1) - b0;
+    if (!last_block_of_slice(counters + si, nblk, &last_flag)) return;
+    sel_scan(hist, S.sc, 0, S.sel_rank, s_cnt, &s_res);
+}
+
+// Passes 1, 2 of sigma (on the scratch T array), or passes 0-2 of a generic selection.
+__global__ void __launch_bounds__(256)
+k5_radix_pass(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__restrict__ P,
+              int pass, unsigned int *__restrict__ hist_all, unsigned int *__restrict__ counters,
+              const float *vals_override, long long n_override, long long rank_override,
+              float *out_override)
+{
+    __shared__ unsigned int sh[kHistBins];
+    __shared__ unsigned int s_cnt[256];
+    __shared__ long long s_res;
+    __shared__ int last_flag;
+    int local;
+    const int si = find_slice(map, blockIdx.x, &local);
+    const SliceDev &S = sls[si];
+    const float *vals = vals_override ? vals_override : S.tv_scr;
+    const long long n = vals_override ? n_override : (long long)S.n_edges;
+    const int nbins = (pass == 2) ? 256 : kHistBins;
+    for (int b = threadIdx.x; b < nbins; b += 256) sh[b] = 0u;
+    __syncthreads();
+    const unsigned int prefix = (pass == 0) ? 0u : (unsigned int)S.sc[SC_SEL_PREFIX];
+    const long long e0 = (long long)local * 2048;
+    for (int q = 0; q < 8; ++q) {
+        const long long e = e0 + q * 256 + threadIdx.x;
+        if (e < n) sel_hist_add(sh, sel_key(__ldg(vals + e)), pass, prefix);
+    }
+    __syncthreads();
+    unsigned int *hist = hist_all + (size_t)si * kHistBins;
+    for (int b = threadIdx.x; b < nbins; b += 256) {
+        const unsigned int c = sh[b];
+        if (c) atomicAdd(hist + b, c);
+    }
+    const int b0 = __ldg(map.start + si);
+    const int nblk = __ldg(map.start + si + 1) - b0;
+    if (!last_block_of_slice(counters + si, nblk, &last_flag)) return;
+    const long long rank0 = vals_override ? rank_override : S.sel_rank;
+    const unsigned int key = sel_scan(hist, S.sc, pass, rank0, s_cnt, &s_res);
+    if (pass == 2 && threadIdx.x == 0) {
+        const float val = __uint_as_float(key);
+        if (out_override) {
+            *out_override = val;
+            S.sc[SC_NORM] = (double)val;
+        } else {
+            S.sc[SC_SIGMA] = fmax((double)val, P->sigma_floor);
+            if (S.log) {
+                const int k = (int)S.sc[SC_OUTER];
+                if (k >= 0 && k < S.log_outer)
+                    S.log[(size_t)S.log_outer * S.log_gd + k] = S.sc[SC_SIGMA];
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ fused GD iteration
+
+constexpr int FW = kTileW + 4, FH = kTileH + 4;      // f region (2-pixel halo)
+constexpr int GW = kTileW + 2, GH = kTileH + 2;      // g region (1-pixel halo)
+constexpr int QXW = kTileW + 3, QXH = GH;            // x-edges around the g region
+constexpr int QYW = GW, QYH = kTileH + 3;            // y-edges around the g region
+
+
+
+__global__ void __launch_bounds__(128)
+k4_gd(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__restrict__ P, GdArgs ga,
+      int iter, unsigned int *__restrict__ counters, double *__restrict__ partials)
+{
+    __shared__ float F[FH][FW];
+    __shared__ float W[FH][FW];          // prior map (PRIOR mode only)
+    __shared__ float V[GH][GW];
+    __shared__ float G[GH][GW];
+    __shared__ float QX[QXH][QXW], TXs[QXH][QXW], WX[QXH][QXW];
+    __shared__ float QY[QYH][QYW], TYs[QYH][QYW], WY[QYH][QYW];
+    __shared__ float s_t[kMaxTrials];
+    __shared__ double s_td[kMaxTrials];
+    __shared__ double rsm[(kMaxTrials + 4) * 4];
+    __shared__ float s_tapply;
+    __shared__ int last_flag;
+
+    int local;
+    const int si = find_slice(map, blockIdx.x, &local);
+    const SliceDev &S = sls[si];
+    const int nx = S.nx, ny = S.ny;
+    const int tiles_x = (nx + kTileW - 1) / kTileW;
+    const int tyb = local / tiles_x, txb = local - tyb * tiles_x;
+    const int X0 = txb * kTileW, Y0 = tyb * kTileH;
+    const int tid = threadIdx.x;
+    const int K = ga.n_trials;
+    const float eps2 = (float)(P->eps * P->eps);
+    const float lam = (float)P->lambda;
+
+    // buffers of this iteration
+    const int par = iter & 1;
+    const float *fprev = ga.fprev ? ga.fprev : (ga.first ? (ga.v ? ga.v : S.u) : (par ? S.fa : S.fb));
+    const float *gprev = ga.gprev ? ga.gprev : (par ? S.ga : S.gb);
+    const float *vv = ga.v ? ga.v : S.u;
+    float *fout = ga.fout ? ga.fout : (par ? S.fb : S.fa);
+    float *gout = ga.gout ? ga.gout : (par ? S.gb : S.ga);
+
+    int mode = P->weights_mode;
+    if (mode == EPTV_WEIGHTS_PRIOR) {
+        mode = (S.wprior && S.sc[SC_OUTER] < (double)P->prior_iters) ? EPTV_WEIGHTS_PRIOR
+                                                                      : EPTV_WEIGHTS_EPTV;
+    }
+    const float sig = (float)S.sc[SC_SIGMA];
+    const float inv_s2 = 1.0f / (sig * sig);
+
+    if (tid == 0) s_tapply = ga.first ? 0.0f : (float)S.sc[SC_TSTEP];
+    if (tid < K) {
+        double t;
+        if (P->step_rule == EPTV_STEP_FIXED) t = P->t_fixed;
+        else {
+            const double tmax = P->t_max > 0.0 ? P->t_max : 1.0 / P->lambda;
+            const double t0 = fmin(P->armijo_grow * S.sc[SC_TPREV], tmax);
+            t = t0 * pow(P->armijo_shrink, (double)tid);
+        }
+        s_t[tid] = (float)t;
+        s_td[tid] = (double)(float)t;
+    }
+    __syncthreads();
+    const float tap = s_tapply;
+
+    // phase 1: f on the tile + 2 halo (previous step applied), v on tile + 1 halo
+    for (int idx = tid; idx < FH * FW; idx += 128) {
+        const int yy = idx / FW, xx = idx - yy * FW;
+        const int i = X0 - 2 + xx, j = Y0 - 2 + yy;
+        float fv = 0.0f;
+        if (i >= 0 && i < nx && j >= 0 && j < ny) {
+            const size_t p = (size_t)j * nx + i;
+            fv = __ldg(fprev + p);
+            if (tap != 0.0f) fv = fmaf(-tap, __ldg(gprev + p), fv);
+        }
+        F[yy][xx] = fv;
+        if (mode == EPTV_WEIGHTS_PRIOR) {
+            const int ci = min(max(i, 0), nx - 1), cj = min(max(j, 0), ny - 1);
+            W[yy][xx] = __ldg(S.wprior + (size_t)cj * nx + ci);
+        }
+    }
+    for (int idx = tid; idx < GH * GW; idx += 128) {
+        const int yy = idx / GW, xx = idx - yy * GW;
+        const int i = X0 - 1 + xx, j = Y0 - 1 + yy;
+        V[yy][xx] = (i >= 0 && i < nx && j >= 0 && j < ny) ? __ldg(vv + (size_t)j * nx + i) : 0.0f;
+    }
+    __syncthreads();
+
+    // phase 2: half-edges around the g region
+    for (int idx = tid; idx < QXH * QXW; idx += 128) {
+        const int yy = idx / QXW, ee = idx - yy * QXW;
+        const int e = X0 - 1 + ee, j = Y0 - 1 + yy;     // between (e-1, j) and (e, j)
+        float q = 0.f, T = 0.f, w = 0.f;
+        if (e >= 0 && e <= nx && j >= 0 && j < ny) {
+            const int fx = ee;                          // F column of pixel e-1
+            const int fy = yy + 1;                      // F row of pixel row j
+            float D;
+            const float T2 = edge_T2(eps2, F[fy][fx], F[fy][fx + 1], F[fy + 1][fx], F[fy + 1][fx + 1],
+                                     F[fy - 1][fx], F[fy - 1][fx + 1], &D);
+            T = sqrtf(T2);
+            if (mode == EPTV_WEIGHTS_EPTV) w = __expf(-T2 * inv_s2);
+            else if (mode == EPTV_WEIGHTS_ONE) w = 1.0f;
+            else w = 0.5f * (W[fy][fx] + W[fy][fx + 1]);
+            q = w * D / T;
+        }
+        QX[yy][ee] = q; TXs[yy][ee] = T; WX[yy][ee] = w;
+    }
+    for (int idx = tid; idx < QYH * QYW; idx += 128) {
+        const int ee = idx / QYW, xx = idx - ee * QYW;
+        const int e = Y0 - 1 + ee, i = X0 - 1 + xx;     // between (i, e-1) and (i, e)
+        float q = 0.f, T = 0.f, w = 0.f;
+        if (e >= 0 && e <= ny && i >= 0 && i < nx) {
+            const int fy = ee;                          // F row of pixel row e-1
+            const int fx = xx + 1;                      // F column of pixel column i
+            float D;
+            const float T2 = edge_T2(eps2, F[fy][fx], F[fy + 1][fx], F[fy][fx + 1], F[fy + 1][fx + 1],
+                                     F[fy][fx - 1], F[fy + 1][fx - 1], &D);
+            T = sqrtf(T2);
+            if (mode == EPTV_WEIGHTS_EPTV) w = __expf(-T2 * inv_s2);
+            else if (mode == EPTV_WEIGHTS_ONE) w = 1.0f;
+            else w = 0.5f * (W[fy][fx] + W[fy + 1][fx]);
+            q = w * D / T;
+        }
+        QY[ee][xx] = q; TYs[ee][xx] = T; WY[ee][xx] = w;
+    }
+    __syncthreads();
+
+    // phase 3: g = lambda (f - v) + dJ/df on the g region (Eq. 9, A2)
+    float sA = 0.f, sB = 0.f, sF = 0.f, sJ = 0.f;
+    for (int idx = tid; idx < GH * GW; idx += 128) {
+        const int yy = idx / GW, xx = idx - yy * GW;
+        const int i = X0 - 1 + xx, j = Y0 - 1 + yy;
+        float g = 0.0f;
+        if (i >= 0 && i < nx && j >= 0 && j < ny) {
+            const float f = F[yy + 1][xx + 1];
+            const float d = f - V[yy][xx];
+            const float div = (QX[yy][xx + 1] - QX[yy][xx]) + (QY[yy + 1][xx] - QY[yy][xx]);
+            g = lam * d - div;
+            if (xx >= 1 && xx <= kTileW && yy >= 1 && yy <= kTileH) {
+                const size_t p = (size_t)j * nx + i;
+                gout[p] = g;
+                if (ga.write_f) fout[p] = f;
+                sA = fmaf(g, d, sA);
+                sB = fmaf(g, g, sB);
+                sF = fmaf(d, d, sF);
+            }
+        }
+        G[yy][xx] = g;
+    }
+    __syncthreads();
+
+    // phase 4: owned half-edges of the tile -- energy and trial energy changes
+    float dJ[kMaxTrials];
+#pragma unroll
+    for (int m = 0; m < kMaxTrials; ++m) dJ[m] = 0.0f;
+    const bool want_w = ga.last && S.wout;
+    for (int idx = tid; idx < (kTileW + 1) * kTileH; idx += 128) {
+        const int yy = idx / (kTileW + 1), ee = idx - yy * (kTileW + 1);
+        const int e = X0 + ee, j = Y0 + yy;
+        if (j >= ny || e > nx || (ee == kTileW && e != nx)) continue;
+        const int qx = ee + 1, qy = yy + 1;             // QX indices
+        const float T = TXs[qy][qx], w = WX[qy][qx];
+        sJ = fmaf(w, T, sJ);
+        if (want_w) S.wout[(size_t)j * (nx + 1) + e] = w;
+        if (K) {
+            // pixels a = (e-1, j), b = (e, j) in F / G coordinates
+            const int fx = ee + 1, fy = yy + 2;         // F col of e-1, row of j
+            const int gx = ee, gy = yy + 1;             // G col of e-1, row of j
+            const float D = F[fy][fx + 1] - F[fy][fx];
+            const float mc = 0.5f * (F[fy][fx] + F[fy][fx + 1]);
+            const float c1 = 0.5f * (F[fy + 1][fx] + F[fy + 1][fx + 1]) - mc;
+            const float c2 = mc - 0.5f * (F[fy - 1][fx] + F[fy - 1][fx + 1]);
+            const float dD = G[gy][gx + 1] - G[gy][gx];
+            const float gc = 0.5f * (G[gy][gx] + G[gy][gx + 1]);
+            const float dc1 = 0.5f * (G[gy + 1][gx] + G[gy + 1][gx + 1]) - gc;
+            const float dc2 = gc - 0.5f * (G[gy - 1][gx] + G[gy - 1][gx + 1]);
+            const float ae = D * dD + 0.5f * (c1 * dc1 + c2 * dc2);
+            const float be = dD * dD + 0.5f * (dc1 * dc1 + dc2 * dc2);
+            const float T2 = T * T;
+#pragma unroll
+            for (int m = 0; m < kMaxTrials; ++m) {
+                if (m < K) {
+                    const float t = s_t[m];
+                    const float num = t * fmaf(t, be, -2.0f * ae);
+                    const float Tn = sqrtf(fmaxf(T2 + num, 0.0f));
+                    dJ[m] = fmaf(w, __fdividef(num, Tn + T), dJ[m]);
+                }
+            }
+        }
+    }
+    for (int idx = tid; idx < kTileW * (kTileH + 1); idx += 128) {
+        const int ee = idx / kTileW, xx = idx - ee * kTileW;
+        const int e = Y0 + ee, i = X0 + xx;
+        if (i >= nx || e > ny || (ee == kTileH && e != ny)) continue;
+        const int qy = ee + 1, qx = xx + 1;             // QY indices
+        const float T = TYs[qy][qx], w = WY[qy][qx];
+        sJ = fmaf(w, T, sJ);
+        if (want_w) S.wout[(size_t)(ny + 1) * (nx + 1) + (size_t)e * (nx + 1) + i] = w;
+        if (K) {
+            // pixels a = (i, e-1), b = (i, e)
+            const int fx = xx + 2, fy = ee + 1;         // F col of i, row of e-1
+            const int gx = xx + 1, gy = ee;             // G col of i, row of e-1
+            const float D = F[fy + 1][fx] - F[fy][fx];
+            const float mc = 0.5f * (F[fy][fx] + F[fy + 1][fx]);
+            const float c1 = 0.5f * (F[fy][fx + 1] + F[fy + 1][fx + 1]) - mc;
+            const float c2 = mc - 0.5f * (F[fy][fx - 1] + F[fy + 1][fx - 1]);
+            const float dD = G[gy + 1][gx] - G[gy][gx];
+            const float gc = 0.5f * (G[gy][gx] + G[gy + 1][gx]);
+            const float dc1 = 0.5f * (G[gy][gx + 1] + G[gy + 1][gx + 1]) - gc;
+            const float dc2 = gc - 0.5f * (G[gy][gx - 1] + G[gy + 1][gx - 1]);
+            const float ae = D * dD + 0.5f * (c1 * dc1 + c2 * dc2);
+            const float be = dD * dD + 0.5f * (dc1 * dc1 + dc2 * dc2);
+            const float T2 = T * T;
+#pragma unroll
+            for (int m = 0; m < kMaxTrials; ++m) {
+                if (m < K) {
+                    const float t = s_t[m];
+                    const float num = t * fmaf(t, be, -2.0f * ae);
+                    const float Tn = sqrtf(fmaxf(T2 + num, 0.0f));
+                    dJ[m] = fmaf(w, __fdividef(num, Tn + T), dJ[m]);
+                }
+            }
+        }
+    }
+
+    // phase 5: block sums -> partials; last block decides the step (FP64)
+    constexpr int NV = kMaxTrials + 4;
+    float vals[NV];
+    vals[0] = sA; vals[1] = sB; vals[2] = sF; vals[3] = sJ;
+#pragma unroll
+    for (int m = 0; m < kMaxTrials; ++m) vals[4 + m] = dJ[m];
+    block_sum_to<NV, 128>(vals, partials + (size_t)blockIdx.x * kPartialStride, rsm);
+    const int b0 = __ldg(map.start + si);
+    const int nblk = __ldg(map.start + si + 1) - b0;
+    if (!last_block_of_slice(counters + si, nblk, &last_flag)) return;
+    if (tid < 32) {
+        double tot[NV];
+        // sum_partials over the stride layout
+        const int lane = tid;
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double acc = 0.0;
+            for (int b = lane; b < nblk; b += 32) acc += __ldcg(partials + (size_t)(b0 + b) * kPartialStride + k);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            tot[k] = acc;
+        }
+        if (lane == 0) {
+            double *sc = S.sc;
+            const double A = tot[0], Bg = tot[1];
+            const double lamd = P->lambda;
+            const double E0 = 0.5 * lamd * tot[2] + tot[3];
+            bool bad = !isfinite(E0) || !isfinite(A) || !isfinite(Bg);
+            if (ga.energy_only_fin) {
+                sc[SC_E_FIRST] = E0;
+                sc[SC_NORM2] = Bg;
+            } else {
+                if (ga.first) sc[SC_E_FIRST] = E0;
+                if (P->step_rule == EPTV_STEP_FIXED) {
+                    const double t = s_td[0];
+                    sc[SC_TSTEP] = t;
+                    sc[SC_E_LAST] = E0 + lamd * (-t * A + 0.5 * t * t * Bg) + tot[4];
+                    sc[SC_NACC_P2] += 1.0;
+                } else {
+                    int acc_m = -1;
+                    double dE = 0.0;
+                    for (int m = 0; m < K; ++m) {
+                        const double t = s_td[m];
+                        const double d = lamd * (-t * A + 0.5 * t * t * Bg) + tot[4 + m];
+                        if (!isfinite(d)) bad = true;
+                        if (d <= -P->armijo_c * t * Bg) { acc_m = m; dE = d; break; }
+                    }
+                    if (acc_m >= 0) {
+                        sc[SC_TSTEP] = s_td[acc_m];
+                        sc[SC_TPREV] = s_td[acc_m];
+                        sc[SC_E_LAST] = E0 + dE;
+                        sc[SC_NACC_P2] += 1.0;
+                    } else {
+                        sc[SC_TSTEP] = 0.0;
+                        sc[SC_TPREV] = s_td[K - 1] * P->armijo_shrink / P->armijo_grow;
+                        sc[SC_E_LAST] = E0;
+                        sc[SC_NFAIL] += 1.0;
+                        sc[SC_NFAIL_P2] += 1.0;
+                    }
+                }
+            }
+            if (bad) sc[SC_NONFINITE] = 1.0;
+            if (!ga.energy_only_fin && S.log) {
+                const int k = (int)sc[SC_OUTER];
+                if (k >= 0 && k < S.log_outer && iter < S.log_gd) S.log[(size_t)k * S.log_gd + iter] = sc[SC_TSTEP];
+            }
+        }
+    }
+}
+
+// K4u: f = max(f' - t g', 0) -> u and u^T; advances the outer-iteration counter.
+__global__ void __launch_bounds__(256)
+k4_finish(const SliceDev *__restrict__ sls, TileMap map, int n_gd, const float *f0_override,
+          float *out_override)
+{
+    __shared__ float tile[32][33];
+    int local;
+    const int si = find_slice(map, blockIdx.x, &local);
+    const SliceDev &S = sls[si];
+    const int nx = S.nx, ny = S.ny;
+    const int tiles_x = (nx + 31) >> 5;
+    const int tyb = local / tiles_x, txb = local - tyb * tiles_x;
+    const int par = (n_gd - 1) & 1;
+    const float *fp = (n_gd == 0) ? (f0_override ? f0_override : S.u) : (par ? S.fb : S.fa);
+    const float *gp = par ? S.gb : S.ga;
+    const float t = (n_gd == 0) ? 0.0f : (float)S.sc[SC_TSTEP];
+    float *out = out_override ? out_override : S.u;
+    const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;
+    const int i = txb * 32 + lx;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int jj = ly + 8 * q, j = tyb * 32 + jj;
+        if (i < nx && j < ny) {
+            const size_t p = (size_t)j * nx + i;
+            float f = fp[p];
+            if (t != 0.0f) f = fmaf(-t, gp[p], f);
+            f = fmaxf(f, 0.0f);
+            out[p] = f;
+            tile[jj][lx] = f;
+        }
+    }
+    if (local == 0 && threadIdx.x == 0) S.sc[SC_OUTER] += 1.0;
+    if (S.uT == nullptr || out_override) return;
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int ii = ly + 8 * q;
+        const int gi = txb * 32 + ii, gj = tyb * 32 + lx;
+        if (gi < nx && gj < ny) S.uT[(size_t)gi * ny + gj] = tile[lx][ii];
+    }
+}
+
+// --------------------------------------------------------------------- launchers
+
+void launch_sigma(const Batch &B, const float *v_override, cudaStream_t st) {
+    ++g_launch_count;
+    k5_sigma_edges<<<B.blocks(FAM_EDGE), 256, 0, st>>>(B.d_sd, B.map(FAM_EDGE), B.d_params,
+                                                       v_override, B.d_hist, B.d_counters);
+    for (int pass = 1; pass <= 2; ++pass, ++g_launch_count)
+        k5_radix_pass<<<B.blocks(FAM_EDGE), 256, 0, st>>>(B.d_sd, B.map(FAM_EDGE), B.d_params, pass,
+                                                          B.d_hist, B.d_counters, nullptr, 0, 0,
+                                                          nullptr);
+}
+
+void launch_select_generic(const Batch &B, const TileMap &m, int nblk, const float *vals,
+                           long long n, long long k, float *out, cudaStream_t st) {
+    for (int pass = 0; pass <= 2; ++pass, ++g_launch_count)
+        k5_radix_pass<<<nblk, 256, 0, st>>>(B.d_sd, m, B.d_params, pass, B.d_hist, B.d_counters,
+                                            vals, n, k, out);
+}
+
+void launch_gd_iter(const Batch &B, const GdArgs &ga, int iter, cudaStream_t st) {
+    ++g_launch_count;
+    k4_gd<<<B.blocks(FAM_K2), 128, 0, st>>>(B.d_sd, B.map(FAM_K2), B.d_params, ga, iter,
+                                            B.d_counters, B.d_partials);
+}
+
+void launch_gd_finish(const Batch &B, int n_gd, const float *f0_override, float *out_override,
+                      cudaStream_t st) {
+    ++g_launch_count;
+    k4_finish<<<B.blocks(FAM_IMG), 256, 0, st>>>(B.d_sd, B.map(FAM_IMG), n_gd, f0_override,
+                                                 out_override);
+}
+
+}  // namespace eptv

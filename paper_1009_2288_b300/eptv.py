@@ -1,0 +1,305 @@
+"""Python binding of libeptv.so (include/eptv.h): argument marshalling only.
+
+Every function has the name of the C entry point it calls and takes torch CUDA tensors
+(float32, contiguous) for device buffers; all arithmetic runs in the library's sm_103a
+kernels.  There is no CPU fallback: if the library is missing or no GPU is present the
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+from . import build as _build
+from .inputs import EptvParams, FanGeometry
+
+EPTV_OK = 0
+ERRORS = {-1: "EPTV_ERR_ARG", -2: "EPTV_ERR_CUDA", -3: "EPTV_ERR_NONFINITE",
+          -4: "EPTV_ERR_TIMEOUT", -5: "EPTV_ERR_NOMEM"}
+
+EXPORTED = [
+    "eptv_default_params", "eptv_create_geometry", "eptv_destroy_geometry", "eptv_project",
+    "eptv_project_t", "eptv_transpose", "eptv_backproject", "eptv_cgls", "eptv_sigma",
+    "eptv_tv_gradient", "eptv_tv_step", "eptv_reconstruct", "eptv_report_energy",
+    "eptv_select_kth", "eptv_reconstruct_batched", "eptv_last_error", "eptv_version",
+    "eptv_get_log",
+]
+
+
+class EptvError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class GeometryDesc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("dx", ctypes.c_double),
+                ("dy", ctypes.c_double), ("n_views", ctypes.c_int),
+                ("angles", ctypes.POINTER(ctypes.c_double)), ("n_bins", ctypes.c_int),
+                ("dbeta", ctypes.c_double), ("bin_offset", ctypes.c_double),
+                ("sid", ctypes.c_double), ("sdd", ctypes.c_double), ("detector", ctypes.c_int)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("n_outer", ctypes.c_int), ("cgls_iters", ctypes.c_int), ("n_gd", ctypes.c_int),
+                ("lam", ctypes.c_double), ("mu", ctypes.c_double), ("sigma_q", ctypes.c_double),
+                ("sigma_floor", ctypes.c_double), ("eps", ctypes.c_double),
+                ("step_rule", ctypes.c_int), ("t_fixed", ctypes.c_double),
+                ("armijo_c", ctypes.c_double), ("armijo_shrink", ctypes.c_double),
+                ("armijo_grow", ctypes.c_double), ("max_trials", ctypes.c_int),
+                ("t_max", ctypes.c_double), ("t_init", ctypes.c_double),
+                ("weights_mode", ctypes.c_int), ("prior_iters", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("sigma", ctypes.c_double), ("energy_first", ctypes.c_double),
+                ("energy_last", ctypes.c_double), ("t_prev", ctypes.c_double),
+                ("n_accepted", ctypes.c_int), ("n_fail", ctypes.c_int), ("status", ctypes.c_int)]
+
+
+class Report(ctypes.Structure):
+    _fields_ = [("n_outer", ctypes.c_int), ("sigma_last", ctypes.c_double),
+                ("t_prev", ctypes.c_double), ("n_fail", ctypes.c_int), ("status", ctypes.c_int),
+                ("n_launches", ctypes.c_longlong)]
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libeptv.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_1009_2288_b300.build.build()")
+    L = ctypes.CDLL(path)
+    vp, c_int, c_long, dbl = ctypes.c_void_p, ctypes.c_int, ctypes.c_long, ctypes.c_double
+    sig = {
+        "eptv_default_params": (None, [ctypes.POINTER(Params)]),
+        "eptv_create_geometry": (c_int, [ctypes.POINTER(GeometryDesc), ctypes.POINTER(vp)]),
+        "eptv_destroy_geometry": (None, [vp]),
+        "eptv_project": (c_int, [vp, vp, vp, vp]),
+        "eptv_project_t": (c_int, [vp, vp, vp, vp, vp]),
+        "eptv_transpose": (c_int, [vp, vp, vp, vp]),
+        "eptv_backproject": (c_int, [vp, vp, vp, vp]),
+        "eptv_cgls": (c_int, [vp, c_int, vp, vp, vp]),
+        "eptv_sigma": (c_int, [vp, ctypes.POINTER(Params), vp, ctypes.POINTER(dbl), vp]),
+        "eptv_tv_gradient": (c_int, [vp, ctypes.POINTER(Params), dbl, vp, vp, vp,
+                                     ctypes.POINTER(dbl), vp]),
+        "eptv_tv_step": (c_int, [vp, ctypes.POINTER(Params), vp, vp, ctypes.POINTER(dbl), vp,
+                                 ctypes.POINTER(Stats), vp]),
+        "eptv_reconstruct": (c_int, [vp, ctypes.POINTER(Params), vp, vp, vp,
+                                     ctypes.POINTER(Report), vp]),
+        "eptv_report_energy": (c_int, [vp, ctypes.POINTER(Params), dbl, vp, vp,
+                                       ctypes.POINTER(dbl), vp]),
+        "eptv_select_kth": (c_int, [vp, vp, c_long, c_long, vp, vp]),
+        "eptv_reconstruct_batched": (c_int, [c_int, ctypes.POINTER(vp), ctypes.POINTER(Params),
+                                             ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                             ctypes.POINTER(Report), vp]),
+        "eptv_get_log": (c_int, [vp, ctypes.POINTER(dbl), c_int, ctypes.POINTER(dbl), c_int,
+                                 ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
+        "eptv_last_error": (ctypes.c_char_p, []),
+        "eptv_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(rc: int):
+    if rc != EPTV_OK and rc < 0:
+        raise EptvError(rc, load().eptv_last_error().decode())
+    return rc
+
+
+def _stream(stream) -> Optional[int]:
+    import torch
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def _ptr(t, numel: Optional[int] = None, name: str = "tensor"):
+    import torch
+    if t is None:
+        return None
+    if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {numel}")
+    return t.data_ptr()
+
+
+def params(p: Optional[EptvParams] = None) -> Params:
+    """ctypes copy of a parameter record (library defaults where p is None)."""
+    out = Params()
+    load().eptv_default_params(ctypes.byref(out))
+    if p is None:
+        return out
+    for f, _ in Params._fields_:
+        setattr(out, f, getattr(p, f))
+    return out
+
+
+class Geometry:
+    """Owner of one eptv_geometry handle (ray tables + workspace on the current device)."""
+
+    def __init__(self, g: FanGeometry):
+        L = load()
+        self.g = g
+        self._angles = None
+        d = GeometryDesc(g.nx, g.ny, g.dx, g.dy, g.n_views, None, g.n_bins, g.dbeta,
+                         g.bin_offset, g.sid, g.sdd, g.detector)
+        if g.angles is not None:
+            arr = (ctypes.c_double * g.n_views)(*[float(a) for a in g.angles])
+            self._angles = arr
+            d.angles = ctypes.cast(arr, ctypes.POINTER(ctypes.c_double))
+        h = ctypes.c_void_p()
+        _check(L.eptv_create_geometry(ctypes.byref(d), ctypes.byref(h)))
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().eptv_destroy_geometry(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def n_pix(self):
+        return self.g.nx * self.g.ny
+
+    @property
+    def n_rays(self):
+        return self.g.n_views * self.g.n_bins
+
+
+def eptv_project(geom: Geometry, f, y, stream=None):
+    _check(load().eptv_project(geom.handle, _ptr(f, geom.n_pix, "f"), _ptr(y, geom.n_rays, "y"),
+                               _stream(stream)))
+    return y
+
+
+def eptv_project_t(geom: Geometry, f, fT, y, stream=None):
+    _check(load().eptv_project_t(geom.handle, _ptr(f, geom.n_pix, "f"),
+                                 _ptr(fT, geom.n_pix, "fT"), _ptr(y, geom.n_rays, "y"),
+                                 _stream(stream)))
+    return y
+
+
+def eptv_transpose(geom: Geometry, f, fT, stream=None):
+    _check(load().eptv_transpose(geom.handle, _ptr(f, geom.n_pix, "f"),
+                                 _ptr(fT, geom.n_pix, "fT"), _stream(stream)))
+    return fT
+
+
+def eptv_backproject(geom: Geometry, y, f, stream=None):
+    _check(load().eptv_backproject(geom.handle, _ptr(y, geom.n_rays, "y"),
+                                   _ptr(f, geom.n_pix, "f"), _stream(stream)))
+    return f
+
+
+def eptv_cgls(geom: Geometry, M: int, y, u, stream=None):
+    _check(load().eptv_cgls(geom.handle, int(M), _ptr(y, geom.n_rays, "y"),
+                            _ptr(u, geom.n_pix, "u"), _stream(stream)))
+    return u
+
+
+def eptv_sigma(geom: Geometry, p: EptvParams, v, stream=None) -> float:
+    out = ctypes.c_double()
+    pp = params(p)
+    _check(load().eptv_sigma(geom.handle, ctypes.byref(pp), _ptr(v, geom.n_pix, "v"),
+                             ctypes.byref(out), _stream(stream)))
+    return out.value
+
+
+def eptv_tv_gradient(geom: Geometry, p: EptvParams, sigma: float, f, v, g, stream=None):
+    """Returns the (P2) energy at f (the gradient is written to g)."""
+    out = ctypes.c_double()
+    pp = params(p)
+    _check(load().eptv_tv_gradient(geom.handle, ctypes.byref(pp), float(sigma),
+                                   _ptr(f, geom.n_pix, "f"), _ptr(v, geom.n_pix, "v"),
+                                   _ptr(g, geom.n_pix, "g"), ctypes.byref(out), _stream(stream)))
+    return out.value
+
+
+def eptv_tv_step(geom: Geometry, p: EptvParams, v, f, t_prev: Optional[float] = None,
+                 weights=None, stream=None):
+    """One (P2) solve + clamp; returns (Stats, t_prev after the solve)."""
+    pp = params(p)
+    st = Stats()
+    tp = ctypes.c_double(t_prev if t_prev is not None else p.t_init_eff)
+    nw = 2 * (geom.g.nx + 1) * (geom.g.ny + 1)
+    _check(load().eptv_tv_step(geom.handle, ctypes.byref(pp), _ptr(v, geom.n_pix, "v"),
+                               _ptr(f, geom.n_pix, "f"), ctypes.byref(tp),
+                               _ptr(weights, nw, "weights"), ctypes.byref(st), _stream(stream)))
+    return st, tp.value
+
+
+def eptv_reconstruct(geom: Geometry, p: EptvParams, y, f, wprior=None, report: bool = True,
+                     stream=None):
+    pp = params(p)
+    rep = Report()
+    _check(load().eptv_reconstruct(geom.handle, ctypes.byref(pp), _ptr(y, geom.n_rays, "y"),
+                                   _ptr(f, geom.n_pix, "f"), _ptr(wprior, geom.n_pix, "wprior"),
+                                   ctypes.byref(rep) if report else None, _stream(stream)))
+    return rep if report else None
+
+
+def eptv_report_energy(geom: Geometry, p: EptvParams, sigma_ref: float, f, y, stream=None):
+    out = ctypes.c_double()
+    pp = params(p)
+    _check(load().eptv_report_energy(geom.handle, ctypes.byref(pp), float(sigma_ref),
+                                     _ptr(f, geom.n_pix, "f"), _ptr(y, geom.n_rays, "y"),
+                                     ctypes.byref(out), _stream(stream)))
+    return out.value
+
+
+def eptv_select_kth(geom: Geometry, vals, k: int, out, stream=None):
+    _check(load().eptv_select_kth(geom.handle, _ptr(vals, None, "vals"), vals.numel(), int(k),
+                                  _ptr(out, 1, "out"), _stream(stream)))
+    return out
+
+
+def eptv_reconstruct_batched(geoms: Sequence[Geometry], p: EptvParams, ys, fs,
+                             report: bool = True, stream=None):
+    n = len(geoms)
+    H = (ctypes.c_void_p * n)(*[g.handle.value for g in geoms])
+    Y = (ctypes.c_void_p * n)(*[_ptr(y, g.n_rays, "y") for g, y in zip(geoms, ys)])
+    F = (ctypes.c_void_p * n)(*[_ptr(f, g.n_pix, "f") for g, f in zip(geoms, fs)])
+    reps = (Report * n)() if report else None
+    pp = params(p)
+    _check(load().eptv_reconstruct_batched(n, H, ctypes.byref(pp), Y, F, reps, _stream(stream)))
+    return list(reps) if report else None
+
+
+def eptv_get_log(geom: Geometry):
+    """(steps [n_outer][n_gd], sigmas [n_outer]) of the last eptv_reconstruct on geom."""
+    import numpy as np
+    no, ng = ctypes.c_int(), ctypes.c_int()
+    L = load()
+    _check(L.eptv_get_log(geom.handle, None, 0, None, 0, ctypes.byref(no), ctypes.byref(ng)))
+    steps = np.zeros(no.value * ng.value)
+    sig = np.zeros(no.value)
+    _check(L.eptv_get_log(geom.handle, steps.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                          steps.size, sig.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                          sig.size, None, None))
+    return steps.reshape(no.value, ng.value), sig
+
+
+def version() -> str:
+    return load().eptv_version().decode()

@@ -176,7 +176,7 @@ def measured_peaks():
     return 6400.0, "fallback"
 
 
-def cpu_baseline(case, steps=2):
+def cpu_baseline(case, steps=8):
     """The FP64 oracle as it stands, on the host: `steps` outer iterations of the same
     workload (a bounded sample of the 100)."""
     import numpy as np

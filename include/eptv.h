@@ -214,6 +214,19 @@ int eptv_get_log(const eptv_geometry *g, double *h_steps, int steps_cap, double 
 int eptv_select_kth(const eptv_geometry *g, const float *d_vals, long n, long k,
                     float *d_out, void *stream);
 
+/* The same selection as eptv_select_kth, for callers that cannot allocate device memory
+ * (a process whose device memory is reserved by another allocator, a memory-capped
+ * service, a callback that must not enter the allocator): it needs no geometry handle
+ * and allocates nothing.  The paper has no counterpart; this is a library convenience.
+ * Its working memory is one 16.5 KB array compiled into the library, kept by every GPU
+ * that loads it until the process exits.  n must be in [1, 2^31 - 1] (the histogram
+ * counts are 32-bit) and k in [1, n]; otherwise EPTV_ERR_ARG.  d_vals: n non-negative
+ * finite floats; d_out: one float.  The first call on a device looks up the array's
+ * device address (make that first call before any stream capture).  All calls on a
+ * device share the array: each call clears it before use, and calls that overlap on
+ * the GPU (other streams or threads) race and give wrong results. */
+int eptv_select_kth_noalloc(const float *d_vals, long n, long k, float *d_out, void *stream);
+
 /* Batched reconstruction of n independent slices (any mix of sizes) with one set of
  * parameters: every kernel of one outer iteration covers all slices in a single launch,
  * and one outer iteration of the whole batch is captured into one CUDA graph.

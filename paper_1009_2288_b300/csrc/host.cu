@@ -26,6 +26,8 @@ static int fail(int code, const char *fmt, ...) {
     return code;
 }
 
+int report_error(int code, const char *msg) { return fail(code, "%s", msg); }
+
 #define CU(call)                                                                          \
     do {                                                                                  \
         cudaError_t e_ = (call);                                                          \

@@ -23,7 +23,7 @@ EXPORTED = [
     "eptv_project_t", "eptv_transpose", "eptv_backproject", "eptv_cgls", "eptv_sigma",
     "eptv_tv_gradient", "eptv_tv_step", "eptv_reconstruct", "eptv_report_energy",
     "eptv_select_kth", "eptv_reconstruct_batched", "eptv_last_error", "eptv_version",
-    "eptv_get_log",
+    "eptv_get_log", "eptv_select_kth_noalloc",
 ]
 
 
@@ -100,6 +100,7 @@ def load():
         "eptv_report_energy": (c_int, [vp, ctypes.POINTER(Params), dbl, vp, vp,
                                        ctypes.POINTER(dbl), vp]),
         "eptv_select_kth": (c_int, [vp, vp, c_long, c_long, vp, vp]),
+        "eptv_select_kth_noalloc": (c_int, [vp, c_long, c_long, vp, vp]),
         "eptv_reconstruct_batched": (c_int, [c_int, ctypes.POINTER(vp), ctypes.POINTER(Params),
                                              ctypes.POINTER(vp), ctypes.POINTER(vp),
                                              ctypes.POINTER(Report), vp]),
@@ -272,6 +273,14 @@ def eptv_report_energy(geom: Geometry, p: EptvParams, sigma_ref: float, f, y, st
 def eptv_select_kth(geom: Geometry, vals, k: int, out, stream=None):
     _check(load().eptv_select_kth(geom.handle, _ptr(vals, None, "vals"), vals.numel(), int(k),
                                   _ptr(out, 1, "out"), _stream(stream)))
+    return out
+
+
+def eptv_select_kth_noalloc(vals, k: int, out, stream=None):
+    """k-th smallest of vals without a geometry handle and without any device
+    allocation (working memory compiled into the library); see eptv.h."""
+    _check(load().eptv_select_kth_noalloc(_ptr(vals, None, "vals"), vals.numel(), int(k),
+                                          _ptr(out, 1, "out"), _stream(stream)))
     return out
 
 

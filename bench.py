@@ -336,24 +336,38 @@ def run_ours(args, world, rank, local):
                 "algorithmic_bytes_per_launch": algo_bytes, "nnz": nnz,
                 "launch_us": {"k1_project": t_k1 * 1e6, "k2_backproject": t_k2 * 1e6}}
 
-    # time to the FP64 oracle's final reported energy (stored by tests/golden/make_oracle_energy.py)
+    # time to the FP64 oracle's energy (stored by tests/golden/make_oracle_energy.py).
+    # The reported energy (Eq. 2) swings from one iteration to the next late in a run, so
+    # both sides are compared on 5-iteration means: the target is the oracle's mean over
+    # its last 5 iterations; the GPU reaches it at the first k whose mean over k-4..k is
+    # within 1e-3 of it (or below).
     tte = None
     gold = os.path.join(ROOT, "tests", "golden", "c2_oracle_energy.json")
     if not args.no_tte and rank == 0 and os.path.exists(gold):
         ref = json.load(open(gold))
-        sig, e_star = ref["sigma_ref"], ref["e_report_final"]
-        pk = I.EptvParams(n_outer=1)
+        sig = ref["sigma_ref"]
+        eo = ref["e_report_per_iteration"]
+        target = sum(eo[-5:]) / 5.0
+        def first_reach(es):
+            for k in range(5, len(es) + 1):
+                if sum(es[k - 5:k]) / 5.0 <= target * (1 + 1e-3):
+                    return k
+            return None
         f_dev.zero_()
-        k_star = None
+        t_prev = p.t_init_eff
         energies = []
+        k_star = None
         for k in range(1, N_OUTER + 1):
+            pk = I.EptvParams(n_outer=1, t_init=t_prev)
             rep = E.eptv_reconstruct(geo, pk, y_dev, f_dev, report=True)
-            pk.t_init = rep.t_prev
-            ek = E.eptv_report_energy(geo, p, sig, f_dev, y_dev)
-            energies.append(ek)
-            if k_star is None and ek <= e_star * (1 + 1e-3):
-                k_star = k
+            t_prev = rep.t_prev
+            energies.append(E.eptv_report_energy(geo, p, sig, f_dev, y_dev))
+            k_star = first_reach(energies)
+            if k_star is not None:
                 break
+        tte = {"target": target, "criterion": "5-iteration mean of E_report within 1e-3 of the "
+                                              "oracle's last-5 mean (sigma_ref = oracle's last sigma)",
+               "oracle_iterations": first_reach(eo), "iterations": k_star, "seconds": None}
         if k_star is not None:
             pt = I.EptvParams(n_outer=k_star)
             ts = []
@@ -365,13 +379,9 @@ def run_ours(args, world, rank, local):
                 e.record(stream)
                 e.synchronize()
                 ts.append(s.elapsed_time(e))
-            tte = {"seconds": min(ts) * 1e-3, "iterations": k_star,
-                   "oracle_iterations": int(next((i + 1 for i, v in enumerate(ref["e_report_per_iteration"])
-                                                  if v <= e_star * (1 + 1e-3)), ref["n_outer"])),
-                   "target": e_star, "criterion": "E_report <= 1.001 x oracle final"}
+            tte["seconds"] = min(ts) * 1e-3
         else:
-            tte = {"seconds": None, "iterations": None, "target": e_star,
-                   "last_energy": energies[-1] if energies else None}
+            tte["last_mean"] = sum(energies[-5:]) / 5.0
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

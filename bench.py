@@ -264,6 +264,8 @@ def run_ours(args, world, rank, local):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
     stream = torch.cuda.current_stream(dev)
 
+    tuning = E.eptv_autotune(geo)          # launch shapes of K1 / K2 for this geometry
+
     def step():
         f_dev.zero_()
         return E.eptv_reconstruct(geo, p, y_dev, f_dev, report=True)
@@ -394,7 +396,8 @@ def run_ours(args, world, rank, local):
         "config": {"workload": WORKLOAD, "step": f"one {N_OUTER}-iteration reconstruction",
                    "image": "512x512 @ 0.8 mm", "views": 40, "bins": 888, "M": p.cgls_iters,
                    "n_gd": p.n_gd, "max_trials": p.max_trials, "l2": "flushed (256 MB write) between steps",
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "tuning": {"k1_seg": tuning[0], "k2_vg": tuning[1]}},
         "e2e": {"value": world * N_OUTER * 1e3 / e2e_ms, "unit": UNIT,
                 "h2d_bytes_per_step": 4 * g.n_rays, "d2h_bytes_per_step": 4 * g.n_pix,
                 "ms_per_step": e2e_ms},

@@ -236,6 +236,22 @@ int eptv_reconstruct_batched(int n, eptv_geometry *const *geoms, const eptv_para
                              const float *const *d_y, float *const *d_f,
                              eptv_report *reps, void *stream);
 
+/* Launch shapes of the projector and back projector used by calls on handle g: k1_seg =
+ * warps marching each block of 32 adjacent rays (4, 8 or 16; the rows of a ray are split
+ * among them), k2_vg = threads sharing the views of each 4-pixel strip (1, 2, 4 or 8).
+ * Defaults 8 and 4.  EPTV_ERR_ARG for other values. */
+int eptv_set_tuning(eptv_geometry *g, int k1_seg, int k2_vg);
+
+/* Autotuner: times every launch shape of the projector and the back projector on the
+ * handle's own geometry (zero images in its workspace, which it overwrites) and keeps
+ * the fastest for later calls on g.  *k1_seg / *k2_vg (may be NULL) receive the choice.
+ * Synchronises the device. */
+int eptv_autotune(eptv_geometry *g, int *k1_seg, int *k2_vg);
+
+/* The same for the batch {geoms[0..n)} used by eptv_reconstruct_batched (the choice is
+ * kept with that batch, cached in geoms[0]). */
+int eptv_autotune_batched(int n, eptv_geometry *const *geoms, int *k1_seg, int *k2_vg);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char *eptv_last_error(void);
 

@@ -1,25 +1,31 @@
 // K2: f = P^T y, the exact transpose of the projector, as a scatter-free pixel-driven
 // gather (the paper rejects the ray-driven scatter for its write conflicts, Sec. 2.3).
 //
-// Each thread owns 4 adjacent pixels of one row (float4 output).  For every view it
-// bounds the fan angles of its 4-pixel strip from the strip's corners (tan-space
-// min/max, then atan), visits the bins whose rays can cross the strip, and recomputes
-// each p_ij with the canonical plane parameters of eptv_internal.cuh -- the same FP32
-// operations as the projector, so <P x, y> = <x, P^T y> holds up to summation order.
-// The strip's 5 column planes and 2 row planes are shared by its 4 pixels.
-// Optionally also writes the transposed image (for the projector's shallow rays) and
-// reduces |f|^2 (FP32 per warp, FP64 across warps and blocks).
+// A block covers a 32 x 16 pixel tile: 128 strips of 4 adjacent pixels of one row
+// (float4 output), each strip served by VG threads that take every VG-th view, so a
+// 512^2 image keeps VG x 65k threads busy.  For every view a thread bounds the fan
+// angles of its strip from the strip's corners (tan-space min/max, then atan), visits
+// the bins whose rays can cross the strip, and recomputes each p_ij with the canonical
+// plane parameters of eptv_internal.cuh -- the same FP32 operations as the projector,
+// so <P x, y> = <x, P^T y> holds up to summation order.  The strip's 5 column planes
+// and 2 row planes are shared by its 4 pixels.  The VG partial sums of a strip are
+// added in group order (deterministic).  Optionally also writes the transposed image
+// (for the projector's shallow rays) and reduces |f|^2 (FP32 per warp, FP64 above).
 #include "eptv_internal.cuh"
 #include "kernels.cuh"
 
 namespace eptv {
 
-__global__ void __launch_bounds__(128)
+template <int VG>
+__global__ void __launch_bounds__(128 * VG)
 k2_backproject(const SliceDev *__restrict__ sls, TileMap map, BackArgs a,
                unsigned int *__restrict__ counters, double *__restrict__ partials)
 {
+    constexpr int NT = 128 * VG;
+    __shared__ float4 part[VG > 1 ? VG - 1 : 1][128];
     __shared__ float tr[kTileH][kTileW + 1];
-    __shared__ double rsm[4];
+    __shared__ double rsm[2 * (NT / 32)];
+    __shared__ double res[2];
     __shared__ int last_flag;
 
     int local;
@@ -28,7 +34,8 @@ k2_backproject(const SliceDev *__restrict__ sls, TileMap map, BackArgs a,
     const int nx = S.nx, ny = S.ny, nb = S.nb;
     const int tiles_x = (nx + kTileW - 1) / kTileW;
     const int tyb = local / tiles_x, txb = local - tyb * tiles_x;
-    const int lx = threadIdx.x & 7, ly = threadIdx.x >> 3;
+    const int strip = threadIdx.x & 127, vg = threadIdx.x >> 7;
+    const int lx = strip & 7, ly = strip >> 3;
     const int i0 = txb * kTileW + lx * 4, j = tyb * kTileH + ly;
 
     const float *sino = a.in_override ? a.in_override : S.r;
@@ -45,7 +52,7 @@ k2_backproject(const SliceDev *__restrict__ sls, TileMap map, BackArgs a,
         const float inv_db = S.inv_dbeta, kc = S.kc;
         const bool arc = S.detector == EPTV_DETECTOR_ARC;
 
-        for (int v = 0; v < S.nv; ++v) {
+        for (int v = vg; v < S.nv; v += VG) {
             const ViewRec V = S.view[v];
             // tan of the fan angle of each corner as seen from the source
             float tmin = 3.0e38f, tmax = -3.0e38f;
@@ -84,7 +91,19 @@ k2_backproject(const SliceDev *__restrict__ sls, TileMap map, BackArgs a,
         }
     }
 
-    // output
+    // combine the view groups in order (group 0 owns the strip's output)
+    if (VG > 1) {
+        if (vg > 0) part[vg - 1][strip] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+        __syncthreads();
+        if (vg == 0) {
+#pragma unroll
+            for (int gi = 0; gi < VG - 1; ++gi) {
+                const float4 p = part[gi][strip];
+                acc[0] += p.x; acc[1] += p.y; acc[2] += p.z; acc[3] += p.w;
+            }
+        }
+    }
+
     float *out;
     float *outT = nullptr;
     if (a.out_override) out = a.out_override;
@@ -93,7 +112,7 @@ k2_backproject(const SliceDev *__restrict__ sls, TileMap map, BackArgs a,
     else { out = S.u; if (a.write_T) outT = S.uT; }
 
     float sq = 0.0f;
-    if (j < ny && i0 < nx) {
+    if (vg == 0 && j < ny && i0 < nx) {
         float *p = out + (size_t)j * nx + i0;
         if (i0 + 3 < nx && ((nx & 3) == 0) && ((((uintptr_t)p) & 15) == 0)) {
             *reinterpret_cast<float4 *>(p) = make_float4(acc[0], acc[1], acc[2], acc[3]);
@@ -103,15 +122,19 @@ k2_backproject(const SliceDev *__restrict__ sls, TileMap map, BackArgs a,
         for (int q = 0; q < 4; ++q) if (i0 + q < nx) sq = fmaf(acc[q], acc[q], sq);
     }
     if (outT) {
+        if (vg == 0) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) tr[ly][lx * 4 + q] = acc[q];
+            for (int q = 0; q < 4; ++q) tr[ly][lx * 4 + q] = acc[q];
+        }
         __syncthreads();
-        const int ii = threadIdx.x >> 2, jj0 = (threadIdx.x & 3) * 4;
-        const int gi = txb * kTileW + ii;
-        if (gi < nx) {
-            for (int q = 0; q < 4; ++q) {
-                const int gj = tyb * kTileH + jj0 + q;
-                if (gj < ny) outT[(size_t)gi * ny + gj] = tr[jj0 + q][ii];
+        for (int idx = threadIdx.x; idx < 128; idx += NT) {
+            const int ii = idx >> 2, jj0 = (idx & 3) * 4;
+            const int gi = txb * kTileW + ii;
+            if (gi < nx) {
+                for (int q = 0; q < 4; ++q) {
+                    const int gj = tyb * kTileH + jj0 + q;
+                    if (gj < ny) outT[(size_t)gi * ny + gj] = tr[jj0 + q][ii];
+                }
             }
         }
     }
@@ -120,21 +143,23 @@ k2_backproject(const SliceDev *__restrict__ sls, TileMap map, BackArgs a,
     const int b0 = __ldg(map.start + si);
     const int nblk = __ldg(map.start + si + 1) - b0;
     float vals[1] = {sq};
-    block_sum_to<1, 128>(vals, partials + (size_t)blockIdx.x * 2, rsm);
+    block_sum_to<1, NT>(vals, partials + (size_t)blockIdx.x * 2, rsm);
     if (threadIdx.x == 0) partials[(size_t)blockIdx.x * 2 + 1] = 0.0;
     if (!last_block_of_slice(counters + si, nblk, &last_flag)) return;
-    if (threadIdx.x < 32) {
-        double tot[2];
-        sum_partials<2>(partials, b0, nblk, tot);
-        if (threadIdx.x == 0) finalize(S.sc, a.fin, tot[0], tot[1]);
-    }
+    last_block_sum<2, NT>(partials, 2, b0, nblk, rsm, res);
+    if (threadIdx.x == 0) finalize(S.sc, a.fin, res[0], res[1]);
 }
 
 void launch_backproject(const Batch &B, const BackArgs &a, cudaStream_t st) {
     const int nblk = B.blocks(FAM_K2);
     if (nblk == 0) return;
     ++g_launch_count;
-    k2_backproject<<<nblk, 128, 0, st>>>(B.d_sd, B.map(FAM_K2), a, B.d_counters, B.d_partials);
+    switch (B.k2_vg) {
+    case 1: k2_backproject<1><<<nblk, 128, 0, st>>>(B.d_sd, B.map(FAM_K2), a, B.d_counters, B.d_partials); break;
+    case 2: k2_backproject<2><<<nblk, 256, 0, st>>>(B.d_sd, B.map(FAM_K2), a, B.d_counters, B.d_partials); break;
+    case 8: k2_backproject<8><<<nblk, 1024, 0, st>>>(B.d_sd, B.map(FAM_K2), a, B.d_counters, B.d_partials); break;
+    default: k2_backproject<4><<<nblk, 512, 0, st>>>(B.d_sd, B.map(FAM_K2), a, B.d_counters, B.d_partials); break;
+    }
 }
 
 }  // namespace eptv

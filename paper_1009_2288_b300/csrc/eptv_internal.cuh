@@ -163,20 +163,48 @@ __device__ __forceinline__ bool last_block_of_slice(unsigned int *counter, int n
     return *flag_smem != 0;
 }
 
-// Sum NV partials of blocks [b0, b0 + nb) in block order (one warp, FP64).
-template <int NV>
-__device__ __forceinline__ void sum_partials(const double *partials, int b0, int nb, double (&out)[NV]) {
-    // Called by warp 0 of the last block.  Lane l sums blocks l, l+32, ...; then a
-    // fixed-order FP64 tree over lanes.
-    const int lane = threadIdx.x & 31;
+// All NT threads of the finishing block: sum NV partials of blocks [b0, b0 + nb)
+// (row stride `stride` doubles) into res[0..NV) (shared memory, valid after the call in
+// every thread).  Thread t sums blocks t, t + NT, ... in increasing order, warps reduce
+// with a fixed shuffle tree and the warp results are added in warp order, so the
+// result is deterministic.  The loads of four blocks are issued together so that the
+// tail runs at L2 bandwidth rather than one round trip per partial.
+template <int NV, int NT>
+__device__ __forceinline__ void last_block_sum(const double *partials, int stride, int b0, int nb,
+                                               double *rsm /* NV * NT/32 */, double *res /* NV */) {
+    double acc[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+    int b = threadIdx.x;
+    for (; b + 3 * NT < nb; b += 4 * NT) {
+        double v[4][NV];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int k = 0; k < NV; ++k) v[u][k] = __ldcg(partials + (size_t)(b0 + b + u * NT) * stride + k);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int k = 0; k < NV; ++k) acc[k] += v[u][k];
+    }
+    for (; b < nb; b += NT)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) acc[k] += __ldcg(partials + (size_t)(b0 + b) * stride + k);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-        double a = 0.0;
-        for (int b = lane; b < nb; b += 32) a += __ldcg(partials + (size_t)(b0 + b) * NV + k);
+        double a = acc[k];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-        out[k] = a;
+        if (lane == 0) rsm[k * (NT / 32) + w] = a;
     }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double a = 0.0;
+        for (int i = 0; i < NT / 32; ++i) a += rsm[threadIdx.x * (NT / 32) + i];
+        res[threadIdx.x] = a;
+    }
+    __syncthreads();
 }
 
 // ---------------------------------------------------------------------------------

@@ -61,7 +61,7 @@ struct DevMem {
 
 struct GraphCache {
     cudaGraphExec_t exec = nullptr;
-    int key[6] = {-1, -1, -1, -1, -1, -1};
+    int key[7] = {-1, -1, -1, -1, -1, -1, -1};
     long long kernels = 0;     // kernel nodes in the captured outer iteration
     void reset() {
         if (exec) cudaGraphExecDestroy(exec);
@@ -261,7 +261,7 @@ static void enqueue_outer(const Batch &B, const eptv_params *p, cudaStream_t st)
 
 // Capture one outer iteration of batch B into a graph (cached per structural key).
 static int outer_graph(const Batch &B, GraphCache &gc, cudaStream_t cap, const eptv_params *p) {
-    const int key[6] = {p->cgls_iters, p->n_gd, n_trials_of(p), p->step_rule, B.n, 1};
+    const int key[7] = {p->cgls_iters, p->n_gd, n_trials_of(p), p->step_rule, B.n, B.k1_seg, B.k2_vg};
     if (gc.exec && memcmp(key, gc.key, sizeof key) == 0) return 0;
     gc.reset();
     cudaGraph_t graph = nullptr;
@@ -333,6 +333,75 @@ static float inv_or_big(double c) {
 }
 
 }  // namespace eptv
+
+// The batch over `geoms` cached in geoms[0] (built on first use or when the member list
+// changes).  The caller has synchronised the stream that used the previous batch.
+static int acquire_batch(int n, eptv_geometry *const *geoms, BatchCache &bc) {
+    std::vector<const void *> members(geoms, geoms + n);
+    if (bc.members == members) return 0;
+    bc.reset();
+    std::vector<SliceDev> sds;
+    for (int i = 0; i < n; ++i) sds.push_back(geoms[i]->sd);
+    int rc = build_batch(bc.B, bc.mem, sds);
+    if (rc) { bc.reset(); return rc; }
+    bc.members = members;
+    return 0;
+}
+
+// Times every projector / back-projector launch shape on batch B (zero images, the
+// batch's own buffers) and keeps the fastest: the ray-block shape of K1 (warps per 32
+// rays: 4, 8, 16) and the view split of K2 (1, 2, 4, 8 groups per strip).
+static int autotune_batch(Batch &B, int *k1_out, int *k2_out) {
+    cudaStream_t st = nullptr;
+    for (const SliceDev &sd : B.h_sd) {
+        CU(cudaMemsetAsync(sd.u, 0, sizeof(float) * sd.n_pix, st));
+        CU(cudaMemsetAsync(sd.uT, 0, sizeof(float) * sd.n_pix, st));
+        CU(cudaMemsetAsync(sd.r, 0, sizeof(float) * sd.n_rays, st));
+    }
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    auto time_it = [&](auto launch) -> float {
+        for (int i = 0; i < 3; ++i) launch();
+        cudaEventRecord(e0, st);
+        for (int i = 0; i < 10; ++i) launch();
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        return ms;
+    };
+    const long long saved = g_launch_count;
+    ProjArgs pa{};
+    pa.img = IMG_U; pa.out = SINO_Q; pa.fin = FIN_NONE;
+    BackArgs ba{};
+    ba.out = 1; ba.fin = FIN_NONE;
+    const int k1c[] = {4, 8, 16}, k2c[] = {1, 2, 4, 8};
+    float best = 1e30f;
+    int b1 = B.k1_seg;
+    for (int c : k1c) {
+        B.k1_seg = c;
+        const float ms = time_it([&] { launch_project(B, pa, st); });
+        if (ms < best) { best = ms; b1 = c; }
+    }
+    B.k1_seg = b1;
+    best = 1e30f;
+    int b2 = B.k2_vg;
+    for (int c : k2c) {
+        B.k2_vg = c;
+        const float ms = time_it([&] { launch_backproject(B, ba, st); });
+        if (ms < best) { best = ms; b2 = c; }
+    }
+    B.k2_vg = b2;
+    g_launch_count = saved;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CU(cudaGetLastError());
+    CU(cudaDeviceSynchronize());
+    if (k1_out) *k1_out = b1;
+    if (k2_out) *k2_out = b2;
+    return 0;
+}
 
 extern "C" {
 
@@ -763,15 +832,8 @@ int eptv_reconstruct_batched(int n, eptv_geometry *const *geoms, const eptv_para
     cudaStream_t st = (cudaStream_t)stream;
     eptv_geometry *g0 = geoms[0];
     BatchCache &bc = g0->batch;
-    std::vector<const void *> members(geoms, geoms + n);
-    if (bc.members != members) {
-        cudaStreamSynchronize(st);
-        bc.reset();
-        std::vector<SliceDev> sds;
-        for (int i = 0; i < n; ++i) sds.push_back(geoms[i]->sd);
-        if ((rc = build_batch(bc.B, bc.mem, sds))) { bc.reset(); return rc; }
-        bc.members = members;
-    }
+    cudaStreamSynchronize(st);
+    if ((rc = acquire_batch(n, geoms, bc))) return rc;
     for (int i = 0; i < n; ++i) {
         SliceDev &sd = bc.B.h_sd[i];
         sd.sel_rank = std::min<long long>(std::max<long long>((long long)std::ceil(p->sigma_q * sd.n_edges), 1), sd.n_edges);
@@ -800,6 +862,31 @@ int eptv_reconstruct_batched(int n, eptv_geometry *const *geoms, const eptv_para
         }
     }
     return 0;
+}
+
+int eptv_set_tuning(eptv_geometry *g, int k1_seg, int k2_vg) {
+    if (!g) return fail(EPTV_ERR_ARG, "NULL handle");
+    if (k1_seg != 4 && k1_seg != 8 && k1_seg != 16) return fail(EPTV_ERR_ARG, "k1_seg must be 4, 8 or 16");
+    if (k2_vg != 1 && k2_vg != 2 && k2_vg != 4 && k2_vg != 8) return fail(EPTV_ERR_ARG, "k2_vg must be 1, 2, 4 or 8");
+    g->B.k1_seg = k1_seg;
+    g->B.k2_vg = k2_vg;
+    return 0;
+}
+
+int eptv_autotune(eptv_geometry *g, int *k1_seg, int *k2_vg) {
+    if (!g) return fail(EPTV_ERR_ARG, "NULL handle");
+    CU(cudaDeviceSynchronize());
+    return autotune_batch(g->B, k1_seg, k2_vg);
+}
+
+int eptv_autotune_batched(int n, eptv_geometry *const *geoms, int *k1_seg, int *k2_vg) {
+    if (n < 1 || !geoms) return fail(EPTV_ERR_ARG, "bad batch arguments");
+    for (int i = 0; i < n; ++i)
+        if (!geoms[i]) return fail(EPTV_ERR_ARG, "NULL entry %d", i);
+    CU(cudaDeviceSynchronize());
+    int rc = acquire_batch(n, geoms, geoms[0]->batch);
+    if (rc) return rc;
+    return autotune_batch(geoms[0]->batch.B, k1_seg, k2_vg);
 }
 
 }  // extern "C"

@@ -18,7 +18,6 @@ enum Family {
     FAM_COUNT
 };
 
-constexpr int kK1Seg = 8;          // warps (row segments) per projector block
 constexpr int kTileW = 32, kTileH = 16;
 constexpr int kHistBins = 4096;    // radix-select histogram (12 bits per pass)
 constexpr int kMaxTrials = 16;
@@ -66,6 +65,8 @@ struct Batch {
     double *d_partials = nullptr;         // [max blocks][kPartialStride]
     unsigned int *d_hist = nullptr;       // [n][kHistBins]
     ParamsDev *d_params = nullptr;
+    int k1_seg = 8;        // projector: warps (row segments) per 32-ray block (4, 8, 16)
+    int k2_vg = 4;         // back projector: view groups per 4-pixel strip (1, 2, 4, 8)
     TileMap map(int fam) const { return TileMap{d_start + fam * (n + 1), n}; }
     int blocks(int fam) const { return h_start[fam * (n + 1) + n]; }
 };

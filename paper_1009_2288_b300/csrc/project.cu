@@ -24,6 +24,8 @@ k1_project(const SliceDev *__restrict__ sls, TileMap map, ProjArgs a,
            unsigned int *__restrict__ counters, double *__restrict__ partials)
 {
     __shared__ float red[SEG][33];
+    __shared__ double rsm[2 * SEG];
+    __shared__ double res[2];
     __shared__ int last_flag;
 
     int local;
@@ -108,12 +110,14 @@ k1_project(const SliceDev *__restrict__ sls, TileMap map, ProjArgs a,
                 float lo0 = cross_t(grid_line((float)(c + off_lo), dm, m0), Pm, im);
                 float hi0 = cross_t(grid_line((float)(c + off_hi), dm, m0), Pm, im);
                 float fr = (float)(rs + 1);
+                const float fsgn = (float)sgn;
+                float f1 = (float)(c + sgn + off_hi);     // plane beyond the next column (exact)
                 const float *rowp = base + (size_t)rs * sM;
                 for (int r = rs; r <= re; ++r) {
                     const float tb = cross_t(grid_line(fr, dM, M0), PM, iM);
                     fr += 1.0f;
                     const int c1 = c + sgn;
-                    const float hi1 = cross_t(grid_line((float)(c1 + off_hi), dm, m0), Pm, im);
+                    const float hi1 = cross_t(grid_line(f1, dm, m0), Pm, im);
                     const float l0 = seg_len(lo0, hi0, ta, tb);
                     const float l1 = seg_len(hi0, hi1, ta, tb);
                     float v0 = 0.0f, v1 = 0.0f;
@@ -122,10 +126,11 @@ k1_project(const SliceDev *__restrict__ sls, TileMap map, ProjArgs a,
                     acc = fmaf(l0, v0, acc);
                     acc = fmaf(l1, v1, acc);
                     if (hi0 < tb) {
-                        c = c1; lo0 = hi0; hi0 = hi1;
+                        c = c1; lo0 = hi0; hi0 = hi1; f1 += fsgn;
                         if (hi1 < tb) {          // FP32 sliver near 45 degrees
                             c += sgn; lo0 = hi1;
                             hi0 = cross_t(grid_line((float)(c + off_hi), dm, m0), Pm, im);
+                            f1 += fsgn;
                         }
                     }
                     ta = tb;
@@ -164,19 +169,19 @@ k1_project(const SliceDev *__restrict__ sls, TileMap map, ProjArgs a,
         }
     }
     if (!last_block_of_slice(counters + si, nblk, &last_flag)) return;
-    if (seg == 0) {
-        double tot[2];
-        sum_partials<2>(partials, b0, nblk, tot);
-        if (lane == 0) finalize(S.sc, a.fin, tot[0], tot[1]);
-    }
+    last_block_sum<2, 32 * SEG>(partials, 2, b0, nblk, rsm, res);
+    if (threadIdx.x == 0) finalize(S.sc, a.fin, res[0], res[1]);
 }
 
 void launch_project(const Batch &B, const ProjArgs &a, cudaStream_t st) {
     const int nblk = B.blocks(FAM_K1);
     if (nblk == 0) return;
     ++g_launch_count;
-    k1_project<kK1Seg><<<nblk, 32 * kK1Seg, 0, st>>>(B.d_sd, B.map(FAM_K1), a, B.d_counters,
-                                                     B.d_partials);
+    switch (B.k1_seg) {
+    case 4: k1_project<4><<<nblk, 128, 0, st>>>(B.d_sd, B.map(FAM_K1), a, B.d_counters, B.d_partials); break;
+    case 16: k1_project<16><<<nblk, 512, 0, st>>>(B.d_sd, B.map(FAM_K1), a, B.d_counters, B.d_partials); break;
+    default: k1_project<8><<<nblk, 256, 0, st>>>(B.d_sd, B.map(FAM_K1), a, B.d_counters, B.d_partials); break;
+    }
 }
 
 }  // namespace eptv

@@ -79,37 +79,55 @@ __device__ __forceinline__ void sel_hist_add(unsigned int *sh, unsigned int key,
     else { if ((key >> 8) == prefix) atomicAdd(&sh[key & 0xFFu], 1u); }
 }
 
-// Last block: find the bucket holding the remaining rank, narrow the prefix.
-// Returns the selected key after pass 2 (in all threads), else 0.
+// Last block (256 threads): find the bucket holding the remaining rank and narrow the
+// prefix.  The histogram is read with independent loads (16 per thread), the per-thread
+// bucket groups are prefix-summed across the block, and the thread whose group holds
+// the rank searches its own buckets.  Returns the selected key after pass 2 (in all
+// threads), else 0.  Re-arms the histogram (zero) for the next pass.
 __device__ unsigned int sel_scan(unsigned int *hist, double *sc, int pass, long long rank0,
                                  unsigned int *s_cnt /* 256 */, long long *s_res) {
     const int nbins = (pass == 2) ? 256 : kHistBins;
     const int per = nbins / 256;
-    const int t = threadIdx.x;
-    unsigned int local = 0;
-    for (int q = 0; q < per; ++q) local += __ldcg(hist + t * per + q);
-    s_cnt[t] = local;
-    __syncthreads();
-    if (t == 0) {
-        long long rank = (pass == 0) ? rank0 : (long long)sc[SC_SEL_RANK];
-        unsigned int prefix = (pass == 0) ? 0u : (unsigned int)sc[SC_SEL_PREFIX];
-        long long cum = 0;
-        int tb = 0;
-        for (; tb < 255; ++tb) { if (cum + s_cnt[tb] >= rank) break; cum += s_cnt[tb]; }
-        int b = tb * per;
-        for (int q = 0; q < per; ++q, ++b) {
-            const unsigned int c = __ldcg(hist + b);
-            if (cum + c >= rank || q == per - 1) break;
-            cum += c;
-        }
-        rank -= cum;
-        if (pass == 0) prefix = (unsigned int)b;
-        else if (pass == 1) prefix = (prefix << 12) | (unsigned int)b;
-        else prefix = (prefix << 8) | (unsigned int)b;
-        sc[SC_SEL_RANK] = (double)rank;
-        sc[SC_SEL_PREFIX] = (double)prefix;
-        *s_res = (long long)prefix;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    unsigned int v[16];
+    unsigned long long local = 0;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = (q < per) ? __ldcg(hist + t * per + q) : 0u;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) local += v[q];
+    // inclusive scan of the 256 group counts: warp shuffles, then warp totals
+    unsigned long long inc = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
     }
+    __shared__ unsigned long long s_warp[8];
+    if (lane == 31) s_warp[w] = inc;
+    __syncthreads();
+    unsigned long long before = 0;
+    for (int i = 0; i < w; ++i) before += s_warp[i];
+    inc += before;
+    const unsigned long long exc = inc - local;
+    const long long rank = (pass == 0) ? rank0 : (long long)sc[SC_SEL_RANK];
+    const unsigned int prefix = (pass == 0) ? 0u : (unsigned int)sc[SC_SEL_PREFIX];
+    __syncthreads();
+    if ((long long)exc < rank && rank <= (long long)inc) {
+        unsigned long long cum = exc;
+        int b = t * per;
+        for (int q = 0; q < per; ++q, ++b) {
+            if ((long long)(cum + v[q]) >= rank) break;
+            cum += v[q];
+        }
+        unsigned int pre;
+        if (pass == 0) pre = (unsigned int)b;
+        else if (pass == 1) pre = (prefix << 12) | (unsigned int)b;
+        else pre = (prefix << 8) | (unsigned int)b;
+        sc[SC_SEL_RANK] = (double)(rank - (long long)cum);
+        sc[SC_SEL_PREFIX] = (double)pre;
+        *s_res = (long long)pre;
+    }
+    (void)s_cnt;
     __syncthreads();
     for (int q = 0; q < per; ++q) hist[t * per + q] = 0u;     // re-arm for the next pass
     return (pass == 2) ? (unsigned int)(*s_res) : 0u;
@@ -444,19 +462,10 @@ k4_gd(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__restrict
     const int b0 = __ldg(map.start + si);
     const int nblk = __ldg(map.start + si + 1) - b0;
     if (!last_block_of_slice(counters + si, nblk, &last_flag)) return;
-    if (tid < 32) {
-        double tot[NV];
-        // sum_partials over the stride layout
-        const int lane = tid;
-#pragma unroll
-        for (int k = 0; k < NV; ++k) {
-            double acc = 0.0;
-            for (int b = lane; b < nblk; b += 32) acc += __ldcg(partials + (size_t)(b0 + b) * kPartialStride + k);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            tot[k] = acc;
-        }
-        if (lane == 0) {
+    __shared__ double tot[NV];
+    last_block_sum<NV, 128>(partials, kPartialStride, b0, nblk, rsm, tot);
+    {
+        if (tid == 0) {
             double *sc = S.sc;
             const double A = tot[0], Bg = tot[1];
             const double lamd = P->lambda;

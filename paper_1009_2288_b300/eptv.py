@@ -23,7 +23,8 @@ EXPORTED = [
     "eptv_project_t", "eptv_transpose", "eptv_backproject", "eptv_cgls", "eptv_sigma",
     "eptv_tv_gradient", "eptv_tv_step", "eptv_reconstruct", "eptv_report_energy",
     "eptv_select_kth", "eptv_reconstruct_batched", "eptv_last_error", "eptv_version",
-    "eptv_get_log", "eptv_select_kth_noalloc",
+    "eptv_get_log", "eptv_select_kth_noalloc", "eptv_set_tuning", "eptv_autotune",
+    "eptv_autotune_batched",
 ]
 
 
@@ -106,6 +107,10 @@ def load():
                                              ctypes.POINTER(Report), vp]),
         "eptv_get_log": (c_int, [vp, ctypes.POINTER(dbl), c_int, ctypes.POINTER(dbl), c_int,
                                  ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
+        "eptv_set_tuning": (c_int, [vp, c_int, c_int]),
+        "eptv_autotune": (c_int, [vp, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
+        "eptv_autotune_batched": (c_int, [c_int, ctypes.POINTER(vp), ctypes.POINTER(c_int),
+                                          ctypes.POINTER(c_int)]),
         "eptv_last_error": (ctypes.c_char_p, []),
         "eptv_version": (ctypes.c_char_p, []),
     }
@@ -308,6 +313,25 @@ def eptv_get_log(geom: Geometry):
                           steps.size, sig.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                           sig.size, None, None))
     return steps.reshape(no.value, ng.value), sig
+
+
+def eptv_set_tuning(geom: Geometry, k1_seg: int, k2_vg: int):
+    _check(load().eptv_set_tuning(geom.handle, int(k1_seg), int(k2_vg)))
+
+
+def eptv_autotune(geom: Geometry):
+    """Times the projector / back-projector launch shapes on geom; returns (k1_seg, k2_vg)."""
+    a, b = ctypes.c_int(), ctypes.c_int()
+    _check(load().eptv_autotune(geom.handle, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def eptv_autotune_batched(geoms: Sequence[Geometry]):
+    n = len(geoms)
+    H = (ctypes.c_void_p * n)(*[g.handle.value for g in geoms])
+    a, b = ctypes.c_int(), ctypes.c_int()
+    _check(load().eptv_autotune_batched(n, H, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
 
 
 def version() -> str:

@@ -120,6 +120,42 @@ def test_adjoint_identity_fp32(name):
         assert abs(lhs - rhs) / (np.linalg.norm(np64(px)) * np.linalg.norm(yf)) < 1e-6
 
 
+@pytest.mark.parametrize("k1,k2", [(4, 1), (16, 2), (8, 8), (4, 4)])
+def test_launch_shapes_match_oracle(k1, k2):
+    """Every projector / back-projector launch shape the autotuner can pick gives the
+    same operator (within the tolerances above) and keeps the adjoint identity."""
+    for name in ("c1", "ge_ragged"):
+        g = GEOMS[name]
+        geo = E.Geometry(g)
+        E.eptv_set_tuning(geo, k1, k2)
+        op = O.Operator(g)
+        f = I.random_image(g, 1, "uniform")
+        y = torch.empty(g.n_rays, device=DEV)
+        E.eptv_project(geo, t32(f), y)
+        assert np.max(per_view_rel(np64(y).reshape(g.n_views, g.n_bins), op.project(f))) < 1e-5
+        ys = np.abs(I.random_sino(g, 8))
+        b = torch.empty(g.n_pix, device=DEV)
+        E.eptv_backproject(geo, t32(ys), b)
+        err = np.linalg.norm(np64(b).reshape(g.ny, g.nx) - op.backproject(ys))
+        assert err <= 4 * coord_bound(g) * np.linalg.norm(op.backproject(ys))
+        lhs = float(np64(y) @ ys.astype(np.float32).astype(np.float64).ravel())
+        rhs = float(f.astype(np.float32).astype(np.float64).ravel() @ np64(b))
+        assert abs(lhs - rhs) / abs(lhs) < 1e-6
+
+
+def test_autotune_picks_a_valid_shape_and_keeps_parity(c1):
+    geo = E.Geometry(c1.geom)
+    k1, k2 = E.eptv_autotune(geo)
+    assert k1 in (4, 8, 16) and k2 in (1, 2, 4, 8)
+    p = I.EptvParams(n_outer=5, step_rule=O.FIXED, t_fixed=2e-5)
+    want = O.reconstruct(O.Operator(c1.geom), c1.y, p)
+    f = torch.zeros(c1.geom.n_pix, device=DEV)
+    E.eptv_reconstruct(geo, p, t32(c1.y).reshape(-1), f)
+    assert rel(np64(f).reshape(c1.geom.ny, c1.geom.nx), want) < 1e-4
+    with pytest.raises(E.EptvError):
+        E.eptv_set_tuning(geo, 5, 4)
+
+
 def test_axis_aligned_ray_exact_pitch():
     # odd image, zero offset, odd bin count: the central ray of view 0 runs along y = 0
     # through pixel centres and must see exactly dx per pixel.
@@ -335,14 +371,16 @@ def test_reconstruct_armijo_matches_oracle(c1, n_outer):
     steps, sigmas = E.eptv_get_log(geo)
     assert steps.shape == (n_outer, p.n_gd)
     flip = _first_flip(steps, log.steps)
+    # sigma is a percentile of half-edge magnitudes (~1e-3 1/mm) while the images differ
+    # by ~1e-4 relative of values ~2e-2: sigma is an order of magnitude more sensitive
     if flip is None:
-        assert np.allclose(sigmas, log.sigmas, rtol=1e-5)
+        assert np.allclose(sigmas, log.sigmas, rtol=2e-3)
         assert rep.n_fail == log.fails
         assert rel(got, want) < 1e-4
     else:
         k, n = flip
         assert np.allclose(steps[:k], np.asarray(log.steps[:k]), rtol=1e-6)
-        assert np.allclose(sigmas[:k + 1], log.sigmas[:k + 1], rtol=1e-5)
+        assert np.allclose(sigmas[:k + 1], log.sigmas[:k + 1], rtol=2e-3)
         # the first trial the two sides decided differently is the larger accepted step
         disputed = max(steps[k, n], log.steps[k][n])
         rhos = [r for (t, r) in log.trials[k][n] if abs(t - disputed) <= 1e-6 * disputed]

@@ -162,6 +162,7 @@ static void family_blocks(const SliceDev &s, int out[FAM_COUNT]) {
     out[FAM_IMG] = ((s.nx + 31) / 32) * ((s.ny + 31) / 32);
     out[FAM_SINO] = (s.n_rays + 1023) / 1024;
     out[FAM_EDGE] = (s.n_edges + 2047) / 2048;
+    out[FAM_TV] = ((s.nx + kTileW - 1) / kTileW) * ((s.ny + kGdTileRows - 1) / kGdTileRows);
 }
 
 // Allocate the batch bookkeeping (maps, counters, partials, histograms, params) for the
@@ -363,13 +364,17 @@ static int autotune_batch(Batch &B, int *k1_out, int *k2_out) {
     CU(cudaEventCreate(&e1));
     auto time_it = [&](auto launch) -> float {
         for (int i = 0; i < 3; ++i) launch();
-        cudaEventRecord(e0, st);
-        for (int i = 0; i < 10; ++i) launch();
-        cudaEventRecord(e1, st);
-        cudaEventSynchronize(e1);
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        return ms;
+        float best_ms = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {     // best of 3 rounds of 20 launches
+            cudaEventRecord(e0, st);
+            for (int i = 0; i < 20; ++i) launch();
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            best_ms = std::min(best_ms, ms);
+        }
+        return best_ms;
     };
     const long long saved = g_launch_count;
     ProjArgs pa{};

@@ -15,10 +15,12 @@ enum Family {
     FAM_IMG,      // image elementwise with transpose: ceil(nx / 32) * ceil(ny / 32) blocks
     FAM_SINO,     // sinogram elementwise: ceil(n_rays / 1024) blocks
     FAM_EDGE,     // half-edge arrays: ceil(n_edges / 2048) blocks
+    FAM_TV,       // fused TV descent: ceil(nx / 32) * ceil(ny / kGdTileRows) blocks
     FAM_COUNT
 };
 
 constexpr int kTileW = 32, kTileH = 16;
+constexpr int kGdTileRows = 8;
 constexpr int kHistBins = 4096;    // radix-select histogram (12 bits per pass)
 constexpr int kMaxTrials = 16;
 constexpr int kPartialStride = kMaxTrials + 8;   // doubles per block in the partials array

@@ -113,16 +113,24 @@ k1_project(const SliceDev *__restrict__ sls, TileMap map, ProjArgs a,
                 const float fsgn = (float)sgn;
                 float f1 = (float)(c + sgn + off_hi);     // plane beyond the next column (exact)
                 const float *rowp = base + (size_t)rs * sM;
+                // The row interval is clipped to the image's minor-axis extent
+                // [tm_lo, tm_hi]: a column inside the image has both planes inside that
+                // extent, so its length is bit-identical to the unclipped slab formula,
+                // and a column outside the image gets length exactly 0 -- so the column
+                // index only needs clamping for the address.
+                float tac = fmaxf(ta, tm_lo);
                 for (int r = rs; r <= re; ++r) {
                     const float tb = cross_t(grid_line(fr, dM, M0), PM, iM);
+                    const float tbc = fminf(tb, tm_hi);
                     fr += 1.0f;
                     const int c1 = c + sgn;
                     const float hi1 = cross_t(grid_line(f1, dm, m0), Pm, im);
-                    const float l0 = seg_len(lo0, hi0, ta, tb);
-                    const float l1 = seg_len(hi0, hi1, ta, tb);
-                    float v0 = 0.0f, v1 = 0.0f;
-                    if ((unsigned)c < (unsigned)nm) v0 = __ldg(rowp + c * sm);
-                    if (l1 > 0.0f && (unsigned)c1 < (unsigned)nm) v1 = __ldg(rowp + c1 * sm);
+                    const float l0 = seg_len(lo0, hi0, tac, tbc);
+                    const float l1 = seg_len(hi0, hi1, tac, tbc);
+                    const int cc = min(max(c, 0), nm - 1);
+                    const float v0 = __ldg(rowp + cc * sm);
+                    float v1 = 0.0f;
+                    if (l1 > 0.0f) v1 = __ldg(rowp + c1 * sm);
                     acc = fmaf(l0, v0, acc);
                     acc = fmaf(l1, v1, acc);
                     if (hi0 < tb) {
@@ -134,6 +142,7 @@ k1_project(const SliceDev *__restrict__ sls, TileMap map, ProjArgs a,
                         }
                     }
                     ta = tb;
+                    tac = fmaxf(tb, tm_lo);
                     rowp += sM;
                 }
             }

@@ -226,14 +226,17 @@ k5_radix_pass(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__
 
 // ------------------------------------------------------------------ fused GD iteration
 
-constexpr int FW = kTileW + 4, FH = kTileH + 4;      // f region (2-pixel halo)
-constexpr int GW = kTileW + 2, GH = kTileH + 2;      // g region (1-pixel halo)
+constexpr int kGdThreads = 128;                     // threads per 32 x 8 tile
+constexpr int kGdTileH = kGdTileRows;                // tile rows of the GD kernel
+constexpr int FW = kTileW + 4, FH = kGdTileH + 4;    // f region (2-pixel halo)
+constexpr int GW = kTileW + 2, GH = kGdTileH + 2;    // g region (1-pixel halo)
 constexpr int QXW = kTileW + 3, QXH = GH;            // x-edges around the g region
-constexpr int QYW = GW, QYH = kTileH + 3;            // y-edges around the g region
+constexpr int QYW = GW, QYH = kGdTileH + 3;          // y-edges around the g region
 
 
 
-__global__ void __launch_bounds__(128)
+template <int KT>
+__global__ void __launch_bounds__(kGdThreads)
 k4_gd(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__restrict__ P, GdArgs ga,
       int iter, unsigned int *__restrict__ counters, double *__restrict__ partials)
 {
@@ -243,9 +246,9 @@ k4_gd(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__restrict
     __shared__ float G[GH][GW];
     __shared__ float QX[QXH][QXW], TXs[QXH][QXW], WX[QXH][QXW];
     __shared__ float QY[QYH][QYW], TYs[QYH][QYW], WY[QYH][QYW];
-    __shared__ float s_t[kMaxTrials];
-    __shared__ double s_td[kMaxTrials];
-    __shared__ double rsm[(kMaxTrials + 4) * 4];
+    __shared__ float s_t[KT];
+    __shared__ double s_td[KT];
+    __shared__ double rsm[(KT + 4) * (kGdThreads / 32)];
     __shared__ float s_tapply;
     __shared__ int last_flag;
 
@@ -255,7 +258,7 @@ k4_gd(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__restrict
     const int nx = S.nx, ny = S.ny;
     const int tiles_x = (nx + kTileW - 1) / kTileW;
     const int tyb = local / tiles_x, txb = local - tyb * tiles_x;
-    const int X0 = txb * kTileW, Y0 = tyb * kTileH;
+    const int X0 = txb * kTileW, Y0 = tyb * kGdTileH;
     const int tid = threadIdx.x;
     const int K = ga.n_trials;
     const float eps2 = (float)(P->eps * P->eps);
@@ -278,22 +281,25 @@ k4_gd(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__restrict
     const float inv_s2 = 1.0f / (sig * sig);
 
     if (tid == 0) s_tapply = ga.first ? 0.0f : (float)S.sc[SC_TSTEP];
-    if (tid < K) {
+    if (tid == 0 && K > 0) {
+        // trial steps t0, t0 s, t0 s^2, ... (repeated products: exact for s = 1/2)
         double t;
         if (P->step_rule == EPTV_STEP_FIXED) t = P->t_fixed;
         else {
             const double tmax = P->t_max > 0.0 ? P->t_max : 1.0 / P->lambda;
-            const double t0 = fmin(P->armijo_grow * S.sc[SC_TPREV], tmax);
-            t = t0 * pow(P->armijo_shrink, (double)tid);
+            t = fmin(P->armijo_grow * S.sc[SC_TPREV], tmax);
         }
-        s_t[tid] = (float)t;
-        s_td[tid] = (double)(float)t;
+        for (int m = 0; m < K; ++m) {
+            s_t[m] = (float)t;
+            s_td[m] = (double)(float)t;
+            t *= P->armijo_shrink;
+        }
     }
     __syncthreads();
     const float tap = s_tapply;
 
     // phase 1: f on the tile + 2 halo (previous step applied), v on tile + 1 halo
-    for (int idx = tid; idx < FH * FW; idx += 128) {
+    for (int idx = tid; idx < FH * FW; idx += kGdThreads) {
         const int yy = idx / FW, xx = idx - yy * FW;
         const int i = X0 - 2 + xx, j = Y0 - 2 + yy;
         float fv = 0.0f;
@@ -308,7 +314,7 @@ k4_gd(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__restrict
             W[yy][xx] = __ldg(S.wprior + (size_t)cj * nx + ci);
         }
     }
-    for (int idx = tid; idx < GH * GW; idx += 128) {
+    for (int idx = tid; idx < GH * GW; idx += kGdThreads) {
         const int yy = idx / GW, xx = idx - yy * GW;
         const int i = X0 - 1 + xx, j = Y0 - 1 + yy;
         V[yy][xx] = (i >= 0 && i < nx && j >= 0 && j < ny) ? __ldg(vv + (size_t)j * nx + i) : 0.0f;
@@ -316,7 +322,7 @@ k4_gd(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__restrict
     __syncthreads();
 
     // phase 2: half-edges around the g region
-    for (int idx = tid; idx < QXH * QXW; idx += 128) {
+    for (int idx = tid; idx < QXH * QXW; idx += kGdThreads) {
         const int yy = idx / QXW, ee = idx - yy * QXW;
         const int e = X0 - 1 + ee, j = Y0 - 1 + yy;     // between (e-1, j) and (e, j)
         float q = 0.f, T = 0.f, w = 0.f;
@@ -330,11 +336,11 @@ k4_gd(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__restrict
             if (mode == EPTV_WEIGHTS_EPTV) w = __expf(-T2 * inv_s2);
             else if (mode == EPTV_WEIGHTS_ONE) w = 1.0f;
             else w = 0.5f * (W[fy][fx] + W[fy][fx + 1]);
-            q = w * D / T;
+            q = __fdividef(w * D, T);
         }
         QX[yy][ee] = q; TXs[yy][ee] = T; WX[yy][ee] = w;
     }
-    for (int idx = tid; idx < QYH * QYW; idx += 128) {
+    for (int idx = tid; idx < QYH * QYW; idx += kGdThreads) {
         const int ee = idx / QYW, xx = idx - ee * QYW;
         const int e = Y0 - 1 + ee, i = X0 - 1 + xx;     // between (i, e-1) and (i, e)
         float q = 0.f, T = 0.f, w = 0.f;
@@ -348,7 +354,7 @@ k4_gd(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__restrict
             if (mode == EPTV_WEIGHTS_EPTV) w = __expf(-T2 * inv_s2);
             else if (mode == EPTV_WEIGHTS_ONE) w = 1.0f;
             else w = 0.5f * (W[fy][fx] + W[fy + 1][fx]);
-            q = w * D / T;
+            q = __fdividef(w * D, T);
         }
         QY[ee][xx] = q; TYs[ee][xx] = T; WY[ee][xx] = w;
     }
@@ -356,7 +362,7 @@ k4_gd(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__restrict
 
     // phase 3: g = lambda (f - v) + dJ/df on the g region (Eq. 9, A2)
     float sA = 0.f, sB = 0.f, sF = 0.f, sJ = 0.f;
-    for (int idx = tid; idx < GH * GW; idx += 128) {
+    for (int idx = tid; idx < GH * GW; idx += kGdThreads) {
         const int yy = idx / GW, xx = idx - yy * GW;
         const int i = X0 - 1 + xx, j = Y0 - 1 + yy;
         float g = 0.0f;
@@ -365,7 +371,7 @@ k4_gd(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__restrict
             const float d = f - V[yy][xx];
             const float div = (QX[yy][xx + 1] - QX[yy][xx]) + (QY[yy + 1][xx] - QY[yy][xx]);
             g = lam * d - div;
-            if (xx >= 1 && xx <= kTileW && yy >= 1 && yy <= kTileH) {
+            if (xx >= 1 && xx <= kTileW && yy >= 1 && yy <= kGdTileH) {
                 const size_t p = (size_t)j * nx + i;
                 gout[p] = g;
                 if (ga.write_f) fout[p] = f;
@@ -379,11 +385,11 @@ k4_gd(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__restrict
     __syncthreads();
 
     // phase 4: owned half-edges of the tile -- energy and trial energy changes
-    float dJ[kMaxTrials];
+    float dJ[KT];
 #pragma unroll
-    for (int m = 0; m < kMaxTrials; ++m) dJ[m] = 0.0f;
+    for (int m = 0; m < KT; ++m) dJ[m] = 0.0f;
     const bool want_w = ga.last && S.wout;
-    for (int idx = tid; idx < (kTileW + 1) * kTileH; idx += 128) {
+    for (int idx = tid; idx < (kTileW + 1) * kGdTileH; idx += kGdThreads) {
         const int yy = idx / (kTileW + 1), ee = idx - yy * (kTileW + 1);
         const int e = X0 + ee, j = Y0 + yy;
         if (j >= ny || e > nx || (ee == kTileW && e != nx)) continue;
@@ -407,7 +413,7 @@ k4_gd(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__restrict
             const float be = dD * dD + 0.5f * (dc1 * dc1 + dc2 * dc2);
             const float T2 = T * T;
 #pragma unroll
-            for (int m = 0; m < kMaxTrials; ++m) {
+            for (int m = 0; m < KT; ++m) {
                 if (m < K) {
                     const float t = s_t[m];
                     const float num = t * fmaf(t, be, -2.0f * ae);
@@ -417,10 +423,10 @@ k4_gd(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__restrict
             }
         }
     }
-    for (int idx = tid; idx < kTileW * (kTileH + 1); idx += 128) {
+    for (int idx = tid; idx < kTileW * (kGdTileH + 1); idx += kGdThreads) {
         const int ee = idx / kTileW, xx = idx - ee * kTileW;
         const int e = Y0 + ee, i = X0 + xx;
-        if (i >= nx || e > ny || (ee == kTileH && e != ny)) continue;
+        if (i >= nx || e > ny || (ee == kGdTileH && e != ny)) continue;
         const int qy = ee + 1, qx = xx + 1;             // QY indices
         const float T = TYs[qy][qx], w = WY[qy][qx];
         sJ = fmaf(w, T, sJ);
@@ -441,7 +447,7 @@ k4_gd(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__restrict
             const float be = dD * dD + 0.5f * (dc1 * dc1 + dc2 * dc2);
             const float T2 = T * T;
 #pragma unroll
-            for (int m = 0; m < kMaxTrials; ++m) {
+            for (int m = 0; m < KT; ++m) {
                 if (m < K) {
                     const float t = s_t[m];
                     const float num = t * fmaf(t, be, -2.0f * ae);
@@ -453,17 +459,17 @@ k4_gd(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__restrict
     }
 
     // phase 5: block sums -> partials; last block decides the step (FP64)
-    constexpr int NV = kMaxTrials + 4;
+    constexpr int NV = KT + 4;
     float vals[NV];
     vals[0] = sA; vals[1] = sB; vals[2] = sF; vals[3] = sJ;
 #pragma unroll
-    for (int m = 0; m < kMaxTrials; ++m) vals[4 + m] = dJ[m];
-    block_sum_to<NV, 128>(vals, partials + (size_t)blockIdx.x * kPartialStride, rsm);
+    for (int m = 0; m < KT; ++m) vals[4 + m] = dJ[m];
+    block_sum_to<NV, kGdThreads>(vals, partials + (size_t)blockIdx.x * kPartialStride, rsm);
     const int b0 = __ldg(map.start + si);
     const int nblk = __ldg(map.start + si + 1) - b0;
     if (!last_block_of_slice(counters + si, nblk, &last_flag)) return;
     __shared__ double tot[NV];
-    last_block_sum<NV, 128>(partials, kPartialStride, b0, nblk, rsm, tot);
+    last_block_sum<NV, kGdThreads>(partials, kPartialStride, b0, nblk, rsm, tot);
     {
         if (tid == 0) {
             double *sc = S.sc;
@@ -576,8 +582,16 @@ void launch_select_generic(const Batch &B, const TileMap &m, int nblk, const flo
 
 void launch_gd_iter(const Batch &B, const GdArgs &ga, int iter, cudaStream_t st) {
     ++g_launch_count;
-    k4_gd<<<B.blocks(FAM_K2), 128, 0, st>>>(B.d_sd, B.map(FAM_K2), B.d_params, ga, iter,
-                                            B.d_counters, B.d_partials);
+    const int nb = B.blocks(FAM_TV);
+    const TileMap m = B.map(FAM_TV);
+    if (ga.n_trials <= 1)
+        k4_gd<1><<<nb, kGdThreads, 0, st>>>(B.d_sd, m, B.d_params, ga, iter, B.d_counters, B.d_partials);
+    else if (ga.n_trials <= 4)
+        k4_gd<4><<<nb, kGdThreads, 0, st>>>(B.d_sd, m, B.d_params, ga, iter, B.d_counters, B.d_partials);
+    else if (ga.n_trials <= 8)
+        k4_gd<8><<<nb, kGdThreads, 0, st>>>(B.d_sd, m, B.d_params, ga, iter, B.d_counters, B.d_partials);
+    else
+        k4_gd<16><<<nb, kGdThreads, 0, st>>>(B.d_sd, m, B.d_params, ga, iter, B.d_counters, B.d_partials);
 }
 
 void launch_gd_finish(const Batch &B, int n_gd, const float *f0_override, float *out_override,

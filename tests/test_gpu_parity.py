@@ -345,7 +345,7 @@ def _oracle_energy_trajectory(op, c, p, n, sigma_ref):
     return np.array(energies), f
 
 
-@pytest.mark.parametrize("n_outer", [10, 50])
+@pytest.mark.parametrize("n_outer", [3, 10, 50])
 def test_reconstruct_armijo_matches_oracle(c1, n_outer):
     """Armijo steps.  The outer iteration amplifies FP32-level differences, and an
     Armijo trial can land within that noise of the acceptance threshold; after such a
@@ -353,7 +353,9 @@ def test_reconstruct_armijo_matches_oracle(c1, n_outer):
     reported energy swings by 5-10 % from one iteration to the next (also in the oracle).
     Checked: the GPU's step log equals the oracle's until the first differing decision,
     where the oracle's own decision must have been marginal (|rho - c| < 1e-2, rho =
-    achieved decrease / (t |g|^2)); without such a decision the image agrees within 1e-4;
+    achieved decrease / (t |g|^2)); the image agrees within max(1e-4, 3x the oracle's own
+    change under 1e-7 perturbations of P and P^T) -- that floor is 4e-6 at 3 iterations
+    but already 1.4e-4 at 5, where marginal decisions start to appear;
     the mean reported energy (Eq. 2) over the last 20 % of the iterations agrees within
     2 % (1e-7 perturbations of P and P^T move the oracle's own by <= 0.4 %); chaining
     one-iteration calls (previous step carried in t_init) reproduces the single call."""
@@ -376,7 +378,6 @@ def test_reconstruct_armijo_matches_oracle(c1, n_outer):
     if flip is None:
         assert np.allclose(sigmas, log.sigmas, rtol=2e-3)
         assert rep.n_fail == log.fails
-        assert rel(got, want) < 1e-4
     else:
         k, n = flip
         assert np.allclose(steps[:k], np.asarray(log.steps[:k]), rtol=1e-6)
@@ -400,6 +401,22 @@ def test_reconstruct_armijo_matches_oracle(c1, n_outer):
     assert torch.equal(fc, f)
     w = max(2, n_outer // 5)
     assert np.mean(e_gpu[-w:]) == pytest.approx(np.mean(e_orc[-w:]), rel=2e-2)
+    rng = np.random.Generator(np.random.PCG64(77))
+
+    class Perturbed:
+        def __init__(self):
+            self.g = g
+
+        def project(self, x):
+            yv = op.project(x)
+            return yv * (1 + 1e-7 * rng.standard_normal(yv.shape))
+
+        def backproject(self, yv):
+            x = op.backproject(yv)
+            return x * (1 + 1e-7 * rng.standard_normal(x.shape))
+
+    floor = rel(O.reconstruct(Perturbed(), c1.y, p), want)
+    assert rel(got, want) <= max(1e-4, 3 * floor)
 
 
 def test_reconstruct_deterministic_and_warm_start(c1):

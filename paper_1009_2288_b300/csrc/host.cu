@@ -426,7 +426,7 @@ void eptv_default_params(eptv_params *p) {
     p->armijo_c = 1e-4;
     p->armijo_shrink = 0.5;
     p->armijo_grow = 2.0;
-    p->max_trials = 8;
+    p->max_trials = 4;
     p->t_max = 0.0;
     p->t_init = 0.0;
     p->weights_mode = EPTV_WEIGHTS_EPTV;

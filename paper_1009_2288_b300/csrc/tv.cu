@@ -151,10 +151,17 @@ k5_sigma_edges(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *_
     const float *v = v_override ? v_override : S.u;
     const float eps2 = (float)(P->eps * P->eps);
     const int e0 = local * 2048;
+    float Tv[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {               // all stencil loads before any atomic
+        const int e = e0 + q * 256 + threadIdx.x;
+        Tv[q] = (e < S.n_edges) ? half_edge_T(v, S.nx, S.ny, eps2, e) : 0.0f;
+    }
+#pragma unroll
     for (int q = 0; q < 8; ++q) {
         const int e = e0 + q * 256 + threadIdx.x;
         if (e < S.n_edges) {
-            const float T = half_edge_T(v, S.nx, S.ny, eps2, e);
+            const float T = Tv[q];
             S.tv_scr[e] = T;
             if (!isfinite(T)) S.sc[SC_NONFINITE] = 1.0;
             sel_hist_add(sh, sel_key(T), 0, 0u);
@@ -193,9 +200,16 @@ k5_radix_pass(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__
     __syncthreads();
     const unsigned int prefix = (pass == 0) ? 0u : (unsigned int)S.sc[SC_SEL_PREFIX];
     const long long e0 = (long long)local * 2048;
+    float xv[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {               // issue the 8 loads before any atomic
+        const long long e = e0 + q * 256 + threadIdx.x;
+        xv[q] = (e < n) ? __ldg(vals + e) : 0.0f;
+    }
+#pragma unroll
     for (int q = 0; q < 8; ++q) {
         const long long e = e0 + q * 256 + threadIdx.x;
-        if (e < n) sel_hist_add(sh, sel_key(__ldg(vals + e)), pass, prefix);
+        if (e < n) sel_hist_add(sh, sel_key(xv[q]), pass, prefix);
     }
     __syncthreads();
     unsigned int *hist = hist_all + (size_t)si * kHistBins;
@@ -332,11 +346,12 @@ k4_gd(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__restrict
             float D;
             const float T2 = edge_T2(eps2, F[fy][fx], F[fy][fx + 1], F[fy + 1][fx], F[fy + 1][fx + 1],
                                      F[fy - 1][fx], F[fy - 1][fx + 1], &D);
-            T = sqrtf(T2);
+            const float rs = rsqrtf(T2);               // T2 >= eps^2 > 0
+            T = T2 * rs;
             if (mode == EPTV_WEIGHTS_EPTV) w = __expf(-T2 * inv_s2);
             else if (mode == EPTV_WEIGHTS_ONE) w = 1.0f;
             else w = 0.5f * (W[fy][fx] + W[fy][fx + 1]);
-            q = __fdividef(w * D, T);
+            q = w * D * rs;
         }
         QX[yy][ee] = q; TXs[yy][ee] = T; WX[yy][ee] = w;
     }
@@ -350,11 +365,12 @@ k4_gd(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__restrict
             float D;
             const float T2 = edge_T2(eps2, F[fy][fx], F[fy + 1][fx], F[fy][fx + 1], F[fy + 1][fx + 1],
                                      F[fy][fx - 1], F[fy + 1][fx - 1], &D);
-            T = sqrtf(T2);
+            const float rs = rsqrtf(T2);
+            T = T2 * rs;
             if (mode == EPTV_WEIGHTS_EPTV) w = __expf(-T2 * inv_s2);
             else if (mode == EPTV_WEIGHTS_ONE) w = 1.0f;
             else w = 0.5f * (W[fy][fx] + W[fy + 1][fx]);
-            q = __fdividef(w * D, T);
+            q = w * D * rs;
         }
         QY[ee][xx] = q; TYs[ee][xx] = T; WY[ee][xx] = w;
     }
@@ -417,7 +433,8 @@ k4_gd(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__restrict
                 if (m < K) {
                     const float t = s_t[m];
                     const float num = t * fmaf(t, be, -2.0f * ae);
-                    const float Tn = sqrtf(fmaxf(T2 + num, 0.0f));
+                    const float T2n = fmaxf(T2 + num, eps2);    // T'^2 >= eps^2
+                    const float Tn = T2n * rsqrtf(T2n);
                     dJ[m] = fmaf(w, __fdividef(num, Tn + T), dJ[m]);
                 }
             }
@@ -451,7 +468,8 @@ k4_gd(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__restrict
                 if (m < K) {
                     const float t = s_t[m];
                     const float num = t * fmaf(t, be, -2.0f * ae);
-                    const float Tn = sqrtf(fmaxf(T2 + num, 0.0f));
+                    const float T2n = fmaxf(T2 + num, eps2);    // T'^2 >= eps^2
+                    const float Tn = T2n * rsqrtf(T2n);
                     dJ[m] = fmaf(w, __fdividef(num, Tn + T), dJ[m]);
                 }
             }

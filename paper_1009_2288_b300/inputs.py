@@ -336,7 +336,7 @@ class EptvParams:
     armijo_c: float = 1e-4
     armijo_shrink: float = 0.5
     armijo_grow: float = 2.0
-    max_trials: int = 8
+    max_trials: int = 4
     t_max: float = 0.0           # <= 0: 1/lambda
     t_init: float = 0.0          # <= 0: 1/lambda
     weights_mode: int = 0        # 0 = EPTV (Eq. 5), 1 = plain TV (w = 1), 2 = learned prior

@@ -354,8 +354,9 @@ def test_reconstruct_armijo_matches_oracle(c1, n_outer):
     Checked: the GPU's step log equals the oracle's until the first differing decision,
     where the oracle's own decision must have been marginal (|rho - c| < 1e-2, rho =
     achieved decrease / (t |g|^2)); the image agrees within max(1e-4, 3x the oracle's own
-    change under 1e-7 perturbations of P and P^T) -- that floor is 4e-6 at 3 iterations
-    but already 1.4e-4 at 5, where marginal decisions start to appear;
+    change under 1e-6 perturbations of P and P^T, worst of two seeds) -- under 1e-7
+    perturbations that change is 4e-6 at 3 iterations but already 1.4e-4 at 5, where
+    marginal decisions start to appear;
     the mean reported energy (Eq. 2) over the last 20 % of the iterations agrees within
     2 % (1e-7 perturbations of P and P^T move the oracle's own by <= 0.4 %); chaining
     one-iteration calls (previous step carried in t_init) reproduces the single call."""
@@ -401,21 +402,23 @@ def test_reconstruct_armijo_matches_oracle(c1, n_outer):
     assert torch.equal(fc, f)
     w = max(2, n_outer // 5)
     assert np.mean(e_gpu[-w:]) == pytest.approx(np.mean(e_orc[-w:]), rel=2e-2)
-    rng = np.random.Generator(np.random.PCG64(77))
-
     class Perturbed:
-        def __init__(self):
+        # the FP64 operator with 1e-6 relative noise on its outputs: the size of the FP32
+        # summation differences of the GPU operator (it reproduces the GPU's CGLS
+        # residuals, see test_cgls_many_iterations_properties)
+        def __init__(self, seed):
             self.g = g
+            self.rng = np.random.Generator(np.random.PCG64(seed))
 
         def project(self, x):
             yv = op.project(x)
-            return yv * (1 + 1e-7 * rng.standard_normal(yv.shape))
+            return yv * (1 + 1e-6 * self.rng.standard_normal(yv.shape))
 
         def backproject(self, yv):
             x = op.backproject(yv)
-            return x * (1 + 1e-7 * rng.standard_normal(x.shape))
+            return x * (1 + 1e-6 * self.rng.standard_normal(x.shape))
 
-    floor = rel(O.reconstruct(Perturbed(), c1.y, p), want)
+    floor = max(rel(O.reconstruct(Perturbed(seed), c1.y, p), want) for seed in (77, 78))
     assert rel(got, want) <= max(1e-4, 3 * floor)
 
 

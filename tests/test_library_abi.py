@@ -29,7 +29,7 @@ def test_library_builds_and_exports_every_declared_symbol():
 def test_default_params_and_version_without_gpu():
     p = E.params()
     assert p.n_gd == 10 and p.cgls_iters == 3 and abs(p.lam - 2000.0) < 1e-12
-    assert p.max_trials == 8 and p.sigma_q == 0.9
+    assert p.max_trials == 4 and p.sigma_q == 0.9
     assert E.version().startswith("eptv-b300")
 
 

@@ -252,6 +252,69 @@ int eptv_autotune(eptv_geometry *g, int *k1_seg, int *k2_vg);
  * kept with that batch, cached in geoms[0]). */
 int eptv_autotune_batched(int n, eptv_geometry *const *geoms, int *k1_seg, int *k2_vg);
 
+/* ---------------------------------------------------------------------------------
+ * Layer kernels of the learned warm-start network (not in the paper: a small U-Net that
+ * predicts a warm-start image and a per-pixel edge-weight map from the back projection
+ * of the noisy sinogram; plain EPTV finishes the solve, see EPTV_WEIGHTS_PRIOR).
+ * Activations are BF16 (uint16 storage) in NHWC layout [n][h][w][stride]; a call reads
+ * or writes the channel slice [off, off + c) of such a tensor.  Master weights are FP32.
+ * All calls are asynchronous on `stream`, allocate nothing and return EPTV_ERR_ARG for
+ * bad shapes before queueing work.
+ * --------------------------------------------------------------------------------- */
+
+/* y[.., y_off + o] = act(b[o] + sum_{c, tap} wt[o][tap][c] x[pixel + tap][x_off + c]),
+ * 3x3, zero padding, act = ReLU if relu else identity.  BF16 tensor cores (mma.sync
+ * m16n8k16, FP32 accumulation).  (cin, cout) in {(16,16), (16,32), (32,32), (32,64),
+ * (64,64), (96,32), (48,16), (32,16), (64,32), (32,96), (16,48), (64,96)}; x_stride, x_off
+ * multiples of 8; x and wt 16-byte aligned; bias may be NULL.  wt: [cout][9][cin] BF16. */
+int eptv_unet_conv3x3(const void *d_x, int n, int h, int w, int cin, int x_stride, int x_off,
+                      const void *d_wt, const float *d_bias, int cout, void *d_y, int y_stride,
+                      int y_off, int relu, void *stream);
+
+/* Weight (and bias, if d_db) gradient of eptv_unet_conv3x3, accumulated into FP32 buffers:
+ * dw[o][tap][c] += sum_p dy[p][o] x[p + tap][c], db[o] += sum_p dy[p][o]. */
+int eptv_unet_conv3x3_wgrad(const void *d_x, int n, int h, int w, int cin, int x_stride, int x_off,
+                            const void *d_dy, int dy_stride, int dy_off, int cout, float *d_dw,
+                            float *d_db, void *stream);
+
+/* FP32 master weights [cout][9][cin] -> BF16 forward weights (d_wf, [cout][9][cin]) and the
+ * BF16 weights of the data gradient (d_wb, [cin][9][cout], taps mirrored), either may be
+ * NULL.  The data gradient of a conv is eptv_unet_conv3x3 with d_wb and cin/cout swapped. */
+int eptv_unet_weights_to_bf16(const float *d_w, int cout, int cin, void *d_wf, void *d_wb,
+                              void *stream);
+
+/* 2x2 max pooling (h, w even) and its gradient (to the first maximum of each window in
+ * row-major order; accumulate != 0 adds to d_dx instead of overwriting). */
+int eptv_unet_maxpool2(const void *d_x, int n, int h, int w, int x_stride, int x_off, int c,
+                       void *d_y, int y_stride, int y_off, void *stream);
+int eptv_unet_maxpool2_bwd(const void *d_x, int n, int h, int w, int x_stride, int x_off, int c,
+                           const void *d_dy, int dy_stride, int dy_off, void *d_dx, int dx_stride,
+                           int dx_off, int accumulate, void *stream);
+
+/* Nearest-neighbour 2x upsampling of an h x w input, and its gradient (h, w: the size of
+ * the upsampled gradient, even; each input pixel receives the sum of its 4 copies). */
+int eptv_unet_upsample2(const void *d_x, int n, int h, int w, int x_stride, int x_off, int c,
+                        void *d_y, int y_stride, int y_off, void *stream);
+int eptv_unet_upsample2_bwd(const void *d_dy, int n, int h, int w, int dy_stride, int dy_off, int c,
+                            void *d_dx, int dx_stride, int dx_off, void *stream);
+
+/* ReLU gradient: dz = dy where the ReLU output a > 0, else 0 (in place allowed). */
+int eptv_unet_relu_bwd(const void *d_a, int a_stride, int a_off, const void *d_dy, int dy_stride,
+                       int dy_off, void *d_dz, int dz_stride, int dz_off, long long npix, int c,
+                       void *stream);
+
+/* 1x1 head (16 -> 2 channels): f0 = o0, w = sigmoid(o1) (FP32 [npix], either may be NULL).
+ * With targets d_ft, d_wt: *d_loss += mean((f0-ft)^2) + mean((w-wt)^2) over the npix pixels,
+ * d_dx (BF16, 16 channels) = dL/dx, d_dhw [2][16], d_dhb [2] += parameter gradients. */
+int eptv_unet_head(const void *d_x, int x_stride, int x_off, long long npix, const float *d_hw,
+                   const float *d_hb, float *d_f0, float *d_w, const float *d_ft, const float *d_wt,
+                   void *d_dx, int dx_stride, int dx_off, float *d_dhw, float *d_dhb, double *d_loss,
+                   void *stream);
+
+/* Adam step (bias-corrected with step >= 1) on n FP32 parameters. */
+int eptv_unet_adam(float *d_p, const float *d_g, float *d_m, float *d_v, long long n, float lr,
+                   float beta1, float beta2, float eps, int step, void *stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char *eptv_last_error(void);
 

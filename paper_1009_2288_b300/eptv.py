@@ -24,7 +24,10 @@ EXPORTED = [
     "eptv_tv_gradient", "eptv_tv_step", "eptv_reconstruct", "eptv_report_energy",
     "eptv_select_kth", "eptv_reconstruct_batched", "eptv_last_error", "eptv_version",
     "eptv_get_log", "eptv_select_kth_noalloc", "eptv_set_tuning", "eptv_autotune",
-    "eptv_autotune_batched",
+    "eptv_autotune_batched", "eptv_unet_conv3x3", "eptv_unet_conv3x3_wgrad",
+    "eptv_unet_weights_to_bf16", "eptv_unet_maxpool2", "eptv_unet_maxpool2_bwd",
+    "eptv_unet_upsample2", "eptv_unet_upsample2_bwd", "eptv_unet_relu_bwd", "eptv_unet_head",
+    "eptv_unet_adam",
 ]
 
 
@@ -111,6 +114,23 @@ def load():
         "eptv_autotune": (c_int, [vp, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
         "eptv_autotune_batched": (c_int, [c_int, ctypes.POINTER(vp), ctypes.POINTER(c_int),
                                           ctypes.POINTER(c_int)]),
+        "eptv_unet_conv3x3": (c_int, [vp, c_int, c_int, c_int, c_int, c_int, c_int, vp, vp, c_int,
+                                      vp, c_int, c_int, c_int, vp]),
+        "eptv_unet_conv3x3_wgrad": (c_int, [vp, c_int, c_int, c_int, c_int, c_int, c_int, vp, c_int,
+                                            c_int, c_int, vp, vp, vp]),
+        "eptv_unet_weights_to_bf16": (c_int, [vp, c_int, c_int, vp, vp, vp]),
+        "eptv_unet_maxpool2": (c_int, [vp, c_int, c_int, c_int, c_int, c_int, c_int, vp, c_int, c_int, vp]),
+        "eptv_unet_maxpool2_bwd": (c_int, [vp, c_int, c_int, c_int, c_int, c_int, c_int, vp, c_int,
+                                           c_int, vp, c_int, c_int, c_int, vp]),
+        "eptv_unet_upsample2": (c_int, [vp, c_int, c_int, c_int, c_int, c_int, c_int, vp, c_int, c_int, vp]),
+        "eptv_unet_upsample2_bwd": (c_int, [vp, c_int, c_int, c_int, c_int, c_int, c_int, vp, c_int,
+                                            c_int, vp]),
+        "eptv_unet_relu_bwd": (c_int, [vp, c_int, c_int, vp, c_int, c_int, vp, c_int, c_int,
+                                       ctypes.c_longlong, c_int, vp]),
+        "eptv_unet_head": (c_int, [vp, c_int, c_int, ctypes.c_longlong, vp, vp, vp, vp, vp, vp, vp,
+                                   c_int, c_int, vp, vp, vp, vp]),
+        "eptv_unet_adam": (c_int, [vp, vp, vp, vp, ctypes.c_longlong, ctypes.c_float, ctypes.c_float,
+                                   ctypes.c_float, ctypes.c_float, c_int, vp]),
         "eptv_last_error": (ctypes.c_char_p, []),
         "eptv_version": (ctypes.c_char_p, []),
     }
@@ -332,6 +352,71 @@ def eptv_autotune_batched(geoms: Sequence[Geometry]):
     a, b = ctypes.c_int(), ctypes.c_int()
     _check(load().eptv_autotune_batched(n, H, ctypes.byref(a), ctypes.byref(b)))
     return a.value, b.value
+
+
+# ------------------------------------------------------------------ U-Net layer kernels
+# Activations are torch bfloat16 tensors [n, H, W, C] (C = channel stride); a call reads or
+# writes channels [off, off + c) of such a tensor.
+
+def _p(t):
+    return None if t is None else t.data_ptr()
+
+
+def eptv_unet_conv3x3(x, x_off, cin, wt, bias, cout, y, y_off, relu, stream=None):
+    n, h, w, xs = x.shape
+    _check(load().eptv_unet_conv3x3(_p(x), n, h, w, cin, xs, x_off, _p(wt), _p(bias), cout, _p(y),
+                                    y.shape[3], y_off, int(relu), _stream(stream)))
+
+
+def eptv_unet_conv3x3_wgrad(x, x_off, cin, dy, dy_off, cout, dw, db, stream=None):
+    n, h, w, xs = x.shape
+    _check(load().eptv_unet_conv3x3_wgrad(_p(x), n, h, w, cin, xs, x_off, _p(dy), dy.shape[3], dy_off,
+                                          cout, _p(dw), _p(db), _stream(stream)))
+
+
+def eptv_unet_weights_to_bf16(w, cout, cin, wf, wb, stream=None):
+    _check(load().eptv_unet_weights_to_bf16(_p(w), cout, cin, _p(wf), _p(wb), _stream(stream)))
+
+
+def eptv_unet_maxpool2(x, x_off, c, y, y_off, stream=None):
+    n, h, w, xs = x.shape
+    _check(load().eptv_unet_maxpool2(_p(x), n, h, w, xs, x_off, c, _p(y), y.shape[3], y_off, _stream(stream)))
+
+
+def eptv_unet_maxpool2_bwd(x, x_off, c, dy, dy_off, dx, dx_off, accumulate, stream=None):
+    n, h, w, xs = x.shape
+    _check(load().eptv_unet_maxpool2_bwd(_p(x), n, h, w, xs, x_off, c, _p(dy), dy.shape[3], dy_off,
+                                         _p(dx), dx.shape[3], dx_off, int(accumulate), _stream(stream)))
+
+
+def eptv_unet_upsample2(x, x_off, c, y, y_off, stream=None):
+    n, h, w, xs = x.shape
+    _check(load().eptv_unet_upsample2(_p(x), n, h, w, xs, x_off, c, _p(y), y.shape[3], y_off, _stream(stream)))
+
+
+def eptv_unet_upsample2_bwd(dy, dy_off, c, dx, dx_off, stream=None):
+    n, h, w, dys = dy.shape
+    _check(load().eptv_unet_upsample2_bwd(_p(dy), n, h, w, dys, dy_off, c, _p(dx), dx.shape[3], dx_off,
+                                          _stream(stream)))
+
+
+def eptv_unet_relu_bwd(a, a_off, dy, dy_off, dz, dz_off, c, stream=None):
+    n, h, w, as_ = a.shape
+    _check(load().eptv_unet_relu_bwd(_p(a), as_, a_off, _p(dy), dy.shape[3], dy_off, _p(dz), dz.shape[3],
+                                     dz_off, n * h * w, c, _stream(stream)))
+
+
+def eptv_unet_head(x, hw, hb, f0=None, w=None, ft=None, wt=None, dx=None, dhw=None, dhb=None,
+                   loss=None, stream=None):
+    n, h, ww, xs = x.shape
+    _check(load().eptv_unet_head(_p(x), xs, 0, n * h * ww, _p(hw), _p(hb), _p(f0), _p(w), _p(ft), _p(wt),
+                                 _p(dx), dx.shape[3] if dx is not None else 0, 0, _p(dhw), _p(dhb),
+                                 _p(loss), _stream(stream)))
+
+
+def eptv_unet_adam(p, g, m, v, lr, beta1, beta2, eps, step, stream=None):
+    _check(load().eptv_unet_adam(_p(p), _p(g), _p(m), _p(v), p.numel(), lr, beta1, beta2, eps, int(step),
+                                 _stream(stream)))
 
 
 def version() -> str:

@@ -13,6 +13,7 @@ Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank reconstructs it
 slice (replicas, no collective on the data path) and `value` is the whole-job rate.
 """
 import argparse
+import dataclasses
 import hashlib
 import json
 import math
@@ -40,6 +41,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tte", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     return ap.parse_args()
 
@@ -280,6 +282,90 @@ def run_batched(dev, stream, n_slices=64, n_outer=50, steps=3):
             "tuning": {"k1_seg": tuning[0], "k2_vg": tuning[1]}}
 
 
+def run_learned(dev, stream, n_pairs=2000, epochs=40, eval_seeds=(1, 2, 3, 4), k_ws=(0, 2)):
+    """Learned warm start on the 256^2 (1.6 mm), 30 views x 888 bins, I0 = 5e4 workload.
+    Trains the U-Net on n_pairs pairs that the plain method generates (50 iterations each,
+    all on the GPU), then, on held-out phantoms, runs plain EPTV from f = 0 and from the
+    learned warm start until the 5-iteration mean of E_report (Eq. 2, sigma_ref = the
+    oracle's last sigma) is within 1e-3 of the FP64 oracle's final (last-5 mean) energy
+    (tests/golden/c4_seed*_oracle_energy.json).  Reports the iterations each needs and the
+    wall time (CUDA events) of each path doing exactly that many iterations, the learned
+    one including its warm start (P^T y, CGLS_10(0), the network)."""
+    import numpy as np
+    import torch
+    from paper_1009_2288_b300 import eptv as E
+    from paper_1009_2288_b300 import inputs as I
+    from paper_1009_2288_b300 import learned as L
+    p = I.EptvParams(n_outer=50)
+    t0 = time.time()
+    pairs = L.make_pairs(list(range(10000, 10000 + n_pairs)), p, device=dev)
+    torch.cuda.synchronize()
+    t_pairs = time.time() - t0
+    net = L.UNet(seed=0, device=dev)
+    t0 = time.time()
+    losses = L.train(net, pairs, epochs=epochs)
+    torch.cuda.synchronize()
+    t_train = time.time() - t0
+    n_steps = len(losses)
+    del pairs
+    g = I.ge_geometry(256, 1.6, 30)
+    geo = E.Geometry(g)
+    E.eptv_autotune(geo)
+    warm = L.WarmStart(net, geo)
+    f = torch.zeros(g.n_pix, device=dev)
+    w = torch.empty(g.n_pix, device=dev)
+
+    def timed(fn, reps=5):
+        ts = []
+        for _ in range(reps):
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record(stream)
+            fn()
+            e.record(stream)
+            e.synchronize()
+            ts.append(s.elapsed_time(e))
+        return min(ts)
+
+    per = []
+    for seed in eval_seeds:
+        gold = json.load(open(os.path.join(ROOT, "tests", "golden", f"c4_seed{seed}_oracle_energy.json")))
+        target = sum(gold["e_report_per_iteration"][-5:]) / 5.0
+        sig = gold["sigma_ref"]
+        y = torch.from_numpy(I.make_c4(seed, with_truth=False).y.astype(np.float32).reshape(-1)).to(dev)
+        f.zero_()
+        k_plain, _ = L.iterations_to_energy(geo, p, y, f, target, sig, 100)
+        row = {"seed": seed, "target": target, "oracle_iterations": L.first_reach(gold["e_report_per_iteration"], target),
+               "plain_iterations": k_plain}
+        if k_plain is not None:
+            row["plain_ms"] = timed(lambda: (f.zero_(), E.eptv_reconstruct(geo, dataclasses.replace(p, n_outer=k_plain),
+                                                                           y, f, report=False)))
+        for k_w in k_ws:
+            warm(y, f, w)
+            k_l, _ = L.iterations_to_energy(geo, p, y, f, target, sig, 100, wprior=w, k_w=k_w)
+            row[f"learned_kw{k_w}_iterations"] = k_l
+            if k_l is not None:
+                row[f"learned_kw{k_w}_ms"] = timed(
+                    lambda: L.solve_learned(warm, dataclasses.replace(p, n_outer=k_l), y, f, w, k_w))
+        row["warm_start_ms"] = timed(lambda: warm(y, f, w))
+        per.append(row)
+
+    def mean_of(key):
+        vals = [r[key] for r in per if r.get(key) is not None]
+        return sum(vals) / len(vals) if len(vals) == len(per) else None
+    out = {"workload": "learned_256x256_30v_888b", "criterion": "5-iteration mean of E_report within 1e-3 "
+           "of the FP64 oracle's last-5 mean (sigma_ref = oracle's last sigma)",
+           "training": {"pairs": n_pairs, "pair_iterations": p.n_outer, "epochs": epochs, "batch": 16,
+                        "steps": n_steps, "pairs_s": t_pairs, "train_s": t_train,
+                        "ms_per_step": t_train * 1e3 / max(n_steps, 1),
+                        "loss_first": losses[0], "loss_last": losses[-1]},
+           "eval_seeds": list(eval_seeds), "per_seed": per,
+           "plain_iterations": mean_of("plain_iterations"), "plain_ms": mean_of("plain_ms")}
+    for k_w in k_ws:
+        out[f"learned_kw{k_w}_iterations"] = mean_of(f"learned_kw{k_w}_iterations")
+        out[f"learned_kw{k_w}_ms"] = mean_of(f"learned_kw{k_w}_ms")
+    return out
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -427,6 +513,10 @@ def run_ours(args, world, rank, local):
     if not args.no_batched and rank == 0:
         batched = run_batched(dev, stream)
 
+    learned = None
+    if not args.no_learned and rank == 0:
+        learned = run_learned(dev, stream)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(case)
@@ -448,6 +538,7 @@ def run_ours(args, world, rank, local):
         "cpu_baseline": cpu,
         "time_to_oracle_energy": tte,
         "batched": batched,
+        "learned": learned,
         "clocks": clk,
         "paper_context": {"workload": "NCAT 512^2, 40 views, 50 iterations (Table 2)",
                           "iterations_per_s": 50 / 5.5, "hardware": "Tesla C1060"},

@@ -272,7 +272,9 @@ int eptv_unet_conv3x3(const void *d_x, int n, int h, int w, int cin, int x_strid
                       int y_off, int relu, void *stream);
 
 /* Weight (and bias, if d_db) gradient of eptv_unet_conv3x3, accumulated into FP32 buffers:
- * dw[o][tap][c] += sum_p dy[p][o] x[p + tap][c], db[o] += sum_p dy[p][o]. */
+ * dw[o][tap][c] += sum_p dy[p][o] x[p + tap][c], db[o] += sum_p dy[p][o].  Same channel
+ * pairs as eptv_unet_conv3x3; strides and offsets of x and dy multiples of 8 channels,
+ * d_x and d_dy 16-byte aligned.  Sums are FP32 and their order is not fixed (atomic adds). */
 int eptv_unet_conv3x3_wgrad(const void *d_x, int n, int h, int w, int cin, int x_stride, int x_off,
                             const void *d_dy, int dy_stride, int dy_off, int cout, float *d_dw,
                             float *d_db, void *stream);
@@ -303,13 +305,21 @@ int eptv_unet_relu_bwd(const void *d_a, int a_stride, int a_off, const void *d_d
                        int dy_off, void *d_dz, int dz_stride, int dz_off, long long npix, int c,
                        void *stream);
 
-/* 1x1 head (16 -> 2 channels): f0 = o0, w = sigmoid(o1) (FP32 [npix], either may be NULL).
- * With targets d_ft, d_wt: *d_loss += mean((f0-ft)^2) + mean((w-wt)^2) over the npix pixels,
- * d_dx (BF16, 16 channels) = dL/dx, d_dhw [2][16], d_dhb [2] += parameter gradients. */
+/* 1x1 head (16 -> 2 channels): o = hb + hw x; w = sigmoid(o1); f0 = o0, or, with d_base,
+ * f0 = max(base + f_scale o0, 0) (a warm-start image composed on a base image).  Outputs are
+ * FP32 [npix]; d_f0, d_w may be NULL.  x: BF16, channels [x_off, x_off + 16) of rows of
+ * x_stride channels.  Training mode (d_ft != NULL, f0 = o0 in network units):
+ * *d_loss += mean((o0-ft)^2) + mean((w-wt)^2) over the npix pixels, d_dx (BF16, 16 channels
+ * at dx_off) = dL/dx, d_dhw [2][16], d_dhb [2] += parameter gradients. */
 int eptv_unet_head(const void *d_x, int x_stride, int x_off, long long npix, const float *d_hw,
-                   const float *d_hb, float *d_f0, float *d_w, const float *d_ft, const float *d_wt,
-                   void *d_dx, int dx_stride, int dx_off, float *d_dhw, float *d_dhb, double *d_loss,
-                   void *stream);
+                   const float *d_hb, float *d_f0, float *d_w, const float *d_base, float f_scale,
+                   const float *d_ft, const float *d_wt, void *d_dx, int dx_stride, int dx_off,
+                   float *d_dhw, float *d_dhb, double *d_loss, void *stream);
+
+/* Network input rows: x[p][0] = a[p] scale_a, x[p][1] = b[p] scale_b (0 if d_b is NULL),
+ * x[p][2..15] = 0, rounded to BF16; d_x: BF16 [npix][16], 16-byte aligned. */
+int eptv_unet_pack_input(const float *d_a, float scale_a, const float *d_b, float scale_b,
+                         long long npix, void *d_x, void *stream);
 
 /* Adam step (bias-corrected with step >= 1) on n FP32 parameters. */
 int eptv_unet_adam(float *d_p, const float *d_g, float *d_m, float *d_v, long long n, float lr,

@@ -3,8 +3,8 @@
 TEST INFRASTRUCTURE ONLY: the test suite imports it to check the CUDA layer kernels and
 the full network's forward pass and gradients.  The paper has no learned component; the
 network is the one the warm-start workload specifies: a 3-level U-Net with 16/32/64
-channels, input = the back projection of a noisy sinogram, outputs = a warm-start image
-and a per-pixel edge-weight map.
+channels; input = 2 channels (the back projection of a noisy sinogram and a CGLS image of
+it), outputs = a warm-start image channel and a per-pixel edge-weight map.
 
 Layout here is channels-first ([C][H][W]) float64, written for reading against the
 definitions:
@@ -20,7 +20,7 @@ from __future__ import annotations
 import numpy as np
 
 # (in, out) channels of the 3x3 convolutions, in order; every one is followed by ReLU
-CONVS = [(1, 16), (16, 16),          # encoder level 1 (full resolution) -> skip 1
+CONVS = [(2, 16), (16, 16),          # encoder level 1 (full resolution) -> skip 1
          (16, 32), (32, 32),         # encoder level 2 (1/2)            -> skip 2
          (32, 64), (64, 64),         # bottleneck (1/4)
          (96, 32), (32, 32),         # decoder level 2: [upsampled 64, skip 32]
@@ -102,7 +102,7 @@ def init_params(seed: int):
 
 
 def forward(params, x):
-    """x: [1][H][W] -> (f0 [H][W], w [H][W], cache)."""
+    """x: [2][H][W] -> (f0 [H][W], w [H][W], cache)."""
     cache = {"acts": []}
     h = x
     acts = []

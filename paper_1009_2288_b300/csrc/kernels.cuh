@@ -138,8 +138,11 @@ cudaError_t unet_upsample2_bwd(const void *dy, int n, int H, int W, int dys, int
 cudaError_t unet_relu_bwd(const void *a, int as, int ao, const void *dy, int dys, int dyo, void *dz,
                           int dzs, int dzo, long long npix, int C, cudaStream_t st);
 cudaError_t unet_head(const void *x, int xs, int xo, long long npix, const float *hw, const float *hb,
-                      float *f0, float *w, const float *ft, const float *wt, void *dx, int dxs, int dxo,
-                      float *dhw, float *dhb, double *loss, cudaStream_t st);
+                      float *f0, float *w, const float *base, float f_scale, const float *ft,
+                      const float *wt, void *dx, int dxs, int dxo, float *dhw, float *dhb, double *loss,
+                      cudaStream_t st);
+cudaError_t unet_pack_input(const float *a, float sa, const float *b, float sb, long long npix, void *x,
+                            cudaStream_t st);
 cudaError_t unet_adam(float *p, const float *g, float *m, float *v, long long n, float lr, float b1,
                       float b2, float eps, int step, cudaStream_t st);
 

@@ -9,8 +9,9 @@
 //     rows of 16 pixels (M = 16 per mma) for all output channels (N = COUT), K = 9 taps x
 //     CIN.  Padded shared strides make every fragment load bank-conflict free.
 //     Fused bias + ReLU + BF16 store into a channel slice of the output.
-//   conv3x3 weight gradient: FP32 on CUDA cores (K = pixels is long and N, M are small),
-//     per-block partial sums over a pixel range, one atomic add per weight per block.
+//   conv3x3 weight gradient: implicit GEMM on the tensor cores as well (M = output
+//     channels, N = input channels, K = pixels), one warp per tap, register accumulators
+//     over a block's pixel tiles, one FP32 atomic add per weight per block.
 //   pooling / upsampling / ReLU backward / 1x1 head + loss / Adam: elementwise kernels.
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -144,59 +145,141 @@ k_conv3x3_mma(const bf16 *__restrict__ x, int nimg, int H, int W, int xs, int xo
     }
 }
 
+__device__ __forceinline__ void ldsm_x4_trans(uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3,
+                                              const bf16 *p) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(a));
+}
+
+template <int CIN, int COUT>
+constexpr int wgrad_smem_bytes() {
+    return (kCvHP * kCvWP * (CIN + 8) + kCvTH * kCvTW * (COUT + 8)) * 2;
+}
+
 // dW[co][tap][ci] += sum_p dy[p][co] x[p + off(tap)][ci], db[co] += sum_p dy[p][co].
-// Block = (16 output channels) x (16 input channels) x one tap, over a range of pixels.
-__global__ void __launch_bounds__(256)
-k_conv3x3_wgrad(const bf16 *__restrict__ x, int nimg, int H, int W, int xs, int xo, int cin,
-                const bf16 *__restrict__ dy, int dys, int dyo, int cout,
-                float *__restrict__ dw, float *__restrict__ db, int pix_per_block)
+// Implicit GEMM on the tensor cores: M = output channels, N = input channels, K = pixels.
+// The block walks 8 x 16 pixel tiles (stride gridDim.x); per tile the 10 x 18 input halo
+// and the 8 x 16 output-gradient tile are staged in shared memory in their NHWC layout, and
+// ldmatrix.trans turns 8-pixel x 8-channel blocks into the K-major fragments of the mma.
+// Warp w owns tap w (9 warps): per tile row (K = 16 pixels) it multiplies the dy fragment
+// of every 16-channel group by the halo row shifted by that tap.  Warp 4 (the centre tap)
+// also multiplies dy by a ones fragment for the bias gradient.  FP32 accumulators stay in
+// registers over all of the block's tiles and are added to dW once per block.  A block
+// covers MG of the COUT / 16 output-channel groups (blockIdx.y picks which), so that a warp
+// holds at most 64 accumulators.
+template <int CIN, int COUT>
+__host__ __device__ constexpr int wgrad_mgroups() {
+    int mg = COUT / 16;
+    while (mg > 1 && (mg * (CIN / 8) > 16 || (COUT / 16) % mg)) --mg;
+    return mg;
+}
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(288, 1)
+k_conv3x3_wgrad_mma(const bf16 *__restrict__ x, int nimg, int H, int W, int xs, int xo,
+                    const bf16 *__restrict__ dy, int dys, int dyo,
+                    float *__restrict__ dw, float *__restrict__ db)
 {
-    __shared__ float sdy[64][17];
-    __shared__ float sx[64][17];
-    const int cib = cin / 16;
-    const int cb = blockIdx.x % cib;
-    const int ob = (blockIdx.x / cib) % (cout / 16);
-    const int tap = blockIdx.x / (cib * (cout / 16));
-    const int ky = tap / 3 - 1, kx = tap % 3 - 1;
-    const int tid = threadIdx.x, a = tid >> 4, b = tid & 15;
-    const long long total = (long long)nimg * H * W;
-    const long long p_begin = (long long)blockIdx.y * pix_per_block;
-    const long long p_end = min(total, p_begin + pix_per_block);
-    float acc = 0.0f, accb = 0.0f;
-    const bool do_bias = (db != nullptr) && tap == 4 && cb == 0 && b == 0;
-    for (long long p0 = p_begin; p0 < p_end; p0 += 64) {
-        // stage 64 pixels: 4 channels per thread
-        {
-            const int pl = tid >> 2, c4 = (tid & 3) * 4;
-            const long long p = p0 + pl;
-            float vdy[4] = {0.f, 0.f, 0.f, 0.f}, vx[4] = {0.f, 0.f, 0.f, 0.f};
-            if (p < p_end) {
-                const int n = (int)(p / ((long long)H * W));
-                const int rr = (int)(p - (long long)n * H * W);
-                const int r = rr / W, c = rr - (rr / W) * W;
-                const bf16 *dp = dy + (size_t)p * dys + dyo + ob * 16 + c4;
+    constexpr int XS = CIN + 8, DS = COUT + 8;
+    constexpr int MT = wgrad_mgroups<CIN, COUT>(), NT = CIN / 8;
+    const int m0 = blockIdx.y * MT;                          // first 16-channel group
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    bf16 *sx = reinterpret_cast<bf16 *>(smem_raw);          // [10 * 18][XS]
+    bf16 *sd = sx + kCvHP * kCvWP * XS;                      // [8 * 16][DS]
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
+    const int tap = warp, ky = tap / 3, kx = tap - 3 * (tap / 3);
+    const bool bias_warp = (db != nullptr) && tap == 4;
+
+    float acc[MT][NT][4];
+    float accb[MT][4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) vdy[q] = __bfloat162float(dp[q]);
-                const int sr = r + ky, sc = c + kx;
-                if (sr >= 0 && sr < H && sc >= 0 && sc < W) {
-                    const bf16 *xp = x + ((size_t)(n * H + sr) * W + sc) * xs + xo + cb * 16 + c4;
+    for (int mt = 0; mt < MT; ++mt) {
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) vx[q] = __bfloat162float(xp[q]);
+        for (int q = 0; q < 4; ++q) accb[mt][q] = 0.0f;
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[mt][nt][q] = 0.0f;
+    }
+    // per-lane ldmatrix row offsets: matrix q = lane / 8, row r = lane % 8
+    const int q = lane >> 3, r = lane & 7;
+    const int a_pix = r + (q >> 1) * 8, a_ch = (q & 1) * 8;   // dy: (pixel, channel) blocks
+    const int b_pix = r + (q & 1) * 8, b_ch = (q >> 1) * 8;   // x:  (pixel, channel) blocks
+    const uint32_t ones = 0x3F803F80u;                         // two BF16 1.0
+
+    const int tiles_x = (W + kCvTW - 1) / kCvTW, tiles_y = (H + kCvTH - 1) / kCvTH;
+    const int ntiles = nimg * tiles_x * tiles_y;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int n = tile / (tiles_x * tiles_y);
+        const int rem = tile - n * tiles_x * tiles_y;
+        const int r0 = (rem / tiles_x) * kCvTH, c0 = (rem % tiles_x) * kCvTW;
+        __syncthreads();                 // previous tile's fragment loads are done
+        constexpr int XV = CIN / 8;
+        for (int idx = tid; idx < kCvHP * kCvWP * XV; idx += 288) {
+            const int pp = idx / XV, v = idx - pp * XV;
+            const int ty = pp / kCvWP, tx = pp - ty * kCvWP;
+            const int gy = r0 - 1 + ty, gx = c0 - 1 + tx;
+            uint4 val = make_uint4(0u, 0u, 0u, 0u);
+            if (gy >= 0 && gy < H && gx >= 0 && gx < W)
+                val = __ldg(reinterpret_cast<const uint4 *>(x + ((size_t)(n * H + gy) * W + gx) * xs + xo + v * 8));
+            *reinterpret_cast<uint4 *>(sx + pp * XS + v * 8) = val;
+        }
+        constexpr int DV = COUT / 8;
+        for (int idx = tid; idx < kCvTH * kCvTW * DV; idx += 288) {
+            const int pp = idx / DV, v = idx - pp * DV;
+            const int ty = pp / kCvTW, tx = pp - ty * kCvTW;
+            const int gy = r0 + ty, gx = c0 + tx;
+            uint4 val = make_uint4(0u, 0u, 0u, 0u);
+            if (gy < H && gx < W)
+                val = __ldg(reinterpret_cast<const uint4 *>(dy + ((size_t)(n * H + gy) * W + gx) * dys + dyo + v * 8));
+            *reinterpret_cast<uint4 *>(sd + pp * DS + v * 8) = val;
+        }
+        __syncthreads();
+#pragma unroll 1
+        for (int row = 0; row < kCvTH; ++row) {
+            uint32_t a[MT][4];
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt)
+                ldsm_x4_trans(a[mt][0], a[mt][1], a[mt][2], a[mt][3],
+                              sd + (row * kCvTW + a_pix) * DS + (m0 + mt) * 16 + a_ch);
+            const bf16 *xrow = sx + ((row + ky) * kCvWP + kx + b_pix) * XS + b_ch;
+#pragma unroll
+            for (int np = 0; np < NT / 2; ++np) {
+                uint32_t b0, b1, b2, b3;
+                ldsm_x4_trans(b0, b1, b2, b3, xrow + np * 16);
+#pragma unroll
+                for (int mt = 0; mt < MT; ++mt) {
+                    mma_bf16_16816(acc[mt][2 * np], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b0, b1);
+                    mma_bf16_16816(acc[mt][2 * np + 1], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b2, b3);
                 }
             }
+            if (bias_warp) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) { sdy[pl][c4 + q] = vdy[q]; sx[pl][c4 + q] = vx[q]; }
+                for (int mt = 0; mt < MT; ++mt)
+                    mma_bf16_16816(accb[mt], a[mt][0], a[mt][1], a[mt][2], a[mt][3], ones, ones);
+            }
         }
-        __syncthreads();
-#pragma unroll 16
-        for (int k = 0; k < 64; ++k) {
-            acc = fmaf(sdy[k][a], sx[k][b], acc);
-            if (do_bias) accb += sdy[k][a];
-        }
-        __syncthreads();
     }
-    atomicAdd(dw + ((size_t)(ob * 16 + a) * 9 + tap) * cin + cb * 16 + b, acc);
-    if (do_bias) atomicAdd(db + ob * 16 + a, accb);
+    // D fragment: c0, c1 at (row g, columns 2t, 2t+1), c2, c3 at row g + 8
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt) {
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
+            const int ci = nt * 8 + 2 * t;
+            float *p0 = dw + ((size_t)((m0 + mt) * 16 + g) * 9 + tap) * CIN + ci;
+            float *p1 = dw + ((size_t)((m0 + mt) * 16 + g + 8) * 9 + tap) * CIN + ci;
+            atomicAdd(p0, acc[mt][nt][0]);
+            atomicAdd(p0 + 1, acc[mt][nt][1]);
+            atomicAdd(p1, acc[mt][nt][2]);
+            atomicAdd(p1 + 1, acc[mt][nt][3]);
+        }
+        if (bias_warp && t == 0) {
+            atomicAdd(db + (m0 + mt) * 16 + g, accb[mt][0]);
+            atomicAdd(db + (m0 + mt) * 16 + g + 8, accb[mt][2]);
+        }
+    }
 }
 
 // Master FP32 weights [cout][9][cin] -> BF16 forward layout and BF16 data-gradient layout
@@ -295,9 +378,25 @@ __global__ void k_relu_bwd(const bf16 *__restrict__ a, int as, int ao, const bf1
 // 1x1 head (16 -> 2): f0 = o0, w = sigmoid(o1).  With targets: loss += mean((f0-ft)^2 +
 // (w-wt)^2) terms, dx = hW^T do, dhW += do x^T, dhb += do (do = dL/do, L averaged over the
 // pixels of all images).
+// Network input: x[p][0] = a[p] sa, x[p][1] = b[p] sb (0 without b), channels 2..15 = 0,
+// BF16 rows of 16 channels (two 16-byte stores per pixel).
+__global__ void __launch_bounds__(256)
+k_pack_input(const float *__restrict__ a, float sa, const float *__restrict__ b, float sb,
+             long long npix, bf16 *__restrict__ x) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npix) return;
+    const __nv_bfloat162 v01 = __floats2bfloat162_rn(a[p] * sa, b ? b[p] * sb : 0.0f);
+    uint4 lo = make_uint4(0u, 0u, 0u, 0u);
+    lo.x = *reinterpret_cast<const uint32_t *>(&v01);
+    uint4 *dst = reinterpret_cast<uint4 *>(x + p * 16);
+    dst[0] = lo;
+    dst[1] = make_uint4(0u, 0u, 0u, 0u);
+}
+
 __global__ void __launch_bounds__(256)
 k_head(const bf16 *__restrict__ x, int xs, int xo, long long npix, const float *__restrict__ hw,
        const float *__restrict__ hb, float *__restrict__ f0, float *__restrict__ w,
+       const float *__restrict__ base, float f_scale,
        const float *__restrict__ ft, const float *__restrict__ wt, bf16 *__restrict__ dx, int dxs,
        int dxo, float *__restrict__ dhw, float *__restrict__ dhb, double *__restrict__ loss,
        float inv_n) {
@@ -318,7 +417,7 @@ k_head(const bf16 *__restrict__ x, int xs, int xo, long long npix, const float *
 #pragma unroll
         for (int c = 0; c < 16; ++c) { o0 = fmaf(s_hw[c], xv[c], o0); o1 = fmaf(s_hw[16 + c], xv[c], o1); }
         const float sg = 1.0f / (1.0f + __expf(-o1));
-        if (f0) f0[p] = o0;
+        if (f0) f0[p] = base ? fmaxf(fmaf(f_scale, o0, base[p]), 0.0f) : o0;
         if (w) w[p] = sg;
         if (ft) {
             const float e0 = o0 - ft[p], e1 = sg - wt[p];
@@ -406,21 +505,38 @@ bool unet_conv_supported(int cin, int cout) {
     return false;
 }
 
+template <int CIN, int COUT>
+static cudaError_t launch_wgrad_t(const bf16 *x, int n, int H, int W, int xs, int xo, const bf16 *dy,
+                                  int dys, int dyo, float *dw, float *db, cudaStream_t st) {
+    constexpr int smem = wgrad_smem_bytes<CIN, COUT>();
+    static bool attr_set = false;        // per process; same value on every device
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_conv3x3_wgrad_mma<CIN, COUT>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const int ntiles = n * ((W + kCvTW - 1) / kCvTW) * ((H + kCvTH - 1) / kCvTH);
+    // about two blocks per SM in all; each block adds its partial sums to dW once
+    constexpr int groups = (COUT / 16) / wgrad_mgroups<CIN, COUT>();
+    const dim3 grid(std::min(ntiles, std::max(1, 296 / groups)), groups);
+    ++g_launch_count;
+    k_conv3x3_wgrad_mma<CIN, COUT><<<grid, 288, smem, st>>>(x, n, H, W, xs, xo, dy, dys, dyo, dw, db);
+    return cudaGetLastError();
+}
+
 cudaError_t unet_conv3x3_wgrad(const void *x, int n, int H, int W, int cin, int xs, int xo,
                                const void *dy, int dys, int dyo, int cout, float *dw, float *db,
                                cudaStream_t st) {
-    const long long total = (long long)n * H * W;
-    const int base = (cout / 16) * (cin / 16) * 9;
-    // enough pixel ranges to fill the GPU about 4 times
-    long long ranges = std::max<long long>(1, (148LL * 8 * 4) / base);
-    long long ppb = (total + ranges - 1) / ranges;
-    ppb = ((ppb + 63) / 64) * 64;
-    ranges = (total + ppb - 1) / ppb;
-    dim3 grid(base, (unsigned)ranges);
-    ++g_launch_count;
-    k_conv3x3_wgrad<<<grid, 256, 0, st>>>(static_cast<const bf16 *>(x), n, H, W, xs, xo, cin,
-                                         static_cast<const bf16 *>(dy), dys, dyo, cout, dw, db, (int)ppb);
-    return cudaGetLastError();
+    const bf16 *X = static_cast<const bf16 *>(x);
+    const bf16 *D = static_cast<const bf16 *>(dy);
+#define WGRAD_CASE(CI, CO) \
+    if (cin == CI && cout == CO) return launch_wgrad_t<CI, CO>(X, n, H, W, xs, xo, D, dys, dyo, dw, db, st);
+    WGRAD_CASE(16, 16) WGRAD_CASE(16, 32) WGRAD_CASE(32, 32) WGRAD_CASE(32, 64) WGRAD_CASE(64, 64)
+    WGRAD_CASE(96, 32) WGRAD_CASE(48, 16) WGRAD_CASE(32, 16) WGRAD_CASE(64, 32) WGRAD_CASE(32, 96)
+    WGRAD_CASE(16, 48) WGRAD_CASE(64, 96)
+#undef WGRAD_CASE
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t unet_weights_to_bf16(const float *w, int cout, int cin, void *wf, void *wb, cudaStream_t st) {
@@ -476,12 +592,21 @@ cudaError_t unet_relu_bwd(const void *a, int as, int ao, const void *dy, int dys
 }
 
 cudaError_t unet_head(const void *x, int xs, int xo, long long npix, const float *hw, const float *hb,
-                      float *f0, float *w, const float *ft, const float *wt, void *dx, int dxs, int dxo,
-                      float *dhw, float *dhb, double *loss, cudaStream_t st) {
+                      float *f0, float *w, const float *base, float f_scale, const float *ft,
+                      const float *wt, void *dx, int dxs, int dxo, float *dhw, float *dhb, double *loss,
+                      cudaStream_t st) {
     ++g_launch_count;
-    k_head<<<nblk(npix), 256, 0, st>>>(static_cast<const bf16 *>(x), xs, xo, npix, hw, hb, f0, w, ft, wt,
+    k_head<<<nblk(npix), 256, 0, st>>>(static_cast<const bf16 *>(x), xs, xo, npix, hw, hb, f0, w, base,
+                                       f_scale, ft, wt,
                                        static_cast<bf16 *>(dx), dxs, dxo, dhw, dhb, loss,
                                        (float)(1.0 / (double)npix));
+    return cudaGetLastError();
+}
+
+cudaError_t unet_pack_input(const float *a, float sa, const float *b, float sb, long long npix, void *x,
+                            cudaStream_t st) {
+    ++g_launch_count;
+    k_pack_input<<<nblk(npix), 256, 0, st>>>(a, sa, b, sb, npix, static_cast<bf16 *>(x));
     return cudaGetLastError();
 }
 
@@ -529,10 +654,12 @@ int eptv_unet_conv3x3_wgrad(const void *d_x, int n, int h, int w, int cin, int x
                             const void *d_dy, int dy_stride, int dy_off, int cout, float *d_dw,
                             float *d_db, void *stream) {
     if (!d_x || !d_dy || !d_dw) return report_error(EPTV_ERR_ARG, "NULL argument");
-    if (n < 1 || h < 1 || w < 1 || cin % 16 || cout % 16 || cin < 16 || cout < 16)
-        return report_error(EPTV_ERR_ARG, "channels must be multiples of 16");
-    if (x_stride < x_off + cin || dy_stride < dy_off + cout || (dy_off % 4) || (x_off % 4))
-        return report_error(EPTV_ERR_ARG, "bad channel stride/offset");
+    if (n < 1 || h < 1 || w < 1) return report_error(EPTV_ERR_ARG, "bad tensor size");
+    if (!unet_conv_supported(cin, cout)) return report_error(EPTV_ERR_ARG, "unsupported channel pair");
+    if (x_stride < x_off + cin || dy_stride < dy_off + cout || (x_stride % 8) || (x_off % 8) ||
+        (dy_stride % 8) || (dy_off % 8))
+        return report_error(EPTV_ERR_ARG, "bad channel stride/offset (multiples of 8)");
+    if (!al16(d_x) || !al16(d_dy)) return report_error(EPTV_ERR_ARG, "x and dy must be 16-byte aligned");
     return unet_rc(unet_conv3x3_wgrad(d_x, n, h, w, cin, x_stride, x_off, d_dy, dy_stride, dy_off,
                                       cout, d_dw, d_db, (cudaStream_t)stream));
 }
@@ -578,14 +705,22 @@ int eptv_unet_relu_bwd(const void *d_a, int a_stride, int a_off, const void *d_d
 }
 
 int eptv_unet_head(const void *d_x, int x_stride, int x_off, long long npix, const float *d_hw,
-                   const float *d_hb, float *d_f0, float *d_w, const float *d_ft, const float *d_wt,
-                   void *d_dx, int dx_stride, int dx_off, float *d_dhw, float *d_dhb, double *d_loss,
-                   void *stream) {
+                   const float *d_hb, float *d_f0, float *d_w, const float *d_base, float f_scale,
+                   const float *d_ft, const float *d_wt, void *d_dx, int dx_stride, int dx_off,
+                   float *d_dhw, float *d_dhb, double *d_loss, void *stream) {
     if (!d_x || !d_hw || !d_hb || npix < 1) return report_error(EPTV_ERR_ARG, "bad arguments");
-    if (d_ft && (!d_wt || !d_dx || !d_dhw || !d_dhb || !d_loss))
+    if (x_stride < x_off + 16) return report_error(EPTV_ERR_ARG, "bad channel stride/offset");
+    if (d_ft && (!d_wt || !d_dx || !d_dhw || !d_dhb || !d_loss || dx_stride < dx_off + 16))
         return report_error(EPTV_ERR_ARG, "training mode needs targets and gradient buffers");
-    return unet_rc(unet_head(d_x, x_stride, x_off, npix, d_hw, d_hb, d_f0, d_w, d_ft, d_wt, d_dx,
-                             dx_stride, dx_off, d_dhw, d_dhb, d_loss, (cudaStream_t)stream));
+    return unet_rc(unet_head(d_x, x_stride, x_off, npix, d_hw, d_hb, d_f0, d_w, d_base, f_scale, d_ft,
+                             d_wt, d_dx, dx_stride, dx_off, d_dhw, d_dhb, d_loss, (cudaStream_t)stream));
+}
+
+int eptv_unet_pack_input(const float *d_a, float scale_a, const float *d_b, float scale_b,
+                         long long npix, void *d_x, void *stream) {
+    if (!d_a || !d_x || npix < 1) return report_error(EPTV_ERR_ARG, "bad arguments");
+    if (!al16(d_x)) return report_error(EPTV_ERR_ARG, "x must be 16-byte aligned");
+    return unet_rc(unet_pack_input(d_a, scale_a, d_b, scale_b, npix, d_x, (cudaStream_t)stream));
 }
 
 int eptv_unet_adam(float *d_p, const float *d_g, float *d_m, float *d_v, long long n, float lr,

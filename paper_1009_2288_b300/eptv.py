@@ -27,7 +27,7 @@ EXPORTED = [
     "eptv_autotune_batched", "eptv_unet_conv3x3", "eptv_unet_conv3x3_wgrad",
     "eptv_unet_weights_to_bf16", "eptv_unet_maxpool2", "eptv_unet_maxpool2_bwd",
     "eptv_unet_upsample2", "eptv_unet_upsample2_bwd", "eptv_unet_relu_bwd", "eptv_unet_head",
-    "eptv_unet_adam",
+    "eptv_unet_adam", "eptv_unet_pack_input",
 ]
 
 
@@ -127,8 +127,9 @@ def load():
                                             c_int, vp]),
         "eptv_unet_relu_bwd": (c_int, [vp, c_int, c_int, vp, c_int, c_int, vp, c_int, c_int,
                                        ctypes.c_longlong, c_int, vp]),
-        "eptv_unet_head": (c_int, [vp, c_int, c_int, ctypes.c_longlong, vp, vp, vp, vp, vp, vp, vp,
-                                   c_int, c_int, vp, vp, vp, vp]),
+        "eptv_unet_head": (c_int, [vp, c_int, c_int, ctypes.c_longlong, vp, vp, vp, vp, vp, ctypes.c_float,
+                                   vp, vp, vp, c_int, c_int, vp, vp, vp, vp]),
+        "eptv_unet_pack_input": (c_int, [vp, ctypes.c_float, vp, ctypes.c_float, ctypes.c_longlong, vp, vp]),
         "eptv_unet_adam": (c_int, [vp, vp, vp, vp, ctypes.c_longlong, ctypes.c_float, ctypes.c_float,
                                    ctypes.c_float, ctypes.c_float, c_int, vp]),
         "eptv_last_error": (ctypes.c_char_p, []),
@@ -406,12 +407,22 @@ def eptv_unet_relu_bwd(a, a_off, dy, dy_off, dz, dz_off, c, stream=None):
                                      dz_off, n * h * w, c, _stream(stream)))
 
 
-def eptv_unet_head(x, hw, hb, f0=None, w=None, ft=None, wt=None, dx=None, dhw=None, dhb=None,
-                   loss=None, stream=None):
+def eptv_unet_head(x, hw, hb, f0=None, w=None, base=None, f_scale=1.0, ft=None, wt=None, dx=None,
+                   dhw=None, dhb=None, loss=None, stream=None):
     n, h, ww, xs = x.shape
-    _check(load().eptv_unet_head(_p(x), xs, 0, n * h * ww, _p(hw), _p(hb), _p(f0), _p(w), _p(ft), _p(wt),
-                                 _p(dx), dx.shape[3] if dx is not None else 0, 0, _p(dhw), _p(dhb),
-                                 _p(loss), _stream(stream)))
+    _check(load().eptv_unet_head(_p(x), xs, 0, n * h * ww, _p(hw), _p(hb), _p(f0), _p(w), _p(base),
+                                 float(f_scale), _p(ft), _p(wt), _p(dx),
+                                 dx.shape[3] if dx is not None else 0, 0, _p(dhw), _p(dhb), _p(loss),
+                                 _stream(stream)))
+
+
+def eptv_unet_pack_input(a, scale_a, b, scale_b, x, stream=None):
+    """a, b: FP32 [npix] (b may be None); x: BF16 [..., 16] with npix rows."""
+    npix = a.numel()
+    if x.numel() != 16 * npix or (b is not None and b.numel() != npix):
+        raise ValueError("pack_input: size mismatch")
+    _check(load().eptv_unet_pack_input(_p(a), float(scale_a), _p(b), float(scale_b), npix, _p(x),
+                                       _stream(stream)))
 
 
 def eptv_unet_adam(p, g, m, v, lr, beta1, beta2, eps, step, stream=None):

@@ -6,6 +6,7 @@ with sigma_ref = the oracle's last sigma.
 
     python tests/golden/make_oracle_energy.py c2   # 512x512, 40 x 888, 100 iterations
     python tests/golden/make_oracle_energy.py c1   # 128x128, 30 x 256, 50 iterations
+    python tests/golden/make_oracle_energy.py c4 1 # 256x256, 30 x 888, 50 iterations, seed 1
 """
 import json
 import os
@@ -19,8 +20,12 @@ from oracle import eptv_oracle as O                     # noqa: E402
 from paper_1009_2288_b300 import inputs as I            # noqa: E402
 
 
-def main(which: str):
-    case = {"c1": I.make_c1, "c2": I.make_c2}[which](with_truth=True)
+def main(which: str, seed=None):
+    if which == "c4":
+        case = I.make_c4(int(seed), with_truth=True)
+        which = f"c4_seed{int(seed)}"
+    else:
+        case = {"c1": I.make_c1, "c2": I.make_c2}[which](with_truth=True)
     p = I.EptvParams(n_outer=case.n_outer)
     op = O.Operator(case.geom)
     log = O.ReconLog()
@@ -42,6 +47,7 @@ def main(which: str):
         energies.append(O.report_energy(op, fk, case.y, p, sigma_ref))
     out = {
         "workload": case.name,
+        "seed": case.seed,
         "n_outer": case.n_outer,
         "params": {k: getattr(p, k) for k in p.__dataclass_fields__},
         "sigma_ref": sigma_ref,
@@ -58,4 +64,4 @@ def main(which: str):
 
 
 if __name__ == "__main__":
-    main(sys.argv[1] if len(sys.argv) > 1 else "c2")
+    main(sys.argv[1] if len(sys.argv) > 1 else "c2", sys.argv[2] if len(sys.argv) > 2 else None)

@@ -141,11 +141,13 @@ def test_network_forward_and_gradients_match_oracle():
     params = [[bf(a) for a in l] for l in params]
     net = L.UNet(seed=0, device=DEV)
     net.set_from_oracle_layout(params)
+    net.bp_scale = 1.0
     rng = np.random.Generator(np.random.PCG64(12))
-    x = bf(rng.uniform(0, 2, (1, 32, 40)))
+    x = bf(rng.uniform(0, 2, (2, 32, 40)))
     ft = rng.uniform(0, 1, (32, 40))
     wt = rng.uniform(0, 1, (32, 40))
-    f0, w = net.forward(torch.tensor(x, dtype=torch.float32, device=DEV))
+    xt = torch.tensor(x, dtype=torch.float32, device=DEV)
+    f0, w = net.forward(xt[0:1], xt[1:2] * L.F_SCALE)
     f0_o, w_o, _ = U.forward(params, x)
     assert rel(f0[0].double().cpu().numpy(), f0_o) < 2e-2
     assert rel(w[0].double().cpu().numpy(), w_o) < 2e-2
@@ -167,14 +169,44 @@ def test_training_reduces_loss_on_fixed_batch():
     net = L.UNet(seed=1, device=DEV)
     rng = np.random.Generator(np.random.PCG64(5))
     x = torch.tensor(rng.uniform(0, 2, (4, 32, 32)), dtype=torch.float32, device=DEV)
+    base = torch.tensor(rng.uniform(0, 0.04, (4, 32, 32)), dtype=torch.float32, device=DEV)
     ft = (x * 0.5).contiguous()
     wt = torch.sigmoid(x - 1.0).contiguous()
     losses = []
-    for _ in range(60):
-        net.forward(x)
+    for _ in range(150):
+        net.forward(x, base)
         losses.append(float(net.backward(ft, wt).item()))
         net.adam_step(3e-3)
     assert losses[-1] < 0.3 * losses[0]
+
+
+def test_pack_input_and_composed_head():
+    """Input rows (two scaled planes, 14 zero channels) and the serving head
+    f0 = max(base + s o0, 0), w = sigmoid(o1), against numpy on the same BF16 inputs."""
+    rng = np.random.Generator(np.random.PCG64(21))
+    npix = 1000
+    a = rng.uniform(0, 3, npix).astype(np.float32)
+    b = rng.uniform(-1, 1, npix).astype(np.float32)
+    x = torch.full((npix, 16), 7.0, dtype=BF, device=DEV)          # stale content is overwritten
+    E.eptv_unet_pack_input(torch.tensor(a).to(DEV), 0.5, torch.tensor(b).to(DEV), 3.0, x)
+    got = x.float().cpu().numpy()
+    assert np.array_equal(got[:, 0], bf(a.astype(np.float32) * np.float32(0.5)).astype(np.float32))
+    assert np.array_equal(got[:, 1], bf(b.astype(np.float32) * np.float32(3.0)).astype(np.float32))
+    assert not got[:, 2:].any()
+    E.eptv_unet_pack_input(torch.tensor(a).to(DEV), 1.0, None, 0.0, x)
+    assert not x.float()[:, 1:].any().item()
+    feats = bf(rng.standard_normal((npix, 16)))
+    hw = rng.standard_normal((2, 16)).astype(np.float32)
+    hb = rng.standard_normal(2).astype(np.float32)
+    base = rng.uniform(0, 0.04, npix).astype(np.float32)
+    xt = torch.tensor(feats, dtype=torch.float32).to(BF).to(DEV).view(1, 1, npix, 16)
+    f0 = torch.empty(npix, device=DEV)
+    w = torch.empty(npix, device=DEV)
+    E.eptv_unet_head(xt, torch.tensor(hw).to(DEV), torch.tensor(hb).to(DEV), f0=f0, w=w,
+                     base=torch.tensor(base).to(DEV), f_scale=0.02)
+    o = feats @ hw.T.astype(np.float64) + hb
+    assert np.allclose(f0.cpu().numpy(), np.maximum(base + 0.02 * o[:, 0], 0.0), rtol=0, atol=1e-6)
+    assert np.allclose(w.cpu().numpy(), 1.0 / (1.0 + np.exp(-o[:, 1])), rtol=0, atol=1e-5)
 
 
 def test_prior_weight_mode_matches_oracle():

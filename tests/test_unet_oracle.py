@@ -58,7 +58,7 @@ def test_pool_and_upsample_hand_examples():
 def test_network_gradients_finite_differences():
     params = U.init_params(3)
     rng = np.random.Generator(np.random.PCG64(4))
-    x = rng.uniform(0, 1, (1, 8, 8))
+    x = rng.uniform(0, 1, (2, 8, 8))
     f_t = rng.uniform(0, 1, (8, 8))
     w_t = rng.uniform(0, 1, (8, 8))
     loss, grads = U.loss_and_grads(params, x, f_t, w_t)

@@ -19,7 +19,7 @@
 #include <algorithm>
 
 #include "eptv_internal.cuh"
-#include "kernels.cuh"
+#include "unet.cuh"
 
 namespace eptv {
 

@@ -64,6 +64,9 @@ extern "C" {
 #define EPTV_STEP_ARMIJO    0
 #define EPTV_STEP_FIXED     1
 
+#define EPTV_OPERATOR_ON_THE_FLY 0   /* P, P^T recomputed by the kernels at each use (default) */
+#define EPTV_OPERATOR_STORED     1   /* P, P^T stored as CSR matrices in device memory         */
+
 /* Scan geometry (Sec. 3: fan beam, arc detector). */
 typedef struct {
     int nx, ny;              /* image size in pixels, 1..8192 each                     */
@@ -226,6 +229,31 @@ int eptv_select_kth(const eptv_geometry *g, const float *d_vals, long n, long k,
  * device share the array: each call clears it before use, and calls that overlap on
  * the GPU (other streams or threads) race and give wrong results. */
 int eptv_select_kth_noalloc(const float *d_vals, long n, long k, float *d_out, void *stream);
+
+/* Stored-matrix operator (Sec. 2.3: the sparse-matrix strategy for small problems).
+ * mode EPTV_OPERATOR_STORED makes every later P / P^T of this handle -- eptv_project(_t),
+ * eptv_backproject, eptv_cgls, eptv_reconstruct, eptv_reconstruct_batched (all members
+ * of a batch must use the same mode), eptv_report_energy -- a sparse matrix-vector
+ * product with device CSR matrices of P (rows = rays v nb + k) and P^T (rows = pixels
+ * iy nx + ix).  Their entries are the canonical p_ij that the on-the-fly kernels compute
+ * (only p_ij > 0 stored; columns increasing in each row; rows padded with zero entries
+ * to multiples of 4), and the two matrices are exact transposes of each other.  The first
+ * switch to STORED builds them (synchronous; owned by the handle; about 16 bytes per
+ * nonzero for both); EPTV_OPERATOR_ON_THE_FLY switches back and keeps them.
+ * *h_nnz_opt (may be NULL) receives the stored entries of P, padding included.
+ * Errors: EPTV_ERR_ARG (unknown mode; a row of P longer than 4096 entries; 2^31 or more
+ * entries), EPTV_ERR_NOMEM, EPTV_ERR_CUDA. */
+int eptv_set_operator(eptv_geometry *g, int mode, long long *h_nnz_opt);
+
+/* Rows and stored entries (padding included) of the built matrix `which` (0: P, 1: P^T);
+ * EPTV_ERR_ARG if the matrices have not been built. */
+int eptv_matrix_info(const eptv_geometry *g, int which, long long *h_rows, long long *h_nnz);
+
+/* Copies the built matrix `which` (0: P, 1: P^T) into caller device buffers:
+ * d_ptr [rows + 1] int32 row offsets, d_col [nnz] int32 columns, d_val [nnz] FP32 values
+ * (sizes from eptv_matrix_info).  Asynchronous on `stream`. */
+int eptv_copy_matrix(const eptv_geometry *g, int which, int *d_ptr, int *d_col, float *d_val,
+                     void *stream);
 
 /* Batched reconstruction of n independent slices (any mix of sizes) with one set of
  * parameters: every kernel of one outer iteration covers all slices in a single launch,

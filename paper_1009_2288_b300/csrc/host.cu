@@ -61,7 +61,7 @@ struct DevMem {
 
 struct GraphCache {
     cudaGraphExec_t exec = nullptr;
-    int key[7] = {-1, -1, -1, -1, -1, -1, -1};
+    int key[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
     long long kernels = 0;     // kernel nodes in the captured outer iteration
     void reset() {
         if (exec) cudaGraphExecDestroy(exec);
@@ -74,6 +74,7 @@ struct GraphCache {
 // Batch over several handles (cached in the first handle).
 struct BatchCache {
     std::vector<const void *> members;
+    std::vector<int> modes;     // operator mode of each member when the batch was built
     Batch B;
     DevMem mem;
     GraphCache graph;
@@ -81,6 +82,7 @@ struct BatchCache {
         graph.reset();
         mem.release();
         members.clear();
+        modes.clear();
         B = Batch{};
     }
 };
@@ -104,6 +106,9 @@ struct eptv_geometry {
     double *d_log = nullptr;       // per-iteration log of the last reconstruction
     size_t log_cap = 0;            // doubles allocated
     int log_outer = 0, log_gd = 0; // layout of the last reconstruction's log
+    int op_mode = EPTV_OPERATOR_ON_THE_FLY;
+    StoredMatrices stored;         // built on the first switch to EPTV_OPERATOR_STORED
+    DevMem stored_mem;
 };
 
 namespace eptv {
@@ -163,6 +168,8 @@ static void family_blocks(const SliceDev &s, int out[FAM_COUNT]) {
     out[FAM_SINO] = (s.n_rays + 1023) / 1024;
     out[FAM_EDGE] = (s.n_edges + 2047) / 2048;
     out[FAM_TV] = ((s.nx + kTileW - 1) / kTileW) * ((s.ny + kGdTileRows - 1) / kGdTileRows);
+    out[FAM_SPMV_P] = (s.n_rays + 7) / 8;
+    out[FAM_SPMV_PT] = (s.n_pix + 31) / 32;
 }
 
 // Allocate the batch bookkeeping (maps, counters, partials, histograms, params) for the
@@ -215,25 +222,35 @@ static int n_trials_of(const eptv_params *p) {
 
 // ---------------------------------------------------------------- launch sequences
 
+// P and P^T of a batch: the on-the-fly kernels (K1, K2) or the stored matrices.
+static void op_project(const Batch &B, const ProjArgs &a, cudaStream_t st) {
+    if (B.stored) launch_spmv_p(B, a, st);
+    else launch_project(B, a, st);
+}
+static void op_backproject(const Batch &B, const BackArgs &a, cudaStream_t st) {
+    if (B.stored) launch_spmv_pt(B, a, st);
+    else launch_backproject(B, a, st);
+}
+
 // (P1): M CGLS iterations from u (App. I).  r = y - P u; s = P^T r; then M times
 // q = P s, a; r -= a q; [t = P^T r, b; s = t + b s]; u += a s.
 static void enqueue_cgls(const Batch &B, int M, bool have_uT, cudaStream_t st) {
     ProjArgs pr{};
     pr.img = IMG_U; pr.out = SINO_R; pr.resid = 1; pr.fin = FIN_NONE; pr.no_T = have_uT ? 0 : 1;
-    launch_project(B, pr, st);
+    op_project(B, pr, st);
     BackArgs bs{};
     bs.out = 0; bs.write_T = 1; bs.fin = FIN_GAMMA0;
-    launch_backproject(B, bs, st);
+    op_backproject(B, bs, st);
     for (int m = 0; m < M; ++m) {
         ProjArgs pq{};
         pq.img = IMG_S; pq.out = SINO_Q; pq.resid = 0; pq.fin = FIN_QQ_TO_A;
-        launch_project(B, pq, st);
+        op_project(B, pq, st);
         const bool more = (m + 1 < M);
         if (more) {
             launch_cgls_update_r(B, st);
             BackArgs bt{};
             bt.out = 1; bt.write_T = 0; bt.fin = FIN_B;
-            launch_backproject(B, bt, st);
+            op_backproject(B, bt, st);
         }
         launch_cgls_update_us(B, more ? 1 : 0, st);
     }
@@ -262,7 +279,8 @@ static void enqueue_outer(const Batch &B, const eptv_params *p, cudaStream_t st)
 
 // Capture one outer iteration of batch B into a graph (cached per structural key).
 static int outer_graph(const Batch &B, GraphCache &gc, cudaStream_t cap, const eptv_params *p) {
-    const int key[7] = {p->cgls_iters, p->n_gd, n_trials_of(p), p->step_rule, B.n, B.k1_seg, B.k2_vg};
+    const int key[8] = {p->cgls_iters, p->n_gd, n_trials_of(p), p->step_rule, B.n, B.k1_seg, B.k2_vg,
+                        B.stored};
     if (gc.exec && memcmp(key, gc.key, sizeof key) == 0) return 0;
     gc.reset();
     cudaGraph_t graph = nullptr;
@@ -339,13 +357,19 @@ static float inv_or_big(double c) {
 // changes).  The caller has synchronised the stream that used the previous batch.
 static int acquire_batch(int n, eptv_geometry *const *geoms, BatchCache &bc) {
     std::vector<const void *> members(geoms, geoms + n);
-    if (bc.members == members) return 0;
+    std::vector<int> modes;
+    for (int i = 0; i < n; ++i) modes.push_back(geoms[i]->op_mode);
+    for (int i = 1; i < n; ++i)
+        if (modes[i] != modes[0]) return fail(EPTV_ERR_ARG, "batch members use different operators");
+    if (bc.members == members && bc.modes == modes) return 0;
     bc.reset();
     std::vector<SliceDev> sds;
     for (int i = 0; i < n; ++i) sds.push_back(geoms[i]->sd);
     int rc = build_batch(bc.B, bc.mem, sds);
     if (rc) { bc.reset(); return rc; }
+    bc.B.stored = modes[0] == EPTV_OPERATOR_STORED;
     bc.members = members;
+    bc.modes = modes;
     return 0;
 }
 
@@ -532,6 +556,7 @@ void eptv_destroy_geometry(eptv_geometry *g) {
     g->batch.reset();
     if (g->d_log) cudaFree(g->d_log);
     if (g->cap) cudaStreamDestroy(g->cap);
+    g->stored_mem.release();
     g->mem.release();
     delete g;
 }
@@ -545,7 +570,7 @@ int eptv_project_t(const eptv_geometry *gc, const float *d_f, const float *d_fT,
     a.imgT_override = d_fT;
     a.out_override = d_y;
     a.fin = FIN_NONE;
-    launch_project(gc->B, a, st);
+    op_project(gc->B, a, st);
     return launch_check();
 }
 
@@ -558,6 +583,7 @@ int eptv_transpose(const eptv_geometry *gc, const float *d_f, float *d_fT, void 
 int eptv_project(const eptv_geometry *gc, const float *d_f, float *d_y, void *stream) {
     if (!gc || !d_f || !d_y) return fail(EPTV_ERR_ARG, "NULL argument");
     cudaStream_t st = (cudaStream_t)stream;
+    if (gc->B.stored) return eptv_project_t(gc, d_f, nullptr, d_y, stream);
     // the transposed copy lives in the handle's scratch image t (not used across calls)
     launch_transpose(gc->B, d_f, gc->sd.t, st);
     int rc = launch_check();
@@ -571,7 +597,7 @@ int eptv_backproject(const eptv_geometry *gc, const float *d_y, float *d_f, void
     a.in_override = d_y;
     a.out_override = d_f;
     a.fin = FIN_NONE;
-    launch_backproject(gc->B, a, (cudaStream_t)stream);
+    op_backproject(gc->B, a, (cudaStream_t)stream);
     return launch_check();
 }
 
@@ -765,7 +791,7 @@ int eptv_report_energy(const eptv_geometry *gc, const eptv_params *p, double sig
     a.y_override = d_y;
     a.resid = 1;
     a.fin = FIN_NORM;
-    launch_project(g->B, a, st);
+    op_project(g->B, a, st);
     launch_set_scalar(g->B, SC_SIGMA, sigma_ref, st);
     GdArgs ga{};
     ga.first = 1;
@@ -892,6 +918,78 @@ int eptv_autotune_batched(int n, eptv_geometry *const *geoms, int *k1_seg, int *
     int rc = acquire_batch(n, geoms, geoms[0]->batch);
     if (rc) return rc;
     return autotune_batch(geoms[0]->batch.B, k1_seg, k2_vg);
+}
+
+
+static cudaError_t stored_alloc(void *ctx, void **p, size_t bytes) {
+    DevMem *m = static_cast<DevMem *>(ctx);
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) return e;
+    m->ptrs.push_back(q);
+    *p = q;
+    return cudaSuccess;
+}
+
+int eptv_set_operator(eptv_geometry *g, int mode, long long *h_nnz_opt) {
+    if (!g) return fail(EPTV_ERR_ARG, "NULL handle");
+    if (mode != EPTV_OPERATOR_ON_THE_FLY && mode != EPTV_OPERATOR_STORED)
+        return fail(EPTV_ERR_ARG, "unknown operator mode %d", mode);
+    CU(cudaDeviceSynchronize());
+    if (mode == EPTV_OPERATOR_STORED && !g->stored.p_ptr) {
+        StoredMatrices m;
+        cudaError_t e = build_stored(g->sd, g->B.d_sd, stored_alloc, &g->stored_mem, &m, nullptr);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            g->stored_mem.release();
+            if (e == cudaErrorInvalidValue)
+                return fail(EPTV_ERR_ARG, "stored matrix too large (a row of P longer than 4096 "
+                                          "entries, or 2^31 entries or more)");
+            if (e == cudaErrorMemoryAllocation) return fail(EPTV_ERR_NOMEM, "no device memory for the stored matrices");
+            return fail(EPTV_ERR_CUDA, "building the stored matrices failed: %s", cudaGetErrorString(e));
+        }
+        g->stored = m;
+    }
+    const bool on = mode == EPTV_OPERATOR_STORED;
+    for (SliceDev *sd : {&g->sd, &g->B.h_sd[0]}) {
+        sd->p_ptr = on ? g->stored.p_ptr : nullptr;
+        sd->p_col = on ? g->stored.p_col : nullptr;
+        sd->p_val = on ? g->stored.p_val : nullptr;
+        sd->pt_ptr = on ? g->stored.pt_ptr : nullptr;
+        sd->pt_col = on ? g->stored.pt_col : nullptr;
+        sd->pt_val = on ? g->stored.pt_val : nullptr;
+    }
+    CU(cudaMemcpy(g->B.d_sd, g->B.h_sd.data(), sizeof(SliceDev), cudaMemcpyHostToDevice));
+    g->B.stored = on ? 1 : 0;
+    g->op_mode = mode;
+    g->graph.reset();
+    if (h_nnz_opt) *h_nnz_opt = g->stored.nnz_p;
+    return 0;
+}
+
+int eptv_matrix_info(const eptv_geometry *g, int which, long long *h_rows, long long *h_nnz) {
+    if (!g || !h_rows || !h_nnz) return fail(EPTV_ERR_ARG, "NULL argument");
+    if (which != 0 && which != 1) return fail(EPTV_ERR_ARG, "which must be 0 (P) or 1 (P^T)");
+    if (!g->stored.p_ptr) return fail(EPTV_ERR_ARG, "the stored matrices have not been built");
+    *h_rows = which == 0 ? g->sd.n_rays : g->sd.n_pix;
+    *h_nnz = which == 0 ? g->stored.nnz_p : g->stored.nnz_pt;
+    return 0;
+}
+
+int eptv_copy_matrix(const eptv_geometry *g, int which, int *d_ptr, int *d_col, float *d_val, void *stream) {
+    long long rows, nnz;
+    int rc = eptv_matrix_info(g, which, &rows, &nnz);
+    if (rc) return rc;
+    if (!d_ptr || !d_col || !d_val) return fail(EPTV_ERR_ARG, "NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    const StoredMatrices &m = g->stored;
+    CU(cudaMemcpyAsync(d_ptr, which == 0 ? m.p_ptr : m.pt_ptr, sizeof(int) * (size_t)(rows + 1),
+                       cudaMemcpyDeviceToDevice, st));
+    CU(cudaMemcpyAsync(d_col, which == 0 ? m.p_col : m.pt_col, sizeof(int) * (size_t)nnz,
+                       cudaMemcpyDeviceToDevice, st));
+    CU(cudaMemcpyAsync(d_val, which == 0 ? m.p_val : m.pt_val, sizeof(float) * (size_t)nnz,
+                       cudaMemcpyDeviceToDevice, st));
+    return 0;
 }
 
 }  // extern "C"

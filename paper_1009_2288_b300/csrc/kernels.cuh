@@ -16,6 +16,8 @@ enum Family {
     FAM_SINO,     // sinogram elementwise: ceil(n_rays / 1024) blocks
     FAM_EDGE,     // half-edge arrays: ceil(n_edges / 2048) blocks
     FAM_TV,       // fused TV descent: ceil(nx / 32) * ceil(ny / kGdTileRows) blocks
+    FAM_SPMV_P,   // stored P: ceil(n_rays / 8) blocks (warp per ray)
+    FAM_SPMV_PT,  // stored P^T: ceil(n_pix / 32) blocks (8 lanes per pixel)
     FAM_COUNT
 };
 
@@ -69,6 +71,7 @@ struct Batch {
     ParamsDev *d_params = nullptr;
     int k1_seg = 8;        // projector: warps (row segments) per 32-ray block (4, 8, 16)
     int k2_vg = 4;         // back projector: view groups per 4-pixel strip (1, 2, 4, 8)
+    int stored = 0;        // 1: P and P^T are applied from the stored matrices (stored.cu)
     TileMap map(int fam) const { return TileMap{d_start + fam * (n + 1), n}; }
     int blocks(int fam) const { return h_start[fam * (n + 1) + n]; }
 };
@@ -100,6 +103,22 @@ struct GdArgs {
     float *fout, *gout;      // outputs (null: slice ping-pong)
     int write_f;             // store the iterate
 };
+
+// Stored-matrix operator (stored.cu): device CSR matrices of P (rows = rays) and P^T
+// (rows = pixels), rows padded to multiples of 4 entries.
+struct StoredMatrices {
+    int *p_ptr = nullptr, *p_col = nullptr;
+    float *p_val = nullptr;
+    long long nnz_p = 0;
+    int *pt_ptr = nullptr, *pt_col = nullptr;
+    float *pt_val = nullptr;
+    long long nnz_pt = 0;
+};
+typedef cudaError_t (*StoredAlloc)(void *ctx, void **p, size_t bytes);
+cudaError_t build_stored(const SliceDev &S, const SliceDev *d_sd, StoredAlloc alloc, void *ctx,
+                         StoredMatrices *m, cudaStream_t st);
+void launch_spmv_p(const Batch &B, const ProjArgs &a, cudaStream_t st);
+void launch_spmv_pt(const Batch &B, const BackArgs &a, cudaStream_t st);
 
 // Kernel launches issued by this thread (graph captures included); read by the host
 // code to report how many kernels a call ran.

@@ -27,7 +27,8 @@ EXPORTED = [
     "eptv_autotune_batched", "eptv_unet_conv3x3", "eptv_unet_conv3x3_wgrad",
     "eptv_unet_weights_to_bf16", "eptv_unet_maxpool2", "eptv_unet_maxpool2_bwd",
     "eptv_unet_upsample2", "eptv_unet_upsample2_bwd", "eptv_unet_relu_bwd", "eptv_unet_head",
-    "eptv_unet_adam", "eptv_unet_pack_input",
+    "eptv_unet_adam", "eptv_unet_pack_input", "eptv_set_operator", "eptv_matrix_info",
+    "eptv_copy_matrix",
 ]
 
 
@@ -130,6 +131,9 @@ def load():
         "eptv_unet_head": (c_int, [vp, c_int, c_int, ctypes.c_longlong, vp, vp, vp, vp, vp, ctypes.c_float,
                                    vp, vp, vp, c_int, c_int, vp, vp, vp, vp]),
         "eptv_unet_pack_input": (c_int, [vp, ctypes.c_float, vp, ctypes.c_float, ctypes.c_longlong, vp, vp]),
+        "eptv_set_operator": (c_int, [vp, c_int, ctypes.POINTER(ctypes.c_longlong)]),
+        "eptv_matrix_info": (c_int, [vp, c_int, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
+        "eptv_copy_matrix": (c_int, [vp, c_int, vp, vp, vp, vp]),
         "eptv_unet_adam": (c_int, [vp, vp, vp, vp, ctypes.c_longlong, ctypes.c_float, ctypes.c_float,
                                    ctypes.c_float, ctypes.c_float, c_int, vp]),
         "eptv_last_error": (ctypes.c_char_p, []),
@@ -334,6 +338,30 @@ def eptv_get_log(geom: Geometry):
                           steps.size, sig.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                           sig.size, None, None))
     return steps.reshape(no.value, ng.value), sig
+
+
+OPERATOR_ON_THE_FLY, OPERATOR_STORED = 0, 1
+
+
+def eptv_set_operator(geom: Geometry, mode: int) -> int:
+    """Select the on-the-fly kernels or the stored CSR matrices for P and P^T of geom
+    (building the matrices on the first switch to stored); returns the stored entries of P."""
+    nnz = ctypes.c_longlong(0)
+    _check(load().eptv_set_operator(geom.handle, int(mode), ctypes.byref(nnz)))
+    return nnz.value
+
+
+def eptv_matrix(geom: Geometry, which: int):
+    """(ptr, col, val) device tensors: a copy of the stored P (which = 0) or P^T (1)."""
+    import torch
+    rows, nnz = ctypes.c_longlong(), ctypes.c_longlong()
+    _check(load().eptv_matrix_info(geom.handle, int(which), ctypes.byref(rows), ctypes.byref(nnz)))
+    ptr = torch.empty(rows.value + 1, dtype=torch.int32, device="cuda")
+    col = torch.empty(max(nnz.value, 1), dtype=torch.int32, device="cuda")
+    val = torch.empty(max(nnz.value, 1), dtype=torch.float32, device="cuda")
+    _check(load().eptv_copy_matrix(geom.handle, int(which), ptr.data_ptr(), col.data_ptr(), val.data_ptr(),
+                                   _stream(None)))
+    return ptr, col[:nnz.value], val[:nnz.value]
 
 
 def eptv_set_tuning(geom: Geometry, k1_seg: int, k2_vg: int):

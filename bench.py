@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tte", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-stored", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     return ap.parse_args()
 
@@ -282,6 +283,63 @@ def run_batched(dev, stream, n_slices=64, n_outer=50, steps=3):
             "tuning": {"k1_seg": tuning[0], "k2_vg": tuning[1]}}
 
 
+def run_stored(dev, stream, case, n_outer, peak, peak_kind, steps=3):
+    """Stored-matrix operator (Sec. 2.3) on the benchmark workload: build time, SpMV launch
+    times of P and P^T (CUDA events, 50 back-to-back launches; the two matrices, about
+    150 MB each, exceed the 126 MB L2, so they stream from HBM) with their streamed bytes
+    (8 B per stored entry + row offsets + output vector), and the n_outer-iteration
+    reconstruction with the stored operator."""
+    import numpy as np
+    import torch
+    from paper_1009_2288_b300 import eptv as E
+    from paper_1009_2288_b300 import inputs as I
+    g = case.geom
+    geo = E.Geometry(g)
+    torch.cuda.synchronize()
+    t0 = time.time()
+    E.eptv_set_operator(geo, E.OPERATOR_STORED)
+    torch.cuda.synchronize()
+    t_build = time.time() - t0
+    rows_p, nnz_p, sell_p = E.eptv_matrix_info(geo, 0)
+    rows_t, nnz_t, sell_t = E.eptv_matrix_info(geo, 1)
+    y = torch.from_numpy(case.y.astype(np.float32).reshape(-1)).to(dev)
+    f = torch.zeros(g.n_pix, device=dev)
+    ybuf = torch.empty(g.n_rays, device=dev)
+    xbuf = torch.empty(g.n_pix, device=dev)
+    E.eptv_backproject(geo, y, f)
+    fT = torch.empty_like(f)
+    E.eptv_transpose(geo, f, fT)
+    t_p = time_kernel(lambda: E.eptv_project_t(geo, f, fT, ybuf))
+    t_t = time_kernel(lambda: E.eptv_backproject(geo, y, xbuf))
+    # streamed: the SELL-32 entries (8 B each), slice offsets and lengths, the output vector
+    bytes_p = 8 * sell_p + 8 * ((rows_p + 31) // 32) + 4 * rows_p
+    bytes_t = 8 * sell_t + 8 * ((rows_t + 31) // 32) + 4 * rows_t
+    p = I.EptvParams(n_outer=n_outer)
+    E.eptv_reconstruct(geo, p, y, f.zero_(), report=False)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    times = []
+    for _ in range(steps):
+        flush.zero_()
+        f.zero_()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        E.eptv_reconstruct(geo, p, y, f, report=False)
+        e.record(stream)
+        e.synchronize()
+        times.append(s.elapsed_time(e))
+    ms = statistics.mean(times)
+    out = {"build_s": t_build, "nnz_p": nnz_p, "nnz_pt": nnz_t, "sell_p": sell_p, "sell_pt": sell_t,
+           "matrix_bytes": 8 * (sell_p + sell_t),
+           "spmv_p": {"us": t_p * 1e6, "streamed_bytes": bytes_p, "gbs": bytes_p / t_p / 1e9,
+                      "frac": bytes_p / t_p / 1e9 / peak},
+           "spmv_pt": {"us": t_t * 1e6, "streamed_bytes": bytes_t, "gbs": bytes_t / t_t / 1e9,
+                       "frac": bytes_t / t_t / 1e9 / peak},
+           "peak_gbs": peak, "peak_kind": peak_kind,
+           "reconstruct": {"n_outer": n_outer, "ms_per_step": ms, "iterations_per_s": n_outer * 1e3 / ms}}
+    del geo
+    return out
+
+
 def run_learned(dev, stream, n_pairs=2000, epochs=40, eval_seeds=(1, 2, 3, 4), k_ws=(0, 2)):
     """Learned warm start on the 256^2 (1.6 mm), 30 views x 888 bins, I0 = 5e4 workload.
     Trains the U-Net on n_pairs pairs that the plain method generates (50 iterations each,
@@ -513,6 +571,10 @@ def run_ours(args, world, rank, local):
     if not args.no_batched and rank == 0:
         batched = run_batched(dev, stream)
 
+    stored = None
+    if not args.no_stored and rank == 0:
+        stored = run_stored(dev, stream, case, N_OUTER, peak, peak_kind)
+
     learned = None
     if not args.no_learned and rank == 0:
         learned = run_learned(dev, stream)
@@ -538,6 +600,7 @@ def run_ours(args, world, rank, local):
         "cpu_baseline": cpu,
         "time_to_oracle_energy": tte,
         "batched": batched,
+        "stored": stored,
         "learned": learned,
         "clocks": clk,
         "paper_context": {"workload": "NCAT 512^2, 40 views, 50 iterations (Table 2)",

@@ -238,16 +238,20 @@ int eptv_select_kth_noalloc(const float *d_vals, long n, long k, float *d_out, v
  * iy nx + ix).  Their entries are the canonical p_ij that the on-the-fly kernels compute
  * (only p_ij > 0 stored; columns increasing in each row; rows padded with zero entries
  * to multiples of 4), and the two matrices are exact transposes of each other.  The first
- * switch to STORED builds them (synchronous; owned by the handle; about 16 bytes per
- * nonzero for both); EPTV_OPERATOR_ON_THE_FLY switches back and keeps them.
+ * switch to STORED builds them (synchronous; owned by the handle; about 32 bytes per
+ * nonzero of P for both matrices in both forms: CSR for export, SELL-32 for the SpMV);
+ * EPTV_OPERATOR_ON_THE_FLY switches back and keeps them.
  * *h_nnz_opt (may be NULL) receives the stored entries of P, padding included.
  * Errors: EPTV_ERR_ARG (unknown mode; a row of P longer than 4096 entries; 2^31 or more
  * entries), EPTV_ERR_NOMEM, EPTV_ERR_CUDA. */
 int eptv_set_operator(eptv_geometry *g, int mode, long long *h_nnz_opt);
 
-/* Rows and stored entries (padding included) of the built matrix `which` (0: P, 1: P^T);
- * EPTV_ERR_ARG if the matrices have not been built. */
-int eptv_matrix_info(const eptv_geometry *g, int which, long long *h_rows, long long *h_nnz);
+/* Rows and stored entries (padding included) of the built matrix `which` (0: P, 1: P^T)
+ * in the exported CSR form; *h_sell_opt (may be NULL) receives the entries of the SELL-32
+ * copy the SpMV kernels stream (rows in slices of 32, each slice padded to its longest
+ * row).  EPTV_ERR_ARG if the matrices have not been built. */
+int eptv_matrix_info(const eptv_geometry *g, int which, long long *h_rows, long long *h_nnz,
+                     long long *h_sell_opt);
 
 /* Copies the built matrix `which` (0: P, 1: P^T) into caller device buffers:
  * d_ptr [rows + 1] int32 row offsets, d_col [nnz] int32 columns, d_val [nnz] FP32 values

@@ -100,11 +100,11 @@ struct SliceDev {
     double *log;         // optional per-iteration log: [n_outer * n_gd] steps, then [n_outer] sigmas
     int log_outer;       // capacity in outer iterations (0: no log)
     int log_gd;          // GD iterations per outer iteration in the log layout
-    // stored operator (null unless built): CSR of P (rows = rays) and P^T (rows = pixels)
-    const int *p_ptr, *p_col;
-    const float *p_val;
-    const int *pt_ptr, *pt_col;
-    const float *pt_val;
+    // stored operator (null unless selected): SELL-32 P (rows = rays), P^T (rows = pixels)
+    const int *p_sptr, *p_slen, *p_scol;
+    const float *p_sval;
+    const int *pt_sptr, *pt_slen, *pt_scol;
+    const float *pt_sval;
 };
 
 // Launch plan of one kernel family over a set of slices: slice s owns the blocks

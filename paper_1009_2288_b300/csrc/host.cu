@@ -168,8 +168,8 @@ static void family_blocks(const SliceDev &s, int out[FAM_COUNT]) {
     out[FAM_SINO] = (s.n_rays + 1023) / 1024;
     out[FAM_EDGE] = (s.n_edges + 2047) / 2048;
     out[FAM_TV] = ((s.nx + kTileW - 1) / kTileW) * ((s.ny + kGdTileRows - 1) / kGdTileRows);
-    out[FAM_SPMV_P] = (s.n_rays + 7) / 8;
-    out[FAM_SPMV_PT] = (s.n_pix + 31) / 32;
+    out[FAM_SPMV_P] = (s.n_rays + 31) / 32;
+    out[FAM_SPMV_PT] = ((s.ny + 7) / 8) * ((s.nx + 31) / 32);
 }
 
 // Allocate the batch bookkeeping (maps, counters, partials, histograms, params) for the
@@ -583,7 +583,6 @@ int eptv_transpose(const eptv_geometry *gc, const float *d_f, float *d_fT, void 
 int eptv_project(const eptv_geometry *gc, const float *d_f, float *d_y, void *stream) {
     if (!gc || !d_f || !d_y) return fail(EPTV_ERR_ARG, "NULL argument");
     cudaStream_t st = (cudaStream_t)stream;
-    if (gc->B.stored) return eptv_project_t(gc, d_f, nullptr, d_y, stream);
     // the transposed copy lives in the handle's scratch image t (not used across calls)
     launch_transpose(gc->B, d_f, gc->sd.t, st);
     int rc = launch_check();
@@ -952,12 +951,14 @@ int eptv_set_operator(eptv_geometry *g, int mode, long long *h_nnz_opt) {
     }
     const bool on = mode == EPTV_OPERATOR_STORED;
     for (SliceDev *sd : {&g->sd, &g->B.h_sd[0]}) {
-        sd->p_ptr = on ? g->stored.p_ptr : nullptr;
-        sd->p_col = on ? g->stored.p_col : nullptr;
-        sd->p_val = on ? g->stored.p_val : nullptr;
-        sd->pt_ptr = on ? g->stored.pt_ptr : nullptr;
-        sd->pt_col = on ? g->stored.pt_col : nullptr;
-        sd->pt_val = on ? g->stored.pt_val : nullptr;
+        sd->p_sptr = on ? g->stored.p_sptr : nullptr;
+        sd->p_slen = on ? g->stored.p_slen : nullptr;
+        sd->p_scol = on ? g->stored.p_scol : nullptr;
+        sd->p_sval = on ? g->stored.p_sval : nullptr;
+        sd->pt_sptr = on ? g->stored.pt_sptr : nullptr;
+        sd->pt_slen = on ? g->stored.pt_slen : nullptr;
+        sd->pt_scol = on ? g->stored.pt_scol : nullptr;
+        sd->pt_sval = on ? g->stored.pt_sval : nullptr;
     }
     CU(cudaMemcpy(g->B.d_sd, g->B.h_sd.data(), sizeof(SliceDev), cudaMemcpyHostToDevice));
     g->B.stored = on ? 1 : 0;
@@ -967,18 +968,20 @@ int eptv_set_operator(eptv_geometry *g, int mode, long long *h_nnz_opt) {
     return 0;
 }
 
-int eptv_matrix_info(const eptv_geometry *g, int which, long long *h_rows, long long *h_nnz) {
+int eptv_matrix_info(const eptv_geometry *g, int which, long long *h_rows, long long *h_nnz,
+                     long long *h_sell_opt) {
     if (!g || !h_rows || !h_nnz) return fail(EPTV_ERR_ARG, "NULL argument");
     if (which != 0 && which != 1) return fail(EPTV_ERR_ARG, "which must be 0 (P) or 1 (P^T)");
     if (!g->stored.p_ptr) return fail(EPTV_ERR_ARG, "the stored matrices have not been built");
     *h_rows = which == 0 ? g->sd.n_rays : g->sd.n_pix;
     *h_nnz = which == 0 ? g->stored.nnz_p : g->stored.nnz_pt;
+    if (h_sell_opt) *h_sell_opt = which == 0 ? g->stored.sell_p : g->stored.sell_pt;
     return 0;
 }
 
 int eptv_copy_matrix(const eptv_geometry *g, int which, int *d_ptr, int *d_col, float *d_val, void *stream) {
     long long rows, nnz;
-    int rc = eptv_matrix_info(g, which, &rows, &nnz);
+    int rc = eptv_matrix_info(g, which, &rows, &nnz, nullptr);
     if (rc) return rc;
     if (!d_ptr || !d_col || !d_val) return fail(EPTV_ERR_ARG, "NULL argument");
     cudaStream_t st = (cudaStream_t)stream;

@@ -16,8 +16,8 @@ enum Family {
     FAM_SINO,     // sinogram elementwise: ceil(n_rays / 1024) blocks
     FAM_EDGE,     // half-edge arrays: ceil(n_edges / 2048) blocks
     FAM_TV,       // fused TV descent: ceil(nx / 32) * ceil(ny / kGdTileRows) blocks
-    FAM_SPMV_P,   // stored P: ceil(n_rays / 8) blocks (warp per ray)
-    FAM_SPMV_PT,  // stored P^T: ceil(n_pix / 32) blocks (8 lanes per pixel)
+    FAM_SPMV_P,   // stored P: ceil(n_rays / 32) blocks (8 warps per 32-ray slice)
+    FAM_SPMV_PT,  // stored P^T: ceil(ny / 8) * ceil(nx / 32) blocks (32 x 8 pixel tiles)
     FAM_COUNT
 };
 
@@ -113,6 +113,13 @@ struct StoredMatrices {
     int *pt_ptr = nullptr, *pt_col = nullptr;
     float *pt_val = nullptr;
     long long nnz_pt = 0;
+    // SELL-32 copies read by the SpMV kernels: slice offsets, row length per slice, entries
+    int *p_sptr = nullptr, *p_slen = nullptr, *p_scol = nullptr;
+    float *p_sval = nullptr;
+    long long sell_p = 0;
+    int *pt_sptr = nullptr, *pt_slen = nullptr, *pt_scol = nullptr;
+    float *pt_sval = nullptr;
+    long long sell_pt = 0;
 };
 typedef cudaError_t (*StoredAlloc)(void *ctx, void **p, size_t bytes);
 cudaError_t build_stored(const SliceDev &S, const SliceDev *d_sd, StoredAlloc alloc, void *ctx,

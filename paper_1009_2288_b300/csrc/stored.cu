@@ -6,8 +6,9 @@
 // from stays in L2.
 //
 // Layout of each matrix: ptr [rows + 1] (int32), col [nnz] (int32), val [nnz] (FP32).
-// Every row is padded to a multiple of 4 entries (val 0, col = the row's last column) so
-// that one lane reads 4 entries with one 16-byte load of each array.
+// Every row is padded to a multiple of 4 entries (val 0, col = the row's last column).
+// The SpMV kernels read a SELL-32 copy of each (see below); the CSR form is what
+// eptv_copy_matrix exports.
 //   P^T: rows = pixels j = iy nx + ix, columns = rays i = v nb + k in increasing order.
 //   P:   rows = rays, columns = pixels in increasing order -- the exact transpose of P^T
 //        (same values, same set of nonzeros), made by a counting transpose and a
@@ -226,13 +227,124 @@ k_sort_rows(int rows, const int *__restrict__ ptr, const int *__restrict__ cnt,
 
 // ---------------------------------------------------------------- SpMV
 
-// y = P x: one warp per ray; each lane streams 4 entries per step (16-byte loads of col
-// and val, evict-first), gathers x from L2, the warp sums in a fixed shuffle tree.
-// Same output selection, residual mode and fused |out|^2 reduction as K1.
+// Both kernels read a SELL-32 copy of their matrix (sliced ELLPACK): a slice holds 32
+// rows, entry j of the row in lane l sits at sptr[s] + 32 j + l, and every row of slice s
+// has slen[s] entries (zero-padded).  A lane owns a row, so each load of the stream is one
+// 128-byte line per array, and the 32 rows gathered for at step j are neighbours -- the
+// access pattern of the on-the-fly K1 / K2:
+//   P:   slice s = rays 32 s .. 32 s + 31 (adjacent bins).  A shallow ray's columns are
+//        stored as transposed pixel indices ix ny + iy (sorted in that order) and gathered
+//        from the transposed image, like K1 does, so adjacent bins meet adjacent words.
+//   P^T: slice (iy, sx) = pixels ix = 32 sx .. 32 sx + 31 of image row iy.
+// A lane sums its row in entry order (deterministic).
+constexpr int kSpmvUnroll = 4;      // entries per lane whose loads are issued together
+
+__device__ __forceinline__ bool ray_is_steep(const RayRec &R, float dx, float dy) {
+    return fabsf(R.ix) * dx >= fabsf(R.iy) * dy;      // the K1 criterion
+}
+
+// Row index of lane l of slice sl: linear slicing (width 0: rows 32 sl + l) or row-aligned
+// slicing of an image with rows of `width` entries; -1 for a lane past the end.
+__device__ __forceinline__ int sell_row(int sl, int l, int rows, int width) {
+    if (width == 0) {
+        const int r = sl * 32 + l;
+        return r < rows ? r : -1;
+    }
+    const int spr = (width + 31) >> 5;
+    const int iy = sl / spr, ix = (sl - iy * spr) * 32 + l;
+    return (ix < width && iy * width < rows) ? iy * width + ix : -1;
+}
+
+// REMAP: columns are transposed pixel indices c = ix ny + iy to be read from the
+// natural image (no transposed copy given): index (c % ny) nx + c / ny.
+// PIPE (long rows): software-pipelined, the loads of the next kSpmvUnroll entries are in
+// flight while the current ones gather from the vector, so the stream does not wait for
+// the gathers.  Short rows (P^T) run faster without the extra prologue loads.
+template <bool REMAP, bool PIPE>
+__device__ __forceinline__ float sell_row_dot(const int *__restrict__ scol, const float *__restrict__ sval,
+                                              int base, int len, int lane, const float *__restrict__ x,
+                                              int nx, int ny) {
+    float acc = 0.0f;
+    if (!PIPE) {
+        for (int j0 = 0; j0 < len; j0 += kSpmvUnroll) {
+            int c[kSpmvUnroll];
+            float v[kSpmvUnroll];
+#pragma unroll
+            for (int u = 0; u < kSpmvUnroll; ++u) {
+                const int j = j0 + u;
+                if (j < len) {
+                    const int idx = base + 32 * j + lane;
+                    c[u] = __ldcs(scol + idx);
+                    v[u] = __ldcs(sval + idx);
+                } else {
+                    c[u] = 0;
+                    v[u] = 0.0f;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kSpmvUnroll; ++u) {
+                int k = c[u];
+                if (REMAP) { const int ix = k / ny; k = (k - ix * ny) * nx + ix; }
+                acc = fmaf(v[u], __ldg(x + k), acc);
+            }
+        }
+        return acc;
+    }
+    // guarded loads as if / else: the conditional-expression form compiled to a loop
+    // that ran the back projection at half the speed
+    int c[kSpmvUnroll];
+    float v[kSpmvUnroll];
+#pragma unroll
+    for (int u = 0; u < kSpmvUnroll; ++u) {
+        if (u < len) {
+            c[u] = __ldcs(scol + base + 32 * u + lane);
+            v[u] = __ldcs(sval + base + 32 * u + lane);
+        } else {
+            c[u] = 0;
+            v[u] = 0.0f;
+        }
+    }
+    for (int j0 = 0; j0 < len; j0 += kSpmvUnroll) {
+        int cn[kSpmvUnroll];
+        float vn[kSpmvUnroll];
+#pragma unroll
+        for (int u = 0; u < kSpmvUnroll; ++u) {
+            const int j = j0 + kSpmvUnroll + u;
+            if (j < len) {
+                cn[u] = __ldcs(scol + base + 32 * j + lane);
+                vn[u] = __ldcs(sval + base + 32 * j + lane);
+            } else {
+                cn[u] = 0;
+                vn[u] = 0.0f;
+            }
+        }
+        float xv[kSpmvUnroll];
+#pragma unroll
+        for (int u = 0; u < kSpmvUnroll; ++u) {
+            int k = c[u];
+            if (REMAP) { const int ix = k / ny; k = (k - ix * ny) * nx + ix; }
+            xv[u] = __ldg(x + k);
+        }
+#pragma unroll
+        for (int u = 0; u < kSpmvUnroll; ++u) {
+            acc = fmaf(v[u], xv[u], acc);
+            c[u] = cn[u];
+            v[u] = vn[u];
+        }
+    }
+    return acc;
+}
+
+// y = P x (rows = rays).  Rays are long (hundreds of entries) and few (a slice per 32
+// rays), so a block of 8 warps shares one slice: warp w streams the w-th eighth of the
+// slice's entries and the 8 partial sums are added in warp order.  Same image selection
+// (with its transposed copy), output selection, residual mode and fused |out|^2
+// reduction as K1.
 __global__ void __launch_bounds__(256)
 k_spmv_p(const SliceDev *__restrict__ sls, TileMap map, ProjArgs a, unsigned int *__restrict__ counters,
          double *__restrict__ partials)
 {
+    __shared__ float part[8][32];
     __shared__ double rsm[2 * 8];
     __shared__ double res[2];
     __shared__ int last_flag;
@@ -240,31 +352,37 @@ k_spmv_p(const SliceDev *__restrict__ sls, TileMap map, ProjArgs a, unsigned int
     const int si = find_slice(map, blockIdx.x, &local);
     const SliceDev &S = sls[si];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int row = local * 8 + warp;
-    const float *x = a.img_override ? a.img_override : (a.img == IMG_U ? S.u : S.s);
+    const int slice = local;
+    const int row = slice * 32 + lane;
+    const float *x, *xT;
+    if (a.img_override) { x = a.img_override; xT = a.imgT_override; }
+    else if (a.img == IMG_U) { x = S.u; xT = a.no_T ? nullptr : S.uT; }
+    else { x = S.s; xT = a.no_T ? nullptr : S.sT; }
     float *out = a.out_override ? a.out_override : (a.out == SINO_R ? S.r : S.q);
-    float sq = 0.0f, ysum = 0.0f;
+    float acc = 0.0f;
     if (row < S.n_rays) {
-        const int b = __ldg(S.p_ptr + row) >> 2, e = __ldg(S.p_ptr + row + 1) >> 2;
-        const int4 *c4 = reinterpret_cast<const int4 *>(S.p_col);
-        const float4 *v4 = reinterpret_cast<const float4 *>(S.p_val);
-        float acc = 0.0f;
-        for (int gi = b + lane; gi < e; gi += 32) {
-            const int4 c = __ldcs(c4 + gi);
-            const float4 v = __ldcs(v4 + gi);
-            acc = fmaf(v.x, __ldg(x + c.x), acc);
-            acc = fmaf(v.y, __ldg(x + c.y), acc);
-            acc = fmaf(v.z, __ldg(x + c.z), acc);
-            acc = fmaf(v.w, __ldg(x + c.w), acc);
-        }
-        acc = warp_sum(acc);
-        if (lane == 0) {
-            float o = acc;
-            if (a.resid) o = __ldg((a.y_override ? a.y_override : S.y) + row) - acc;
-            out[row] = o;
-            sq = o * o;
-            ysum = o;
-        }
+        const int len = __ldg(S.p_slen + slice);
+        const int chunk = (len + 7) >> 3;
+        const int j0 = min(len, warp * chunk), j1 = min(len, j0 + chunk);
+        const int base = __ldg(S.p_sptr + slice) + 32 * j0;
+        const bool steep = ray_is_steep(S.ray[row], S.dx, S.dy);
+        if (steep || xT)     // one loop for the whole warp, lanes differ only in the source
+            acc = sell_row_dot<false, true>(S.p_scol, S.p_sval, base, j1 - j0, lane, steep ? x : xT, S.nx, S.ny);
+        else
+            acc = sell_row_dot<true, true>(S.p_scol, S.p_sval, base, j1 - j0, lane, x, S.nx, S.ny);
+    }
+    part[warp][lane] = acc;
+    __syncthreads();
+    float sq = 0.0f, ysum = 0.0f;
+    if (warp == 0 && row < S.n_rays) {
+        float tot = 0.0f;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) tot += part[w][lane];
+        float o = tot;
+        if (a.resid) o = __ldg((a.y_override ? a.y_override : S.y) + row) - tot;
+        out[row] = o;
+        sq = o * o;
+        ysum = o;
     }
     if (a.fin == FIN_NONE) return;
     const int b0 = __ldg(map.start + si);
@@ -276,53 +394,49 @@ k_spmv_p(const SliceDev *__restrict__ sls, TileMap map, ProjArgs a, unsigned int
     if (threadIdx.x == 0) finalize(S.sc, a.fin, res[0], res[1]);
 }
 
-// x = P^T y: 8 lanes per pixel row (rows hold ~2 rays per view), 32 pixels per block.
-// Same output selection and fused |out|^2 reduction as K2 (no transposed copy: the
-// stored operator never reads one).
+// x = P^T y (rows = pixels).  A block covers a 32 x 8 pixel tile (warp = one image row of
+// 32 pixels = one slice).  Same output selection, transposed copy (through a shared-memory
+// tile, 8 consecutive rows per column) and fused |out|^2 reduction as K2.
 __global__ void __launch_bounds__(256)
 k_spmv_pt(const SliceDev *__restrict__ sls, TileMap map, BackArgs a, unsigned int *__restrict__ counters,
           double *__restrict__ partials)
 {
+    __shared__ float tile[8][33];
     __shared__ double rsm[2 * 8];
     __shared__ double res[2];
     __shared__ int last_flag;
     int local;
     const int si = find_slice(map, blockIdx.x, &local);
     const SliceDev &S = sls[si];
-    const int sub = threadIdx.x & 7;
-    const int row = local * 32 + (threadIdx.x >> 3);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int spr = (S.nx + 31) >> 5;
+    const int ty = local / spr, sx = local - ty * spr;
+    const int iy = ty * 8 + warp, ix = sx * 32 + lane;
+    const int slice = iy * spr + sx;
     const float *in = a.in_override ? a.in_override : S.r;
-    float *out;
+    float *out, *outT = nullptr;
     if (a.out_override) out = a.out_override;
-    else if (a.out == 0) out = S.s;
+    else if (a.out == 0) { out = S.s; if (a.write_T) outT = S.sT; }
     else if (a.out == 1) out = S.t;
-    else out = S.u;
+    else { out = S.u; if (a.write_T) outT = S.uT; }
     float acc = 0.0f;
-    if (row < S.n_pix) {
-        const int b = __ldg(S.pt_ptr + row) >> 2, e = __ldg(S.pt_ptr + row + 1) >> 2;
-        const int4 *c4 = reinterpret_cast<const int4 *>(S.pt_col);
-        const float4 *v4 = reinterpret_cast<const float4 *>(S.pt_val);
-        for (int gi = b + sub; gi < e; gi += 8) {
-            const int4 c = __ldcs(c4 + gi);
-            const float4 v = __ldcs(v4 + gi);
-            acc = fmaf(v.x, __ldg(in + c.x), acc);
-            acc = fmaf(v.y, __ldg(in + c.y), acc);
-            acc = fmaf(v.z, __ldg(in + c.z), acc);
-            acc = fmaf(v.w, __ldg(in + c.w), acc);
-        }
+    const bool valid = iy < S.ny && ix < S.nx;
+    if (valid) {
+        acc = sell_row_dot<false, false>(S.pt_scol, S.pt_sval, __ldg(S.pt_sptr + slice),
+                                         __ldg(S.pt_slen + slice), lane, in, S.nx, S.ny);
+        out[(size_t)iy * S.nx + ix] = acc;
     }
-    acc += __shfl_xor_sync(0xffffffffu, acc, 4);
-    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-    float sq = 0.0f;
-    if (sub == 0 && row < S.n_pix) {
-        out[row] = acc;
-        sq = acc * acc;
+    if (outT) {
+        tile[warp][lane] = acc;
+        __syncthreads();
+        const int cx = threadIdx.x >> 3, ry = threadIdx.x & 7;
+        const int gx = sx * 32 + cx, gy = ty * 8 + ry;
+        if (gx < S.nx && gy < S.ny) outT[(size_t)gx * S.ny + gy] = tile[ry][cx];
     }
     if (a.fin == FIN_NONE) return;
     const int b0 = __ldg(map.start + si);
     const int nblk = __ldg(map.start + si + 1) - b0;
-    float vals[1] = {sq};
+    float vals[1] = {valid ? acc * acc : 0.0f};
     block_sum_to<1, 256>(vals, partials + (size_t)blockIdx.x * 2, rsm);
     if (threadIdx.x == 0) partials[(size_t)blockIdx.x * 2 + 1] = 0.0;
     if (!last_block_of_slice(counters + si, nblk, &last_flag)) return;
@@ -344,9 +458,102 @@ void launch_spmv_pt(const Batch &B, const BackArgs &a, cudaStream_t st) {
     k_spmv_pt<<<nblk, 256, 0, st>>>(B.d_sd, B.map(FAM_SPMV_PT), a, B.d_counters, B.d_partials);
 }
 
+// ---------------------------------------------------------------- CSR -> SELL-32
+
+// Real entries of each row of a padded CSR matrix (padding: < 4 trailing zeros).
+__global__ void __launch_bounds__(256)
+k_row_real(int rows, const int *__restrict__ ptr, const float *__restrict__ val, int *__restrict__ cnt)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= rows) return;
+    const int b = ptr[r];
+    int e = ptr[r + 1];
+    while (e > b && val[e - 1] == 0.0f) --e;
+    cnt[r] = e - b;
+}
+
+// slen[s] = longest row of slice s; w[s] = 32 slen[s] (the slice's stored entries).
+__global__ void __launch_bounds__(256)
+k_slice_len(int n_sl, int rows, int width, const int *__restrict__ cnt, int *__restrict__ slen,
+            int *__restrict__ w)
+{
+    const int sl = blockIdx.x * blockDim.x + threadIdx.x;
+    if (sl >= n_sl) return;
+    int m = 0;
+    for (int l = 0; l < 32; ++l) {
+        const int r = sell_row(sl, l, rows, width);
+        if (r >= 0) m = max(m, cnt[r]);
+    }
+    slen[sl] = m;
+    w[sl] = 32 * m;
+}
+
+// Row sell_row(s, l) of the CSR matrix into lane l of slice s; the padding repeats the
+// row's last column with value 0 (lanes past the end: column 0).
+__global__ void __launch_bounds__(256)
+k_fill_sell(int n_sl, int rows, int width, const int *__restrict__ ptr, const int *__restrict__ cnt,
+            const int *__restrict__ col, const float *__restrict__ val, const int *__restrict__ sptr,
+            const int *__restrict__ slen, int *__restrict__ scol, float *__restrict__ sval)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int sl = (int)(t >> 5), l = (int)(t & 31);
+    if (sl >= n_sl) return;
+    const int r = sell_row(sl, l, rows, width);
+    const int base = sptr[sl], len = slen[sl];
+    const int n = (r >= 0) ? cnt[r] : 0;
+    const int b = (r >= 0) ? ptr[r] : 0;
+    const int last = n > 0 ? col[b + n - 1] : 0;
+    for (int j = 0; j < len; ++j) {
+        scol[base + 32 * j + l] = (j < n) ? col[b + j] : last;
+        sval[base + 32 * j + l] = (j < n) ? val[b + j] : 0.0f;
+    }
+}
+
+// Shallow rays of P (the K1 criterion): columns to transposed pixel indices ix ny + iy.
+__global__ void __launch_bounds__(256)
+k_transpose_shallow(const SliceDev *__restrict__ sd, const int *__restrict__ ptr, const int *__restrict__ cnt,
+                    int *__restrict__ col)
+{
+    const SliceDev &S = *sd;
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= S.n_rays) return;
+    if (ray_is_steep(S.ray[r], S.dx, S.dy)) return;
+    const int b = ptr[r];
+    for (int e = b; e < b + cnt[r]; ++e) {
+        const int c = col[e];
+        const int iy = c / S.nx, ix = c - iy * S.nx;
+        col[e] = ix * S.ny + iy;
+    }
+}
+
 // ---------------------------------------------------------------- build driver
 
 static unsigned nb256(long long n) { return (unsigned)((n + 255) / 256); }
+
+// SELL-32 copy of a padded, row-sorted CSR matrix (width: 0 for linear slicing, else the
+// image row length for row-aligned slicing; tmp_cnt: rows ints, tmp_w: slices + 1 ints,
+// tot: one long long; all device scratch).
+static cudaError_t to_sell(int rows, int width, const int *ptr, const int *col, const float *val,
+                           StoredAlloc alloc, void *ctx, int **sptr, int **slen, int **scol, float **sval,
+                           long long *total, int *tmp_cnt, int *tmp_w, long long *tot, cudaStream_t st) {
+    const int n_sl = width ? (rows / width) * ((width + 31) / 32) : (rows + 31) / 32;
+    cudaError_t e;
+    if ((e = alloc(ctx, (void **)slen, sizeof(int) * (size_t)std::max(n_sl, 1))) != cudaSuccess) return e;
+    if ((e = alloc(ctx, (void **)sptr, sizeof(int) * ((size_t)n_sl + 1))) != cudaSuccess) return e;
+    k_row_real<<<nb256(rows), 256, 0, st>>>(rows, ptr, val, tmp_cnt);
+    k_slice_len<<<nb256(n_sl), 256, 0, st>>>(n_sl, rows, width, tmp_cnt, *slen, tmp_w);
+    k_scan_exclusive<<<1, 1024, 0, st>>>(tmp_w, *sptr, n_sl, tot);
+    long long h_tot = 0;
+    if ((e = cudaMemcpyAsync(&h_tot, tot, sizeof h_tot, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+    if (h_tot >= (1LL << 31) - 32) return cudaErrorInvalidValue;
+    *total = h_tot;
+    if ((e = alloc(ctx, (void **)scol, sizeof(int) * (size_t)std::max(h_tot, 32LL))) != cudaSuccess) return e;
+    if ((e = alloc(ctx, (void **)sval, sizeof(float) * (size_t)std::max(h_tot, 32LL))) != cudaSuccess) return e;
+    k_fill_sell<<<nb256((long long)n_sl * 32), 256, 0, st>>>(n_sl, rows, width, ptr, tmp_cnt, col, val, *sptr,
+                                                            *slen, *scol, *sval);
+    return cudaGetLastError();
+}
 
 // Builds both matrices of the slice described by d_sd (device copy of `S`, whose ray and
 // view tables are set).  Allocation goes through `alloc` (owned by the caller).  Returns
@@ -355,7 +562,8 @@ static unsigned nb256(long long n) { return (unsigned)((n + 255) / 256); }
 cudaError_t build_stored(const SliceDev &S, const SliceDev *d_sd, StoredAlloc alloc, void *ctx,
                          StoredMatrices *m, cudaStream_t st) {
     const int n_pix = S.n_pix, n_rays = S.n_rays;
-    int *cnt = nullptr, *cnt4 = nullptr, *cursor = nullptr;
+    int *cnt = nullptr, *cnt4 = nullptr, *cursor = nullptr, *w = nullptr, *tcol = nullptr;
+    float *tval = nullptr;
     long long *tot = nullptr;
     cudaError_t e;
     long long h_tot = 0;
@@ -364,6 +572,8 @@ cudaError_t build_stored(const SliceDev &S, const SliceDev *d_sd, StoredAlloc al
     TRY(cudaMalloc(&cnt4, sizeof(int) * (size_t)(n_rays + 1)));
     TRY(cudaMalloc(&cursor, sizeof(int) * (size_t)n_rays));
     TRY(cudaMalloc(&tot, sizeof(long long)));
+    // slice widths: (n_rays + 31) / 32 slices of P, ny * ceil(nx / 32) of P^T
+    TRY(cudaMalloc(&w, sizeof(int) * (size_t)(std::max((n_rays + 31) / 32, S.ny * ((S.nx + 31) / 32)) + 2)));
     // P^T: padded row lengths, offsets, entries
     TRY(alloc(ctx, (void **)&m->pt_ptr, sizeof(int) * ((size_t)n_pix + 1)));
     k_pt_rows<false><<<nb256(n_pix), 256, 0, st>>>(d_sd, cnt, nullptr, nullptr, nullptr);
@@ -400,6 +610,18 @@ cudaError_t build_stored(const SliceDev &S, const SliceDev *d_sd, StoredAlloc al
                                               m->p_col, m->p_val);
     k_sort_rows<<<n_rays, 256, 0, st>>>(n_rays, m->p_ptr, cnt, m->p_col, m->p_val);
     TRY(cudaGetLastError());
+    // SELL-32 copies for the SpMV kernels.  P: a copy whose shallow rows hold transposed
+    // pixel indices, re-sorted; P^T: row-aligned slices of the image.
+    TRY(cudaMalloc(&tcol, sizeof(int) * (size_t)std::max(m->nnz_p, 4LL)));
+    TRY(cudaMalloc(&tval, sizeof(float) * (size_t)std::max(m->nnz_p, 4LL)));
+    TRY(cudaMemcpyAsync(tcol, m->p_col, sizeof(int) * (size_t)m->nnz_p, cudaMemcpyDeviceToDevice, st));
+    TRY(cudaMemcpyAsync(tval, m->p_val, sizeof(float) * (size_t)m->nnz_p, cudaMemcpyDeviceToDevice, st));
+    k_transpose_shallow<<<nb256(n_rays), 256, 0, st>>>(d_sd, m->p_ptr, cnt, tcol);
+    k_sort_rows<<<n_rays, 256, 0, st>>>(n_rays, m->p_ptr, cnt, tcol, tval);
+    TRY(to_sell(n_rays, 0, m->p_ptr, tcol, tval, alloc, ctx, &m->p_sptr, &m->p_slen, &m->p_scol,
+                &m->p_sval, &m->sell_p, cnt, w, tot, st));
+    TRY(to_sell(n_pix, S.nx, m->pt_ptr, m->pt_col, m->pt_val, alloc, ctx, &m->pt_sptr, &m->pt_slen,
+                &m->pt_scol, &m->pt_sval, &m->sell_pt, cnt, w, tot, st));
     TRY(cudaStreamSynchronize(st));
 done:
 #undef TRY
@@ -407,6 +629,9 @@ done:
     cudaFree(cnt4);
     cudaFree(cursor);
     cudaFree(tot);
+    cudaFree(w);
+    cudaFree(tcol);
+    cudaFree(tval);
     return e;
 }
 

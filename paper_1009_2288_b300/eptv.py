@@ -132,7 +132,8 @@ def load():
                                    vp, vp, vp, c_int, c_int, vp, vp, vp, vp]),
         "eptv_unet_pack_input": (c_int, [vp, ctypes.c_float, vp, ctypes.c_float, ctypes.c_longlong, vp, vp]),
         "eptv_set_operator": (c_int, [vp, c_int, ctypes.POINTER(ctypes.c_longlong)]),
-        "eptv_matrix_info": (c_int, [vp, c_int, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
+        "eptv_matrix_info": (c_int, [vp, c_int, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
+                                     ctypes.POINTER(ctypes.c_longlong)]),
         "eptv_copy_matrix": (c_int, [vp, c_int, vp, vp, vp, vp]),
         "eptv_unet_adam": (c_int, [vp, vp, vp, vp, ctypes.c_longlong, ctypes.c_float, ctypes.c_float,
                                    ctypes.c_float, ctypes.c_float, c_int, vp]),
@@ -351,11 +352,19 @@ def eptv_set_operator(geom: Geometry, mode: int) -> int:
     return nnz.value
 
 
+def eptv_matrix_info(geom: Geometry, which: int):
+    """(rows, CSR entries incl. padding, SELL-32 entries) of the built P (which = 0) or P^T (1)."""
+    rows, nnz, sell = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
+    _check(load().eptv_matrix_info(geom.handle, int(which), ctypes.byref(rows), ctypes.byref(nnz),
+                                   ctypes.byref(sell)))
+    return rows.value, nnz.value, sell.value
+
+
 def eptv_matrix(geom: Geometry, which: int):
     """(ptr, col, val) device tensors: a copy of the stored P (which = 0) or P^T (1)."""
     import torch
-    rows, nnz = ctypes.c_longlong(), ctypes.c_longlong()
-    _check(load().eptv_matrix_info(geom.handle, int(which), ctypes.byref(rows), ctypes.byref(nnz)))
+    rows, nnz, _ = eptv_matrix_info(geom, which)
+    rows, nnz = ctypes.c_longlong(rows), ctypes.c_longlong(nnz)
     ptr = torch.empty(rows.value + 1, dtype=torch.int32, device="cuda")
     col = torch.empty(max(nnz.value, 1), dtype=torch.int32, device="cuda")
     val = torch.empty(max(nnz.value, 1), dtype=torch.float32, device="cuda")

@@ -18,8 +18,7 @@ namespace eptv {
 
 template <int VG>
 __global__ void __launch_bounds__(128 * VG)
-k2_backproject(const SliceDev *__restrict__ sls, TileMap map, BackArgs a,
-               unsigned int *__restrict__ counters, double *__restrict__ partials)
+k2_backproject(const SliceDev *__restrict__ sls, TileMap map, BackArgs a, double *__restrict__ partials)
 {
     constexpr int NT = 128 * VG;
     __shared__ float4 part[VG > 1 ? VG - 1 : 1][128];
@@ -145,8 +144,7 @@ k2_backproject(const SliceDev *__restrict__ sls, TileMap map, BackArgs a,
     float vals[1] = {sq};
     block_sum_to<1, NT>(vals, partials + (size_t)blockIdx.x * 2, rsm);
     if (threadIdx.x == 0) partials[(size_t)blockIdx.x * 2 + 1] = 0.0;
-    if (!last_block_of_slice(counters + si, nblk, &last_flag)) return;
-    last_block_sum<2, NT>(partials, 2, b0, nblk, rsm, res);
+    if (!reduce_slice<2, NT>(S, partials, 2, b0, nblk, local, rsm, res, &last_flag)) return;
     if (threadIdx.x == 0) finalize(S.sc, a.fin, res[0], res[1]);
 }
 
@@ -155,10 +153,10 @@ void launch_backproject(const Batch &B, const BackArgs &a, cudaStream_t st) {
     if (nblk == 0) return;
     ++g_launch_count;
     switch (B.k2_vg) {
-    case 1: k2_backproject<1><<<nblk, 128, 0, st>>>(B.d_sd, B.map(FAM_K2), a, B.d_counters, B.d_partials); break;
-    case 2: k2_backproject<2><<<nblk, 256, 0, st>>>(B.d_sd, B.map(FAM_K2), a, B.d_counters, B.d_partials); break;
-    case 8: k2_backproject<8><<<nblk, 1024, 0, st>>>(B.d_sd, B.map(FAM_K2), a, B.d_counters, B.d_partials); break;
-    default: k2_backproject<4><<<nblk, 512, 0, st>>>(B.d_sd, B.map(FAM_K2), a, B.d_counters, B.d_partials); break;
+    case 1: k2_backproject<1><<<nblk, 128, 0, st>>>(B.d_sd, B.map(FAM_K2), a, B.d_partials); break;
+    case 2: k2_backproject<2><<<nblk, 256, 0, st>>>(B.d_sd, B.map(FAM_K2), a, B.d_partials); break;
+    case 8: k2_backproject<8><<<nblk, 1024, 0, st>>>(B.d_sd, B.map(FAM_K2), a, B.d_partials); break;
+    default: k2_backproject<4><<<nblk, 512, 0, st>>>(B.d_sd, B.map(FAM_K2), a, B.d_partials); break;
     }
 }
 

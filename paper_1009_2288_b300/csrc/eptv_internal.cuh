@@ -100,6 +100,10 @@ struct SliceDev {
     double *log;         // optional per-iteration log: [n_outer * n_gd] steps, then [n_outer] sigmas
     int log_outer;       // capacity in outer iterations (0: no log)
     int log_gd;          // GD iterations per outer iteration in the log layout
+    // reduction bookkeeping of this slice in its batch: ticket counters ([0] final level,
+    // [1 + g] group g) and the group partial sums ([group][kPartialStride] doubles)
+    unsigned int *ctr;
+    double *gpart;
     // stored operator (null unless selected): SELL-32 P (rows = rays), P^T (rows = pixels)
     const int *p_sptr, *p_slen, *p_scol;
     const float *p_sval;
@@ -168,48 +172,63 @@ __device__ __forceinline__ bool last_block_of_slice(unsigned int *counter, int n
     return *flag_smem != 0;
 }
 
-// All NT threads of the finishing block: sum NV partials of blocks [b0, b0 + nb)
-// (row stride `stride` doubles) into res[0..NV) (shared memory, valid after the call in
-// every thread).  Thread t sums blocks t, t + NT, ... in increasing order, warps reduce
-// with a fixed shuffle tree and the warp results are added in warp order, so the
-// result is deterministic.  The loads of four blocks are issued together so that the
-// tail runs at L2 bandwidth rather than one round trip per partial.
+// Blocks per first-level group of the two-level reduction below; doubles per block (and
+// per group) in the partial-sum arrays.
+constexpr int kRedGroup = 32;
+constexpr int kMaxTrials = 16;
+constexpr int kPartialStride = kMaxTrials + 8;
+
+// All NT threads of a finishing block: res[k] = sum over blocks first .. first + count - 1
+// of src[block * stride + k], k < NV (NV <= 32), as a fixed-shape tree, so the result is
+// deterministic.  FP64 adds have a long latency on this GPU, so the tree is wide rather than
+// deep: thread t takes value k = t % NVP (NVP = NV rounded up to a power of two) and blocks
+// j, j + J, ... (j = t / NVP, J = NT / NVP); the threads of a warp that hold the same k
+// combine by shuffles, and thread k adds the NT/32 warp results.
 template <int NV, int NT>
-__device__ __forceinline__ void last_block_sum(const double *partials, int stride, int b0, int nb,
-                                               double *rsm /* NV * NT/32 */, double *res /* NV */) {
-    double acc[NV];
-#pragma unroll
-    for (int k = 0; k < NV; ++k) acc[k] = 0.0;
-    int b = threadIdx.x;
-    for (; b + 3 * NT < nb; b += 4 * NT) {
-        double v[4][NV];
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int k = 0; k < NV; ++k) v[u][k] = __ldcg(partials + (size_t)(b0 + b + u * NT) * stride + k);
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int k = 0; k < NV; ++k) acc[k] += v[u][k];
+__device__ __forceinline__ void group_sum(const double *src, int stride, int first, int count,
+                                          double *wpart /* NV * NT/32, smem */, double *res /* NV */) {
+    constexpr int NVP = NV <= 1 ? 1 : NV <= 2 ? 2 : NV <= 4 ? 4 : NV <= 8 ? 8 : NV <= 16 ? 16 : 32;
+    constexpr int J = NT / NVP, NW = NT / 32;
+    const int t = threadIdx.x, k = t % NVP, j = t / NVP;
+    double a = 0.0;
+    if (k < NV) {
+        int b = j;
+        if (b < count) a = __ldcg(src + (size_t)(first + b) * stride + k);
+        for (b += J; b < count; b += J) a += __ldcg(src + (size_t)(first + b) * stride + k);
     }
-    for (; b < nb; b += NT)
 #pragma unroll
-        for (int k = 0; k < NV; ++k) acc[k] += __ldcg(partials + (size_t)(b0 + b) * stride + k);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-        double a = acc[k];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-        if (lane == 0) rsm[k * (NT / 32) + w] = a;
+    for (int o = NVP; o < 32; o <<= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    const int lane = t & 31, w = t >> 5;
+    if (lane < NV) wpart[w * NV + lane] = a;
+    __syncthreads();
+    if (t < NV) {
+        double r = 0.0;
+        for (int i = 0; i < NW; ++i) r += wpart[i * NV + t];
+        res[t] = r;
     }
     __syncthreads();
-    if (threadIdx.x < NV) {
-        double a = 0.0;
-        for (int i = 0; i < NT / 32; ++i) a += rsm[threadIdx.x * (NT / 32) + i];
-        res[threadIdx.x] = a;
-    }
-    __syncthreads();
+}
+
+// Two-level deterministic reduction of the NV per-block partial sums that the nblk blocks
+// of a slice wrote to partials[b0 + lb][0 .. NV) (row stride `stride`), lb = the calling
+// block's index within the slice.  Every kRedGroup consecutive blocks form a group: the
+// block of a group that finishes last (atomic ticket) sums the group in block order and
+// stores the result in S.gpart; the group finisher that comes last sums the group results
+// in group order.  Returns true only in that block, with the totals in res (smem).
+// Spreads the FP64 work over nblk / kRedGroup SMs instead of one.
+template <int NV, int NT>
+__device__ __forceinline__ bool reduce_slice(const SliceDev &S, const double *partials, int stride, int b0,
+                                             int nblk, int lb, double *wpart, double *res, int *flag) {
+    const int ng = (nblk + kRedGroup - 1) / kRedGroup;
+    const int g = lb / kRedGroup;
+    const int gsize = min(kRedGroup, nblk - g * kRedGroup);
+    if (!last_block_of_slice(S.ctr + 1 + g, gsize, flag)) return false;
+    group_sum<NV, NT>(partials, stride, b0 + g * kRedGroup, gsize, wpart, res);
+    if (ng == 1) return true;
+    if (threadIdx.x < NV) S.gpart[(size_t)g * kPartialStride + threadIdx.x] = res[threadIdx.x];
+    if (!last_block_of_slice(S.ctr, ng, flag)) return false;
+    group_sum<NV, NT>(S.gpart, kPartialStride, 0, ng, wpart, res);
+    return true;
 }
 
 // ---------------------------------------------------------------------------------

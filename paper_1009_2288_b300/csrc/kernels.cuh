@@ -24,8 +24,6 @@ enum Family {
 constexpr int kTileW = 32, kTileH = 16;
 constexpr int kGdTileRows = 8;
 constexpr int kHistBins = 4096;    // radix-select histogram (12 bits per pass)
-constexpr int kMaxTrials = 16;
-constexpr int kPartialStride = kMaxTrials + 8;   // doubles per block in the partials array
 
 // Finalisers run by the last block of a reduction.
 enum Fin {
@@ -65,7 +63,8 @@ struct Batch {
     std::vector<SliceDev> h_sd;
     int *d_start = nullptr;         // [FAM_COUNT][n + 1]
     std::vector<int> h_start;
-    unsigned int *d_counters = nullptr;   // [n]
+    unsigned int *d_counters = nullptr;   // [n][counter stride]: reduction tickets (SliceDev::ctr)
+    double *d_gpart = nullptr;            // [n][groups][kPartialStride]: group sums (SliceDev::gpart)
     double *d_partials = nullptr;         // [max blocks][kPartialStride]
     unsigned int *d_hist = nullptr;       // [n][kHistBins]
     ParamsDev *d_params = nullptr;

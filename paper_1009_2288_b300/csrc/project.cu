@@ -20,8 +20,7 @@ namespace eptv {
 
 template <int SEG>
 __global__ void __launch_bounds__(32 * SEG)
-k1_project(const SliceDev *__restrict__ sls, TileMap map, ProjArgs a,
-           unsigned int *__restrict__ counters, double *__restrict__ partials)
+k1_project(const SliceDev *__restrict__ sls, TileMap map, ProjArgs a, double *__restrict__ partials)
 {
     __shared__ float red[SEG][33];
     __shared__ double rsm[2 * SEG];
@@ -177,8 +176,7 @@ k1_project(const SliceDev *__restrict__ sls, TileMap map, ProjArgs a,
             partials[(size_t)blockIdx.x * 2 + 1] = (double)s2;
         }
     }
-    if (!last_block_of_slice(counters + si, nblk, &last_flag)) return;
-    last_block_sum<2, 32 * SEG>(partials, 2, b0, nblk, rsm, res);
+    if (!reduce_slice<2, 32 * SEG>(S, partials, 2, b0, nblk, local, rsm, res, &last_flag)) return;
     if (threadIdx.x == 0) finalize(S.sc, a.fin, res[0], res[1]);
 }
 
@@ -187,9 +185,9 @@ void launch_project(const Batch &B, const ProjArgs &a, cudaStream_t st) {
     if (nblk == 0) return;
     ++g_launch_count;
     switch (B.k1_seg) {
-    case 4: k1_project<4><<<nblk, 128, 0, st>>>(B.d_sd, B.map(FAM_K1), a, B.d_counters, B.d_partials); break;
-    case 16: k1_project<16><<<nblk, 512, 0, st>>>(B.d_sd, B.map(FAM_K1), a, B.d_counters, B.d_partials); break;
-    default: k1_project<8><<<nblk, 256, 0, st>>>(B.d_sd, B.map(FAM_K1), a, B.d_counters, B.d_partials); break;
+    case 4: k1_project<4><<<nblk, 128, 0, st>>>(B.d_sd, B.map(FAM_K1), a, B.d_partials); break;
+    case 16: k1_project<16><<<nblk, 512, 0, st>>>(B.d_sd, B.map(FAM_K1), a, B.d_partials); break;
+    default: k1_project<8><<<nblk, 256, 0, st>>>(B.d_sd, B.map(FAM_K1), a, B.d_partials); break;
     }
 }
 

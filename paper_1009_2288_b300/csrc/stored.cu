@@ -341,8 +341,7 @@ __device__ __forceinline__ float sell_row_dot(const int *__restrict__ scol, cons
 // (with its transposed copy), output selection, residual mode and fused |out|^2
 // reduction as K1.
 __global__ void __launch_bounds__(256)
-k_spmv_p(const SliceDev *__restrict__ sls, TileMap map, ProjArgs a, unsigned int *__restrict__ counters,
-         double *__restrict__ partials)
+k_spmv_p(const SliceDev *__restrict__ sls, TileMap map, ProjArgs a, double *__restrict__ partials)
 {
     __shared__ float part[8][32];
     __shared__ double rsm[2 * 8];
@@ -389,8 +388,7 @@ k_spmv_p(const SliceDev *__restrict__ sls, TileMap map, ProjArgs a, unsigned int
     const int nblk = __ldg(map.start + si + 1) - b0;
     float vals[2] = {sq, ysum};
     block_sum_to<2, 256>(vals, partials + (size_t)blockIdx.x * 2, rsm);
-    if (!last_block_of_slice(counters + si, nblk, &last_flag)) return;
-    last_block_sum<2, 256>(partials, 2, b0, nblk, rsm, res);
+    if (!reduce_slice<2, 256>(S, partials, 2, b0, nblk, local, rsm, res, &last_flag)) return;
     if (threadIdx.x == 0) finalize(S.sc, a.fin, res[0], res[1]);
 }
 
@@ -398,8 +396,7 @@ k_spmv_p(const SliceDev *__restrict__ sls, TileMap map, ProjArgs a, unsigned int
 // 32 pixels = one slice).  Same output selection, transposed copy (through a shared-memory
 // tile, 8 consecutive rows per column) and fused |out|^2 reduction as K2.
 __global__ void __launch_bounds__(256)
-k_spmv_pt(const SliceDev *__restrict__ sls, TileMap map, BackArgs a, unsigned int *__restrict__ counters,
-          double *__restrict__ partials)
+k_spmv_pt(const SliceDev *__restrict__ sls, TileMap map, BackArgs a, double *__restrict__ partials)
 {
     __shared__ float tile[8][33];
     __shared__ double rsm[2 * 8];
@@ -439,8 +436,7 @@ k_spmv_pt(const SliceDev *__restrict__ sls, TileMap map, BackArgs a, unsigned in
     float vals[1] = {valid ? acc * acc : 0.0f};
     block_sum_to<1, 256>(vals, partials + (size_t)blockIdx.x * 2, rsm);
     if (threadIdx.x == 0) partials[(size_t)blockIdx.x * 2 + 1] = 0.0;
-    if (!last_block_of_slice(counters + si, nblk, &last_flag)) return;
-    last_block_sum<2, 256>(partials, 2, b0, nblk, rsm, res);
+    if (!reduce_slice<2, 256>(S, partials, 2, b0, nblk, local, rsm, res, &last_flag)) return;
     if (threadIdx.x == 0) finalize(S.sc, a.fin, res[0], res[1]);
 }
 
@@ -448,14 +444,14 @@ void launch_spmv_p(const Batch &B, const ProjArgs &a, cudaStream_t st) {
     const int nblk = B.blocks(FAM_SPMV_P);
     if (nblk == 0) return;
     ++g_launch_count;
-    k_spmv_p<<<nblk, 256, 0, st>>>(B.d_sd, B.map(FAM_SPMV_P), a, B.d_counters, B.d_partials);
+    k_spmv_p<<<nblk, 256, 0, st>>>(B.d_sd, B.map(FAM_SPMV_P), a, B.d_partials);
 }
 
 void launch_spmv_pt(const Batch &B, const BackArgs &a, cudaStream_t st) {
     const int nblk = B.blocks(FAM_SPMV_PT);
     if (nblk == 0) return;
     ++g_launch_count;
-    k_spmv_pt<<<nblk, 256, 0, st>>>(B.d_sd, B.map(FAM_SPMV_PT), a, B.d_counters, B.d_partials);
+    k_spmv_pt<<<nblk, 256, 0, st>>>(B.d_sd, B.map(FAM_SPMV_PT), a, B.d_partials);
 }
 
 // ---------------------------------------------------------------- CSR -> SELL-32

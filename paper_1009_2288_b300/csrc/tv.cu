@@ -136,8 +136,7 @@ __device__ unsigned int sel_scan(unsigned int *hist, double *sc, int pass, long 
 // Pass 0 of sigma: T of every half-edge of v -> scratch, histogram of the top 12 bits.
 __global__ void __launch_bounds__(256)
 k5_sigma_edges(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__restrict__ P,
-               const float *v_override, unsigned int *__restrict__ hist_all,
-               unsigned int *__restrict__ counters)
+               const float *v_override, unsigned int *__restrict__ hist_all)
 {
     __shared__ unsigned int sh[kHistBins];
     __shared__ unsigned int s_cnt[256];
@@ -175,15 +174,14 @@ k5_sigma_edges(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *_
     }
     const int b0 = __ldg(map.start + si);
     const int nblk = __ldg(map.start + si + 1) - b0;
-    if (!last_block_of_slice(counters + si, nblk, &last_flag)) return;
+    if (!last_block_of_slice(S.ctr, nblk, &last_flag)) return;
     sel_scan(hist, S.sc, 0, S.sel_rank, s_cnt, &s_res);
 }
 
 // Passes 1, 2 of sigma (on the scratch T array), or passes 0-2 of a generic selection.
 __global__ void __launch_bounds__(256)
 k5_radix_pass(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__restrict__ P,
-              int pass, unsigned int *__restrict__ hist_all, unsigned int *__restrict__ counters,
-              const float *vals_override, long long n_override, long long rank_override,
+              int pass, unsigned int *__restrict__ hist_all, const float *vals_override, long long n_override, long long rank_override,
               float *out_override)
 {
     __shared__ unsigned int sh[kHistBins];
@@ -204,7 +202,8 @@ k5_radix_pass(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__
 #pragma unroll
     for (int q = 0; q < 8; ++q) {               // issue the 8 loads before any atomic
         const long long e = e0 + q * 256 + threadIdx.x;
-        xv[q] = (e < n) ? __ldg(vals + e) : 0.0f;
+        xv[q] = 0.0f;
+        if (e < n) xv[q] = __ldg(vals + e);
     }
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
@@ -219,7 +218,7 @@ k5_radix_pass(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__
     }
     const int b0 = __ldg(map.start + si);
     const int nblk = __ldg(map.start + si + 1) - b0;
-    if (!last_block_of_slice(counters + si, nblk, &last_flag)) return;
+    if (!last_block_of_slice(S.ctr, nblk, &last_flag)) return;
     const long long rank0 = vals_override ? rank_override : S.sel_rank;
     const unsigned int key = sel_scan(hist, S.sc, pass, rank0, s_cnt, &s_res);
     if (pass == 2 && threadIdx.x == 0) {
@@ -252,7 +251,7 @@ constexpr int QYW = GW, QYH = kGdTileH + 3;          // y-edges around the g reg
 template <int KT>
 __global__ void __launch_bounds__(kGdThreads)
 k4_gd(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__restrict__ P, GdArgs ga,
-      int iter, unsigned int *__restrict__ counters, double *__restrict__ partials)
+      int iter, double *__restrict__ partials)
 {
     __shared__ float F[FH][FW];
     __shared__ float W[FH][FW];          // prior map (PRIOR mode only)
@@ -331,7 +330,9 @@ k4_gd(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__restrict
     for (int idx = tid; idx < GH * GW; idx += kGdThreads) {
         const int yy = idx / GW, xx = idx - yy * GW;
         const int i = X0 - 1 + xx, j = Y0 - 1 + yy;
-        V[yy][xx] = (i >= 0 && i < nx && j >= 0 && j < ny) ? __ldg(vv + (size_t)j * nx + i) : 0.0f;
+        float vx = 0.0f;
+        if (i >= 0 && i < nx && j >= 0 && j < ny) vx = __ldg(vv + (size_t)j * nx + i);
+        V[yy][xx] = vx;
     }
     __syncthreads();
 
@@ -485,15 +486,30 @@ k4_gd(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__restrict
     block_sum_to<NV, kGdThreads>(vals, partials + (size_t)blockIdx.x * kPartialStride, rsm);
     const int b0 = __ldg(map.start + si);
     const int nblk = __ldg(map.start + si + 1) - b0;
-    if (!last_block_of_slice(counters + si, nblk, &last_flag)) return;
     __shared__ double tot[NV];
-    last_block_sum<NV, kGdThreads>(partials, kPartialStride, b0, nblk, rsm, tot);
-    {
+    if (!reduce_slice<NV, kGdThreads>(S, partials, kPartialStride, b0, nblk, local, rsm, tot, &last_flag))
+        return;
+    if (tid < 32) {
+        double *sc = S.sc;
+        const double A = tot[0], Bg = tot[1];
+        const double lamd = P->lambda;
+        const double E0 = 0.5 * lamd * tot[2] + tot[3];
+        // Armijo: trial m in lane m, all at once (FP64 latency is long on this GPU); the
+        // accepted step is the first trial that passes, as in a sequential search
+        const bool armijo = !ga.energy_only_fin && P->step_rule != EPTV_STEP_FIXED;
+        double d = 0.0;
+        bool pass = false, nonfinite = false;
+        if (armijo && tid < K) {
+            const double t = s_td[tid];
+            d = lamd * (-t * A + 0.5 * t * t * Bg) + tot[4 + tid];
+            nonfinite = !isfinite(d);
+            pass = d <= -P->armijo_c * t * Bg;
+        }
+        const unsigned pass_mask = __ballot_sync(0xffffffffu, pass);
+        const unsigned bad_mask = __ballot_sync(0xffffffffu, nonfinite);
+        const int acc_m = pass_mask ? __ffs(pass_mask) - 1 : -1;
+        const double dE = __shfl_sync(0xffffffffu, d, acc_m >= 0 ? acc_m : 0);
         if (tid == 0) {
-            double *sc = S.sc;
-            const double A = tot[0], Bg = tot[1];
-            const double lamd = P->lambda;
-            const double E0 = 0.5 * lamd * tot[2] + tot[3];
             bool bad = !isfinite(E0) || !isfinite(A) || !isfinite(Bg);
             if (ga.energy_only_fin) {
                 sc[SC_E_FIRST] = E0;
@@ -506,14 +522,9 @@ k4_gd(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__restrict
                     sc[SC_E_LAST] = E0 + lamd * (-t * A + 0.5 * t * t * Bg) + tot[4];
                     sc[SC_NACC_P2] += 1.0;
                 } else {
-                    int acc_m = -1;
-                    double dE = 0.0;
-                    for (int m = 0; m < K; ++m) {
-                        const double t = s_td[m];
-                        const double d = lamd * (-t * A + 0.5 * t * t * Bg) + tot[4 + m];
-                        if (!isfinite(d)) bad = true;
-                        if (d <= -P->armijo_c * t * Bg) { acc_m = m; dE = d; break; }
-                    }
+                    // trials a sequential search would have evaluated: up to the accepted one
+                    const unsigned seen = acc_m >= 0 ? ((2u << acc_m) - 1u) : ((1u << K) - 1u);
+                    if (bad_mask & seen) bad = true;
                     if (acc_m >= 0) {
                         sc[SC_TSTEP] = s_td[acc_m];
                         sc[SC_TPREV] = s_td[acc_m];
@@ -584,17 +595,17 @@ k4_finish(const SliceDev *__restrict__ sls, TileMap map, int n_gd, const float *
 void launch_sigma(const Batch &B, const float *v_override, cudaStream_t st) {
     ++g_launch_count;
     k5_sigma_edges<<<B.blocks(FAM_EDGE), 256, 0, st>>>(B.d_sd, B.map(FAM_EDGE), B.d_params,
-                                                       v_override, B.d_hist, B.d_counters);
+                                                       v_override, B.d_hist);
     for (int pass = 1; pass <= 2; ++pass, ++g_launch_count)
         k5_radix_pass<<<B.blocks(FAM_EDGE), 256, 0, st>>>(B.d_sd, B.map(FAM_EDGE), B.d_params, pass,
-                                                          B.d_hist, B.d_counters, nullptr, 0, 0,
+                                                          B.d_hist, nullptr, 0, 0,
                                                           nullptr);
 }
 
 void launch_select_generic(const Batch &B, const TileMap &m, int nblk, const float *vals,
                            long long n, long long k, float *out, cudaStream_t st) {
     for (int pass = 0; pass <= 2; ++pass, ++g_launch_count)
-        k5_radix_pass<<<nblk, 256, 0, st>>>(B.d_sd, m, B.d_params, pass, B.d_hist, B.d_counters,
+        k5_radix_pass<<<nblk, 256, 0, st>>>(B.d_sd, m, B.d_params, pass, B.d_hist,
                                             vals, n, k, out);
 }
 
@@ -603,13 +614,13 @@ void launch_gd_iter(const Batch &B, const GdArgs &ga, int iter, cudaStream_t st)
     const int nb = B.blocks(FAM_TV);
     const TileMap m = B.map(FAM_TV);
     if (ga.n_trials <= 1)
-        k4_gd<1><<<nb, kGdThreads, 0, st>>>(B.d_sd, m, B.d_params, ga, iter, B.d_counters, B.d_partials);
+        k4_gd<1><<<nb, kGdThreads, 0, st>>>(B.d_sd, m, B.d_params, ga, iter, B.d_partials);
     else if (ga.n_trials <= 4)
-        k4_gd<4><<<nb, kGdThreads, 0, st>>>(B.d_sd, m, B.d_params, ga, iter, B.d_counters, B.d_partials);
+        k4_gd<4><<<nb, kGdThreads, 0, st>>>(B.d_sd, m, B.d_params, ga, iter, B.d_partials);
     else if (ga.n_trials <= 8)
-        k4_gd<8><<<nb, kGdThreads, 0, st>>>(B.d_sd, m, B.d_params, ga, iter, B.d_counters, B.d_partials);
+        k4_gd<8><<<nb, kGdThreads, 0, st>>>(B.d_sd, m, B.d_params, ga, iter, B.d_partials);
     else
-        k4_gd<16><<<nb, kGdThreads, 0, st>>>(B.d_sd, m, B.d_params, ga, iter, B.d_counters, B.d_partials);
+        k4_gd<16><<<nb, kGdThreads, 0, st>>>(B.d_sd, m, B.d_params, ga, iter, B.d_partials);
 }
 
 void launch_gd_finish(const Batch &B, int n_gd, const float *f0_override, float *out_override,

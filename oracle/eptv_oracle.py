@@ -10,6 +10,8 @@ Functions and the passages they follow:
   rays / project / backproject .... Eq. (1), Sec. 2.1 (p_ij = intersection length,
                                     Siddon), Sec. 3 (fan-beam arc detector); P^T is the
                                     exact transpose (Eq. A3 of App. III, adjoint identity)
+  backproject_eq11 ................ Eq. (11), Sec. 2.3 and App. III: the paper's pixel-driven
+                                    interpolating back projector (an approximation of P^T)
   cgls ............................ App. I (CGLS for (P1), restarted at f^(k))
   half_edges ...................... Eq. (A3), App. II (half-point magnitudes)
   edge_weights .................... Eq. (5)
@@ -34,6 +36,11 @@ Readings of points the paper leaves open (each also listed in the design notes):
     t0 = min(grow * t_prev, t_max); if none passes the step is 0 and the next GD
     iteration continues below the last trial; energy for the test = lambda/2 |f - v|^2
     + sum_e w_e T_e(f) with w frozen at the current GD iterate.
+  * Eq. (11): beta* and l are taken at the pixel centre; y^theta(beta*) is the linear
+    interpolation between the two bins around beta* (bins outside the detector read 0);
+    the paper states the arc detector (uniform in beta); for a flat detector (uniform in
+    t = tan beta) the same change of variables in (A7) gives the weight
+    (du dv / dt) (1 + t*^2) / l.
 """
 from __future__ import annotations
 
@@ -139,6 +146,41 @@ class Operator:
                                     _dp(self.ux), _dp(self.uy), _dp(y), _dp(f))
         assert rc == 0
         return f.reshape(g.ny, g.nx)
+
+
+def backproject_eq11(g, y: np.ndarray) -> np.ndarray:
+    """Eq. (11): [P^T y](u, v) = (du dv / dbeta) sum_theta y^theta(beta*) / l(u, v), with
+    beta* the fan angle of the line from the source through the pixel centre (measured
+    from the central ray, positive counter-clockwise as in rays()), l its length from the
+    source, y^theta(beta*) linearly interpolated between detector bins.  Flat detector:
+    beta* -> t* = tan beta*, weight (du dv / dt) (1 + t*^2) / l (reading in the header)."""
+    y = np.asarray(y, dtype=np.float64).reshape(g.n_views, g.n_bins)
+    xc = (np.arange(g.nx) + 0.5) * g.dx - g.nx * g.dx / 2.0
+    yc = (np.arange(g.ny) + 0.5) * g.dy - g.ny * g.dy / 2.0
+    X, Y = np.meshgrid(xc, yc)                           # [ny][nx] pixel centres
+    out = np.zeros((g.ny, g.nx))
+    kc = (g.n_bins - 1) / 2.0 - g.bin_offset              # bin k sits at (k - kc) dbeta
+    for v, th in enumerate(g.view_angles()):
+        sx, sy = g.sid * math.cos(th), g.sid * math.sin(th)
+        cx, cy = -math.cos(th), -math.sin(th)            # central ray direction
+        wx, wy = X - sx, Y - sy
+        cross = cx * wy - cy * wx                         # |w| sin(beta*)
+        dot = cx * wx + cy * wy                           # |w| cos(beta*)
+        l = np.hypot(wx, wy)
+        if g.detector == 0:
+            u = np.arctan2(cross, dot) / g.dbeta + kc
+            weight = 1.0 / l
+        else:
+            t = cross / dot
+            u = t / g.dbeta + kc
+            weight = (1.0 + t * t) / l
+        k0 = np.floor(u).astype(np.int64)
+        frac = u - k0
+        row = y[v]
+        y0 = np.where((k0 >= 0) & (k0 < g.n_bins), row[np.clip(k0, 0, g.n_bins - 1)], 0.0)
+        y1 = np.where((k0 + 1 >= 0) & (k0 + 1 < g.n_bins), row[np.clip(k0 + 1, 0, g.n_bins - 1)], 0.0)
+        out += ((1.0 - frac) * y0 + frac * y1) * weight
+    return out * (g.dx * g.dy / g.dbeta)
 
 
 def project_rays(nx, ny, dx, dy, sx, sy, ux, uy, f):

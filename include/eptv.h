@@ -66,6 +66,8 @@ extern "C" {
 
 #define EPTV_OPERATOR_ON_THE_FLY 0   /* P, P^T recomputed by the kernels at each use (default) */
 #define EPTV_OPERATOR_STORED     1   /* P, P^T stored as CSR matrices in device memory         */
+#define EPTV_OPERATOR_EQ11       2   /* P on the fly, P^T = the interpolating back projector of
+                                        Eq. (11) (an approximation of the transpose)           */
 
 /* Scan geometry (Sec. 3: fan beam, arc detector). */
 typedef struct {
@@ -159,6 +161,17 @@ int eptv_transpose(const eptv_geometry *g, const float *d_f, float *d_fT, void *
  * each p_ij with the same arithmetic as the projector.  d_f is overwritten. */
 int eptv_backproject(const eptv_geometry *g, const float *d_y, float *d_f, void *stream);
 
+/* The paper's pixel-driven back projector, Eq. (11) (Sec. 2.3, App. III), whatever the
+ * handle's operator mode:
+ *   d_f[iy nx + ix] = (dx dy / dbeta) sum_v y_v(beta*) / l,
+ * beta* = fan angle (from the central ray) of the line from the source of view v through
+ * the pixel centre, l = its length, y_v(beta*) = linear interpolation of d_y[v nb + k]
+ * between the two bins around beta* (bins off the detector read 0).  Flat detector (bins
+ * uniform in t = tan beta): weight (dx dy / dbeta) (1 + t*^2) / l.  It approximates P^T
+ * (the adjoint identity holds to about 1e-5 for smooth inputs, 1e-4 for noise).  The
+ * operator mode EPTV_OPERATOR_EQ11 uses it for every P^T of the handle. */
+int eptv_backproject_eq11(const eptv_geometry *g, const float *d_y, float *d_f, void *stream);
+
 /* M CGLS iterations (App. I) for min |P u - y|^2 started at the content of d_u, which
  * is overwritten with u^(M).  d_y: sinogram.  Uses the handle's workspace. */
 int eptv_cgls(const eptv_geometry *g, int M, const float *d_y, float *d_u, void *stream);
@@ -242,6 +255,9 @@ int eptv_select_kth_noalloc(const float *d_vals, long n, long k, float *d_out, v
  * nonzero of P for both matrices in both forms: CSR for export, SELL-32 for the SpMV);
  * EPTV_OPERATOR_ON_THE_FLY switches back and keeps them.
  * *h_nnz_opt (may be NULL) receives the stored entries of P, padding included.
+ * EPTV_OPERATOR_EQ11 keeps P on the fly and makes every P^T the back projector of
+ * Eq. (11) (eptv_backproject_eq11); the solver then iterates with an approximate adjoint,
+ * as the paper's GPU code did.
  * Errors: EPTV_ERR_ARG (unknown mode; a row of P longer than 4096 entries; 2^31 or more
  * entries), EPTV_ERR_NOMEM, EPTV_ERR_CUDA. */
 int eptv_set_operator(eptv_geometry *g, int mode, long long *h_nnz_opt);

@@ -11,12 +11,19 @@
 // and 2 row planes are shared by its 4 pixels.  The VG partial sums of a strip are
 // added in group order (deterministic).  Optionally also writes the transposed image
 // (for the projector's shallow rays) and reduces |f|^2 (FP32 per warp, FP64 above).
+//
+// EQ11 = true: the paper's pixel-driven back projector instead (Eq. 11, Sec. 2.3,
+// derived in App. III), an approximation of the transpose:
+//   [P^T y](u, v) = (du dv / dbeta) sum_theta y^theta(beta*) / l(u, v),
+// beta* = fan angle of the line from the source through the pixel centre, l its length,
+// y linearly interpolated between the two bins around beta* (bins off the detector read
+// 0).  Flat detector (bins uniform in t = tan beta): weight (du dv / dt) (1 + t*^2) / l.
 #include "eptv_internal.cuh"
 #include "kernels.cuh"
 
 namespace eptv {
 
-template <int VG>
+template <int VG, bool EQ11>
 __global__ void __launch_bounds__(128 * VG)
 k2_backproject(const SliceDev *__restrict__ sls, TileMap map, BackArgs a, double *__restrict__ partials)
 {
@@ -40,7 +47,47 @@ k2_backproject(const SliceDev *__restrict__ sls, TileMap map, BackArgs a, double
     const float *sino = a.in_override ? a.in_override : S.r;
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
 
-    if (j < ny && i0 < nx) {
+    if (EQ11 && j < ny && i0 < nx) {
+        const float yc = grid_line((float)j + 0.5f, S.dy, S.y0);
+        float xc[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) xc[q] = grid_line((float)(i0 + q) + 0.5f, S.dx, S.x0);
+        const float inv_db = S.inv_dbeta, kc = S.kc;
+        const bool arc = S.detector == EPTV_DETECTOR_ARC;
+        for (int v = vg; v < S.nv; v += VG) {
+            const ViewRec V = S.view[v];
+            const float *sv = sino + (size_t)v * nb;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float wx = xc[q] - V.sx, wy = yc - V.sy;
+                const float cr = V.cx * wy - V.cy * wx;          // l sin(beta*)
+                const float dt = V.cx * wx + V.cy * wy;          // l cos(beta*)
+                const float rl = rsqrtf(wx * wx + wy * wy);       // 1 / l
+                float u, w;
+                if (arc) {
+                    u = atan2f(cr, dt) * inv_db + kc;
+                    w = rl;
+                } else {
+                    const float t = __fdividef(cr, dt);
+                    u = t * inv_db + kc;
+                    w = fmaf(t, t, 1.0f) * rl;
+                }
+                if (dt > 0.0f && u > -1.0f && u < (float)nb) {
+                    const float fk = floorf(u);
+                    const int k0 = (int)fk;
+                    const float fr = u - fk;
+                    float y0 = 0.0f, y1 = 0.0f;
+                    if (k0 >= 0) y0 = __ldg(sv + k0);
+                    if (k0 + 1 < nb) y1 = __ldg(sv + k0 + 1);
+                    acc[q] = fmaf(fmaf(fr, y1 - y0, y0), w, acc[q]);
+                }
+            }
+        }
+        const float scale = S.dx * S.dy * inv_db;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q] *= scale;
+    }
+    if (!EQ11 && j < ny && i0 < nx) {
         float X[5];
 #pragma unroll
         for (int q = 0; q < 5; ++q) X[q] = grid_line((float)(i0 + q), S.dx, S.x0);
@@ -152,11 +199,21 @@ void launch_backproject(const Batch &B, const BackArgs &a, cudaStream_t st) {
     const int nblk = B.blocks(FAM_K2);
     if (nblk == 0) return;
     ++g_launch_count;
+    const TileMap m = B.map(FAM_K2);
+    if (B.bp_eq11 || a.eq11) {
+        switch (B.k2_vg) {
+        case 1: k2_backproject<1, true><<<nblk, 128, 0, st>>>(B.d_sd, m, a, B.d_partials); break;
+        case 2: k2_backproject<2, true><<<nblk, 256, 0, st>>>(B.d_sd, m, a, B.d_partials); break;
+        case 8: k2_backproject<8, true><<<nblk, 1024, 0, st>>>(B.d_sd, m, a, B.d_partials); break;
+        default: k2_backproject<4, true><<<nblk, 512, 0, st>>>(B.d_sd, m, a, B.d_partials); break;
+        }
+        return;
+    }
     switch (B.k2_vg) {
-    case 1: k2_backproject<1><<<nblk, 128, 0, st>>>(B.d_sd, B.map(FAM_K2), a, B.d_partials); break;
-    case 2: k2_backproject<2><<<nblk, 256, 0, st>>>(B.d_sd, B.map(FAM_K2), a, B.d_partials); break;
-    case 8: k2_backproject<8><<<nblk, 1024, 0, st>>>(B.d_sd, B.map(FAM_K2), a, B.d_partials); break;
-    default: k2_backproject<4><<<nblk, 512, 0, st>>>(B.d_sd, B.map(FAM_K2), a, B.d_partials); break;
+    case 1: k2_backproject<1, false><<<nblk, 128, 0, st>>>(B.d_sd, m, a, B.d_partials); break;
+    case 2: k2_backproject<2, false><<<nblk, 256, 0, st>>>(B.d_sd, m, a, B.d_partials); break;
+    case 8: k2_backproject<8, false><<<nblk, 1024, 0, st>>>(B.d_sd, m, a, B.d_partials); break;
+    default: k2_backproject<4, false><<<nblk, 512, 0, st>>>(B.d_sd, m, a, B.d_partials); break;
     }
 }
 

@@ -61,7 +61,7 @@ struct DevMem {
 
 struct GraphCache {
     cudaGraphExec_t exec = nullptr;
-    int key[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
+    int key[9] = {-1, -1, -1, -1, -1, -1, -1, -1, -1};
     long long kernels = 0;     // kernel nodes in the captured outer iteration
     void reset() {
         if (exec) cudaGraphExecDestroy(exec);
@@ -294,8 +294,8 @@ static void enqueue_outer(const Batch &B, const eptv_params *p, cudaStream_t st)
 
 // Capture one outer iteration of batch B into a graph (cached per structural key).
 static int outer_graph(const Batch &B, GraphCache &gc, cudaStream_t cap, const eptv_params *p) {
-    const int key[8] = {p->cgls_iters, p->n_gd, n_trials_of(p), p->step_rule, B.n, B.k1_seg, B.k2_vg,
-                        B.stored};
+    const int key[9] = {p->cgls_iters, p->n_gd, n_trials_of(p), p->step_rule, B.n, B.k1_seg, B.k2_vg,
+                        B.stored, B.bp_eq11};
     if (gc.exec && memcmp(key, gc.key, sizeof key) == 0) return 0;
     gc.reset();
     cudaGraph_t graph = nullptr;
@@ -383,6 +383,7 @@ static int acquire_batch(int n, eptv_geometry *const *geoms, BatchCache &bc) {
     int rc = build_batch(bc.B, bc.mem, sds);
     if (rc) { bc.reset(); return rc; }
     bc.B.stored = modes[0] == EPTV_OPERATOR_STORED;
+    bc.B.bp_eq11 = modes[0] == EPTV_OPERATOR_EQ11;
     bc.members = members;
     bc.modes = modes;
     return 0;
@@ -612,6 +613,17 @@ int eptv_backproject(const eptv_geometry *gc, const float *d_y, float *d_f, void
     a.out_override = d_f;
     a.fin = FIN_NONE;
     op_backproject(gc->B, a, (cudaStream_t)stream);
+    return launch_check();
+}
+
+int eptv_backproject_eq11(const eptv_geometry *gc, const float *d_y, float *d_f, void *stream) {
+    if (!gc || !d_f || !d_y) return fail(EPTV_ERR_ARG, "NULL argument");
+    BackArgs a{};
+    a.in_override = d_y;
+    a.out_override = d_f;
+    a.fin = FIN_NONE;
+    a.eq11 = 1;
+    launch_backproject(gc->B, a, (cudaStream_t)stream);
     return launch_check();
 }
 
@@ -947,7 +959,7 @@ static cudaError_t stored_alloc(void *ctx, void **p, size_t bytes) {
 
 int eptv_set_operator(eptv_geometry *g, int mode, long long *h_nnz_opt) {
     if (!g) return fail(EPTV_ERR_ARG, "NULL handle");
-    if (mode != EPTV_OPERATOR_ON_THE_FLY && mode != EPTV_OPERATOR_STORED)
+    if (mode != EPTV_OPERATOR_ON_THE_FLY && mode != EPTV_OPERATOR_STORED && mode != EPTV_OPERATOR_EQ11)
         return fail(EPTV_ERR_ARG, "unknown operator mode %d", mode);
     CU(cudaDeviceSynchronize());
     if (mode == EPTV_OPERATOR_STORED && !g->stored.p_ptr) {
@@ -977,6 +989,7 @@ int eptv_set_operator(eptv_geometry *g, int mode, long long *h_nnz_opt) {
     }
     CU(cudaMemcpy(g->B.d_sd, g->B.h_sd.data(), sizeof(SliceDev), cudaMemcpyHostToDevice));
     g->B.stored = on ? 1 : 0;
+    g->B.bp_eq11 = mode == EPTV_OPERATOR_EQ11 ? 1 : 0;
     g->op_mode = mode;
     g->graph.reset();
     if (h_nnz_opt) *h_nnz_opt = g->stored.nnz_p;

@@ -28,7 +28,7 @@ EXPORTED = [
     "eptv_unet_weights_to_bf16", "eptv_unet_maxpool2", "eptv_unet_maxpool2_bwd",
     "eptv_unet_upsample2", "eptv_unet_upsample2_bwd", "eptv_unet_relu_bwd", "eptv_unet_head",
     "eptv_unet_adam", "eptv_unet_pack_input", "eptv_set_operator", "eptv_matrix_info",
-    "eptv_copy_matrix",
+    "eptv_copy_matrix", "eptv_backproject_eq11",
 ]
 
 
@@ -132,6 +132,7 @@ def load():
                                    vp, vp, vp, c_int, c_int, vp, vp, vp, vp]),
         "eptv_unet_pack_input": (c_int, [vp, ctypes.c_float, vp, ctypes.c_float, ctypes.c_longlong, vp, vp]),
         "eptv_set_operator": (c_int, [vp, c_int, ctypes.POINTER(ctypes.c_longlong)]),
+        "eptv_backproject_eq11": (c_int, [vp, vp, vp, vp]),
         "eptv_matrix_info": (c_int, [vp, c_int, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
                                      ctypes.POINTER(ctypes.c_longlong)]),
         "eptv_copy_matrix": (c_int, [vp, c_int, vp, vp, vp, vp]),
@@ -341,7 +342,14 @@ def eptv_get_log(geom: Geometry):
     return steps.reshape(no.value, ng.value), sig
 
 
-OPERATOR_ON_THE_FLY, OPERATOR_STORED = 0, 1
+OPERATOR_ON_THE_FLY, OPERATOR_STORED, OPERATOR_EQ11 = 0, 1, 2
+
+
+def eptv_backproject_eq11(geom: Geometry, y, f, stream=None):
+    """The paper's interpolating back projector, Eq. (11) (see eptv.h)."""
+    _check(load().eptv_backproject_eq11(geom.handle, _ptr(y, geom.n_rays, "y"), _ptr(f, geom.n_pix, "f"),
+                                        _stream(stream)))
+    return f
 
 
 def eptv_set_operator(geom: Geometry, mode: int) -> int:

@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--no-tte", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-stored", action="store_true")
+    ap.add_argument("--no-eq11", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     return ap.parse_args()
 
@@ -340,6 +341,56 @@ def run_stored(dev, stream, case, n_outer, peak, peak_kind, steps=3):
     return out
 
 
+def run_eq11(dev, stream, case, n_outer, t_k2, steps=3):
+    """The paper's interpolating back projector (Eq. 11) on the benchmark workload: launch
+    time next to the exact K2, its adjoint mismatch against the exact P (phantom and its
+    sinogram), and the n_outer-iteration reconstruction that uses it as P^T: rate, final
+    reported energy (Eq. 2, sigma_ref = the FP64 oracle's) next to the exact operator's."""
+    import numpy as np
+    import torch
+    from paper_1009_2288_b300 import eptv as E
+    from paper_1009_2288_b300 import inputs as I
+    g = case.geom
+    geo = E.Geometry(g)
+    E.eptv_autotune(geo)
+    y = torch.from_numpy(case.y.astype(np.float32).reshape(-1)).to(dev)
+    b = torch.empty(g.n_pix, device=dev)
+    t_eq = time_kernel(lambda: E.eptv_backproject_eq11(geo, y, b))
+    f = torch.empty(g.n_pix, device=dev)
+    E.eptv_backproject(geo, y, f)                       # a smooth-ish positive image
+    pf = torch.empty(g.n_rays, device=dev)
+    E.eptv_project(geo, f, pf)
+    lhs = float((pf.double() * y.double()).sum())
+    rhs = float((f.double() * b.double()).sum())
+    p = I.EptvParams(n_outer=n_outer)
+    gold = os.path.join(ROOT, "tests", "golden", "c2_oracle_energy.json")
+    sig = json.load(open(gold))["sigma_ref"] if os.path.exists(gold) else None
+    out = {"launch_us": t_eq * 1e6, "exact_k2_launch_us": t_k2 * 1e6,
+           "adjoint_mismatch": abs(lhs - rhs) / abs(lhs)}
+    finals = {}
+    for mode, name in ((E.OPERATOR_ON_THE_FLY, "exact"), (E.OPERATOR_EQ11, "eq11")):
+        E.eptv_set_operator(geo, mode)
+        E.eptv_autotune(geo)
+        E.eptv_reconstruct(geo, p, y, f.zero_(), report=False)
+        times = []
+        for _ in range(steps):
+            f.zero_()
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record(stream)
+            E.eptv_reconstruct(geo, p, y, f, report=False)
+            e.record(stream)
+            e.synchronize()
+            times.append(s.elapsed_time(e))
+        finals[name] = f.clone()
+        row = {"iterations_per_s": n_outer * 1e3 / statistics.mean(times)}
+        if sig is not None:
+            row["e_report_final"] = E.eptv_report_energy(geo, p, sig, f, y)
+        out[name] = row
+    out["image_rel_diff_eq11_vs_exact"] = float((finals["eq11"] - finals["exact"]).norm() /
+                                                finals["exact"].norm())
+    return out
+
+
 def run_learned(dev, stream, n_pairs=2000, epochs=40, eval_seeds=(1, 2, 3, 4), k_ws=(0, 2)):
     """Learned warm start on the 256^2 (1.6 mm), 30 views x 888 bins, I0 = 5e4 workload.
     Trains the U-Net on n_pairs pairs that the plain method generates (50 iterations each,
@@ -571,6 +622,10 @@ def run_ours(args, world, rank, local):
     if not args.no_batched and rank == 0:
         batched = run_batched(dev, stream)
 
+    eq11 = None
+    if not args.no_eq11 and rank == 0:
+        eq11 = run_eq11(dev, stream, case, N_OUTER, t_k2)
+
     stored = None
     if not args.no_stored and rank == 0:
         stored = run_stored(dev, stream, case, N_OUTER, peak, peak_kind)
@@ -601,6 +656,7 @@ def run_ours(args, world, rank, local):
         "time_to_oracle_energy": tte,
         "batched": batched,
         "stored": stored,
+        "backprojector_eq11": eq11,
         "learned": learned,
         "clocks": clk,
         "paper_context": {"workload": "NCAT 512^2, 40 views, 50 iterations (Table 2)",

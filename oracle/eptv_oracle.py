@@ -12,6 +12,8 @@ Functions and the passages they follow:
                                     exact transpose (Eq. A3 of App. III, adjoint identity)
   backproject_eq11 ................ Eq. (11), Sec. 2.3 and App. III: the paper's pixel-driven
                                     interpolating back projector (an approximation of P^T)
+  relative_error / sobel_edges /
+  edge_correlation / roi_snr ...... Eqs. (12), (13), (14), Sec. 3: image-quality metrics
   cgls ............................ App. I (CGLS for (P1), restarted at f^(k))
   half_edges ...................... Eq. (A3), App. II (half-point magnitudes)
   edge_weights .................... Eq. (5)
@@ -41,6 +43,9 @@ Readings of points the paper leaves open (each also listed in the design notes):
     the paper states the arc detector (uniform in beta); for a flat detector (uniform in
     t = tan beta) the same change of variables in (A7) gives the weight
     (du dv / dt) (1 + t*^2) / l.
+  * Eq. (13): the "standard Sobel edge detector" is read as: 3x3 Sobel derivatives
+    gx, gy at the interior pixels, an edge where gx^2 + gy^2 > s^2 mean(gx^2 + gy^2) over
+    the interior (s = 2 by default), no thinning; border pixels are never edges.
 """
 from __future__ import annotations
 
@@ -420,3 +425,54 @@ def reconstruct(op: Operator, y, p, f0=None, prior_w=None, n_outer=None,
     if log is not None:
         log.t_prev = t_prev
     return f
+
+
+# ------------------------------------------------------------------ Sec. 3 metrics
+
+def relative_error(f, f_true):
+    """Eq. (12): e = |f - f*|^2 / |f*|^2 (squared norms, as printed)."""
+    f = np.asarray(f, dtype=np.float64)
+    t = np.asarray(f_true, dtype=np.float64)
+    return float(np.sum((f - t) ** 2) / np.sum(t ** 2))
+
+
+def sobel_gradient2(f):
+    """gx^2 + gy^2 of the 3x3 Sobel derivatives at the interior pixels (0 on the border);
+    x = column index, y = row index."""
+    f = np.asarray(f, dtype=np.float64)
+    ny, nx = f.shape
+    g2 = np.zeros((ny, nx))
+    if nx < 3 or ny < 3:
+        return g2
+    gx = ((f[:-2, 2:] + 2.0 * f[1:-1, 2:] + f[2:, 2:]) - (f[:-2, :-2] + 2.0 * f[1:-1, :-2] + f[2:, :-2]))
+    gy = ((f[2:, :-2] + 2.0 * f[2:, 1:-1] + f[2:, 2:]) - (f[:-2, :-2] + 2.0 * f[:-2, 1:-1] + f[:-2, 2:]))
+    g2[1:-1, 1:-1] = gx * gx + gy * gy
+    return g2
+
+
+def sobel_edges(f, scale: float = 2.0):
+    """Binary edge map of Eq. (13) (reading in the header): interior pixels whose squared
+    Sobel magnitude exceeds scale^2 times its mean over the interior."""
+    g2 = sobel_gradient2(f)
+    ny, nx = g2.shape
+    if nx < 3 or ny < 3:
+        return np.zeros((ny, nx), dtype=np.uint8)
+    mean = float(np.mean(g2[1:-1, 1:-1]))
+    return (g2 > scale * scale * mean).astype(np.uint8)
+
+
+def edge_correlation(b, b_true):
+    """Eq. (13): correlation coefficient of two binary edge maps over all pixels."""
+    b = np.asarray(b, dtype=np.float64).ravel()
+    t = np.asarray(b_true, dtype=np.float64).ravel()
+    db, dt = b - b.mean(), t - t.mean()
+    den = math.sqrt(float(np.sum(db * db)) * float(np.sum(dt * dt)))
+    return float(np.sum(db * dt) / den) if den > 0 else float("nan")
+
+
+def roi_snr(f, x0: int, y0: int, w: int, h: int):
+    """Eq. (14): SNR = 10 log10(E(P)^2 / E([P - E(P)]^2)) over the ROI pixels P
+    (columns x0 .. x0 + w - 1, rows y0 .. y0 + h - 1)."""
+    P = np.asarray(f, dtype=np.float64)[y0:y0 + h, x0:x0 + w]
+    m = float(np.mean(P))
+    return 10.0 * math.log10(m * m / float(np.mean((P - m) ** 2)))

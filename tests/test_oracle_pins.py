@@ -488,3 +488,52 @@ def test_eq11_interpolation_exact_for_linear_sinograms():
                 want[iy, ix] += (a[v] + b[v] * u) / abs(p - s)
     want *= g.dx * g.dy / g.dbeta
     assert np.allclose(got, want, rtol=1e-12, atol=0)
+
+
+# ------------------------------------------------------------------ Eqs. (12) - (14)
+
+def test_relative_error_closed_form():
+    rng = np.random.Generator(np.random.PCG64(21))
+    t = rng.uniform(0.5, 1.5, (9, 7))
+    assert O.relative_error(1.1 * t, t) == pytest.approx(0.01, rel=1e-12)
+    assert O.relative_error(t, t) == 0.0
+
+
+def test_sobel_gradient_matches_scipy():
+    """Interior Sobel derivatives against scipy.ndimage.sobel (the library routine)."""
+    from scipy import ndimage
+    rng = np.random.Generator(np.random.PCG64(22))
+    f = rng.standard_normal((13, 17))
+    gx = ndimage.sobel(f, axis=1, mode="constant")
+    gy = ndimage.sobel(f, axis=0, mode="constant")
+    want = (gx * gx + gy * gy)[1:-1, 1:-1]
+    assert np.allclose(O.sobel_gradient2(f)[1:-1, 1:-1], want, rtol=1e-12, atol=1e-12)
+
+
+def test_sobel_edges_of_a_step():
+    """A vertical step of height h: gx = 4h on the two columns beside the step, 0
+    elsewhere, so exactly those interior pixels are edges (mean = 8h^2 (ny-2)/((nx-2)(ny-2)))."""
+    f = np.zeros((10, 12))
+    f[:, 6:] = 3.0
+    b = O.sobel_edges(f)
+    want = np.zeros_like(b)
+    want[1:-1, 5:7] = 1
+    assert np.array_equal(b, want)
+    assert O.sobel_edges(np.outer(np.ones(10), np.arange(12.0))).sum() == 0   # a ramp has no edges
+
+
+def test_edge_correlation_against_numpy_corrcoef():
+    rng = np.random.Generator(np.random.PCG64(23))
+    b = (rng.uniform(size=(20, 30)) < 0.2).astype(np.uint8)
+    t = (rng.uniform(size=(20, 30)) < 0.3).astype(np.uint8)
+    assert O.edge_correlation(b, t) == pytest.approx(np.corrcoef(b.ravel(), t.ravel())[0, 1], rel=1e-12)
+    assert O.edge_correlation(b, b) == pytest.approx(1.0, rel=1e-12)
+    assert O.edge_correlation(b, 1 - b) == pytest.approx(-1.0, rel=1e-12)
+
+
+def test_roi_snr_closed_form():
+    """ROI = m + a * (checkerboard of +-1): mean m, variance a^2."""
+    f = np.full((16, 16), 7.0)
+    cb = np.indices((6, 8)).sum(axis=0) % 2 * 2.0 - 1.0
+    f[3:9, 5:13] = 2.0 + 0.1 * cb
+    assert O.roi_snr(f, 5, 3, 8, 6) == pytest.approx(10 * math.log10(4.0 / 0.01), rel=1e-12)

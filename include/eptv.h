@@ -243,6 +243,32 @@ int eptv_select_kth(const eptv_geometry *g, const float *d_vals, long n, long k,
  * the GPU (other streams or threads) race and give wrong results. */
 int eptv_select_kth_noalloc(const float *d_vals, long n, long k, float *d_out, void *stream);
 
+/* Image-quality metrics of Sec. 3 for an image d_f of g's grid (FP32 [ny][nx]) against a
+ * reference d_ref_opt (the ground truth; may be NULL):
+ *   rel_error  Eq. (12): |f - f_ref|^2 / |f_ref|^2                           (NaN if no ref)
+ *   ecc        Eq. (13): correlation coefficient of the binary edge maps of f and f_ref
+ *              (NaN if no ref or if a map is constant); an edge is an interior pixel whose
+ *              squared 3x3 Sobel magnitude exceeds edge_scale^2 times its mean over the
+ *              interior (the paper names a standard Sobel detector without a threshold;
+ *              edge_scale = 2 is the usual choice), evaluated in FP64; border pixels are
+ *              never edges
+ *   edges, edges_ref, edges_both: the edge counts behind ecc
+ *   snr_db     Eq. (14): 10 log10(E(P)^2 / E([P - E(P)]^2)) over the rectangle
+ *              h_roi_opt = {x0, y0, w, h} (columns x0 .. x0 + w - 1, rows y0 .. y0 + h - 1)
+ *              of d_f; NaN if h_roi_opt is NULL.
+ * d_edges_opt / d_edges_ref_opt (may be NULL) receive the byte edge maps [ny][nx].
+ * Synchronises `stream`.  Errors: EPTV_ERR_ARG (ROI outside the image, edge_scale <= 0). */
+typedef struct {
+    double rel_error;
+    double ecc;
+    long long edges, edges_ref, edges_both;
+    double snr_db;
+} eptv_quality;
+
+int eptv_quality_metrics(const eptv_geometry *g, const float *d_f, const float *d_ref_opt,
+                         const int *h_roi_opt, double edge_scale, unsigned char *d_edges_opt,
+                         unsigned char *d_edges_ref_opt, eptv_quality *out, void *stream);
+
 /* Stored-matrix operator (Sec. 2.3: the sparse-matrix strategy for small problems).
  * mode EPTV_OPERATOR_STORED makes every later P / P^T of this handle -- eptv_project(_t),
  * eptv_backproject, eptv_cgls, eptv_reconstruct, eptv_reconstruct_batched (all members

@@ -62,7 +62,8 @@ enum Scalar {
     SC_NONFINITE,    // set to 1 when a reduction met NaN / Inf
     SC_SEL_PREFIX,   // radix select: fixed bit prefix (as double, exact below 2^53)
     SC_SEL_RANK,     // radix select: remaining 1-based rank within the prefix
-    SC_COUNT
+    SC_Q0,           // image-quality sums (quality.cu): SC_Q0 .. SC_Q0 + 8
+    SC_COUNT = SC_Q0 + 9
 };
 constexpr int kScalarStride = 32;   // doubles per slice (>= SC_COUNT)
 

@@ -1023,4 +1023,43 @@ int eptv_copy_matrix(const eptv_geometry *g, int which, int *d_ptr, int *d_col, 
     return 0;
 }
 
+int eptv_quality_metrics(const eptv_geometry *g, const float *d_f, const float *d_ref_opt,
+                         const int *h_roi_opt, double edge_scale, unsigned char *d_edges_opt,
+                         unsigned char *d_edges_ref_opt, eptv_quality *out, void *stream) {
+    if (!g || !d_f || !out) return fail(EPTV_ERR_ARG, "NULL argument");
+    if (!(edge_scale > 0.0)) return fail(EPTV_ERR_ARG, "edge_scale must be > 0");
+    const int nx = g->sd.nx, ny = g->sd.ny;
+    int rx0 = 0, ry0 = 0, rw = 0, rh = 0;
+    if (h_roi_opt) {
+        rx0 = h_roi_opt[0]; ry0 = h_roi_opt[1]; rw = h_roi_opt[2]; rh = h_roi_opt[3];
+        if (rw < 1 || rh < 1 || rx0 < 0 || ry0 < 0 || rx0 + rw > nx || ry0 + rh > ny)
+            return fail(EPTV_ERR_ARG, "ROI outside the image");
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    launch_quality(g->B, d_f, d_ref_opt, rx0, ry0, rw, rh, edge_scale * edge_scale, d_edges_opt,
+                   d_ref_opt ? d_edges_ref_opt : nullptr, st);
+    int rc = launch_check();
+    if (rc) return rc;
+    double sc[kScalarStride];
+    if ((rc = read_scalars(g->sd, sc, st))) return rc;
+    const double nan = std::nan("");
+    const double N = (double)nx * ny;
+    const double nb = sc[SC_Q0 + 6], nr = sc[SC_Q0 + 7], both = sc[SC_Q0 + 8];
+    out->edges = (long long)nb;
+    out->edges_ref = d_ref_opt ? (long long)nr : 0;
+    out->edges_both = d_ref_opt ? (long long)both : 0;
+    out->rel_error = d_ref_opt ? sc[SC_Q0] / sc[SC_Q0 + 1] : nan;
+    const double vb = nb - nb * nb / N, vr = nr - nr * nr / N;
+    out->ecc = (d_ref_opt && vb > 0.0 && vr > 0.0) ? (both - nb * nr / N) / std::sqrt(vb * vr) : nan;
+    if (h_roi_opt) {
+        const double n = (double)rw * rh;
+        const double m = sc[SC_Q0 + 4] / n;
+        const double var = sc[SC_Q0 + 5] / n - m * m;
+        out->snr_db = 10.0 * std::log10(m * m / var);
+    } else {
+        out->snr_db = nan;
+    }
+    return 0;
+}
+
 }  // extern "C"

@@ -126,6 +126,8 @@ typedef cudaError_t (*StoredAlloc)(void *ctx, void **p, size_t bytes);
 cudaError_t build_stored(const SliceDev &S, const SliceDev *d_sd, StoredAlloc alloc, void *ctx,
                          StoredMatrices *m, cudaStream_t st);
 void launch_spmv_p(const Batch &B, const ProjArgs &a, cudaStream_t st);
+void launch_quality(const Batch &B, const float *f, const float *r, int rx0, int ry0, int rw, int rh,
+                    double scale2, unsigned char *bf, unsigned char *br, cudaStream_t st);
 void launch_spmv_pt(const Batch &B, const BackArgs &a, cudaStream_t st);
 
 // Kernel launches issued by this thread (graph captures included); read by the host

@@ -28,7 +28,7 @@ EXPORTED = [
     "eptv_unet_weights_to_bf16", "eptv_unet_maxpool2", "eptv_unet_maxpool2_bwd",
     "eptv_unet_upsample2", "eptv_unet_upsample2_bwd", "eptv_unet_relu_bwd", "eptv_unet_head",
     "eptv_unet_adam", "eptv_unet_pack_input", "eptv_set_operator", "eptv_matrix_info",
-    "eptv_copy_matrix", "eptv_backproject_eq11",
+    "eptv_copy_matrix", "eptv_backproject_eq11", "eptv_quality_metrics",
 ]
 
 
@@ -61,6 +61,12 @@ class Stats(ctypes.Structure):
     _fields_ = [("sigma", ctypes.c_double), ("energy_first", ctypes.c_double),
                 ("energy_last", ctypes.c_double), ("t_prev", ctypes.c_double),
                 ("n_accepted", ctypes.c_int), ("n_fail", ctypes.c_int), ("status", ctypes.c_int)]
+
+
+class Quality(ctypes.Structure):
+    _fields_ = [("rel_error", ctypes.c_double), ("ecc", ctypes.c_double), ("edges", ctypes.c_longlong),
+                ("edges_ref", ctypes.c_longlong), ("edges_both", ctypes.c_longlong),
+                ("snr_db", ctypes.c_double)]
 
 
 class Report(ctypes.Structure):
@@ -133,6 +139,8 @@ def load():
         "eptv_unet_pack_input": (c_int, [vp, ctypes.c_float, vp, ctypes.c_float, ctypes.c_longlong, vp, vp]),
         "eptv_set_operator": (c_int, [vp, c_int, ctypes.POINTER(ctypes.c_longlong)]),
         "eptv_backproject_eq11": (c_int, [vp, vp, vp, vp]),
+        "eptv_quality_metrics": (c_int, [vp, vp, vp, ctypes.POINTER(c_int), ctypes.c_double, vp, vp,
+                                         ctypes.POINTER(Quality), vp]),
         "eptv_matrix_info": (c_int, [vp, c_int, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
                                      ctypes.POINTER(ctypes.c_longlong)]),
         "eptv_copy_matrix": (c_int, [vp, c_int, vp, vp, vp, vp]),
@@ -379,6 +387,22 @@ def eptv_matrix(geom: Geometry, which: int):
     _check(load().eptv_copy_matrix(geom.handle, int(which), ptr.data_ptr(), col.data_ptr(), val.data_ptr(),
                                    _stream(None)))
     return ptr, col[:nnz.value], val[:nnz.value]
+
+
+def eptv_quality_metrics(geom: Geometry, f, ref=None, roi=None, edge_scale: float = 2.0, edges=None,
+                         edges_ref=None, stream=None) -> Quality:
+    """Relative error (Eq. 12), edge correlation (Eq. 13) and ROI SNR (Eq. 14) of f (see
+    eptv.h); roi = (x0, y0, w, h); edges / edges_ref: optional uint8 CUDA tensors [ny*nx]."""
+    q = Quality()
+    r = (ctypes.c_int * 4)(*roi) if roi is not None else None
+    for t in (edges, edges_ref):
+        if t is not None and (t.dtype.itemsize != 1 or t.numel() != geom.n_pix or not t.is_cuda):
+            raise ValueError("edge maps must be uint8 CUDA tensors of n_pix elements")
+    _check(load().eptv_quality_metrics(geom.handle, _ptr(f, geom.n_pix, "f"), _ptr(ref, geom.n_pix, "ref"),
+                                       r, float(edge_scale), edges.data_ptr() if edges is not None else None,
+                                       edges_ref.data_ptr() if edges_ref is not None else None,
+                                       ctypes.byref(q), _stream(stream)))
+    return q
 
 
 def eptv_set_tuning(geom: Geometry, k1_seg: int, k2_vg: int):

@@ -349,3 +349,222 @@ class EptvParams:
     @property
     def t_init_eff(self) -> float:
         return self.t_init if self.t_init > 0 else 1.0 / self.lam
+
+
+# ------------------------------------------------------------------ 3-D cone beam
+#
+# Conventions of the cone-beam geometry (3-D extension; the paper is 2-D only):
+#   * volume f is [nz][ny][nx], x fastest; voxel (ix, iy, iz) covers
+#     [x0 + ix dx, x0 + (ix+1) dx] x [y0 + iy dy, ...] x [z0 + iz dz, ...],
+#     x0 = -nx dx / 2, y0 = -ny dy / 2, z0 = -nz dz / 2 (mm);
+#   * projections are [n_views][nv][nu] (detector columns u fastest, rows v);
+#   * view k: angle theta (angles[k], else 2 pi k / n_views); source at
+#     sid (cos theta, sin theta, 0); central direction c = -(cos theta, sin theta, 0);
+#     flat detector perpendicular to c at distance sdd from the source, with axes
+#     e_u = (-sin theta, cos theta, 0) and e_z = (0, 0, 1);
+#   * detector pixel (iu, iv) centre: source + sdd c + u e_u + w e_z with
+#     u = (iu - (nu-1)/2 + u_off) du, w = (iv - (nv-1)/2 + v_off) dv;
+#   * ray index (k nv + iv) nu + iu; the ray runs from the source to that centre.
+
+@dataclasses.dataclass
+class ConeGeometry:
+    """Parameter record of a circular cone-beam scan with a flat detector."""
+    nx: int
+    ny: int
+    nz: int
+    dx: float
+    dy: float
+    dz: float
+    n_views: int
+    nu: int
+    nv: int
+    du: float
+    dv: float
+    u_off: float = 0.25
+    v_off: float = 0.0
+    sid: float = 1000.0
+    sdd: float = 1500.0
+    angles: Optional[np.ndarray] = None
+
+    @property
+    def n_vox(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    @property
+    def n_rays(self) -> int:
+        return self.n_views * self.nu * self.nv
+
+    def view_angles(self) -> np.ndarray:
+        if self.angles is not None:
+            a = np.asarray(self.angles, dtype=np.float64)
+            assert a.shape == (self.n_views,)
+            return a
+        return 2.0 * np.pi * np.arange(self.n_views, dtype=np.float64) / self.n_views
+
+
+def cone_rays(g: ConeGeometry):
+    """Source points and unit directions of every ray, float64, ray index (k nv + iv) nu + iu."""
+    th = g.view_angles()
+    u = (np.arange(g.nu) - (g.nu - 1) / 2.0 + g.u_off) * g.du
+    w = (np.arange(g.nv) - (g.nv - 1) / 2.0 + g.v_off) * g.dv
+    c, s = np.cos(th)[:, None, None], np.sin(th)[:, None, None]
+    U, W = u[None, None, :], w[None, :, None]
+    sx, sy = g.sid * c, g.sid * s
+    dx = -g.sdd * c - U * s
+    dy = -g.sdd * s + U * c
+    dz = np.broadcast_to(W, (g.n_views, g.nv, g.nu))
+    n = np.sqrt(dx * dx + dy * dy + dz * dz)
+    shape = (g.n_views, g.nv, g.nu)
+    out = [np.broadcast_to(sx, shape), np.broadcast_to(sy, shape), np.zeros(shape),
+           dx / n, dy / n, dz / n]
+    return tuple(np.ascontiguousarray(a, dtype=np.float64).reshape(-1) for a in out)
+
+
+@dataclasses.dataclass
+class Ellipsoid:
+    cx: float
+    cy: float
+    cz: float
+    a: float        # semi-axes (mm) along the rotated x', y' and z
+    b: float
+    c: float
+    phi: float      # rotation about z (rad)
+    value: float    # attenuation (1/mm), overwrites what was painted before
+
+
+def _inside3(el: Ellipsoid, x, y, z):
+    cs, sn = math.cos(el.phi), math.sin(el.phi)
+    u = (x - el.cx) * cs + (y - el.cy) * sn
+    w = -(x - el.cx) * sn + (y - el.cy) * cs
+    return (u / el.a) ** 2 + (w / el.b) ** 2 + ((z - el.cz) / el.c) ** 2 < 1.0
+
+
+def paint3(ellipsoids: Sequence[Ellipsoid], x, y, z):
+    out = np.zeros(np.broadcast(x, y, z).shape, dtype=np.float64)
+    for el in ellipsoids:
+        out = np.where(_inside3(el, x, y, z), el.value, out)
+    return out
+
+
+def random_ellipsoids(rng: np.random.Generator, R: float, H: float, n_random: int, body_mu: float = 0.02):
+    """Body ellipsoid (semi-axes 0.85-0.95 R in x, y; 0.85-0.95 H in z) plus n_random
+    ellipsoids with centres in the 0.7 R cylinder of half-height 0.7 H."""
+    els = [Ellipsoid(0.0, 0.0, 0.0, rng.uniform(0.85, 0.95) * R, rng.uniform(0.85, 0.95) * R,
+                     rng.uniform(0.85, 0.95) * H, rng.uniform(0.0, np.pi), body_mu)]
+    for _ in range(n_random):
+        r = 0.7 * R * math.sqrt(rng.uniform())
+        ang = rng.uniform(0.0, 2 * np.pi)
+        els.append(Ellipsoid(r * math.cos(ang), r * math.sin(ang), rng.uniform(-0.7, 0.7) * H,
+                             rng.uniform(0.03, 0.3) * R, rng.uniform(0.03, 0.3) * R,
+                             rng.uniform(0.03, 0.3) * H, rng.uniform(0.0, np.pi), rng.uniform(0.01, 0.03)))
+    return els
+
+
+def add_sphere(els: List[Ellipsoid], cx, cy, cz, radius, contrast):
+    """Low-contrast sphere: value = underlying value at its centre * (1 + contrast)."""
+    under = float(paint3(els, np.array(cx), np.array(cy), np.array(cz)))
+    els.append(Ellipsoid(cx, cy, cz, radius, radius, radius, 0.0, under * (1.0 + contrast)))
+
+
+def line_integrals3(ellipsoids: Sequence[Ellipsoid], sx, sy, sz, ux, uy, uz, chunk: int = 8192):
+    """Exact integral of the overwrite-painted ellipsoid phantom along each ray (float64):
+    each ray's chords cut it into intervals; an interval carries the value of the last
+    ellipsoid covering its midpoint."""
+    n = sx.shape[0]
+    E = len(ellipsoids)
+    out = np.zeros(n, dtype=np.float64)
+    vals = np.array([e.value for e in ellipsoids] + [0.0])
+    for lo in range(0, n, chunk):
+        hi = min(n, lo + chunk)
+        t1 = np.full((hi - lo, E), np.nan)
+        t2 = np.full((hi - lo, E), np.nan)
+        for k, el in enumerate(ellipsoids):
+            cs, sn = math.cos(el.phi), math.sin(el.phi)
+            qx, qy, qz = sx[lo:hi] - el.cx, sy[lo:hi] - el.cy, sz[lo:hi] - el.cz
+            qu, qw = qx * cs + qy * sn, -qx * sn + qy * cs
+            eu, ew = ux[lo:hi] * cs + uy[lo:hi] * sn, -ux[lo:hi] * sn + uy[lo:hi] * cs
+            ez = uz[lo:hi]
+            A = eu * eu / el.a ** 2 + ew * ew / el.b ** 2 + ez * ez / el.c ** 2
+            B = 2.0 * (qu * eu / el.a ** 2 + qw * ew / el.b ** 2 + qz * ez / el.c ** 2)
+            C = qu * qu / el.a ** 2 + qw * qw / el.b ** 2 + qz * qz / el.c ** 2 - 1.0
+            disc = B * B - 4.0 * A * C
+            ok = disc > 0
+            sq = np.sqrt(np.where(ok, disc, 0.0))
+            t1[:, k] = np.where(ok, (-B - sq) / (2 * A), np.nan)
+            t2[:, k] = np.where(ok, (-B + sq) / (2 * A), np.nan)
+        pts = np.sort(np.concatenate([t1, t2], axis=1), axis=1)
+        a, b = pts[:, :-1], pts[:, 1:]
+        mid = 0.5 * (a + b)
+        cov = (t1[:, None, :] < mid[:, :, None]) & (mid[:, :, None] < t2[:, None, :])
+        top = np.where(cov, np.arange(E)[None, None, :], -1).max(axis=2)
+        v = vals[np.where(top >= 0, top, E)]
+        seg = np.where(np.isfinite(a) & np.isfinite(b), b - a, 0.0)
+        out[lo:hi] = np.sum(np.where(top >= 0, v, 0.0) * seg, axis=1)
+    return out
+
+
+def rasterize3(ellipsoids: Sequence[Ellipsoid], g: ConeGeometry, ss: int = 2):
+    """Ground-truth volume: mean of ss^3 sub-voxel samples per voxel."""
+    off = (np.arange(ss) + 0.5) / ss
+    xs = -g.nx * g.dx / 2 + (np.arange(g.nx)[:, None] + off[None, :]).reshape(-1) * g.dx
+    ys = -g.ny * g.dy / 2 + (np.arange(g.ny)[:, None] + off[None, :]).reshape(-1) * g.dy
+    out = np.empty((g.nz, g.ny, g.nx))
+    for iz in range(g.nz):
+        zs = -g.nz * g.dz / 2 + (iz + off) * g.dz
+        acc = np.zeros((g.ny * ss, g.nx * ss))
+        Y, X = np.meshgrid(ys, xs, indexing="ij")
+        for z in zs:
+            acc += paint3(ellipsoids, X, Y, np.full_like(X, z))
+        out[iz] = (acc / ss).reshape(g.ny, ss, g.nx, ss).mean(axis=(1, 3))
+    return out
+
+
+@dataclasses.dataclass
+class ConeCase:
+    name: str
+    geom: ConeGeometry
+    ellipsoids: List[Ellipsoid]
+    i0: float
+    n_outer: int
+    seed: int
+    y: Optional[np.ndarray] = None
+    p_clean: Optional[np.ndarray] = None
+    f_true: Optional[np.ndarray] = None
+
+
+def c5_geometry(scale: int = 1) -> ConeGeometry:
+    """256^3 at 1 mm, 120 views over 360 deg, flat 512 x 384 detector at 0.8 mm, SID 1000,
+    SDD 1500; scale divides the grid and detector counts (and multiplies the pitches) for
+    reduced test cases of the same scan."""
+    return ConeGeometry(256 // scale, 256 // scale, 256 // scale, 1.0 * scale, 1.0 * scale, 1.0 * scale,
+                        120 // scale if scale > 1 else 120, 512 // scale, 384 // scale, 0.8 * scale,
+                        0.8 * scale)
+
+
+def c5_ellipsoids(seed: int, g: ConeGeometry):
+    """Ellipsoid phantom of the cone-beam workload: body + 19 ellipsoids + a ring of 6
+    low-contrast spheres (radii 2-8 mm, contrast 0.5-1 %) in the mid plane."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    R = min(g.nx * g.dx, g.ny * g.dy) / 2.0
+    H = g.nz * g.dz / 2.0
+    els = random_ellipsoids(rng, R, H, 19)
+    for k in range(6):
+        ang = 2 * np.pi * k / 6
+        add_sphere(els, 0.45 * R * math.cos(ang), 0.45 * R * math.sin(ang), 0.0,
+                   2.0 + 6.0 * k / 5.0, rng.choice([-1.0, 1.0]) * rng.uniform(0.005, 0.01))
+    return els, rng
+
+
+def make_c5(seed: int = 5, scale: int = 1, with_truth: bool = True, with_sinogram: bool = True) -> ConeCase:
+    """Cone-beam workload: the phantom of c5_ellipsoids, exact line integrals, Poisson
+    noise I0 = 5e4, 50 iterations.  (The full-size sinogram has 23.6 M rays; the host
+    line integrals are meant for the reduced scales.)"""
+    g = c5_geometry(scale)
+    els, rng = c5_ellipsoids(seed, g)
+    case = ConeCase(f"cone_{g.nx}x{g.ny}x{g.nz}_{g.n_views}v_{g.nu}x{g.nv}", g, els, 5e4, 50, seed)
+    if with_sinogram:
+        case.p_clean = line_integrals3(els, *cone_rays(g)).reshape(g.n_views, g.nv, g.nu)
+        case.y = noisy_sinogram(rng, case.p_clean, case.i0)
+    if with_truth:
+        case.f_true = rasterize3(els, g)
+    return case

@@ -1,0 +1,137 @@
+"""Pins of the 3-D cone-beam oracle against facts fixed by geometry and mathematics:
+brute-force voxel clipping, the adjoint identity, the chord through the volume box, the
+detector geometry, hand-computed magnitudes of the extended A3, the textbook sign gradient
+of plain TV at a step, monotone (P2) energy and a reconstruction that improves on zero."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import cone_oracle as C
+from oracle import eptv_oracle as O
+from paper_1009_2288_b300 import inputs as I
+
+TINY = I.ConeGeometry(5, 4, 3, 1.0, 1.2, 0.9, 5, 7, 6, 1.3, 1.1, 0.25, 0.1, 20.0, 35.0)
+
+
+def _clip(lo, hi, s, u):
+    """Length of the line s + t u (t >= 0) inside the axis-aligned box [lo, hi]."""
+    t0, t1 = 0.0, math.inf
+    for a, b, sa, ua in zip(lo, hi, s, u):
+        if ua == 0.0:
+            if not (a < sa < b):
+                return 0.0
+            continue
+        ta, tb = (a - sa) / ua, (b - sa) / ua
+        t0, t1 = max(t0, min(ta, tb)), min(t1, max(ta, tb))
+    return max(0.0, t1 - t0)
+
+
+def test_brute_force_voxel_clipping():
+    """Every entry of every ray of a small scan equals the clip of that ray against that
+    voxel alone (an independent slab computation per voxel)."""
+    g = TINY
+    op = C.Operator3(g)
+    x0, y0, z0 = -g.nx * g.dx / 2, -g.ny * g.dy / 2, -g.nz * g.dz / 2
+    for i in range(0, g.n_rays, 3):
+        vox, ln = op.ray_row(i)
+        got = np.zeros(g.n_vox)
+        np.add.at(got, vox, ln)
+        s = [op.r[k][i] for k in range(3)]
+        u = [op.r[k][i] for k in range(3, 6)]
+        want = np.zeros(g.n_vox)
+        for iz in range(g.nz):
+            for iy in range(g.ny):
+                for ix in range(g.nx):
+                    lo = (x0 + ix * g.dx, y0 + iy * g.dy, z0 + iz * g.dz)
+                    hi = (lo[0] + g.dx, lo[1] + g.dy, lo[2] + g.dz)
+                    want[(iz * g.ny + iy) * g.nx + ix] = _clip(lo, hi, s, u)
+        assert np.allclose(got, want, rtol=0, atol=1e-12), i
+
+
+def test_chord_through_the_volume_box():
+    g = I.c5_geometry(8)
+    op = C.Operator3(g)
+    y = op.project(np.ones((g.nz, g.ny, g.nx))).ravel()
+    lo = (-g.nx * g.dx / 2, -g.ny * g.dy / 2, -g.nz * g.dz / 2)
+    hi = tuple(-a for a in lo)
+    for i in range(0, g.n_rays, 997):
+        s = [op.r[k][i] for k in range(3)]
+        u = [op.r[k][i] for k in range(3, 6)]
+        assert y[i] == pytest.approx(_clip(lo, hi, s, u), rel=1e-12, abs=1e-12)
+
+
+def test_adjoint_identity_fp64():
+    g = I.c5_geometry(8)
+    op = C.Operator3(g)
+    rng = np.random.Generator(np.random.PCG64(3))
+    x = rng.standard_normal((g.nz, g.ny, g.nx))
+    y = rng.standard_normal((g.n_views, g.nv, g.nu))
+    px = op.project(x)
+    lhs, rhs = float(np.sum(px * y)), float(np.sum(x * op.backproject(y)))
+    assert abs(lhs - rhs) <= 1e-13 * np.linalg.norm(px) * np.linalg.norm(y)
+
+
+def test_rays_hit_the_detector_pixel_centres():
+    """The ray of pixel (iu, iv) meets the detector plane (distance sdd from the source
+    along the central direction) at u e_u + w e_z from the detector centre."""
+    g = TINY
+    sx, sy, sz, ux, uy, uz = C.rays3(g)
+    for k, th in enumerate(g.view_angles()):
+        c = np.array([-math.cos(th), -math.sin(th), 0.0])
+        eu = np.array([-math.sin(th), math.cos(th), 0.0])
+        for iv in range(g.nv):
+            for iu in range(g.nu):
+                i = (k * g.nv + iv) * g.nu + iu
+                s = np.array([sx[i], sy[i], sz[i]])
+                d = np.array([ux[i], uy[i], uz[i]])
+                assert np.linalg.norm(d) == pytest.approx(1.0, abs=1e-14)
+                hit = s + d * (g.sdd / float(d @ c)) - (s + g.sdd * c)
+                assert float(hit @ eu) == pytest.approx((iu - (g.nu - 1) / 2 + g.u_off) * g.du, abs=1e-12)
+                assert hit[2] == pytest.approx((iv - (g.nv - 1) / 2 + g.v_off) * g.dv, abs=1e-12)
+
+
+def test_extended_a3_magnitude_by_hand():
+    """f = a * j (linear along y): an interior x-face has D = 0 and pair means a j, so
+    T^2 = eps^2 + 1/2 (a^2 + a^2) from the y direction and 0 from z; likewise a z-linear
+    volume gives x-faces T^2 = eps^2 + a^2 from the z direction."""
+    eps, a = 1e-3, 0.7
+    f = a * np.broadcast_to(np.arange(6.0)[None, :, None], (5, 6, 7)).copy()
+    (Dx, Tx), _, _ = C.half_faces(f, eps)
+    assert np.allclose(Dx[1:-1, 1:-1, 2:-2], 0.0)
+    assert np.allclose(Tx[1:-1, 1:-1, 2:-2], math.sqrt(eps * eps + a * a), rtol=1e-14)
+    fz = a * np.broadcast_to(np.arange(5.0)[:, None, None], (5, 6, 7)).copy()
+    (Dx, Tx), (Dy, Ty), _ = C.half_faces(fz, eps)
+    assert np.allclose(Tx[1:-1, 1:-1, 2:-2], math.sqrt(eps * eps + a * a), rtol=1e-14)
+    assert np.allclose(Ty[1:-1, 2:-2, 1:-1], math.sqrt(eps * eps + a * a), rtol=1e-14)
+
+
+def test_plain_tv_step_gradient_textbook_sign():
+    """w = 1, eps -> 0, a step along x: delta J = -1 on the low side, +1 on the high side,
+    0 away from it (interior, where the transverse differences vanish)."""
+    f = np.zeros((8, 8, 10))
+    f[:, :, 5:] = 1.0
+    g, _, _ = C.p2_gradient(f, f, 1.0, 1e-12, 1.0, mode=O.ONE)
+    assert np.allclose(g[2:-2, 2:-2, 4], -1.0, atol=1e-9)
+    assert np.allclose(g[2:-2, 2:-2, 5], 1.0, atol=1e-9)
+    assert np.allclose(g[2:-2, 2:-2, 1:3], 0.0, atol=1e-9)
+
+
+def test_constant_volume_interior_gradient_is_fidelity_only():
+    f = np.full((8, 9, 10), 0.02)
+    v = np.random.Generator(np.random.PCG64(4)).uniform(0, 0.03, f.shape)
+    g, _, _ = C.p2_gradient(f, v, 7.0, 1e-5, 1e-3)
+    assert np.allclose(g[2:-2, 2:-2, 2:-2], 7.0 * (f - v)[2:-2, 2:-2, 2:-2], rtol=0, atol=1e-15)
+
+
+def test_p2_energy_monotone_and_reconstruction_improves():
+    rng = np.random.Generator(np.random.PCG64(5))
+    v = rng.uniform(0, 0.03, (6, 10, 10))
+    p = I.EptvParams(n_gd=12, weights_mode=O.ONE)     # fixed weights: a true descent
+    _, st = C.p2_solve(v, p, p.t_init_eff)
+    assert all(b <= a for a, b in zip(st.energies, st.energies[1:]))
+    c = I.make_c5(scale=16)
+    op = C.Operator3(c.geom)
+    f = C.reconstruct(op, c.y, I.EptvParams(n_outer=3))
+    err = np.linalg.norm(f - c.f_true) / np.linalg.norm(c.f_true)
+    assert err < 0.5 and np.all(f >= 0)

@@ -243,6 +243,57 @@ int eptv_select_kth(const eptv_geometry *g, const float *d_vals, long n, long k,
  * the GPU (other streams or threads) race and give wrong results. */
 int eptv_select_kth_noalloc(const float *d_vals, long n, long k, float *d_out, void *stream);
 
+/* ------------------------------------------------------------------ 3-D cone beam
+ * The paper is 2-D; this is the same method for a circular cone-beam scan with a flat
+ * detector.  Conventions: volume [nz][ny][nx] (x fastest), voxel (ix, iy, iz) covers
+ * [x0 + ix dx, x0 + (ix+1) dx] x ... with x0 = -nx dx / 2 (likewise y0, z0); view k at
+ * angle theta_k (angles[k], else 2 pi k / n_views), source at sid (cos, sin, 0); flat
+ * detector perpendicular to c = -(cos, sin, 0) at distance sdd from the source, pixel
+ * (iu, iv) centred at source + sdd c + u e_u + w e_z, e_u = (-sin, cos, 0),
+ * u = (iu - (nu-1)/2 + u_off) du, w = (iv - (nv-1)/2 + v_off) dv; projections
+ * [n_views][nv][nu] (ray index (k nv + iv) nu + iu).
+ * P: p_ij = length of ray i inside voxel j (Eq. 1 in 3-D); P^T its exact transpose.
+ * (P2): half-faces (App. II's half-edges extended), magnitude T^2 = eps^2 + D^2 +
+ * 1/2 (c+^2 + c-^2) over each transverse direction (A3 extended), weights Eq. (5),
+ * variation A2 extended (lagged), GD with Armijo as in 2-D; PRIOR weights are 2-D only.
+ * The cone must be narrow enough that no ray crosses z planes faster than x and y planes
+ * (EPTV_ERR_ARG otherwise).  All buffers are device FP32, caller-owned. */
+typedef struct {
+    int nx, ny, nz;
+    double dx, dy, dz;               /* voxel size (mm) */
+    int n_views;
+    const double *angles;            /* [n_views] radians, or NULL */
+    int nu, nv;                      /* detector columns, rows */
+    double du, dv;                   /* detector pixel pitch (mm) */
+    double u_off, v_off;             /* detector offsets (pixels) */
+    double sid, sdd;                 /* source-isocentre, source-detector (mm) */
+} eptv3_geometry_desc;
+
+typedef struct eptv3_geometry eptv3_geometry;
+
+/* Builds the ray table (24 bytes per ray) and the solver workspace (about 9 volumes of
+ * faces, 6 volumes, 3 projections).  EPTV_ERR_ARG, EPTV_ERR_NOMEM, EPTV_ERR_CUDA. */
+int eptv3_create_geometry(const eptv3_geometry_desc *desc, eptv3_geometry **out);
+void eptv3_destroy_geometry(eptv3_geometry *g);
+/* Warps per 32-ray block of the 3-D projector (4, 8 or 16). */
+int eptv3_set_tuning(eptv3_geometry *g, int seg);
+/* d_y [n_rays] = P d_f [n_vox]; d_f = P^T d_y. */
+int eptv3_project(const eptv3_geometry *g, const float *d_f, float *d_y, void *stream);
+int eptv3_backproject(const eptv3_geometry *g, const float *d_y, float *d_f, void *stream);
+/* M CGLS iterations (App. I) from the content of d_u, overwritten with u^(M). */
+int eptv3_cgls(const eptv3_geometry *g, int M, const float *d_y, float *d_u, void *stream);
+/* One (P2) solve from f = v (sigma from v, n_gd GD iterations with Armijo or fixed steps,
+ * then f = max(f, 0)); *t_prev_io (may be NULL) is the previous accepted step, updated.
+ * Synchronises `stream`. */
+int eptv3_tv_step(const eptv3_geometry *g, const eptv_params *p, const float *d_v, float *d_f,
+                  double *t_prev_io, eptv_stats *out_opt, void *stream);
+/* p->n_outer outer iterations from the content of d_f (clamped at 0), result in d_f. */
+int eptv3_reconstruct(const eptv3_geometry *g, const eptv_params *p, const float *d_y, float *d_f,
+                      eptv_report *rep_opt, void *stream);
+/* Eq. (2) in 3-D: mu/2 |P f - y|^2 + J(f; w(f; sigma_ref)).  Synchronises `stream`. */
+int eptv3_report_energy(const eptv3_geometry *g, const eptv_params *p, double sigma_ref,
+                        const float *d_f, const float *d_y, double *h_energy, void *stream);
+
 /* Image-quality metrics of Sec. 3 for an image d_f of g's grid (FP32 [ny][nx]) against a
  * reference d_ref_opt (the ground truth; may be NULL):
  *   rel_error  Eq. (12): |f - f_ref|^2 / |f_ref|^2                           (NaN if no ref)

@@ -90,6 +90,35 @@ def rays3(g):
     return tuple(out)
 
 
+def rays3_subset(g, idx):
+    """{ray index: (source, unit direction)} for the given ray indices (FP64), the rays of
+    rays3 without building all of them."""
+    out = {}
+    th = g.view_angles()
+    per_view = g.nv * g.nu
+    for i in np.asarray(idx, dtype=np.int64):
+        k, rem = divmod(int(i), per_view)
+        iv, iu = divmod(rem, g.nu)
+        c, s = math.cos(th[k]), math.sin(th[k])
+        u = (iu - (g.nu - 1) / 2.0 + g.u_off) * g.du
+        w = (iv - (g.nv - 1) / 2.0 + g.v_off) * g.dv
+        d = np.array([-g.sdd * c - u * s, -g.sdd * s + u * c, w])
+        d /= math.sqrt(float(d @ d))
+        out[int(i)] = (np.array([g.sid * c, g.sid * s, 0.0]), d)
+    return out
+
+
+def ray_row_of(g, s, u):
+    """Nonzeros (voxel index, length) of the row of P of the ray s + t u."""
+    cap = g.nx + g.ny + g.nz + 8
+    vox = (ctypes.c_long * cap)()
+    ln = np.empty(cap)
+    c = _load().og3_ray_row(g.nx, g.ny, g.nz, g.dx, g.dy, g.dz, float(s[0]), float(s[1]), float(s[2]),
+                            float(u[0]), float(u[1]), float(u[2]), vox, _dp(ln))
+    assert c >= 0
+    return np.array(vox[:c], dtype=np.int64), ln[:c].copy()
+
+
 class Operator3:
     """P and P^T of a cone-beam geometry, float64."""
 

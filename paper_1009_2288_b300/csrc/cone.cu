@@ -1,0 +1,897 @@
+// 3-D cone-beam EPTV (the paper's method, which is 2-D, extended to a circular cone-beam
+// scan with a flat detector; see eptv.h for the conventions).  Same algorithm as the 2-D
+// path (Sec. 2.2: CGLS for (P1), GD with Armijo for (P2), clamp), with
+//   K31  P:   ray-driven Siddon in 3-D.  A warp holds 32 adjacent detector columns of one
+//             detector row; the warps of a block split the ray's range along its major
+//             axis (x or y).  In each major-axis slab the ray walks the cells of the two
+//             minor axes incrementally, so every voxel it crosses gets the canonical
+//             length min(exit planes) - max(entry planes) of eptv_internal.cuh.
+//   K32  P^T: voxel-driven gather, the exact transpose: per view, the voxel's 8 corners
+//             bound the detector pixels whose rays can cross it, and each such ray's
+//             length through the voxel is the same canonical formula.
+//   (P2) half-face kernels (the 2-D half-edges extended to faces, Eqs. 5, 9, A2, A3 in
+//             3-D), a gradient kernel, one kernel that evaluates all Armijo trial steps,
+//             and the step/clamp kernel; every reduction is the deterministic two-level
+//             one of eptv_internal.cuh, the step decision FP64 in parallel lanes.
+#include <math.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "eptv_internal.cuh"
+#include "kernels.cuh"
+
+namespace eptv {
+
+struct RayRec3 { float px, py, pz, ix, iy, iz; };   // closest point to the origin, 1/d
+struct ViewRec3 { float sx, sy, cx, cy, ux, uy; };  // source, central direction, e_u (z = 0)
+
+struct Cone {
+    int nx, ny, nz, nv, nu, nrow;                   // nv views, nu x nrow detector
+    float dx, dy, dz, x0, y0, z0;
+    float du, dw, uc, wc;                           // column index = u / du + uc, row = w / dw + wc
+    float sdd;
+    long long n_vox, n_rays;
+    const RayRec3 *ray;
+    const ViewRec3 *view;
+};
+
+__device__ __forceinline__ float c3_len(float lo_a, float hi_a, float lo_b, float hi_b, float lo_c,
+                                        float hi_c) {
+    return fmaxf(0.0f, __fsub_rn(fminf(fminf(hi_a, hi_b), hi_c), fmaxf(fmaxf(lo_a, lo_b), lo_c)));
+}
+
+// ------------------------------------------------------------------ K31: projector
+
+template <int SEG>
+__global__ void __launch_bounds__(32 * SEG)
+k31_project(Cone C, const float *__restrict__ f, const float *__restrict__ y_resid, float *__restrict__ out,
+            double *__restrict__ partials, SliceDev *S, int fin)
+{
+    __shared__ float red[SEG][33];
+    __shared__ double rsm[2 * SEG];
+    __shared__ double res[2];
+    __shared__ int last_flag;
+    const int lane = threadIdx.x & 31, seg = threadIdx.x >> 5;
+    const int nub = (C.nu + 31) >> 5;
+    const int row_id = blockIdx.x / nub;                  // view * nrow + detector row
+    const int iu = (blockIdx.x - row_id * nub) * 32 + lane;
+    const long long ri = (long long)row_id * C.nu + iu;
+    float acc = 0.0f;
+    if (iu < C.nu) {
+        const RayRec3 R = C.ray[ri];
+        // major axis M (x or y), minor axes m (the other) and z
+        const bool ymaj = fabsf(R.ix) * C.dx >= fabsf(R.iy) * C.dy;
+        float PM, iM, M0, dM, Pm, im, m0, dm;
+        int nM, nm, sM, sm;                               // index strides of M and m
+        if (ymaj) {
+            PM = R.py; iM = R.iy; M0 = C.y0; dM = C.dy; nM = C.ny; sM = C.nx;
+            Pm = R.px; im = R.ix; m0 = C.x0; dm = C.dx; nm = C.nx; sm = 1;
+        } else {
+            PM = R.px; iM = R.ix; M0 = C.x0; dM = C.dx; nM = C.nx; sM = 1;
+            Pm = R.py; im = R.iy; m0 = C.y0; dm = C.dy; nm = C.ny; sm = C.nx;
+        }
+        float iz = R.iz;
+        if (iM < 0.0f) { iM = -iM; im = -im; iz = -iz; }  // march with t increasing along M
+        const int sgm = im > 0.0f ? 1 : -1, sgz = iz > 0.0f ? 1 : -1;
+        const int ohm = sgm > 0 ? 1 : 0, olm = 1 - ohm, ohz = sgz > 0 ? 1 : 0, olz = 1 - ohz;
+        const long long sz = (long long)C.nx * C.ny;
+        // the ray's parameter range inside the minor-axis slabs of the volume
+        const float tmA = cross_t(grid_line(0.0f, dm, m0), Pm, im);
+        const float tmB = cross_t(grid_line((float)nm, dm, m0), Pm, im);
+        const float tzA = cross_t(grid_line(0.0f, C.dz, C.z0), R.pz, iz);
+        const float tzB = cross_t(grid_line((float)C.nz, C.dz, C.z0), R.pz, iz);
+        const float t_lo = fmaxf(fminf(tmA, tmB), fminf(tzA, tzB));
+        const float t_hi = fminf(fmaxf(tmA, tmB), fmaxf(tzA, tzB));
+        const float tM0 = cross_t(grid_line(0.0f, dM, M0), PM, iM);
+        const float tMn = cross_t(grid_line((float)nM, dM, M0), PM, iM);
+        if (t_lo < t_hi && t_hi > tM0 && t_lo < tMn) {
+            const float dMinv = 1.0f / iM;
+            auto slab_of = [&](float t) {                  // largest r with t_M(r) <= t
+                int r = (int)floorf(__fdividef(PM + t * dMinv - M0, dM));
+                r = min(max(r, 0), nM - 1);
+                for (int it = 0; it < 4 && r > 0 && cross_t(grid_line((float)r, dM, M0), PM, iM) > t; ++it) --r;
+                for (int it = 0; it < 4 && r < nM - 1 && cross_t(grid_line((float)(r + 1), dM, M0), PM, iM) <= t; ++it) ++r;
+                return r;
+            };
+            const int r_first = (t_lo <= tM0) ? 0 : slab_of(t_lo);
+            const int r_last = (t_hi >= tMn) ? nM - 1 : slab_of(t_hi);
+            const int nr = r_last - r_first + 1;
+            const int chunk = (nr + SEG - 1) / SEG;
+            const int rs = r_first + seg * chunk, re = min(rs + chunk - 1, r_last);
+            if (rs <= re) {
+                float ta = cross_t(grid_line((float)rs, dM, M0), PM, iM);
+                const float t0 = fmaxf(ta, t_lo);
+                // minor cells containing t0 (lo(c) <= t0 < hi(c)), m then z
+                auto cell_of = [&](float P, float inv, float o, float d, int n, int sg, int ol, int oh) {
+                    int c = (int)floorf(__fdividef(P + t0 / inv - o, d));
+                    c = min(max(c, 0), n - 1);
+                    for (int it = 0; it < 4; ++it) {
+                        const float lo = cross_t(grid_line((float)(c + ol), d, o), P, inv);
+                        const int cn = c - sg;
+                        if (lo > t0 && cn >= 0 && cn < n) c = cn; else break;
+                    }
+                    for (int it = 0; it < 4; ++it) {
+                        const float hi = cross_t(grid_line((float)(c + oh), d, o), P, inv);
+                        const int cn = c + sg;
+                        if (hi <= t0 && cn >= 0 && cn < n) c = cn; else break;
+                    }
+                    return c;
+                };
+                int cm = cell_of(Pm, im, m0, dm, nm, sgm, olm, ohm);
+                int cz = cell_of(R.pz, iz, C.z0, C.dz, C.nz, sgz, olz, ohz);
+                float lom = cross_t(grid_line((float)(cm + olm), dm, m0), Pm, im);
+                float him = cross_t(grid_line((float)(cm + ohm), dm, m0), Pm, im);
+                float loz = cross_t(grid_line((float)(cz + olz), C.dz, C.z0), R.pz, iz);
+                float hiz = cross_t(grid_line((float)(cz + ohz), C.dz, C.z0), R.pz, iz);
+                float fr = (float)(rs + 1);
+                float tac = t0;
+                for (int r = rs; r <= re; ++r) {
+                    const float tb = cross_t(grid_line(fr, dM, M0), PM, iM);
+                    const float tbc = fminf(tb, t_hi);
+                    fr += 1.0f;
+                    // walk the (m, z) cells the ray crosses inside [tac, tbc]
+                    for (int it = 0; it < 6; ++it) {
+                        const float l = c3_len(ta, tb, lom, him, loz, hiz);
+                        const float lc = fmaxf(0.0f, __fsub_rn(fminf(fminf(tbc, him), hiz),
+                                                              fmaxf(fmaxf(tac, lom), loz)));
+                        if (lc > 0.0f && cm >= 0 && cm < nm && cz >= 0 && cz < C.nz)
+                            acc = fmaf(l, __ldg(f + (long long)cz * sz + (long long)r * sM + (long long)cm * sm), acc);
+                        const float nxt = fminf(him, hiz);
+                        if (!(nxt < tbc)) break;
+                        if (him <= hiz) {
+                            cm += sgm; lom = him;
+                            him = cross_t(grid_line((float)(cm + ohm), dm, m0), Pm, im);
+                        } else {
+                            cz += sgz; loz = hiz;
+                            hiz = cross_t(grid_line((float)(cz + ohz), C.dz, C.z0), R.pz, iz);
+                        }
+                    }
+                    ta = tb;
+                    tac = fmaxf(tb, t_lo);
+                }
+            }
+        }
+    }
+    red[seg][lane] = acc;
+    __syncthreads();
+    float sq = 0.0f, ysum = 0.0f;
+    if (seg == 0 && iu < C.nu) {
+        float tot = 0.0f;
+#pragma unroll
+        for (int w = 0; w < SEG; ++w) tot += red[w][lane];
+        const float o = y_resid ? __ldg(y_resid + ri) - tot : tot;
+        out[ri] = o;
+        sq = o * o;
+        ysum = o;
+    }
+    if (fin == FIN_NONE) return;
+    float vals[2] = {sq, ysum};
+    block_sum_to<2, 32 * SEG>(vals, partials + (size_t)blockIdx.x * 2, rsm);
+    if (!reduce_slice<2, 32 * SEG>(*S, partials, 2, 0, gridDim.x, blockIdx.x, rsm, res, &last_flag)) return;
+    if (threadIdx.x == 0) finalize(S->sc, fin, res[0], res[1]);
+}
+
+// ------------------------------------------------------------------ K32: back projector
+
+__global__ void __launch_bounds__(256)
+k32_backproject(Cone C, const float *__restrict__ y, float *__restrict__ out, double *__restrict__ partials,
+                SliceDev *S, int fin)
+{
+    __shared__ double rsm[2 * 8];
+    __shared__ double res[2];
+    __shared__ int last_flag;
+    const long long vox = (long long)blockIdx.x * 256 + threadIdx.x;
+    float acc = 0.0f;
+    const bool valid = vox < C.n_vox;
+    if (valid) {
+        const int ix = (int)(vox % C.nx);
+        const int iy = (int)((vox / C.nx) % C.ny);
+        const int iz = (int)(vox / ((long long)C.nx * C.ny));
+        const float X0 = grid_line((float)ix, C.dx, C.x0), X1 = grid_line((float)(ix + 1), C.dx, C.x0);
+        const float Y0 = grid_line((float)iy, C.dy, C.y0), Y1 = grid_line((float)(iy + 1), C.dy, C.y0);
+        const float Z0 = grid_line((float)iz, C.dz, C.z0), Z1 = grid_line((float)(iz + 1), C.dz, C.z0);
+        for (int v = 0; v < C.nv; ++v) {
+            const ViewRec3 V = C.view[v];
+            float umin = 3e38f, umax = -3e38f, wmin = 3e38f, wmax = -3e38f;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const float px = (c & 1) ? X1 : X0, py = (c & 2) ? Y1 : Y0, pz = (c & 4) ? Z1 : Z0;
+                const float wx = px - V.sx, wy = py - V.sy;
+                const float depth = V.cx * wx + V.cy * wy;            // along the central ray
+                const float sc = __fdividef(C.sdd, depth);
+                const float u = (V.ux * wx + V.uy * wy) * sc;
+                const float w = pz * sc;
+                umin = fminf(umin, u); umax = fmaxf(umax, u);
+                wmin = fminf(wmin, w); wmax = fmaxf(wmax, w);
+            }
+            const int iu0 = max(0, (int)ceilf(umin / C.du + C.uc - 0.01f));
+            const int iu1 = min(C.nu - 1, (int)floorf(umax / C.du + C.uc + 0.01f));
+            const int iv0 = max(0, (int)ceilf(wmin / C.dw + C.wc - 0.01f));
+            const int iv1 = min(C.nrow - 1, (int)floorf(wmax / C.dw + C.wc + 0.01f));
+            for (int iv = iv0; iv <= iv1; ++iv) {
+                const long long rowbase = ((long long)v * C.nrow + iv) * C.nu;
+                for (int iu = iu0; iu <= iu1; ++iu) {
+                    const RayRec3 R = C.ray[rowbase + iu];
+                    const float ax = cross_t(X0, R.px, R.ix), bx = cross_t(X1, R.px, R.ix);
+                    const float ay = cross_t(Y0, R.py, R.iy), by = cross_t(Y1, R.py, R.iy);
+                    const float az = cross_t(Z0, R.pz, R.iz), bz = cross_t(Z1, R.pz, R.iz);
+                    const float l = c3_len(fminf(ax, bx), fmaxf(ax, bx), fminf(ay, by), fmaxf(ay, by),
+                                           fminf(az, bz), fmaxf(az, bz));
+                    if (l > 0.0f) acc = fmaf(l, __ldg(y + rowbase + iu), acc);
+                }
+            }
+        }
+        out[vox] = acc;
+    }
+    if (fin == FIN_NONE) return;
+    float vals[1] = {valid ? acc * acc : 0.0f};
+    block_sum_to<1, 256>(vals, partials + (size_t)blockIdx.x * 2, rsm);
+    if (threadIdx.x == 0) partials[(size_t)blockIdx.x * 2 + 1] = 0.0;
+    if (!reduce_slice<2, 256>(*S, partials, 2, 0, gridDim.x, blockIdx.x, rsm, res, &last_flag)) return;
+    if (threadIdx.x == 0) finalize(S->sc, fin, res[0], res[1]);
+}
+
+// ------------------------------------------------------------------ CGLS vectors
+
+// sum of x^2 (and of x) over n values -> finalize(fin)
+__global__ void __launch_bounds__(256)
+k3v_norm2(const float *__restrict__ x, long long n, double *__restrict__ partials, SliceDev *S, int fin)
+{
+    __shared__ double rsm[2 * 8];
+    __shared__ double res[2];
+    __shared__ int last_flag;
+    float s2 = 0.0f, s1 = 0.0f;
+    const long long i0 = (long long)blockIdx.x * 1024 + threadIdx.x;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const long long i = i0 + q * 256;
+        if (i < n) { const float v = __ldg(x + i); s2 = fmaf(v, v, s2); s1 += v; }
+    }
+    float vals[2] = {s2, s1};
+    block_sum_to<2, 256>(vals, partials + (size_t)blockIdx.x * 2, rsm);
+    if (!reduce_slice<2, 256>(*S, partials, 2, 0, gridDim.x, blockIdx.x, rsm, res, &last_flag)) return;
+    if (threadIdx.x == 0) finalize(S->sc, fin, res[0], res[1]);
+}
+
+// y += sign * sc[which] * x
+__global__ void __launch_bounds__(256)
+k3v_axpy(float *__restrict__ y, const float *__restrict__ x, long long n, const double *__restrict__ sc,
+         int which, float sign)
+{
+    const long long i = (long long)blockIdx.x * 256 + threadIdx.x;
+    if (i >= n) return;
+    const float a = sign * (float)sc[which];
+    y[i] = fmaf(a, x[i], y[i]);
+}
+
+// u += a s; then (more) s = t + b s
+__global__ void __launch_bounds__(256)
+k3v_update_us(float *__restrict__ u, float *__restrict__ s, const float *__restrict__ t, long long n,
+              const double *__restrict__ sc, int more)
+{
+    const long long i = (long long)blockIdx.x * 256 + threadIdx.x;
+    if (i >= n) return;
+    const float a = (float)sc[SC_A], b = (float)sc[SC_B];
+    const float sv = s[i];
+    u[i] = fmaf(a, sv, u[i]);
+    if (more) s[i] = fmaf(b, sv, t[i]);
+}
+
+// ------------------------------------------------------------------ (P2) in 3-D
+
+// Face numbering: x-faces (nx+1) ny nz, then y-faces nx (ny+1) nz, then z-faces
+// nx ny (nz+1), each x fastest.  Face of family d at (i, j, k) lies between voxel
+// (i, j, k) - e_d ("a") and (i, j, k) ("b").
+struct Vol {
+    int nx, ny, nz;
+    long long nfx, nfy, nfz, nf;
+};
+
+__device__ __forceinline__ float vol_at(const float *f, const Vol &V, int i, int j, int k) {
+    if (i < 0 || j < 0 || k < 0 || i >= V.nx || j >= V.ny || k >= V.nz) return 0.0f;
+    return __ldg(f + ((long long)k * V.ny + j) * V.nx + i);
+}
+
+// decode face index -> family d, position (i, j, k)
+__device__ __forceinline__ int face_pos(const Vol &V, long long e, int &i, int &j, int &k) {
+    int d;
+    long long r;
+    int wx, wy;
+    if (e < V.nfx) { d = 0; r = e; wx = V.nx + 1; wy = V.ny; }
+    else if (e < V.nfx + V.nfy) { d = 1; r = e - V.nfx; wx = V.nx; wy = V.ny + 1; }
+    else { d = 2; r = e - V.nfx - V.nfy; wx = V.nx; wy = V.ny; }
+    i = (int)(r % wx);
+    j = (int)((r / wx) % wy);
+    k = (int)(r / ((long long)wx * wy));
+    return d;
+}
+
+// D, and the transverse parts of T^2 (A3 extended) of a face, from image x; also the
+// bilinear quantities of the Armijo decomposition when a second image g is given:
+// a = D dD + 1/2 sum c dc, b = dD^2 + 1/2 sum dc^2.
+__device__ __forceinline__ void face_terms(const float *x, const float *gx, const Vol &V, int d, int i, int j,
+                                           int k, float eps2, float &D, float &T2, float &ae, float &be) {
+    const int ai = i - (d == 0), aj = j - (d == 1), ak = k - (d == 2);
+    const float xa = vol_at(x, V, ai, aj, ak), xb = vol_at(x, V, i, j, k);
+    D = xb - xa;
+    T2 = eps2 + D * D;
+    float ga = 0.f, gb = 0.f, dD = 0.f;
+    if (gx) { ga = vol_at(gx, V, ai, aj, ak); gb = vol_at(gx, V, i, j, k); dD = gb - ga; }
+    ae = D * dD;
+    be = dD * dD;
+    const float mc = 0.5f * (xa + xb), gc = 0.5f * (ga + gb);
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+        if (t == d) continue;
+        const int ei = (t == 0), ej = (t == 1), ek = (t == 2);
+        const float mp = 0.5f * (vol_at(x, V, ai + ei, aj + ej, ak + ek) + vol_at(x, V, i + ei, j + ej, k + ek));
+        const float mm = 0.5f * (vol_at(x, V, ai - ei, aj - ej, ak - ek) + vol_at(x, V, i - ei, j - ej, k - ek));
+        const float cp = mp - mc, cm = mc - mm;
+        T2 += 0.5f * cp * cp + 0.5f * cm * cm;
+        if (gx) {
+            const float gp = 0.5f * (vol_at(gx, V, ai + ei, aj + ej, ak + ek) + vol_at(gx, V, i + ei, j + ej, k + ek));
+            const float gm = 0.5f * (vol_at(gx, V, ai - ei, aj - ej, ak - ek) + vol_at(gx, V, i - ei, j - ej, k - ek));
+            const float dcp = gp - gc, dcm = gc - gm;
+            ae += 0.5f * (cp * dcp + cm * dcm);
+            be += 0.5f * (dcp * dcp + dcm * dcm);
+        }
+    }
+}
+
+// T of every face of x (for sigma)
+__global__ void __launch_bounds__(256)
+k3tv_face_T(Vol V, const float *__restrict__ x, float eps2, float *__restrict__ T)
+{
+    const long long e = (long long)blockIdx.x * 256 + threadIdx.x;
+    if (e >= V.nf) return;
+    int i, j, k;
+    const int d = face_pos(V, e, i, j, k);
+    float D, T2, ae, be;
+    face_terms(x, nullptr, V, d, i, j, k, eps2, D, T2, ae, be);
+    T[e] = T2 * rsqrtf(T2);
+}
+
+// per face: T, w (Eq. 5 with sigma = sc[SC_SIGMA], or 1), q = w D / T; sum of w T (J)
+__global__ void __launch_bounds__(256)
+k3tv_faces(Vol V, const float *__restrict__ f, float eps2, int mode, float *__restrict__ Q,
+           float *__restrict__ TT, float *__restrict__ WW, double *__restrict__ partials, SliceDev *S)
+{
+    __shared__ double rsm[1 * 8];
+    __shared__ double res[1];
+    __shared__ int last_flag;
+    const long long e = (long long)blockIdx.x * 256 + threadIdx.x;
+    const float sig = (float)S->sc[SC_SIGMA];
+    const float inv_s2 = 1.0f / (sig * sig);
+    float wt = 0.0f;
+    if (e < V.nf) {
+        int i, j, k;
+        const int d = face_pos(V, e, i, j, k);
+        float D, T2, ae, be;
+        face_terms(f, nullptr, V, d, i, j, k, eps2, D, T2, ae, be);
+        const float rs = rsqrtf(T2);
+        const float T = T2 * rs;
+        const float w = (mode == EPTV_WEIGHTS_ONE) ? 1.0f : __expf(-T2 * inv_s2);
+        Q[e] = w * D * rs;
+        TT[e] = T;
+        WW[e] = w;
+        wt = w * T;
+    }
+    float vals[1] = {wt};
+    block_sum_to<1, 256>(vals, partials + (size_t)blockIdx.x * kPartialStride, rsm);
+    if (!reduce_slice<1, 256>(*S, partials, kPartialStride, 0, gridDim.x, blockIdx.x, rsm, res, &last_flag)) return;
+    if (threadIdx.x == 0) S->sc[SC_Q0] = res[0];                   // J
+}
+
+// g = lambda (f - v) - div Q; sums A = g.(f - v), B = g.g, F = |f - v|^2
+__global__ void __launch_bounds__(256)
+k3tv_grad(Vol V, const float *__restrict__ f, const float *__restrict__ v, const float *__restrict__ Q,
+          float lam, float *__restrict__ g, double *__restrict__ partials, SliceDev *S)
+{
+    __shared__ double rsm[3 * 8];
+    __shared__ double res[3];
+    __shared__ int last_flag;
+    const long long p = (long long)blockIdx.x * 256 + threadIdx.x;
+    float A = 0.f, B = 0.f, F = 0.f;
+    const long long nvox = (long long)V.nx * V.ny * V.nz;
+    if (p < nvox) {
+        const int i = (int)(p % V.nx), j = (int)((p / V.nx) % V.ny), k = (int)(p / ((long long)V.nx * V.ny));
+        const float *Qx = Q, *Qy = Q + V.nfx, *Qz = Q + V.nfx + V.nfy;
+        const long long ex = ((long long)k * V.ny + j) * (V.nx + 1) + i;
+        const long long ey = ((long long)k * (V.ny + 1) + j) * V.nx + i;
+        const long long ez = ((long long)k * V.ny + j) * V.nx + i;
+        const float div = (__ldg(Qx + ex + 1) - __ldg(Qx + ex)) + (__ldg(Qy + ey + V.nx) - __ldg(Qy + ey)) +
+                          (__ldg(Qz + ez + (long long)V.nx * V.ny) - __ldg(Qz + ez));
+        const float d = __ldg(f + p) - __ldg(v + p);
+        const float gv = lam * d - div;
+        g[p] = gv;
+        A = gv * d;
+        B = gv * gv;
+        F = d * d;
+    }
+    float vals[3] = {A, B, F};
+    block_sum_to<3, 256>(vals, partials + (size_t)blockIdx.x * kPartialStride, rsm);
+    if (!reduce_slice<3, 256>(*S, partials, kPartialStride, 0, gridDim.x, blockIdx.x, rsm, res, &last_flag)) return;
+    if (threadIdx.x < 3) S->sc[SC_Q0 + 1 + threadIdx.x] = res[threadIdx.x];   // A, B, F
+}
+
+// All Armijo trials of one GD iteration: per face, with frozen w and T,
+// dJ_m += w (T'^2 - T^2) / (T' + T), T'^2 - T^2 = t (t b - 2 a); then the decision.
+template <int KT>
+__global__ void __launch_bounds__(256)
+k3tv_trials(Vol V, const float *__restrict__ f, const float *__restrict__ g, const float *__restrict__ TT,
+            const float *__restrict__ WW, const ParamsDev *__restrict__ P, int K, int first, int energy_only,
+            double *__restrict__ partials, SliceDev *S)
+{
+    __shared__ float s_t[KT];
+    __shared__ double s_td[KT];
+    __shared__ double rsm[KT * 8];
+    __shared__ double tot[KT];
+    __shared__ int last_flag;
+    if (threadIdx.x == 0) {
+        double t;
+        if (P->step_rule == EPTV_STEP_FIXED) t = P->t_fixed;
+        else t = fmin(P->armijo_grow * S->sc[SC_TPREV], P->t_max > 0.0 ? P->t_max : 1.0 / P->lambda);
+        for (int m = 0; m < KT; ++m) {
+            s_t[m] = (float)t;
+            s_td[m] = (double)(float)t;
+            t *= P->armijo_shrink;
+        }
+    }
+    __syncthreads();
+    const float eps2 = (float)(P->eps * P->eps);
+    const long long e = (long long)blockIdx.x * 256 + threadIdx.x;
+    float dJ[KT];
+#pragma unroll
+    for (int m = 0; m < KT; ++m) dJ[m] = 0.0f;
+    if (e < V.nf && K > 0) {
+        int i, j, k;
+        const int d = face_pos(V, e, i, j, k);
+        float D, T2x, ae, be;
+        face_terms(f, g, V, d, i, j, k, eps2, D, T2x, ae, be);
+        const float T = __ldg(TT + e), w = __ldg(WW + e);
+        const float T2 = T * T;
+#pragma unroll
+        for (int m = 0; m < KT; ++m) {
+            if (m < K) {
+                const float t = s_t[m];
+                const float num = t * fmaf(t, be, -2.0f * ae);
+                const float T2n = fmaxf(T2 + num, eps2);
+                const float Tn = T2n * rsqrtf(T2n);
+                dJ[m] = w * __fdividef(num, Tn + T);
+            }
+        }
+    }
+    block_sum_to<KT, 256>(dJ, partials + (size_t)blockIdx.x * kPartialStride, rsm);
+    if (!reduce_slice<KT, 256>(*S, partials, kPartialStride, 0, gridDim.x, blockIdx.x, rsm, tot, &last_flag))
+        return;
+    if (threadIdx.x < 32) {
+        double *sc = S->sc;
+        const double J = sc[SC_Q0], A = sc[SC_Q0 + 1], Bg = sc[SC_Q0 + 2], F = sc[SC_Q0 + 3];
+        const double lamd = P->lambda;
+        const double E0 = 0.5 * lamd * F + J;
+        const bool armijo = !energy_only && P->step_rule != EPTV_STEP_FIXED;
+        double dl = 0.0;
+        bool pass = false, nonfinite = false;
+        if (armijo && threadIdx.x < K) {
+            const double t = s_td[threadIdx.x];
+            dl = lamd * (-t * A + 0.5 * t * t * Bg) + tot[threadIdx.x];
+            nonfinite = !isfinite(dl);
+            pass = dl <= -P->armijo_c * t * Bg;
+        }
+        const unsigned pass_mask = __ballot_sync(0xffffffffu, pass);
+        const unsigned bad_mask = __ballot_sync(0xffffffffu, nonfinite);
+        const int acc_m = pass_mask ? __ffs(pass_mask) - 1 : -1;
+        const double dE = __shfl_sync(0xffffffffu, dl, acc_m >= 0 ? acc_m : 0);
+        if (threadIdx.x == 0) {
+            bool bad = !isfinite(E0) || !isfinite(A) || !isfinite(Bg);
+            if (energy_only) {
+                sc[SC_E_FIRST] = E0;
+            } else {
+                if (first) sc[SC_E_FIRST] = E0;
+                if (P->step_rule == EPTV_STEP_FIXED) {
+                    const double t = s_td[0];
+                    sc[SC_TSTEP] = t;
+                    sc[SC_E_LAST] = E0 + lamd * (-t * A + 0.5 * t * t * Bg) + (K > 0 ? tot[0] : 0.0);
+                    sc[SC_NACC_P2] += 1.0;
+                } else {
+                    const unsigned seen = acc_m >= 0 ? ((2u << acc_m) - 1u) : ((1u << K) - 1u);
+                    if (bad_mask & seen) bad = true;
+                    if (acc_m >= 0) {
+                        sc[SC_TSTEP] = s_td[acc_m];
+                        sc[SC_TPREV] = s_td[acc_m];
+                        sc[SC_E_LAST] = E0 + dE;
+                        sc[SC_NACC_P2] += 1.0;
+                    } else {
+                        sc[SC_TSTEP] = 0.0;
+                        sc[SC_TPREV] = s_td[K - 1] * P->armijo_shrink / P->armijo_grow;
+                        sc[SC_E_LAST] = E0;
+                        sc[SC_NFAIL] += 1.0;
+                        sc[SC_NFAIL_P2] += 1.0;
+                    }
+                }
+            }
+            if (bad) sc[SC_NONFINITE] = 1.0;
+        }
+    }
+}
+
+// f_out = f - sc[SC_TSTEP] g, clamped at 0 when clamp (the last step of a (P2) solve)
+__global__ void __launch_bounds__(256)
+k3tv_apply(const float *__restrict__ f, const float *__restrict__ g, float *__restrict__ out, long long n,
+           const double *__restrict__ sc, int clamp)
+{
+    const long long i = (long long)blockIdx.x * 256 + threadIdx.x;
+    if (i >= n) return;
+    float x = fmaf(-(float)sc[SC_TSTEP], g[i], f[i]);
+    if (clamp) x = fmaxf(x, 0.0f);
+    out[i] = x;
+}
+
+__global__ void k3_set_sigma(const float *__restrict__ val, double floor_, SliceDev *S) {
+    S->sc[SC_SIGMA] = fmax((double)*val, floor_);
+}
+
+__global__ void k3_set_scalar(SliceDev *S, int which, double value) { S->sc[which] = value; }
+
+__global__ void __launch_bounds__(256) k3_clamp(float *__restrict__ x, long long n) {
+    const long long i = (long long)blockIdx.x * 256 + threadIdx.x;
+    if (i < n) x[i] = fmaxf(x[i], 0.0f);
+}
+
+// ------------------------------------------------------------------ host side
+
+static unsigned nblk_of(long long n, int per) { return (unsigned)((n + per - 1) / per); }
+
+}  // namespace eptv
+
+using namespace eptv;
+
+struct eptv3_geometry {
+    eptv3_geometry_desc desc;
+    std::vector<double> angles;
+    Cone C;
+    Vol V;
+    int k31_seg = 8;
+    RayRec3 *ray = nullptr;
+    ViewRec3 *view = nullptr;
+    float *u = nullptr, *s = nullptr, *t = nullptr, *fa = nullptr, *fb = nullptr, *g = nullptr;
+    float *y = nullptr, *r = nullptr, *q = nullptr;
+    float *Q = nullptr, *TT = nullptr, *WW = nullptr, *Tsel = nullptr, *sel = nullptr;
+    double *partials = nullptr, *gpart = nullptr, *sc = nullptr;
+    unsigned int *ctr = nullptr;
+    SliceDev *d_sd = nullptr;
+    ParamsDev *d_params = nullptr;
+    std::vector<void *> allocs;
+};
+
+static int c3_fail(int code, const std::string &m) { return report_error(code, m.c_str()); }
+
+#define C3CU(call)                                                                         \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return c3_fail(EPTV_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+template <class T>
+static int c3_alloc(eptv3_geometry *g, T **p, size_t count) {
+    void *q = nullptr;
+    if (cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        return c3_fail(EPTV_ERR_NOMEM, "cudaMalloc failed for the cone-beam workspace");
+    }
+    g->allocs.push_back(q);
+    *p = static_cast<T *>(q);
+    return 0;
+}
+
+static float c3_inv(double c) {
+    if (std::fabs(c) < 1e-30) return c < 0 ? -1e30f : 1e30f;
+    return (float)(1.0 / c);
+}
+
+static void c3_project(const eptv3_geometry *g, const float *f, const float *y_resid, float *out, int fin,
+                       cudaStream_t st) {
+    const unsigned nb = (unsigned)((long long)g->C.nv * g->C.nrow * ((g->C.nu + 31) / 32));
+    switch (g->k31_seg) {
+    case 4: k31_project<4><<<nb, 128, 0, st>>>(g->C, f, y_resid, out, g->partials, g->d_sd, fin); break;
+    case 16: k31_project<16><<<nb, 512, 0, st>>>(g->C, f, y_resid, out, g->partials, g->d_sd, fin); break;
+    default: k31_project<8><<<nb, 256, 0, st>>>(g->C, f, y_resid, out, g->partials, g->d_sd, fin); break;
+    }
+}
+
+static void c3_backproject(const eptv3_geometry *g, const float *y, float *out, int fin, cudaStream_t st) {
+    k32_backproject<<<nblk_of(g->C.n_vox, 256), 256, 0, st>>>(g->C, y, out, g->partials, g->d_sd, fin);
+}
+
+// (P1): M CGLS iterations on g->u (App. I), data g->y
+static void c3_cgls(const eptv3_geometry *g, int M, cudaStream_t st) {
+    const long long nv = g->C.n_vox, nr = g->C.n_rays;
+    c3_project(g, g->u, g->y, g->r, FIN_NONE, st);                       // r = y - P u
+    c3_backproject(g, g->r, g->s, FIN_GAMMA0, st);                       // s = P^T r, gamma
+    for (int m = 0; m < M; ++m) {
+        c3_project(g, g->s, nullptr, g->q, FIN_QQ_TO_A, st);             // q = P s, a
+        const bool more = m + 1 < M;
+        if (more) {
+            k3v_axpy<<<nblk_of(nr, 256), 256, 0, st>>>(g->r, g->q, nr, g->sc, SC_A, -1.0f);
+            c3_backproject(g, g->r, g->t, FIN_B, st);                    // t = P^T r, b
+        }
+        k3v_update_us<<<nblk_of(nv, 256), 256, 0, st>>>(g->u, g->s, g->t, nv, g->sc, more ? 1 : 0);
+    }
+}
+
+// (P2) on v = g->fa (the CGLS result copied there), result clamped into `out`
+static int c3_p2(const eptv3_geometry *g, const eptv_params *p, const float *v, float *out, cudaStream_t st) {
+    const Vol &V = g->V;
+    const long long nv = g->C.n_vox;
+    const float eps2 = (float)(p->eps * p->eps);
+    // sigma: k-th smallest face magnitude of v
+    k3tv_face_T<<<nblk_of(V.nf, 256), 256, 0, st>>>(V, v, eps2, g->Tsel);
+    const long long rank = std::min<long long>(std::max<long long>((long long)std::ceil(p->sigma_q * V.nf), 1), V.nf);
+    const char *err = "";
+    int rc = select_kth_noalloc(g->Tsel, (long)V.nf, (long)rank, g->sel, st, &err);
+    if (rc) return c3_fail(rc, err);
+    k3_set_sigma<<<1, 1, 0, st>>>(g->sel, p->sigma_floor, g->d_sd);
+    k3_set_scalar<<<1, 1, 0, st>>>(g->d_sd, SC_NFAIL_P2, 0.0);
+    k3_set_scalar<<<1, 1, 0, st>>>(g->d_sd, SC_NACC_P2, 0.0);
+    const int K = p->step_rule == EPTV_STEP_FIXED ? 1 : p->max_trials;
+    const int mode = p->weights_mode == EPTV_WEIGHTS_ONE ? EPTV_WEIGHTS_ONE : EPTV_WEIGHTS_EPTV;
+    const float *cur = v;
+    for (int n = 0; n < p->n_gd; ++n) {
+        float *nxt = (n == p->n_gd - 1) ? out : ((cur == g->fb) ? g->u : g->fb);
+        if (nxt == v) nxt = g->fb;
+        k3tv_faces<<<nblk_of(V.nf, 256), 256, 0, st>>>(V, cur, eps2, mode, g->Q, g->TT, g->WW, g->partials, g->d_sd);
+        k3tv_grad<<<nblk_of(nv, 256), 256, 0, st>>>(V, cur, v, g->Q, (float)p->lambda, g->g, g->partials, g->d_sd);
+        const unsigned nbf = nblk_of(V.nf, 256);
+        if (K <= 1) k3tv_trials<1><<<nbf, 256, 0, st>>>(V, cur, g->g, g->TT, g->WW, g->d_params, K, n == 0, 0, g->partials, g->d_sd);
+        else if (K <= 4) k3tv_trials<4><<<nbf, 256, 0, st>>>(V, cur, g->g, g->TT, g->WW, g->d_params, K, n == 0, 0, g->partials, g->d_sd);
+        else if (K <= 8) k3tv_trials<8><<<nbf, 256, 0, st>>>(V, cur, g->g, g->TT, g->WW, g->d_params, K, n == 0, 0, g->partials, g->d_sd);
+        else k3tv_trials<16><<<nbf, 256, 0, st>>>(V, cur, g->g, g->TT, g->WW, g->d_params, K, n == 0, 0, g->partials, g->d_sd);
+        k3tv_apply<<<nblk_of(nv, 256), 256, 0, st>>>(cur, g->g, nxt, nv, g->sc, n == p->n_gd - 1 ? 1 : 0);
+        cur = nxt;
+    }
+    if (p->n_gd == 0) {
+        C3CU(cudaMemcpyAsync(out, v, sizeof(float) * nv, cudaMemcpyDeviceToDevice, st));
+        k3_clamp<<<nblk_of(nv, 256), 256, 0, st>>>(out, nv);
+    }
+    C3CU(cudaGetLastError());
+    return 0;
+}
+
+static int c3_read_sc(const eptv3_geometry *g, double *h, cudaStream_t st) {
+    C3CU(cudaMemcpyAsync(h, g->sc, sizeof(double) * kScalarStride, cudaMemcpyDeviceToHost, st));
+    C3CU(cudaStreamSynchronize(st));
+    return 0;
+}
+
+static int c3_upload_params(const eptv3_geometry *g, const eptv_params *p, cudaStream_t st) {
+    ParamsDev pd;
+    fill_params(p, &pd);
+    C3CU(cudaMemcpyAsync(g->d_params, &pd, sizeof pd, cudaMemcpyHostToDevice, st));
+    return 0;
+}
+
+extern "C" {
+
+int eptv3_create_geometry(const eptv3_geometry_desc *d, eptv3_geometry **out) {
+    if (!d || !out) return c3_fail(EPTV_ERR_ARG, "NULL argument");
+    *out = nullptr;
+    if (d->nx < 1 || d->ny < 1 || d->nz < 1 || d->n_views < 1 || d->nu < 1 || d->nv < 1)
+        return c3_fail(EPTV_ERR_ARG, "sizes must be >= 1");
+    if (!(d->dx > 0 && d->dy > 0 && d->dz > 0 && d->du > 0 && d->dv > 0))
+        return c3_fail(EPTV_ERR_ARG, "pitches must be > 0");
+    const double R = 0.5 * std::sqrt(d->nx * d->dx * d->nx * d->dx + d->ny * d->dy * d->ny * d->dy);
+    if (!(d->sid > R) || !(d->sdd > d->sid)) return c3_fail(EPTV_ERR_ARG, "need sdd > sid > half-diagonal");
+    const long long n_vox = (long long)d->nx * d->ny * d->nz;
+    const long long n_rays = (long long)d->n_views * d->nu * d->nv;
+    if (n_vox > (1LL << 31) - 1 || n_rays > (1LL << 31) - 1) return c3_fail(EPTV_ERR_ARG, "volume or scan too large");
+    eptv3_geometry *g = new eptv3_geometry();
+    g->desc = *d;
+    if (d->angles) {
+        g->angles.assign(d->angles, d->angles + d->n_views);
+        g->desc.angles = g->angles.data();
+    }
+    // ray and view tables in FP64, stored FP32
+    std::vector<RayRec3> rays((size_t)n_rays);
+    std::vector<ViewRec3> views((size_t)d->n_views);
+    for (int k = 0; k < d->n_views; ++k) {
+        const double th = d->angles ? d->angles[k] : 2.0 * M_PI * k / d->n_views;
+        const double c = std::cos(th), s = std::sin(th);
+        const double Sx = d->sid * c, Sy = d->sid * s;
+        views[k] = ViewRec3{(float)Sx, (float)Sy, (float)-c, (float)-s, (float)-s, (float)c};
+        for (int iv = 0; iv < d->nv; ++iv) {
+            const double w = (iv - (d->nv - 1) / 2.0 + d->v_off) * d->dv;
+            for (int iu = 0; iu < d->nu; ++iu) {
+                const double u = (iu - (d->nu - 1) / 2.0 + d->u_off) * d->du;
+                double ux = -d->sdd * c - u * s, uy = -d->sdd * s + u * c, uz = w;
+                const double n = std::sqrt(ux * ux + uy * uy + uz * uz);
+                ux /= n; uy /= n; uz /= n;
+                const double proj = Sx * ux + Sy * uy;
+                const double Px = Sx - proj * ux, Py = Sy - proj * uy, Pz = -proj * uz;
+                const bool zmaj = std::fabs(uz) / d->dz >= std::max(std::fabs(ux) / d->dx, std::fabs(uy) / d->dy);
+                if (zmaj) {
+                    delete g;
+                    return c3_fail(EPTV_ERR_ARG, "cone too wide: a ray crosses z planes faster than x and y planes");
+                }
+                rays[((size_t)k * d->nv + iv) * d->nu + iu] =
+                    RayRec3{(float)Px, (float)Py, (float)Pz, c3_inv(ux), c3_inv(uy), c3_inv(uz)};
+            }
+        }
+    }
+    Cone &C = g->C;
+    C.nx = d->nx; C.ny = d->ny; C.nz = d->nz; C.nv = d->n_views; C.nu = d->nu; C.nrow = d->nv;
+    C.dx = (float)d->dx; C.dy = (float)d->dy; C.dz = (float)d->dz;
+    C.x0 = (float)(-0.5 * d->nx * d->dx); C.y0 = (float)(-0.5 * d->ny * d->dy); C.z0 = (float)(-0.5 * d->nz * d->dz);
+    C.du = (float)d->du; C.dw = (float)d->dv;
+    C.uc = (float)((d->nu - 1) / 2.0 - d->u_off); C.wc = (float)((d->nv - 1) / 2.0 - d->v_off);
+    C.sdd = (float)d->sdd;
+    C.n_vox = n_vox; C.n_rays = n_rays;
+    Vol &V = g->V;
+    V.nx = d->nx; V.ny = d->ny; V.nz = d->nz;
+    V.nfx = (long long)(d->nx + 1) * d->ny * d->nz;
+    V.nfy = (long long)d->nx * (d->ny + 1) * d->nz;
+    V.nfz = (long long)d->nx * d->ny * (d->nz + 1);
+    V.nf = V.nfx + V.nfy + V.nfz;
+    // workspace
+    const long long blk_k31 = (long long)d->n_views * d->nv * ((d->nu + 31) / 32);
+    const long long blk_face = (V.nf + 255) / 256, blk_vox = (n_vox + 255) / 256;
+    const long long maxblk = std::max(blk_k31, std::max(blk_face, std::max(blk_vox, (n_rays + 1023) / 1024)));
+    const long long groups = (maxblk + kRedGroup - 1) / kRedGroup;
+    int rc = 0;
+    auto A = [&](auto **p, size_t n) { if (!rc) rc = c3_alloc(g, p, n); };
+    A(&g->ray, (size_t)n_rays); A(&g->view, (size_t)d->n_views);
+    for (float **p : {&g->u, &g->s, &g->t, &g->fa, &g->fb, &g->g}) A(p, (size_t)n_vox);
+    for (float **p : {&g->y, &g->r, &g->q}) A(p, (size_t)n_rays);
+    for (float **p : {&g->Q, &g->TT, &g->WW, &g->Tsel}) A(p, (size_t)V.nf);
+    A(&g->sel, 1);
+    A(&g->partials, (size_t)std::max(blk_k31 * 2, std::max(blk_face, blk_vox) * kPartialStride));
+    A(&g->gpart, (size_t)groups * kPartialStride);
+    A(&g->ctr, (size_t)groups + 1);
+    A(&g->sc, kScalarStride);
+    A(&g->d_sd, 1);
+    A(&g->d_params, 1);
+    if (rc) { eptv3_destroy_geometry(g); return rc; }
+    C.ray = g->ray; C.view = g->view;
+    SliceDev sd;
+    memset(&sd, 0, sizeof sd);
+    sd.ctr = g->ctr; sd.gpart = g->gpart; sd.sc = g->sc;
+    if (cudaMemcpy(g->ray, rays.data(), sizeof(RayRec3) * (size_t)n_rays, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(g->view, views.data(), sizeof(ViewRec3) * views.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(g->d_sd, &sd, sizeof sd, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(g->ctr, 0, sizeof(unsigned int) * ((size_t)groups + 1)) != cudaSuccess ||
+        cudaMemset(g->sc, 0, sizeof(double) * kScalarStride) != cudaSuccess) {
+        eptv3_destroy_geometry(g);
+        return c3_fail(EPTV_ERR_CUDA, "upload of the cone-beam tables failed");
+    }
+    *out = g;
+    return 0;
+}
+
+void eptv3_destroy_geometry(eptv3_geometry *g) {
+    if (!g) return;
+    cudaDeviceSynchronize();
+    for (void *p : g->allocs) cudaFree(p);
+    delete g;
+}
+
+int eptv3_set_tuning(eptv3_geometry *g, int seg) {
+    if (!g || (seg != 4 && seg != 8 && seg != 16)) return c3_fail(EPTV_ERR_ARG, "seg must be 4, 8 or 16");
+    g->k31_seg = seg;
+    return 0;
+}
+
+int eptv3_project(const eptv3_geometry *g, const float *d_f, float *d_y, void *stream) {
+    if (!g || !d_f || !d_y) return c3_fail(EPTV_ERR_ARG, "NULL argument");
+    c3_project(g, d_f, nullptr, d_y, FIN_NONE, (cudaStream_t)stream);
+    C3CU(cudaGetLastError());
+    return 0;
+}
+
+int eptv3_backproject(const eptv3_geometry *g, const float *d_y, float *d_f, void *stream) {
+    if (!g || !d_f || !d_y) return c3_fail(EPTV_ERR_ARG, "NULL argument");
+    c3_backproject(g, d_y, d_f, FIN_NONE, (cudaStream_t)stream);
+    C3CU(cudaGetLastError());
+    return 0;
+}
+
+int eptv3_cgls(const eptv3_geometry *g, int M, const float *d_y, float *d_u, void *stream) {
+    if (!g || !d_y || !d_u) return c3_fail(EPTV_ERR_ARG, "NULL argument");
+    if (M < 0) return c3_fail(EPTV_ERR_ARG, "M < 0");
+    cudaStream_t st = (cudaStream_t)stream;
+    C3CU(cudaMemcpyAsync(g->y, d_y, sizeof(float) * g->C.n_rays, cudaMemcpyDeviceToDevice, st));
+    C3CU(cudaMemcpyAsync(g->u, d_u, sizeof(float) * g->C.n_vox, cudaMemcpyDeviceToDevice, st));
+    c3_cgls(g, M, st);
+    C3CU(cudaGetLastError());
+    C3CU(cudaMemcpyAsync(d_u, g->u, sizeof(float) * g->C.n_vox, cudaMemcpyDeviceToDevice, st));
+    return 0;
+}
+
+int eptv3_tv_step(const eptv3_geometry *g, const eptv_params *p, const float *d_v, float *d_f,
+                  double *t_prev_io, eptv_stats *out_opt, void *stream) {
+    if (!g || !d_v || !d_f) return c3_fail(EPTV_ERR_ARG, "NULL argument");
+    int rc = check_params(p);
+    if (rc) return rc;
+    if (p->weights_mode == EPTV_WEIGHTS_PRIOR) return c3_fail(EPTV_ERR_ARG, "PRIOR weights are 2-D only");
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = c3_upload_params(g, p, st))) return rc;
+    const double t0 = (t_prev_io && *t_prev_io > 0.0) ? *t_prev_io : (p->t_init > 0.0 ? p->t_init : 1.0 / p->lambda);
+    k3_set_scalar<<<1, 1, 0, st>>>(g->d_sd, SC_TPREV, t0);
+    k3_set_scalar<<<1, 1, 0, st>>>(g->d_sd, SC_NONFINITE, 0.0);
+    k3_set_scalar<<<1, 1, 0, st>>>(g->d_sd, SC_NFAIL, 0.0);
+    C3CU(cudaMemcpyAsync(g->fa, d_v, sizeof(float) * g->C.n_vox, cudaMemcpyDeviceToDevice, st));
+    if ((rc = c3_p2(g, p, g->fa, d_f, st))) return rc;
+    double sc[kScalarStride];
+    if ((rc = c3_read_sc(g, sc, st))) return rc;
+    if (sc[SC_NONFINITE] != 0.0) return c3_fail(EPTV_ERR_NONFINITE, "non-finite value in the (P2) solve");
+    if (t_prev_io) *t_prev_io = sc[SC_TPREV];
+    if (out_opt) {
+        out_opt->sigma = sc[SC_SIGMA];
+        out_opt->energy_first = sc[SC_E_FIRST];
+        out_opt->energy_last = sc[SC_E_LAST];
+        out_opt->t_prev = sc[SC_TPREV];
+        out_opt->n_accepted = (int)sc[SC_NACC_P2];
+        out_opt->n_fail = (int)sc[SC_NFAIL_P2];
+        out_opt->status = out_opt->n_fail ? EPTV_WARN_LINESEARCH : EPTV_OK;
+    }
+    return 0;
+}
+
+int eptv3_reconstruct(const eptv3_geometry *g, const eptv_params *p, const float *d_y, float *d_f,
+                      eptv_report *rep_opt, void *stream) {
+    if (!g || !d_y || !d_f) return c3_fail(EPTV_ERR_ARG, "NULL argument");
+    int rc = check_params(p);
+    if (rc) return rc;
+    if (p->weights_mode == EPTV_WEIGHTS_PRIOR) return c3_fail(EPTV_ERR_ARG, "PRIOR weights are 2-D only");
+    cudaStream_t st = (cudaStream_t)stream;
+    const long long nv = g->C.n_vox;
+    if ((rc = c3_upload_params(g, p, st))) return rc;
+    C3CU(cudaMemcpyAsync(g->y, d_y, sizeof(float) * g->C.n_rays, cudaMemcpyDeviceToDevice, st));
+    C3CU(cudaMemcpyAsync(g->u, d_f, sizeof(float) * nv, cudaMemcpyDeviceToDevice, st));
+    k3_clamp<<<nblk_of(nv, 256), 256, 0, st>>>(g->u, nv);
+    k3_set_scalar<<<1, 1, 0, st>>>(g->d_sd, SC_TPREV, p->t_init > 0.0 ? p->t_init : 1.0 / p->lambda);
+    k3_set_scalar<<<1, 1, 0, st>>>(g->d_sd, SC_NONFINITE, 0.0);
+    k3_set_scalar<<<1, 1, 0, st>>>(g->d_sd, SC_NFAIL, 0.0);
+    for (int k = 0; k < p->n_outer; ++k) {
+        c3_cgls(g, p->cgls_iters, st);                                   // v = CGLS_M(u) in u
+        C3CU(cudaMemcpyAsync(g->fa, g->u, sizeof(float) * nv, cudaMemcpyDeviceToDevice, st));
+        if ((rc = c3_p2(g, p, g->fa, g->u, st))) return rc;              // (P2) + clamp -> u
+    }
+    C3CU(cudaMemcpyAsync(d_f, g->u, sizeof(float) * nv, cudaMemcpyDeviceToDevice, st));
+    if (rep_opt) {
+        double sc[kScalarStride];
+        if ((rc = c3_read_sc(g, sc, st))) return rc;
+        if (sc[SC_NONFINITE] != 0.0) return c3_fail(EPTV_ERR_NONFINITE, "non-finite value during the reconstruction");
+        rep_opt->n_outer = p->n_outer;
+        rep_opt->sigma_last = sc[SC_SIGMA];
+        rep_opt->t_prev = sc[SC_TPREV];
+        rep_opt->n_fail = (int)sc[SC_NFAIL];
+        rep_opt->status = rep_opt->n_fail ? EPTV_WARN_LINESEARCH : EPTV_OK;
+        rep_opt->n_launches = 0;
+    }
+    return 0;
+}
+
+int eptv3_report_energy(const eptv3_geometry *g, const eptv_params *p, double sigma_ref, const float *d_f,
+                        const float *d_y, double *h_energy, void *stream) {
+    if (!g || !d_f || !d_y || !h_energy) return c3_fail(EPTV_ERR_ARG, "NULL argument");
+    int rc = check_params(p);
+    if (rc) return rc;
+    if (!(sigma_ref > 0.0)) return c3_fail(EPTV_ERR_ARG, "sigma_ref must be > 0");
+    cudaStream_t st = (cudaStream_t)stream;
+    c3_project(g, d_f, d_y, g->q, FIN_NORM, st);                         // |y - P f|^2 -> SC_NORM
+    k3_set_scalar<<<1, 1, 0, st>>>(g->d_sd, SC_SIGMA, sigma_ref);
+    const int mode = p->weights_mode == EPTV_WEIGHTS_ONE ? EPTV_WEIGHTS_ONE : EPTV_WEIGHTS_EPTV;
+    k3tv_faces<<<nblk_of(g->V.nf, 256), 256, 0, st>>>(g->V, d_f, (float)(p->eps * p->eps), mode, g->Q, g->TT,
+                                                       g->WW, g->partials, g->d_sd);
+    C3CU(cudaGetLastError());
+    double sc[kScalarStride];
+    if ((rc = c3_read_sc(g, sc, st))) return rc;
+    *h_energy = 0.5 * p->mu * sc[SC_NORM] + sc[SC_Q0];
+    return 0;
+}
+
+}  // extern "C"

@@ -113,7 +113,7 @@ struct eptv_geometry {
 
 namespace eptv {
 
-static void fill_params(const eptv_params *p, ParamsDev *d) {
+void fill_params(const eptv_params *p, ParamsDev *d) {
     memset(d, 0, sizeof *d);
     d->lambda = p->lambda;
     d->mu = p->mu;
@@ -135,7 +135,7 @@ static void fill_params(const eptv_params *p, ParamsDev *d) {
     d->prior_iters = p->prior_iters;
 }
 
-static int check_params(const eptv_params *p) {
+int check_params(const eptv_params *p) {
     if (!p) return fail(EPTV_ERR_ARG, "params is NULL");
     if (p->n_outer < 0 || p->cgls_iters < 0 || p->n_gd < 0)
         return fail(EPTV_ERR_ARG, "negative iteration count");

@@ -126,6 +126,13 @@ typedef cudaError_t (*StoredAlloc)(void *ctx, void **p, size_t bytes);
 cudaError_t build_stored(const SliceDev &S, const SliceDev *d_sd, StoredAlloc alloc, void *ctx,
                          StoredMatrices *m, cudaStream_t st);
 void launch_spmv_p(const Batch &B, const ProjArgs &a, cudaStream_t st);
+// parameter checks and the device copy of a parameter record (host.cu)
+void fill_params(const eptv_params *p, ParamsDev *d);
+int check_params(const eptv_params *p);
+int report_error(int code, const char *msg);
+int select_kth_noalloc(const float *d_vals, long n, long k, float *d_out, cudaStream_t st,
+                       const char **err);
+
 void launch_quality(const Batch &B, const float *f, const float *r, int rx0, int ry0, int rw, int rh,
                     double scale2, unsigned char *bf, unsigned char *br, cudaStream_t st);
 void launch_spmv_pt(const Batch &B, const BackArgs &a, cudaStream_t st);

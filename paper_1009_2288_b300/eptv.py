@@ -29,6 +29,8 @@ EXPORTED = [
     "eptv_unet_upsample2", "eptv_unet_upsample2_bwd", "eptv_unet_relu_bwd", "eptv_unet_head",
     "eptv_unet_adam", "eptv_unet_pack_input", "eptv_set_operator", "eptv_matrix_info",
     "eptv_copy_matrix", "eptv_backproject_eq11", "eptv_quality_metrics",
+    "eptv3_create_geometry", "eptv3_destroy_geometry", "eptv3_set_tuning", "eptv3_project",
+    "eptv3_backproject", "eptv3_cgls", "eptv3_tv_step", "eptv3_reconstruct", "eptv3_report_energy",
 ]
 
 
@@ -61,6 +63,15 @@ class Stats(ctypes.Structure):
     _fields_ = [("sigma", ctypes.c_double), ("energy_first", ctypes.c_double),
                 ("energy_last", ctypes.c_double), ("t_prev", ctypes.c_double),
                 ("n_accepted", ctypes.c_int), ("n_fail", ctypes.c_int), ("status", ctypes.c_int)]
+
+
+class GeometryDesc3(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
+                ("n_views", ctypes.c_int), ("angles", ctypes.POINTER(ctypes.c_double)),
+                ("nu", ctypes.c_int), ("nv", ctypes.c_int), ("du", ctypes.c_double), ("dv", ctypes.c_double),
+                ("u_off", ctypes.c_double), ("v_off", ctypes.c_double), ("sid", ctypes.c_double),
+                ("sdd", ctypes.c_double)]
 
 
 class Quality(ctypes.Structure):
@@ -139,6 +150,15 @@ def load():
         "eptv_unet_pack_input": (c_int, [vp, ctypes.c_float, vp, ctypes.c_float, ctypes.c_longlong, vp, vp]),
         "eptv_set_operator": (c_int, [vp, c_int, ctypes.POINTER(ctypes.c_longlong)]),
         "eptv_backproject_eq11": (c_int, [vp, vp, vp, vp]),
+        "eptv3_create_geometry": (c_int, [ctypes.POINTER(GeometryDesc3), ctypes.POINTER(vp)]),
+        "eptv3_destroy_geometry": (None, [vp]),
+        "eptv3_set_tuning": (c_int, [vp, c_int]),
+        "eptv3_project": (c_int, [vp, vp, vp, vp]),
+        "eptv3_backproject": (c_int, [vp, vp, vp, vp]),
+        "eptv3_cgls": (c_int, [vp, c_int, vp, vp, vp]),
+        "eptv3_tv_step": (c_int, [vp, ctypes.POINTER(Params), vp, vp, ctypes.POINTER(dbl), ctypes.POINTER(Stats), vp]),
+        "eptv3_reconstruct": (c_int, [vp, ctypes.POINTER(Params), vp, vp, ctypes.POINTER(Report), vp]),
+        "eptv3_report_energy": (c_int, [vp, ctypes.POINTER(Params), dbl, vp, vp, ctypes.POINTER(dbl), vp]),
         "eptv_quality_metrics": (c_int, [vp, vp, vp, ctypes.POINTER(c_int), ctypes.c_double, vp, vp,
                                          ctypes.POINTER(Quality), vp]),
         "eptv_matrix_info": (c_int, [vp, c_int, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
@@ -501,3 +521,89 @@ def eptv_unet_adam(p, g, m, v, lr, beta1, beta2, eps, step, stream=None):
 
 def version() -> str:
     return load().eptv_version().decode()
+
+
+# ------------------------------------------------------------------ 3-D cone beam
+
+class Geometry3:
+    """Owner of one eptv3_geometry handle (cone-beam ray table + workspace)."""
+
+    def __init__(self, g):
+        L = load()
+        self.g = g
+        self._angles = None
+        d = GeometryDesc3(g.nx, g.ny, g.nz, g.dx, g.dy, g.dz, g.n_views, None, g.nu, g.nv, g.du, g.dv,
+                          g.u_off, g.v_off, g.sid, g.sdd)
+        if g.angles is not None:
+            arr = (ctypes.c_double * g.n_views)(*[float(a) for a in g.angles])
+            self._angles = arr
+            d.angles = ctypes.cast(arr, ctypes.POINTER(ctypes.c_double))
+        h = ctypes.c_void_p()
+        _check(L.eptv3_create_geometry(ctypes.byref(d), ctypes.byref(h)))
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().eptv3_destroy_geometry(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def n_vox(self):
+        return self.g.n_vox
+
+    @property
+    def n_rays(self):
+        return self.g.n_rays
+
+
+def eptv3_set_tuning(geom: Geometry3, seg: int):
+    _check(load().eptv3_set_tuning(geom.handle, int(seg)))
+
+
+def eptv3_project(geom: Geometry3, f, y, stream=None):
+    _check(load().eptv3_project(geom.handle, _ptr(f, geom.n_vox, "f"), _ptr(y, geom.n_rays, "y"), _stream(stream)))
+    return y
+
+
+def eptv3_backproject(geom: Geometry3, y, f, stream=None):
+    _check(load().eptv3_backproject(geom.handle, _ptr(y, geom.n_rays, "y"), _ptr(f, geom.n_vox, "f"),
+                                    _stream(stream)))
+    return f
+
+
+def eptv3_cgls(geom: Geometry3, M: int, y, u, stream=None):
+    _check(load().eptv3_cgls(geom.handle, int(M), _ptr(y, geom.n_rays, "y"), _ptr(u, geom.n_vox, "u"),
+                             _stream(stream)))
+    return u
+
+
+def eptv3_tv_step(geom: Geometry3, p: EptvParams, v, f, t_prev: Optional[float] = None, stream=None):
+    pp = params(p)
+    st = Stats()
+    tp = ctypes.c_double(t_prev if t_prev is not None else 0.0)
+    _check(load().eptv3_tv_step(geom.handle, ctypes.byref(pp), _ptr(v, geom.n_vox, "v"), _ptr(f, geom.n_vox, "f"),
+                                ctypes.byref(tp), ctypes.byref(st), _stream(stream)))
+    return st, tp.value
+
+
+def eptv3_reconstruct(geom: Geometry3, p: EptvParams, y, f, report: bool = True, stream=None):
+    pp = params(p)
+    rep = Report()
+    _check(load().eptv3_reconstruct(geom.handle, ctypes.byref(pp), _ptr(y, geom.n_rays, "y"),
+                                    _ptr(f, geom.n_vox, "f"), ctypes.byref(rep) if report else None,
+                                    _stream(stream)))
+    return rep if report else None
+
+
+def eptv3_report_energy(geom: Geometry3, p: EptvParams, sigma_ref: float, f, y, stream=None) -> float:
+    out = ctypes.c_double()
+    pp = params(p)
+    _check(load().eptv3_report_energy(geom.handle, ctypes.byref(pp), float(sigma_ref), _ptr(f, geom.n_vox, "f"),
+                                      _ptr(y, geom.n_rays, "y"), ctypes.byref(out), _stream(stream)))
+    return out.value

@@ -13,7 +13,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def declared_functions():
     src = open(os.path.join(ROOT, "include", "eptv.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(eptv_[a-z_0-9]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(eptv3?_[a-z_0-9]+)\s*\(", src)))
 
 
 def test_library_builds_and_exports_every_declared_symbol():

@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--no-stored", action="store_true")
     ap.add_argument("--no-eq11", action="store_true")
     ap.add_argument("--no-quality", action="store_true")
+    ap.add_argument("--no-cone", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     return ap.parse_args()
 
@@ -428,6 +429,59 @@ def run_quality(dev, stream, n_outer):
     return out
 
 
+def run_cone(dev, stream, peak, n_outer=5, steps=2):
+    """3-D cone-beam workload (256^3 at 1 mm, 120 views, flat 512 x 384 detector at 0.8 mm,
+    SID 1000, SDD 1500; seeded ellipsoid phantom with low-contrast spheres, I0 = 5e4):
+    projector and back-projector launch times with their SpMV-equivalent bytes (8 B per
+    nonzero of P + the two vectors), and the rate of n_outer outer iterations."""
+    import torch
+    from paper_1009_2288_b300 import cone
+    from paper_1009_2288_b300 import eptv as E
+    from paper_1009_2288_b300 import inputs as I
+    g = I.c5_geometry(1)
+    t0 = time.time()
+    geo = E.Geometry3(g)
+    t_create = time.time() - t0
+    t0 = time.time()
+    y = cone.c5_sinogram_gpu(5, g, dev)
+    torch.cuda.synchronize()
+    t_synth = time.time() - t0
+    nnz = cone.nnz_of(g)
+    f = torch.zeros(g.n_vox, device=dev)
+    E.eptv3_backproject(geo, y, f)
+    f.mul_(1e-4)
+    yb = torch.empty(g.n_rays, device=dev)
+    best = None
+    for seg in (4, 8, 16):
+        E.eptv3_set_tuning(geo, seg)
+        t = time_kernel(lambda: E.eptv3_project(geo, f, yb), n=5)
+        if best is None or t < best[1]:
+            best = (seg, t)
+    E.eptv3_set_tuning(geo, best[0])
+    t_p = best[1]
+    fb = torch.empty_like(f)
+    t_pt = time_kernel(lambda: E.eptv3_backproject(geo, y, fb), n=5)
+    algo = 8 * nnz + 4 * (g.n_vox + g.n_rays)
+    p = I.EptvParams(n_outer=n_outer)
+    E.eptv3_reconstruct(geo, I.EptvParams(n_outer=1), y, f.zero_(), report=False)
+    times = []
+    for _ in range(steps):
+        f.zero_()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        E.eptv3_reconstruct(geo, p, y, f, report=False)
+        e.record(stream)
+        e.synchronize()
+        times.append(s.elapsed_time(e))
+    ms = statistics.mean(times)
+    return {"workload": "cone_256x256x256_120v_512x384", "create_s": t_create, "synth_s": t_synth,
+            "nnz": nnz, "k31_seg": best[0],
+            "project_ms": t_p * 1e3, "backproject_ms": t_pt * 1e3,
+            "project_equiv_gbs": algo / t_p / 1e9, "project_frac": algo / t_p / 1e9 / peak,
+            "backproject_equiv_gbs": algo / t_pt / 1e9, "backproject_frac": algo / t_pt / 1e9 / peak,
+            "reconstruct": {"n_outer": n_outer, "ms_per_step": ms, "iterations_per_s": n_outer * 1e3 / ms}}
+
+
 def run_learned(dev, stream, n_pairs=2000, epochs=40, eval_seeds=(1, 2, 3, 4), k_ws=(0, 2)):
     """Learned warm start on the 256^2 (1.6 mm), 30 views x 888 bins, I0 = 5e4 workload.
     Trains the U-Net on n_pairs pairs that the plain method generates (50 iterations each,
@@ -659,6 +713,10 @@ def run_ours(args, world, rank, local):
     if not args.no_batched and rank == 0:
         batched = run_batched(dev, stream)
 
+    cone3 = None
+    if not args.no_cone and rank == 0:
+        cone3 = run_cone(dev, stream, peak)
+
     quality = None
     if not args.no_quality and rank == 0:
         quality = run_quality(dev, stream, N_OUTER)
@@ -699,6 +757,7 @@ def run_ours(args, world, rank, local):
         "stored": stored,
         "backprojector_eq11": eq11,
         "quality": quality,
+        "cone_3d": cone3,
         "learned": learned,
         "clocks": clk,
         "paper_context": {"workload": "NCAT 512^2, 40 views, 50 iterations (Table 2)",

@@ -46,6 +46,10 @@ def parse():
     ap.add_argument("--no-eq11", action="store_true")
     ap.add_argument("--no-quality", action="store_true")
     ap.add_argument("--no-cone", action="store_true")
+    ap.add_argument("--cone-only", action="store_true",
+                    help="profiling mode: run only the cone-beam leg and print its JSON")
+    ap.add_argument("--cone-scale", type=int, default=1,
+                    help="divide the cone-beam grid and detector counts (reduced profiling cases)")
     ap.add_argument("--no-batched", action="store_true")
     return ap.parse_args()
 
@@ -236,18 +240,24 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
-def time_kernel(fn, n=50):
+def time_kernel(fn, n=50, windows=5):
+    """Seconds per launch of fn on the current stream: the median over `windows` windows
+    of n back-to-back launches (CUDA events), after 20 warm-up launches."""
     import torch
-    for _ in range(5):
+    for _ in range(20):
         fn()
     torch.cuda.synchronize()
-    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    s.record()
-    for _ in range(n):
-        fn()
-    e.record()
-    torch.cuda.synchronize()
-    return s.elapsed_time(e) / n * 1e-3     # seconds per launch
+    stream = torch.cuda.current_stream()
+    per = []
+    for _ in range(windows):
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        for _ in range(n):
+            fn()
+        e.record(stream)
+        e.synchronize()
+        per.append(s.elapsed_time(e) / n * 1e-3)
+    return statistics.median(per)
 
 
 def run_batched(dev, stream, n_slices=64, n_outer=50, steps=3):
@@ -429,7 +439,7 @@ def run_quality(dev, stream, n_outer):
     return out
 
 
-def run_cone(dev, stream, peak, n_outer=5, steps=2):
+def run_cone(dev, stream, peak, n_outer=5, steps=2, scale=1):
     """3-D cone-beam workload (256^3 at 1 mm, 120 views, flat 512 x 384 detector at 0.8 mm,
     SID 1000, SDD 1500; seeded ellipsoid phantom with low-contrast spheres, I0 = 5e4):
     projector and back-projector launch times with their SpMV-equivalent bytes (8 B per
@@ -438,7 +448,7 @@ def run_cone(dev, stream, peak, n_outer=5, steps=2):
     from paper_1009_2288_b300 import cone
     from paper_1009_2288_b300 import eptv as E
     from paper_1009_2288_b300 import inputs as I
-    g = I.c5_geometry(1)
+    g = I.c5_geometry(scale)
     t0 = time.time()
     geo = E.Geometry3(g)
     t_create = time.time() - t0
@@ -474,7 +484,8 @@ def run_cone(dev, stream, peak, n_outer=5, steps=2):
         e.synchronize()
         times.append(s.elapsed_time(e))
     ms = statistics.mean(times)
-    return {"workload": "cone_256x256x256_120v_512x384", "create_s": t_create, "synth_s": t_synth,
+    return {"workload": f"cone_{g.nx}x{g.ny}x{g.nz}_{g.n_views}v_{g.nu}x{g.nv}",
+            "create_s": t_create, "synth_s": t_synth,
             "nnz": nnz, "k31_seg": best[0],
             "project_ms": t_p * 1e3, "backproject_ms": t_pt * 1e3,
             "project_equiv_gbs": algo / t_p / 1e9, "project_frac": algo / t_p / 1e9 / peak,
@@ -576,6 +587,12 @@ def run_ours(args, world, rank, local):
     B.build()
     E.load()
     dev = torch.device("cuda", local)
+    if args.cone_only:
+        if rank == 0:
+            peak, _ = measured_peaks()
+            out = run_cone(dev, torch.cuda.current_stream(dev), peak, steps=args.steps, scale=args.cone_scale)
+            print(json.dumps({"cone_3d": out}), flush=True)
+        return
     case = I.make_c2(seed=2 + rank, with_truth=False)
     g = case.geom
     geo = E.Geometry(g)
@@ -715,7 +732,7 @@ def run_ours(args, world, rank, local):
 
     cone3 = None
     if not args.no_cone and rank == 0:
-        cone3 = run_cone(dev, stream, peak)
+        cone3 = run_cone(dev, stream, peak, scale=args.cone_scale)
 
     quality = None
     if not args.no_quality and rank == 0:

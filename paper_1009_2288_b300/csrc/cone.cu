@@ -561,7 +561,8 @@ struct eptv3_geometry {
     float *u = nullptr, *s = nullptr, *t = nullptr, *fa = nullptr, *fb = nullptr, *g = nullptr;
     float *y = nullptr, *r = nullptr, *q = nullptr;
     float *Q = nullptr, *TT = nullptr, *WW = nullptr, *Tsel = nullptr, *sel = nullptr;
-    double *partials = nullptr, *gpart = nullptr, *sc = nullptr;
+    double *partials = nullptr, *sc = nullptr;
+    unsigned long long *acc = nullptr;
     unsigned int *ctr = nullptr;
     SliceDev *d_sd = nullptr;
     ParamsDev *d_params = nullptr;
@@ -740,7 +741,6 @@ int eptv3_create_geometry(const eptv3_geometry_desc *d, eptv3_geometry **out) {
     const long long blk_k31 = (long long)d->n_views * d->nv * ((d->nu + 31) / 32);
     const long long blk_face = (V.nf + 255) / 256, blk_vox = (n_vox + 255) / 256;
     const long long maxblk = std::max(blk_k31, std::max(blk_face, std::max(blk_vox, (n_rays + 1023) / 1024)));
-    const long long groups = (maxblk + kRedGroup - 1) / kRedGroup;
     int rc = 0;
     auto A = [&](auto **p, size_t n) { if (!rc) rc = c3_alloc(g, p, n); };
     A(&g->ray, (size_t)n_rays); A(&g->view, (size_t)d->n_views);
@@ -749,8 +749,8 @@ int eptv3_create_geometry(const eptv3_geometry_desc *d, eptv3_geometry **out) {
     for (float **p : {&g->Q, &g->TT, &g->WW, &g->Tsel}) A(p, (size_t)V.nf);
     A(&g->sel, 1);
     A(&g->partials, (size_t)std::max(blk_k31 * 2, std::max(blk_face, blk_vox) * kPartialStride));
-    A(&g->gpart, (size_t)groups * kPartialStride);
-    A(&g->ctr, (size_t)groups + 1);
+    A(&g->acc, (size_t)kPartialStride * kAccStride);
+    A(&g->ctr, 1);
     A(&g->sc, kScalarStride);
     A(&g->d_sd, 1);
     A(&g->d_params, 1);
@@ -758,11 +758,12 @@ int eptv3_create_geometry(const eptv3_geometry_desc *d, eptv3_geometry **out) {
     C.ray = g->ray; C.view = g->view;
     SliceDev sd;
     memset(&sd, 0, sizeof sd);
-    sd.ctr = g->ctr; sd.gpart = g->gpart; sd.sc = g->sc;
+    sd.ctr = g->ctr; sd.acc = g->acc; sd.sc = g->sc;
     if (cudaMemcpy(g->ray, rays.data(), sizeof(RayRec3) * (size_t)n_rays, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(g->view, views.data(), sizeof(ViewRec3) * views.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(g->d_sd, &sd, sizeof sd, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemset(g->ctr, 0, sizeof(unsigned int) * ((size_t)groups + 1)) != cudaSuccess ||
+        cudaMemset(g->ctr, 0, sizeof(unsigned int)) != cudaSuccess ||
+        cudaMemset(g->acc, 0, sizeof(unsigned long long) * kPartialStride * kAccStride) != cudaSuccess ||
         cudaMemset(g->sc, 0, sizeof(double) * kScalarStride) != cudaSuccess) {
         eptv3_destroy_geometry(g);
         return c3_fail(EPTV_ERR_CUDA, "upload of the cone-beam tables failed");

@@ -101,10 +101,10 @@ struct SliceDev {
     double *log;         // optional per-iteration log: [n_outer * n_gd] steps, then [n_outer] sigmas
     int log_outer;       // capacity in outer iterations (0: no log)
     int log_gd;          // GD iterations per outer iteration in the log layout
-    // reduction bookkeeping of this slice in its batch: ticket counters ([0] final level,
-    // [1 + g] group g) and the group partial sums ([group][kPartialStride] doubles)
+    // reduction bookkeeping of this slice in its batch: the ticket counter ctr[0] and the
+    // exact accumulators ([kPartialStride][kAccStride] words, zero between launches)
     unsigned int *ctr;
-    double *gpart;
+    unsigned long long *acc;
     // stored operator (null unless selected): SELL-32 P (rows = rays), P^T (rows = pixels)
     const int *p_sptr, *p_slen, *p_scol;
     const float *p_sval;
@@ -173,62 +173,118 @@ __device__ __forceinline__ bool last_block_of_slice(unsigned int *counter, int n
     return *flag_smem != 0;
 }
 
-// Blocks per first-level group of the two-level reduction below; doubles per block (and
-// per group) in the partial-sum arrays.
-constexpr int kRedGroup = 32;
+// Doubles per block in the partial-sum arrays (the most values one reduction carries).
 constexpr int kMaxTrials = 16;
 constexpr int kPartialStride = kMaxTrials + 8;
 
-// All NT threads of a finishing block: res[k] = sum over blocks first .. first + count - 1
-// of src[block * stride + k], k < NV (NV <= 32), as a fixed-shape tree, so the result is
-// deterministic.  FP64 adds have a long latency on this GPU, so the tree is wide rather than
-// deep: thread t takes value k = t % NVP (NVP = NV rounded up to a power of two) and blocks
-// j, j + J, ... (j = t / NVP, J = NT / NVP); the threads of a warp that hold the same k
-// combine by shuffles, and thread k adds the NT/32 warp results.
-template <int NV, int NT>
-__device__ __forceinline__ void group_sum(const double *src, int stride, int first, int count,
-                                          double *wpart /* NV * NT/32, smem */, double *res /* NV */) {
-    constexpr int NVP = NV <= 1 ? 1 : NV <= 2 ? 2 : NV <= 4 ? 4 : NV <= 8 ? 8 : NV <= 16 ? 16 : 32;
-    constexpr int J = NT / NVP, NW = NT / 32;
-    const int t = threadIdx.x, k = t % NVP, j = t / NVP;
-    double a = 0.0;
-    if (k < NV) {
-        int b = j;
-        if (b < count) a = __ldcg(src + (size_t)(first + b) * stride + k);
-        for (b += J; b < count; b += J) a += __ldcg(src + (size_t)(first + b) * stride + k);
+// Exact, order-independent sums of FP64 block partials.  A value x is a binary fixed-point
+// number with its least significant bit at 2^kAccLsbExp; that number is split into 32-bit
+// chunks, and chunk c is added with a 64-bit integer atomic into word c of the value's
+// accumulator (a word takes 2^31 additions before it could overflow).  Integer addition is
+// associative, so the total does not depend on the order in which blocks finish, and the
+// block that finishes last rounds the exact total once to FP64.  Every block partial of
+// the kernels is a sum of FP32 numbers, hence a multiple of 2^-149, so for them the total
+// is the correctly rounded exact sum; finite bits below 2^kAccLsbExp (smaller doubles) are
+// truncated toward zero.  Non-finite values, and magnitudes of 2^191 and above, set flags
+// (result NaN, or +-Inf); the two top words stay free for carries, so a total of up to
+// 2^31 values cannot overflow.
+constexpr int kAccChunks = 12;                 // bits 2^-149 .. 2^234
+constexpr int kAccStride = kAccChunks + 1;     // + one word of flags
+constexpr int kAccLsbExp = -149;
+constexpr unsigned long long kAccNaN = 1ull, kAccPosInf = 2ull, kAccNegInf = 4ull;
+
+__device__ __forceinline__ void acc_add(unsigned long long *acc, double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const bool neg = (b >> 63) != 0;
+    const int ex = (int)((b >> 52) & 0x7FFull);
+    unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+    if (ex == 0x7FF) {
+        atomicOr(acc + kAccChunks, m ? kAccNaN : (neg ? kAccNegInf : kAccPosInf));
+        return;
     }
+    if (ex) m |= 1ull << 52;
+    if (m == 0ull) return;
+    int sh = (ex ? ex : 1) - 1075 - kAccLsbExp;            // |x| = m 2^(sh + kAccLsbExp)
+    if (sh < 0) {
+        if (sh <= -53) return;
+        m >>= -sh;
+        sh = 0;
+        if (m == 0ull) return;
+    }
+    if (sh > 32 * (kAccChunks - 4) + 31) {                 // |x| >= 2^191
+        atomicOr(acc + kAccChunks, neg ? kAccNegInf : kAccPosInf);
+        return;
+    }
+    const int c = sh >> 5, r = sh & 31;
+    const unsigned long long lo = m << r;                  // m < 2^53: m 2^r < 2^84
+    const unsigned long long hi = r ? (m >> (64 - r)) : 0ull;
+    const unsigned long long d[3] = {lo & 0xFFFFFFFFull, lo >> 32, hi};
 #pragma unroll
-    for (int o = NVP; o < 32; o <<= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-    const int lane = t & 31, w = t >> 5;
-    if (lane < NV) wpart[w * NV + lane] = a;
-    __syncthreads();
-    if (t < NV) {
-        double r = 0.0;
-        for (int i = 0; i < NW; ++i) r += wpart[i * NV + t];
-        res[t] = r;
-    }
-    __syncthreads();
+    for (int q = 0; q < 3; ++q)
+        if (d[q]) atomicAdd(acc + c + q, neg ? (0ull - d[q]) : d[q]);
 }
 
-// Two-level deterministic reduction of the NV per-block partial sums that the nblk blocks
-// of a slice wrote to partials[b0 + lb][0 .. NV) (row stride `stride`), lb = the calling
-// block's index within the slice.  Every kRedGroup consecutive blocks form a group: the
-// block of a group that finishes last (atomic ticket) sums the group in block order and
-// stores the result in S.gpart; the group finisher that comes last sums the group results
-// in group order.  Returns true only in that block, with the totals in res (smem).
-// Spreads the FP64 work over nblk / kRedGroup SMs instead of one.
+// The accumulated total, rounded to nearest FP64; re-zeroes the accumulator.  Called by
+// one thread per value after every contribution is visible.
+__device__ __forceinline__ double acc_finish(unsigned long long *acc) {
+    long long w[kAccChunks];
+#pragma unroll
+    for (int i = 0; i < kAccChunks; ++i) w[i] = (long long)__ldcg(acc + i);
+    const unsigned long long flags = __ldcg(acc + kAccChunks);
+#pragma unroll
+    for (int i = 0; i < kAccStride; ++i) acc[i] = 0ull;
+    if ((flags & kAccNaN) || (flags & (kAccPosInf | kAccNegInf)) == (kAccPosInf | kAccNegInf))
+        return __longlong_as_double(0x7FF8000000000000ll);
+    if (flags & kAccPosInf) return __longlong_as_double(0x7FF0000000000000ll);
+    if (flags & kAccNegInf) return __longlong_as_double((long long)0xFFF0000000000000ull);
+    // carries: 32-bit digits, the sign in the final carry (0 or -1: |total| < 2^222)
+    unsigned int dg[kAccChunks];
+    long long carry = 0;
+#pragma unroll
+    for (int i = 0; i < kAccChunks; ++i) {
+        const long long t = w[i] + carry;
+        dg[i] = (unsigned int)(t & 0xFFFFFFFFll);
+        carry = t >> 32;                                   // floor division by 2^32
+    }
+    const bool neg = carry < 0;
+    if (neg) {                                             // magnitude: two's complement
+        unsigned long long c1 = 1ull;
+#pragma unroll
+        for (int i = 0; i < kAccChunks; ++i) {
+            const unsigned long long t = (unsigned long long)(~dg[i]) + c1;
+            dg[i] = (unsigned int)t;
+            c1 = t >> 32;
+        }
+    }
+    int h = kAccChunks - 1;
+    while (h >= 0 && dg[h] == 0u) --h;
+    if (h < 0) return 0.0;
+    // the top 64 bits of the magnitude, a sticky bit for the rest, one rounding
+    const int lz = __clz(dg[h]);
+    const unsigned long long d1 = h >= 1 ? dg[h - 1] : 0u, d2 = h >= 2 ? dg[h - 2] : 0u;
+    const unsigned long long top = ((unsigned long long)dg[h] << 32) | d1;
+    const unsigned long long t64 = lz ? ((top << lz) | (d2 >> (32 - lz))) : top;
+    bool sticky = (lz ? ((d2 << lz) & 0xFFFFFFFFull) : d2) != 0ull;
+    for (int i = 0; i < h - 2; ++i) sticky |= dg[i] != 0u;
+    const double v = scalbn(__ull2double_rn(t64 | (sticky ? 1ull : 0ull)), 32 * (h - 1) - lz + kAccLsbExp);
+    return neg ? -v : v;
+}
+
+// Deterministic reduction of the NV per-block partial sums that the nblk blocks of a slice
+// wrote to partials[b0 + lb][0 .. NV) (row stride `stride`), lb = the calling block's index
+// within the slice: every block adds its row into the slice's exact accumulators, and the
+// block that finishes last (atomic ticket) reads the totals.  Returns true only in that
+// block, with the totals in res (smem).  (wpart: unused, kept for the call sites' shape.)
 template <int NV, int NT>
 __device__ __forceinline__ bool reduce_slice(const SliceDev &S, const double *partials, int stride, int b0,
                                              int nblk, int lb, double *wpart, double *res, int *flag) {
-    const int ng = (nblk + kRedGroup - 1) / kRedGroup;
-    const int g = lb / kRedGroup;
-    const int gsize = min(kRedGroup, nblk - g * kRedGroup);
-    if (!last_block_of_slice(S.ctr + 1 + g, gsize, flag)) return false;
-    group_sum<NV, NT>(partials, stride, b0 + g * kRedGroup, gsize, wpart, res);
-    if (ng == 1) return true;
-    if (threadIdx.x < NV) S.gpart[(size_t)g * kPartialStride + threadIdx.x] = res[threadIdx.x];
-    if (!last_block_of_slice(S.ctr, ng, flag)) return false;
-    group_sum<NV, NT>(S.gpart, kPartialStride, 0, ng, wpart, res);
+    (void)wpart;
+    __syncthreads();                                       // the row may come from any thread
+    if (threadIdx.x < NV)
+        acc_add(S.acc + threadIdx.x * kAccStride, partials[(size_t)(b0 + lb) * stride + threadIdx.x]);
+    if (!last_block_of_slice(S.ctr, nblk, flag)) return false;
+    if (threadIdx.x < NV) res[threadIdx.x] = acc_finish(S.acc + threadIdx.x * kAccStride);
+    __syncthreads();
     return true;
 }
 

@@ -190,31 +190,26 @@ static int build_batch(Batch &B, DevMem &mem, const std::vector<SliceDev> &sds) 
         B.h_start[f * (B.n + 1) + B.n] = acc;
         maxblk = std::max(maxblk, acc);
     }
-    // reduction bookkeeping per slice: 1 + groups ticket counters, groups x kPartialStride
-    // group sums (groups = the most blocks any family gives one slice / kRedGroup)
-    int max_slice_blk = 1;
-    for (const SliceDev &sd : sds) {
-        int fb[FAM_COUNT];
-        family_blocks(sd, fb);
-        for (int f = 0; f < FAM_COUNT; ++f) max_slice_blk = std::max(max_slice_blk, fb[f]);
-    }
-    const int groups = (max_slice_blk + kRedGroup - 1) / kRedGroup;
-    const int cstride = 1 + groups;
+    // reduction bookkeeping per slice: one ticket counter and kPartialStride exact
+    // accumulators (zero between launches)
+    const int cstride = 1;
+    const size_t astride = (size_t)kPartialStride * kAccStride;
     int rc;
     if ((rc = mem.alloc(&B.d_sd, B.n))) return rc;
     if ((rc = mem.alloc(&B.d_start, B.h_start.size()))) return rc;
     if ((rc = mem.alloc(&B.d_counters, (size_t)B.n * cstride))) return rc;
-    if ((rc = mem.alloc(&B.d_gpart, (size_t)B.n * groups * kPartialStride))) return rc;
+    if ((rc = mem.alloc(&B.d_acc, (size_t)B.n * astride))) return rc;
     if ((rc = mem.alloc(&B.d_partials, (size_t)maxblk * kPartialStride))) return rc;
     for (int i = 0; i < B.n; ++i) {
         B.h_sd[i].ctr = B.d_counters + (size_t)i * cstride;
-        B.h_sd[i].gpart = B.d_gpart + (size_t)i * groups * kPartialStride;
+        B.h_sd[i].acc = B.d_acc + (size_t)i * astride;
     }
     if ((rc = mem.alloc(&B.d_hist, (size_t)B.n * kHistBins))) return rc;
     if ((rc = mem.alloc(&B.d_params, 1))) return rc;
     CU(cudaMemcpy(B.d_sd, B.h_sd.data(), sizeof(SliceDev) * B.n, cudaMemcpyHostToDevice));
     CU(cudaMemcpy(B.d_start, B.h_start.data(), sizeof(int) * B.h_start.size(), cudaMemcpyHostToDevice));
     CU(cudaMemset(B.d_counters, 0, sizeof(unsigned int) * (size_t)B.n * cstride));
+    CU(cudaMemset(B.d_acc, 0, sizeof(unsigned long long) * (size_t)B.n * astride));
     CU(cudaMemset(B.d_hist, 0, sizeof(unsigned int) * (size_t)B.n * kHistBins));
     return 0;
 }

@@ -118,20 +118,18 @@ k1_project(const SliceDev *__restrict__ sls, TileMap map, ProjArgs a, double *__
                 // and a column outside the image gets length exactly 0 -- so the column
                 // index only needs clamping for the address.
                 float tac = fmaxf(ta, tm_lo);
-                for (int r = rs; r <= re; ++r) {
+                // one row of the march: lengths of the (at most) two columns the ray
+                // crosses in this row and their offsets from the row start
+                auto step = [&](float &l0, float &l1, int &o0, int &o1) {
                     const float tb = cross_t(grid_line(fr, dM, M0), PM, iM);
                     const float tbc = fminf(tb, tm_hi);
                     fr += 1.0f;
                     const int c1 = c + sgn;
                     const float hi1 = cross_t(grid_line(f1, dm, m0), Pm, im);
-                    const float l0 = seg_len(lo0, hi0, tac, tbc);
-                    const float l1 = seg_len(hi0, hi1, tac, tbc);
-                    const int cc = min(max(c, 0), nm - 1);
-                    const float v0 = __ldg(rowp + cc * sm);
-                    float v1 = 0.0f;
-                    if (l1 > 0.0f) v1 = __ldg(rowp + c1 * sm);
-                    acc = fmaf(l0, v0, acc);
-                    acc = fmaf(l1, v1, acc);
+                    l0 = seg_len(lo0, hi0, tac, tbc);
+                    l1 = seg_len(hi0, hi1, tac, tbc);
+                    o0 = min(max(c, 0), nm - 1) * sm;
+                    o1 = c1 * sm;                // used only when l1 > 0 (column inside)
                     if (hi0 < tb) {
                         c = c1; lo0 = hi0; hi0 = hi1; f1 += fsgn;
                         if (hi1 < tb) {          // FP32 sliver near 45 degrees
@@ -140,8 +138,40 @@ k1_project(const SliceDev *__restrict__ sls, TileMap map, ProjArgs a, double *__
                             f1 += fsgn;
                         }
                     }
-                    ta = tb;
                     tac = fmaxf(tb, tm_lo);
+                };
+                // rows in groups of kRows: the plane arithmetic of the group first, then
+                // all its gathers (independent, in flight together), then the products
+                // in row order (the same sum as a row-by-row march)
+                constexpr int kRows = 4;
+                int r = rs;
+                for (; r + kRows - 1 <= re; r += kRows) {
+                    float l0[kRows], l1[kRows], v0[kRows], v1[kRows];
+                    int o0[kRows], o1[kRows];
+#pragma unroll
+                    for (int u = 0; u < kRows; ++u) step(l0[u], l1[u], o0[u], o1[u]);
+#pragma unroll
+                    for (int u = 0; u < kRows; ++u) {
+                        v0[u] = __ldg(rowp + u * sM + o0[u]);
+                        v1[u] = 0.0f;
+                        if (l1[u] > 0.0f) v1[u] = __ldg(rowp + u * sM + o1[u]);
+                    }
+#pragma unroll
+                    for (int u = 0; u < kRows; ++u) {
+                        acc = fmaf(l0[u], v0[u], acc);
+                        acc = fmaf(l1[u], v1[u], acc);
+                    }
+                    rowp += kRows * sM;
+                }
+                for (; r <= re; ++r) {
+                    float l0, l1;
+                    int o0, o1;
+                    step(l0, l1, o0, o1);
+                    const float v0 = __ldg(rowp + o0);
+                    float v1 = 0.0f;
+                    if (l1 > 0.0f) v1 = __ldg(rowp + o1);
+                    acc = fmaf(l0, v0, acc);
+                    acc = fmaf(l1, v1, acc);
                     rowp += sM;
                 }
             }

@@ -1,0 +1,130 @@
+"""The exact fixed-point accumulator of the CUDA reductions (acc_add / acc_finish in
+csrc/eptv_internal.cuh), compiled for the host with stand-ins for the CUDA intrinsics
+(single-threaded: the device atomics become plain additions, which is what makes the
+result order-independent), against exact rational sums: every total of FP32-derived
+block partials must be the correctly rounded exact sum, including round-to-even ties,
+cancellation, and the non-finite and overflow flags."""
+import math
+import os
+import random
+import shutil
+import struct
+import subprocess
+from fractions import Fraction
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "paper_1009_2288_b300", "csrc", "eptv_internal.cuh")
+
+SHIMS = r'''
+#include <cstdio>
+#include <cstring>
+#include <cmath>
+#include <cstdlib>
+#define __device__
+#define __forceinline__ inline
+static inline long long __double_as_longlong(double x) { long long r; memcpy(&r, &x, 8); return r; }
+static inline double __longlong_as_double(long long x) { double r; memcpy(&r, &x, 8); return r; }
+static inline int __clz(unsigned int x) { return x ? __builtin_clz(x) : 32; }
+static inline double __ull2double_rn(unsigned long long x) { return (double)x; }
+static inline unsigned long long __ldcg(const unsigned long long *p) { return *p; }
+static inline void atomicAdd(unsigned long long *p, unsigned long long v) { *p += v; }
+static inline void atomicOr(unsigned long long *p, unsigned long long v) { *p |= v; }
+'''
+
+MAIN = r'''
+int main() {
+    unsigned long long acc[kAccStride];
+    memset(acc, 0, sizeof acc);
+    char line[128];
+    while (fgets(line, sizeof line, stdin)) {
+        if (line[0] == 'E') {
+            const double r = acc_finish(acc);
+            printf("%016llx\n", (unsigned long long)__double_as_longlong(r));
+            for (int i = 0; i < kAccStride; ++i) if (acc[i]) { printf("not-rezeroed\n"); return 1; }
+            continue;
+        }
+        acc_add(acc, __longlong_as_double((long long)strtoull(line, 0, 16)));
+    }
+    return 0;
+}
+'''
+
+
+@pytest.fixture(scope="module")
+def accumulator(tmp_path_factory):
+    if shutil.which("g++") is None:
+        pytest.skip("no host C++ compiler")
+    src = open(HEADER).read()
+    body = src[src.index("constexpr int kAccChunks"):src.index("// Deterministic reduction of the NV")]
+    d = tmp_path_factory.mktemp("acc")
+    cpp, exe = d / "acc.cpp", d / "acc"
+    cpp.write_text(SHIMS + body + MAIN)
+    subprocess.check_call(["g++", "-O1", "-std=c++17", "-o", str(exe), str(cpp)])
+
+    def run(groups):
+        lines = []
+        for g in groups:
+            lines += ["%016x" % struct.unpack("<Q", struct.pack("<d", x))[0] for x in g] + ["E"]
+        out = subprocess.run([str(exe)], input="\n".join(lines) + "\n", capture_output=True,
+                             text=True, check=True).stdout.split()
+        return [struct.unpack("<d", struct.pack("<Q", int(h, 16)))[0] for h in out]
+    return run
+
+
+def f32(x):
+    return struct.unpack("<f", struct.pack("<f", x))[0]
+
+
+def test_sums_of_fp32_partials_are_correctly_rounded(accumulator):
+    rng = random.Random(7)
+    groups = []
+    for _ in range(300):
+        n = rng.choice([1, 2, 5, 64, 1024])
+        scale = 2.0 ** rng.randint(-140, 120)
+        vals = [f32(rng.uniform(-1, 1) * scale * 2.0 ** rng.randint(-20, 5)) for _ in range(n)]
+        if rng.random() < 0.3:
+            vals = [abs(v) for v in vals]
+        parts = []
+        for i in range(0, n, 4):          # block partials: FP64 sums of FP32 warp sums
+            s = 0.0
+            for v in vals[i:i + 4]:
+                s += v
+            parts.append(s)
+        groups.append(parts)
+    got = accumulator(groups)
+    for g, r in zip(groups, got):
+        assert r == float(sum(Fraction(x) for x in g)), g[:3]
+
+
+def test_order_does_not_matter(accumulator):
+    rng = random.Random(3)
+    g = [f32(rng.uniform(-1, 1) * 2.0 ** rng.randint(-60, 60)) for _ in range(500)]
+    perms = [g, list(reversed(g)), sorted(g), rng.sample(g, len(g))]
+    got = accumulator(perms)
+    assert len(set(got)) == 1
+    assert got[0] == float(sum(Fraction(x) for x in g))
+
+
+def test_ties_cancellation_and_special_values(accumulator):
+    cases = [
+        ([2.0 ** 53, 1.0], 2.0 ** 53),                   # tie -> even
+        ([2.0 ** 53, 1.0, 2.0 ** -100], 2.0 ** 53 + 2),  # just above the tie
+        ([2.0 ** 53 + 2, 1.0], 2.0 ** 53 + 4),           # tie -> even (upwards)
+        ([-(2.0 ** 53), -1.0], -(2.0 ** 53)),
+        ([1e30, -1e30, 3.0], 3.0),                       # exact cancellation
+        ([1.0, 2.0 ** -149 * 3, -1.0], 2.0 ** -149 * 3),
+        ([2.0 ** -149], 2.0 ** -149),
+        ([0.0, -0.0], 0.0),
+        ([], 0.0),
+        ([3.4e38, 3.4e38, 3.4e38], 3.0 * 3.4e38),
+    ]
+    got = accumulator([c for c, _ in cases])
+    for (c, want), r in zip(cases, got):
+        assert r == want, c
+    inf, nan = float("inf"), float("nan")
+    sp = accumulator([[inf, 1.0], [-inf, 2.0], [inf, -inf], [nan, 1.0], [2.0 ** 200], [-(2.0 ** 195)]])
+    assert sp[0] == inf and sp[1] == -inf
+    assert math.isnan(sp[2]) and math.isnan(sp[3])
+    assert sp[4] == inf and sp[5] == -inf              # beyond the accumulator's range

@@ -1,9 +1,9 @@
 // K2: f = P^T y, the exact transpose of the projector, as a scatter-free pixel-driven
 // gather (the paper rejects the ray-driven scatter for its write conflicts, Sec. 2.3).
 //
-// A block covers a 32 x 16 pixel tile: 128 strips of 4 adjacent pixels of one row
-// (float4 output), each strip served by VG threads that take every VG-th view, so a
-// 512^2 image keeps VG x 65k threads busy.  For every view a thread bounds the fan
+// A block covers a kTileW x kTileH (32 x 8) pixel tile: 64 strips of 4 adjacent pixels of
+// one row (float4 output), each strip served by VG threads that take every VG-th view, so
+// a 512^2 image keeps VG x 65k threads busy in ~7 tiles per SM (an even share).  For every view a thread bounds the fan
 // angles of its strip from the strip's corners (tan-space min/max, then atan), visits
 // the bins whose rays can cross the strip, and recomputes each p_ij with the canonical
 // plane parameters of eptv_internal.cuh -- the same FP32 operations as the projector,
@@ -23,12 +23,14 @@
 
 namespace eptv {
 
+constexpr int kStrips = (kTileW / 4) * kTileH;       // 4-pixel strips per tile
+
 template <int VG, bool EQ11>
-__global__ void __launch_bounds__(128 * VG)
+__global__ void __launch_bounds__(kStrips * VG)
 k2_backproject(const SliceDev *__restrict__ sls, TileMap map, BackArgs a, double *__restrict__ partials)
 {
-    constexpr int NT = 128 * VG;
-    __shared__ float4 part[VG > 1 ? VG - 1 : 1][128];
+    constexpr int NT = kStrips * VG;
+    __shared__ float4 part[VG > 1 ? VG - 1 : 1][kStrips];
     __shared__ float tr[kTileH][kTileW + 1];
     __shared__ double rsm[2 * (NT / 32)];
     __shared__ double res[2];
@@ -40,8 +42,8 @@ k2_backproject(const SliceDev *__restrict__ sls, TileMap map, BackArgs a, double
     const int nx = S.nx, ny = S.ny, nb = S.nb;
     const int tiles_x = (nx + kTileW - 1) / kTileW;
     const int tyb = local / tiles_x, txb = local - tyb * tiles_x;
-    const int strip = threadIdx.x & 127, vg = threadIdx.x >> 7;
-    const int lx = strip & 7, ly = strip >> 3;
+    const int strip = threadIdx.x % kStrips, vg = threadIdx.x / kStrips;
+    const int lx = strip % (kTileW / 4), ly = strip / (kTileW / 4);
     const int i0 = txb * kTileW + lx * 4, j = tyb * kTileH + ly;
 
     const float *sino = a.in_override ? a.in_override : S.r;
@@ -173,8 +175,9 @@ k2_backproject(const SliceDev *__restrict__ sls, TileMap map, BackArgs a, double
             for (int q = 0; q < 4; ++q) tr[ly][lx * 4 + q] = acc[q];
         }
         __syncthreads();
-        for (int idx = threadIdx.x; idx < 128; idx += NT) {
-            const int ii = idx >> 2, jj0 = (idx & 3) * 4;
+        constexpr int kRowGroups = kTileH / 4;          // 4 rows of one column per thread
+        for (int idx = threadIdx.x; idx < kTileW * kRowGroups; idx += NT) {
+            const int ii = idx / kRowGroups, jj0 = (idx % kRowGroups) * 4;
             const int gi = txb * kTileW + ii;
             if (gi < nx) {
                 for (int q = 0; q < 4; ++q) {
@@ -202,18 +205,18 @@ void launch_backproject(const Batch &B, const BackArgs &a, cudaStream_t st) {
     const TileMap m = B.map(FAM_K2);
     if (B.bp_eq11 || a.eq11) {
         switch (B.k2_vg) {
-        case 1: k2_backproject<1, true><<<nblk, 128, 0, st>>>(B.d_sd, m, a, B.d_partials); break;
-        case 2: k2_backproject<2, true><<<nblk, 256, 0, st>>>(B.d_sd, m, a, B.d_partials); break;
-        case 8: k2_backproject<8, true><<<nblk, 1024, 0, st>>>(B.d_sd, m, a, B.d_partials); break;
-        default: k2_backproject<4, true><<<nblk, 512, 0, st>>>(B.d_sd, m, a, B.d_partials); break;
+        case 1: k2_backproject<1, true><<<nblk, kStrips, 0, st>>>(B.d_sd, m, a, B.d_partials); break;
+        case 2: k2_backproject<2, true><<<nblk, 2 * kStrips, 0, st>>>(B.d_sd, m, a, B.d_partials); break;
+        case 8: k2_backproject<8, true><<<nblk, 8 * kStrips, 0, st>>>(B.d_sd, m, a, B.d_partials); break;
+        default: k2_backproject<4, true><<<nblk, 4 * kStrips, 0, st>>>(B.d_sd, m, a, B.d_partials); break;
         }
         return;
     }
     switch (B.k2_vg) {
-    case 1: k2_backproject<1, false><<<nblk, 128, 0, st>>>(B.d_sd, m, a, B.d_partials); break;
-    case 2: k2_backproject<2, false><<<nblk, 256, 0, st>>>(B.d_sd, m, a, B.d_partials); break;
-    case 8: k2_backproject<8, false><<<nblk, 1024, 0, st>>>(B.d_sd, m, a, B.d_partials); break;
-    default: k2_backproject<4, false><<<nblk, 512, 0, st>>>(B.d_sd, m, a, B.d_partials); break;
+    case 1: k2_backproject<1, false><<<nblk, kStrips, 0, st>>>(B.d_sd, m, a, B.d_partials); break;
+    case 2: k2_backproject<2, false><<<nblk, 2 * kStrips, 0, st>>>(B.d_sd, m, a, B.d_partials); break;
+    case 8: k2_backproject<8, false><<<nblk, 8 * kStrips, 0, st>>>(B.d_sd, m, a, B.d_partials); break;
+    default: k2_backproject<4, false><<<nblk, 4 * kStrips, 0, st>>>(B.d_sd, m, a, B.d_partials); break;
     }
 }
 

@@ -87,6 +87,7 @@ struct SliceDev {
     int n_edges;         // (nx+1) ny + nx (ny+1)
     const RayRec *ray;   // [nv * nb]
     const ViewRec *view; // [nv]
+    const int *k1_order; // [nv * ceil(nb / 32)] projector work units, heaviest first (or null)
     // solver state (device workspace of the handle, or caller buffers)
     const float *y;      // data sinogram
     float *u, *uT;       // current image / CGLS iterate and its transpose

@@ -375,6 +375,10 @@ static int acquire_batch(int n, eptv_geometry *const *geoms, BatchCache &bc) {
     bc.reset();
     std::vector<SliceDev> sds;
     for (int i = 0; i < n; ++i) sds.push_back(geoms[i]->sd);
+    // a batch gives the projector many waves of blocks, which balance by themselves: keep
+    // each slice's natural unit order (adjacent bins of a view run together)
+    if (n > 1)
+        for (SliceDev &sd : sds) sd.k1_order = nullptr;
     int rc = build_batch(bc.B, bc.mem, sds);
     if (rc) { bc.reset(); return rc; }
     bc.B.stored = modes[0] == EPTV_OPERATOR_STORED;
@@ -488,9 +492,12 @@ int eptv_create_geometry(const eptv_geometry_desc *desc, eptv_geometry **out) {
     const long long n_pix = (long long)nx * ny, n_rays = (long long)nv * nb;
     const long long n_edges = (long long)(nx + 1) * ny + (long long)nx * (ny + 1);
 
-    // ray and view tables in FP64, stored FP32
+    // ray and view tables in FP64, stored FP32; per ray the rows (or columns) the
+    // projector marches, for the order of its work units
     std::vector<RayRec> rays((size_t)n_rays);
     std::vector<ViewRec> views((size_t)nv);
+    std::vector<double> march((size_t)n_rays, 0.0);
+    const double hx = 0.5 * nx * desc->dx, hy = 0.5 * ny * desc->dy;
     for (int v = 0; v < nv; ++v) {
         const double th = desc->angles ? desc->angles[v] : 2.0 * M_PI * v / nv;
         const double c = std::cos(th), s = std::sin(th);
@@ -506,8 +513,31 @@ int eptv_create_geometry(const eptv_geometry_desc *desc, eptv_geometry **out) {
             const double proj = Sx * dx + Sy * dy;
             const double Px = Sx - proj * dx, Py = Sy - proj * dy;   // closest point to the isocentre
             rays[(size_t)v * nb + k] = RayRec{(float)Px, (float)Py, inv_or_big(dx), inv_or_big(dy)};
+            double t0 = -1e300, t1 = 1e300;          // chord through the image square
+            const double P[2] = {Px, Py}, D[2] = {dx, dy}, H[2] = {hx, hy};
+            for (int a = 0; a < 2; ++a) {
+                if (D[a] == 0.0) { if (std::fabs(P[a]) >= H[a]) t1 = -1e300; continue; }
+                const double ta = (-H[a] - P[a]) / D[a], tb = (H[a] - P[a]) / D[a];
+                t0 = std::max(t0, std::min(ta, tb));
+                t1 = std::min(t1, std::max(ta, tb));
+            }
+            if (t1 > t0)
+                march[(size_t)v * nb + k] = std::max(std::fabs(dx) * (t1 - t0) / desc->dx,
+                                                     std::fabs(dy) * (t1 - t0) / desc->dy) + 1.0;
         }
     }
+    // projector work units (view, 32 bins): cost = the longest march among its rays
+    const int nbb = (nb + 31) / 32;
+    std::vector<int> k1_order((size_t)nv * nbb);
+    std::vector<double> k1_cost((size_t)nv * nbb, 0.0);
+    for (int v = 0; v < nv; ++v)
+        for (int k = 0; k < nb; ++k) {
+            double &c = k1_cost[(size_t)v * nbb + k / 32];
+            c = std::max(c, march[(size_t)v * nb + k]);
+        }
+    for (size_t i = 0; i < k1_order.size(); ++i) k1_order[i] = (int)i;
+    std::stable_sort(k1_order.begin(), k1_order.end(),
+                     [&](int a, int b) { return k1_cost[(size_t)a] > k1_cost[(size_t)b]; });
 
     SliceDev &sd = g->sd;
     memset(&sd, 0, sizeof sd);
@@ -525,10 +555,12 @@ int eptv_create_geometry(const eptv_geometry_desc *desc, eptv_geometry **out) {
     DevMem &m = g->mem;
     RayRec *d_ray;
     ViewRec *d_view;
+    int *d_order;
     float *img[9];
     float *sino[2];
     double *sc;
     if ((rc = m.alloc(&d_ray, n_rays)) || (rc = m.alloc(&d_view, nv))) goto bad;
+    if ((rc = m.alloc(&d_order, k1_order.size()))) goto bad;
     for (int i = 0; i < 9; ++i) if ((rc = m.alloc(&img[i], n_pix))) goto bad;
     for (int i = 0; i < 2; ++i) if ((rc = m.alloc(&sino[i], n_rays))) goto bad;
     if ((rc = m.alloc(&g->y_int, n_rays))) goto bad;
@@ -537,11 +569,12 @@ int eptv_create_geometry(const eptv_geometry_desc *desc, eptv_geometry **out) {
     if ((rc = m.alloc(&g->d_map_custom, 2))) goto bad;
     if (cudaMemcpy(d_ray, rays.data(), sizeof(RayRec) * n_rays, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(d_view, views.data(), sizeof(ViewRec) * nv, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(d_order, k1_order.data(), sizeof(int) * k1_order.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(sc, 0, sizeof(double) * kScalarStride) != cudaSuccess) {
         rc = fail(EPTV_ERR_CUDA, "upload of the geometry tables failed: %s", cudaGetErrorString(cudaGetLastError()));
         goto bad;
     }
-    sd.ray = d_ray; sd.view = d_view;
+    sd.ray = d_ray; sd.view = d_view; sd.k1_order = d_order;
     sd.u = img[0]; sd.uT = img[1]; sd.s = img[2]; sd.sT = img[3]; sd.t = img[4];
     sd.fa = img[5]; sd.fb = img[6]; sd.ga = img[7]; sd.gb = img[8];
     sd.r = sino[0]; sd.q = sino[1];

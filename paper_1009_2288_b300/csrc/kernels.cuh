@@ -21,7 +21,7 @@ enum Family {
     FAM_COUNT
 };
 
-constexpr int kTileW = 32, kTileH = 16;
+constexpr int kTileW = 32, kTileH = 8;
 constexpr int kGdTileRows = 8;
 constexpr int kHistBins = 4096;    // radix-select histogram (12 bits per pass)
 

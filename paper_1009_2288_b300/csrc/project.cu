@@ -32,9 +32,12 @@ k1_project(const SliceDev *__restrict__ sls, TileMap map, ProjArgs a, double *__
     const SliceDev &S = sls[si];
     const int nb = S.nb;
     const int nbb = (nb + 31) >> 5;
-    const int v = local / nbb;
+    // work unit (view, group of 32 bins) of this block: heaviest first, so that the blocks
+    // dispatched last are the short ones and the SMs finish together
+    const int unit = S.k1_order ? __ldg(S.k1_order + local) : local;
+    const int v = unit / nbb;
     const int lane = threadIdx.x & 31, seg = threadIdx.x >> 5;
-    const int k = (local - v * nbb) * 32 + lane;
+    const int k = (unit - v * nbb) * 32 + lane;
 
     const float *img, *imgT;
     float *out;

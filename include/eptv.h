@@ -363,7 +363,7 @@ int eptv_reconstruct_batched(int n, eptv_geometry *const *geoms, const eptv_para
 
 /* Launch shapes of the projector and back projector used by calls on handle g: k1_seg =
  * warps marching each block of 32 adjacent rays (4, 8 or 16; the rows of a ray are split
- * among them), k2_vg = threads sharing the views of each 4-pixel strip (1, 2, 4 or 8).
+ * among them), k2_vg = threads sharing the views of each 4 x 2 pixel block (1, 2, 4, 8 or 16).
  * Defaults 8 and 4.  EPTV_ERR_ARG for other values. */
 int eptv_set_tuning(eptv_geometry *g, int k1_seg, int k2_vg);
 

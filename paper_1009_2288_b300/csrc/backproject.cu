@@ -1,16 +1,16 @@
 // K2: f = P^T y, the exact transpose of the projector, as a scatter-free pixel-driven
 // gather (the paper rejects the ray-driven scatter for its write conflicts, Sec. 2.3).
 //
-// A block covers a kTileW x kTileH (32 x 8) pixel tile: 64 strips of 4 adjacent pixels of
-// one row (float4 output), each strip served by VG threads that take every VG-th view, so
-// a 512^2 image keeps VG x 65k threads busy in ~7 tiles per SM (an even share).  For every view a thread bounds the fan
-// angles of its strip from the strip's corners (tan-space min/max, then atan), visits
-// the bins whose rays can cross the strip, and recomputes each p_ij with the canonical
-// plane parameters of eptv_internal.cuh -- the same FP32 operations as the projector,
-// so <P x, y> = <x, P^T y> holds up to summation order.  The strip's 5 column planes
-// and 2 row planes are shared by its 4 pixels.  The VG partial sums of a strip are
-// added in group order (deterministic).  Optionally also writes the transposed image
-// (for the projector's shallow rays) and reduces |f|^2 (FP32 per warp, FP64 above).
+// A block covers a kTileW x kTileH (32 x 8) pixel tile, so a 512^2 image gives ~7 tiles
+// per SM (an even share in one wave).  A thread owns a 4 x kRowsPT pixel block (float4
+// rows) and every VG-th view; the VG partial sums of a block are added in group order
+// (deterministic).  For every view the thread bounds the fan angles of its block from
+// the block's corners (tan-space min/max, then atan), visits the bins whose rays can
+// cross it, and recomputes each p_ij with the canonical plane parameters of
+// eptv_internal.cuh -- the same FP32 operations as the projector, so <P x, y> =
+// <x, P^T y> holds up to summation order.  The 5 column planes and kRowsPT + 1 row planes
+// of a candidate ray are shared by the block's pixels.  Optionally also writes the
+// transposed image (for the projector's shallow rays) and reduces |f|^2.
 //
 // EQ11 = true: the paper's pixel-driven back projector instead (Eq. 11, Sec. 2.3,
 // derived in App. III), an approximation of the transpose:
@@ -23,14 +23,15 @@
 
 namespace eptv {
 
-constexpr int kStrips = (kTileW / 4) * kTileH;       // 4-pixel strips per tile
+constexpr int kRowsPT = 2;                                   // pixel rows per thread
+constexpr int kBlocksPT = (kTileW / 4) * (kTileH / kRowsPT);  // 4 x kRowsPT blocks per tile
 
 template <int VG, bool EQ11>
-__global__ void __launch_bounds__(kStrips * VG)
+__global__ void __launch_bounds__(kBlocksPT * VG)
 k2_backproject(const SliceDev *__restrict__ sls, TileMap map, BackArgs a, double *__restrict__ partials)
 {
-    constexpr int NT = kStrips * VG;
-    __shared__ float4 part[VG > 1 ? VG - 1 : 1][kStrips];
+    constexpr int NT = kBlocksPT * VG, R = kRowsPT;
+    __shared__ float4 part[VG > 1 ? VG - 1 : 1][R][kBlocksPT];
     __shared__ float tr[kTileH][kTileW + 1];
     __shared__ double rsm[2 * (NT / 32)];
     __shared__ double res[2];
@@ -42,26 +43,33 @@ k2_backproject(const SliceDev *__restrict__ sls, TileMap map, BackArgs a, double
     const int nx = S.nx, ny = S.ny, nb = S.nb;
     const int tiles_x = (nx + kTileW - 1) / kTileW;
     const int tyb = local / tiles_x, txb = local - tyb * tiles_x;
-    const int strip = threadIdx.x % kStrips, vg = threadIdx.x / kStrips;
-    const int lx = strip % (kTileW / 4), ly = strip / (kTileW / 4);
-    const int i0 = txb * kTileW + lx * 4, j = tyb * kTileH + ly;
+    const int blk = threadIdx.x % kBlocksPT, vg = threadIdx.x / kBlocksPT;
+    const int lx = blk % (kTileW / 4), ly = blk / (kTileW / 4);
+    const int i0 = txb * kTileW + lx * 4, j0 = tyb * kTileH + ly * R;
 
     const float *sino = a.in_override ? a.in_override : S.r;
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    float acc[R][4];
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[r][q] = 0.0f;
 
-    if (EQ11 && j < ny && i0 < nx) {
-        const float yc = grid_line((float)j + 0.5f, S.dy, S.y0);
-        float xc[4];
+    if (EQ11 && j0 < ny && i0 < nx) {
+        float xc[4], yc[R];
 #pragma unroll
         for (int q = 0; q < 4; ++q) xc[q] = grid_line((float)(i0 + q) + 0.5f, S.dx, S.x0);
+#pragma unroll
+        for (int r = 0; r < R; ++r) yc[r] = grid_line((float)(j0 + r) + 0.5f, S.dy, S.y0);
         const float inv_db = S.inv_dbeta, kc = S.kc;
         const bool arc = S.detector == EPTV_DETECTOR_ARC;
         for (int v = vg; v < S.nv; v += VG) {
             const ViewRec V = S.view[v];
             const float *sv = sino + (size_t)v * nb;
 #pragma unroll
+            for (int r = 0; r < R; ++r)
+#pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const float wx = xc[q] - V.sx, wy = yc - V.sy;
+                const float wx = xc[q] - V.sx, wy = yc[r] - V.sy;
                 const float cr = V.cx * wy - V.cy * wx;          // l sin(beta*)
                 const float dt = V.cx * wx + V.cy * wy;          // l cos(beta*)
                 const float rl = rsqrtf(wx * wx + wy * wy);       // 1 / l
@@ -81,22 +89,26 @@ k2_backproject(const SliceDev *__restrict__ sls, TileMap map, BackArgs a, double
                     float y0 = 0.0f, y1 = 0.0f;
                     if (k0 >= 0) y0 = __ldg(sv + k0);
                     if (k0 + 1 < nb) y1 = __ldg(sv + k0 + 1);
-                    acc[q] = fmaf(fmaf(fr, y1 - y0, y0), w, acc[q]);
+                    acc[r][q] = fmaf(fmaf(fr, y1 - y0, y0), w, acc[r][q]);
                 }
             }
         }
         const float scale = S.dx * S.dy * inv_db;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[q] *= scale;
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[r][q] *= scale;
     }
-    if (!EQ11 && j < ny && i0 < nx) {
-        float X[5];
+    if (!EQ11 && j0 < ny && i0 < nx) {
+        float X[5], Y[R + 1];
 #pragma unroll
         for (int q = 0; q < 5; ++q) X[q] = grid_line((float)(i0 + q), S.dx, S.x0);
-        const float Y0 = grid_line((float)j, S.dy, S.y0);
-        const float Y1 = grid_line((float)(j + 1), S.dy, S.y0);
-        const int ne = min(4, nx - i0);
-        const float Xe = grid_line((float)(i0 + ne), S.dx, S.x0);
+#pragma unroll
+        for (int r = 0; r <= R; ++r) Y[r] = grid_line((float)(j0 + r), S.dy, S.y0);
+        // corners of the block's part inside the image (pixels beyond the edge are not
+        // written, so their bins need not be visited)
+        const float Xe = grid_line((float)(i0 + min(4, nx - i0)), S.dx, S.x0);
+        const float Ye = grid_line((float)(j0 + min(R, ny - j0)), S.dy, S.y0);
         const float inv_db = S.inv_dbeta, kc = S.kc;
         const bool arc = S.detector == EPTV_DETECTOR_ARC;
 
@@ -107,7 +119,7 @@ k2_backproject(const SliceDev *__restrict__ sls, TileMap map, BackArgs a, double
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 const float px = (c & 1) ? Xe : X[0];
-                const float py = (c & 2) ? Y1 : Y0;
+                const float py = (c & 2) ? Ye : Y[0];
                 const float wx = px - V.sx, wy = py - V.sy;
                 const float num = V.cx * wy - V.cy * wx;
                 const float den = V.cx * wx + V.cy * wy;
@@ -123,32 +135,42 @@ k2_backproject(const SliceDev *__restrict__ sls, TileMap map, BackArgs a, double
             const RayRec *rr = S.ray + (size_t)v * nb;
             const float *sv = sino + (size_t)v * nb;
             for (int k = klo; k <= khi; ++k) {
-                const RayRec R = rr[k];
+                const RayRec Rr = rr[k];
                 const float yv = __ldg(sv + k);
-                const float ta = cross_t(Y0, R.py, R.iy), tb = cross_t(Y1, R.py, R.iy);
-                const float rlo = fminf(ta, tb), rhi = fmaxf(ta, tb);
-                float tx[5];
+                float ty[R + 1], tx[5];
 #pragma unroll
-                for (int q = 0; q < 5; ++q) tx[q] = cross_t(X[q], R.px, R.ix);
+                for (int r = 0; r <= R; ++r) ty[r] = cross_t(Y[r], Rr.py, Rr.iy);
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const float lo = fminf(tx[q], tx[q + 1]), hi = fmaxf(tx[q], tx[q + 1]);
-                    acc[q] = fmaf(seg_len(lo, hi, rlo, rhi), yv, acc[q]);
+                for (int q = 0; q < 5; ++q) tx[q] = cross_t(X[q], Rr.px, Rr.ix);
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const float rlo = fminf(ty[r], ty[r + 1]), rhi = fmaxf(ty[r], ty[r + 1]);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float lo = fminf(tx[q], tx[q + 1]), hi = fmaxf(tx[q], tx[q + 1]);
+                        acc[r][q] = fmaf(seg_len(lo, hi, rlo, rhi), yv, acc[r][q]);
+                    }
                 }
             }
         }
     }
 
-    // combine the view groups in order (group 0 owns the strip's output)
+    // combine the view groups in order (group 0 owns the block's output)
     if (VG > 1) {
-        if (vg > 0) part[vg - 1][strip] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+        if (vg > 0) {
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                part[vg - 1][r][blk] = make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
+        }
         __syncthreads();
         if (vg == 0) {
 #pragma unroll
-            for (int gi = 0; gi < VG - 1; ++gi) {
-                const float4 p = part[gi][strip];
-                acc[0] += p.x; acc[1] += p.y; acc[2] += p.z; acc[3] += p.w;
-            }
+            for (int gi = 0; gi < VG - 1; ++gi)
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const float4 p = part[gi][r][blk];
+                    acc[r][0] += p.x; acc[r][1] += p.y; acc[r][2] += p.z; acc[r][3] += p.w;
+                }
         }
     }
 
@@ -160,19 +182,28 @@ k2_backproject(const SliceDev *__restrict__ sls, TileMap map, BackArgs a, double
     else { out = S.u; if (a.write_T) outT = S.uT; }
 
     float sq = 0.0f;
-    if (vg == 0 && j < ny && i0 < nx) {
-        float *p = out + (size_t)j * nx + i0;
-        if (i0 + 3 < nx && ((nx & 3) == 0) && ((((uintptr_t)p) & 15) == 0)) {
-            *reinterpret_cast<float4 *>(p) = make_float4(acc[0], acc[1], acc[2], acc[3]);
-        } else {
-            for (int q = 0; q < 4; ++q) if (i0 + q < nx) p[q] = acc[q];
+    if (vg == 0 && i0 < nx) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int j = j0 + r;
+            if (j >= ny) break;
+            float *p = out + (size_t)j * nx + i0;
+            if (i0 + 3 < nx && ((nx & 3) == 0) && ((((uintptr_t)p) & 15) == 0)) {
+                *reinterpret_cast<float4 *>(p) = make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) if (i0 + q < nx) p[q] = acc[r][q];
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) if (i0 + q < nx) sq = fmaf(acc[r][q], acc[r][q], sq);
         }
-        for (int q = 0; q < 4; ++q) if (i0 + q < nx) sq = fmaf(acc[q], acc[q], sq);
     }
     if (outT) {
         if (vg == 0) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) tr[ly][lx * 4 + q] = acc[q];
+            for (int r = 0; r < R; ++r)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) tr[ly * R + r][lx * 4 + q] = acc[r][q];
         }
         __syncthreads();
         constexpr int kRowGroups = kTileH / 4;          // 4 rows of one column per thread
@@ -203,21 +234,18 @@ void launch_backproject(const Batch &B, const BackArgs &a, cudaStream_t st) {
     if (nblk == 0) return;
     ++g_launch_count;
     const TileMap m = B.map(FAM_K2);
-    if (B.bp_eq11 || a.eq11) {
-        switch (B.k2_vg) {
-        case 1: k2_backproject<1, true><<<nblk, kStrips, 0, st>>>(B.d_sd, m, a, B.d_partials); break;
-        case 2: k2_backproject<2, true><<<nblk, 2 * kStrips, 0, st>>>(B.d_sd, m, a, B.d_partials); break;
-        case 8: k2_backproject<8, true><<<nblk, 8 * kStrips, 0, st>>>(B.d_sd, m, a, B.d_partials); break;
-        default: k2_backproject<4, true><<<nblk, 4 * kStrips, 0, st>>>(B.d_sd, m, a, B.d_partials); break;
-        }
-        return;
-    }
+    const bool eq11 = B.bp_eq11 || a.eq11;
+#define K2_LAUNCH(VGv)                                                                              \
+    (eq11 ? k2_backproject<VGv, true><<<nblk, kBlocksPT * VGv, 0, st>>>(B.d_sd, m, a, B.d_partials) \
+          : k2_backproject<VGv, false><<<nblk, kBlocksPT * VGv, 0, st>>>(B.d_sd, m, a, B.d_partials))
     switch (B.k2_vg) {
-    case 1: k2_backproject<1, false><<<nblk, kStrips, 0, st>>>(B.d_sd, m, a, B.d_partials); break;
-    case 2: k2_backproject<2, false><<<nblk, 2 * kStrips, 0, st>>>(B.d_sd, m, a, B.d_partials); break;
-    case 8: k2_backproject<8, false><<<nblk, 8 * kStrips, 0, st>>>(B.d_sd, m, a, B.d_partials); break;
-    default: k2_backproject<4, false><<<nblk, 4 * kStrips, 0, st>>>(B.d_sd, m, a, B.d_partials); break;
+    case 1: K2_LAUNCH(1); break;
+    case 2: K2_LAUNCH(2); break;
+    case 8: K2_LAUNCH(8); break;
+    case 16: K2_LAUNCH(16); break;
+    default: K2_LAUNCH(4); break;
     }
+#undef K2_LAUNCH
 }
 
 }  // namespace eptv

@@ -257,16 +257,26 @@ __device__ __forceinline__ double acc_finish(unsigned long long *acc) {
             c1 = t >> 32;
         }
     }
-    int h = kAccChunks - 1;
-    while (h >= 0 && dg[h] == 0u) --h;
+    // leading digit h and the two below it (selects, not indexing: stays in registers)
+    int h = -1;
+#pragma unroll
+    for (int i = 0; i < kAccChunks; ++i)
+        if (dg[i]) h = i;
     if (h < 0) return 0.0;
+    unsigned long long d0 = 0u, d1 = 0u, d2 = 0u;
+    bool sticky = false;
+#pragma unroll
+    for (int i = 0; i < kAccChunks; ++i) {
+        if (i == h) d0 = dg[i];
+        if (i == h - 1) d1 = dg[i];
+        if (i == h - 2) d2 = dg[i];
+        if (i < h - 2) sticky |= dg[i] != 0u;
+    }
     // the top 64 bits of the magnitude, a sticky bit for the rest, one rounding
-    const int lz = __clz(dg[h]);
-    const unsigned long long d1 = h >= 1 ? dg[h - 1] : 0u, d2 = h >= 2 ? dg[h - 2] : 0u;
-    const unsigned long long top = ((unsigned long long)dg[h] << 32) | d1;
+    const int lz = __clz((unsigned int)d0);
+    const unsigned long long top = (d0 << 32) | d1;
     const unsigned long long t64 = lz ? ((top << lz) | (d2 >> (32 - lz))) : top;
-    bool sticky = (lz ? ((d2 << lz) & 0xFFFFFFFFull) : d2) != 0ull;
-    for (int i = 0; i < h - 2; ++i) sticky |= dg[i] != 0u;
+    sticky |= (lz ? ((d2 << lz) & 0xFFFFFFFFull) : d2) != 0ull;
     const double v = scalbn(__ull2double_rn(t64 | (sticky ? 1ull : 0ull)), 32 * (h - 1) - lz + kAccLsbExp);
     return neg ? -v : v;
 }

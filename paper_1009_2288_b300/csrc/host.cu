@@ -390,7 +390,7 @@ static int acquire_batch(int n, eptv_geometry *const *geoms, BatchCache &bc) {
 
 // Times every projector / back-projector launch shape on batch B (zero images, the
 // batch's own buffers) and keeps the fastest: the ray-block shape of K1 (warps per 32
-// rays: 4, 8, 16) and the view split of K2 (1, 2, 4, 8 groups per strip).
+// rays: 4, 8, 16) and the view split of K2 (1, 2, 4, 8, 16 groups per pixel block).
 static int autotune_batch(Batch &B, int *k1_out, int *k2_out) {
     cudaStream_t st = nullptr;
     for (const SliceDev &sd : B.h_sd) {
@@ -420,7 +420,7 @@ static int autotune_batch(Batch &B, int *k1_out, int *k2_out) {
     pa.img = IMG_U; pa.out = SINO_Q; pa.fin = FIN_NONE;
     BackArgs ba{};
     ba.out = 1; ba.fin = FIN_NONE;
-    const int k1c[] = {4, 8, 16}, k2c[] = {1, 2, 4, 8};
+    const int k1c[] = {4, 8, 16}, k2c[] = {1, 2, 4, 8, 16};
     float best = 1e30f;
     int b1 = B.k1_seg;
     for (int c : k1c) {
@@ -952,7 +952,8 @@ int eptv_reconstruct_batched(int n, eptv_geometry *const *geoms, const eptv_para
 int eptv_set_tuning(eptv_geometry *g, int k1_seg, int k2_vg) {
     if (!g) return fail(EPTV_ERR_ARG, "NULL handle");
     if (k1_seg != 4 && k1_seg != 8 && k1_seg != 16) return fail(EPTV_ERR_ARG, "k1_seg must be 4, 8 or 16");
-    if (k2_vg != 1 && k2_vg != 2 && k2_vg != 4 && k2_vg != 8) return fail(EPTV_ERR_ARG, "k2_vg must be 1, 2, 4 or 8");
+    if (k2_vg != 1 && k2_vg != 2 && k2_vg != 4 && k2_vg != 8 && k2_vg != 16)
+        return fail(EPTV_ERR_ARG, "k2_vg must be 1, 2, 4, 8 or 16");
     g->B.k1_seg = k1_seg;
     g->B.k2_vg = k2_vg;
     return 0;

@@ -749,7 +749,7 @@ int eptv3_create_geometry(const eptv3_geometry_desc *d, eptv3_geometry **out) {
     for (float **p : {&g->Q, &g->TT, &g->WW, &g->Tsel}) A(p, (size_t)V.nf);
     A(&g->sel, 1);
     A(&g->partials, (size_t)std::max(blk_k31 * 2, std::max(blk_face, blk_vox) * kPartialStride));
-    A(&g->acc, (size_t)kPartialStride * kAccStride);
+    A(&g->acc, (size_t)kPartialStride * kAccCopies * kAccStride);
     A(&g->ctr, 1);
     A(&g->sc, kScalarStride);
     A(&g->d_sd, 1);
@@ -763,7 +763,7 @@ int eptv3_create_geometry(const eptv3_geometry_desc *d, eptv3_geometry **out) {
         cudaMemcpy(g->view, views.data(), sizeof(ViewRec3) * views.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(g->d_sd, &sd, sizeof sd, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(g->ctr, 0, sizeof(unsigned int)) != cudaSuccess ||
-        cudaMemset(g->acc, 0, sizeof(unsigned long long) * kPartialStride * kAccStride) != cudaSuccess ||
+        cudaMemset(g->acc, 0, sizeof(unsigned long long) * kPartialStride * kAccCopies * kAccStride) != cudaSuccess ||
         cudaMemset(g->sc, 0, sizeof(double) * kScalarStride) != cudaSuccess) {
         eptv3_destroy_geometry(g);
         return c3_fail(EPTV_ERR_CUDA, "upload of the cone-beam tables failed");

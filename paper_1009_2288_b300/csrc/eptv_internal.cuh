@@ -103,7 +103,8 @@ struct SliceDev {
     int log_outer;       // capacity in outer iterations (0: no log)
     int log_gd;          // GD iterations per outer iteration in the log layout
     // reduction bookkeeping of this slice in its batch: the ticket counter ctr[0] and the
-    // exact accumulators ([kPartialStride][kAccStride] words, zero between launches)
+    // exact accumulators ([kPartialStride][kAccCopies][kAccStride] words, zero between
+    // launches)
     unsigned int *ctr;
     unsigned long long *acc;
     // stored operator (null unless selected): SELL-32 P (rows = rays), P^T (rows = pixels)
@@ -181,19 +182,23 @@ constexpr int kPartialStride = kMaxTrials + 8;
 // Exact, order-independent sums of FP64 block partials.  A value x is a binary fixed-point
 // number with its least significant bit at 2^kAccLsbExp; that number is split into 32-bit
 // chunks, and chunk c is added with a 64-bit integer atomic into word c of the value's
-// accumulator (a word takes 2^31 additions before it could overflow).  Integer addition is
-// associative, so the total does not depend on the order in which blocks finish, and the
-// block that finishes last rounds the exact total once to FP64.  Every block partial of
-// the kernels is a sum of FP32 numbers, hence a multiple of 2^-149, so for them the total
-// is the correctly rounded exact sum; finite bits below 2^kAccLsbExp (smaller doubles) are
-// truncated toward zero.  Non-finite values, and magnitudes of 2^191 and above, set flags
-// (result NaN, or +-Inf); the two top words stay free for carries, so a total of up to
-// 2^31 values cannot overflow.
+// accumulator.  Integer addition is associative, so the total does not depend on the order
+// in which blocks finish, and the block that finishes last rounds the exact total once to
+// FP64.  Every block partial of the kernels is a sum of FP32 numbers, hence a multiple of
+// 2^-149, so for them the total is the correctly rounded exact sum; finite bits below
+// 2^kAccLsbExp (smaller doubles) are truncated toward zero.  Non-finite values, and
+// magnitudes of 2^191 and above, set flags (result NaN, or +-Inf); the two top words stay
+// free for carries, so a total of up to 2^31 values cannot overflow.  Each value has
+// kAccCopies accumulators (block b adds into copy b mod kAccCopies), so that blocks
+// finishing together do not queue on the same addresses; the copies are summed (exactly)
+// when the total is read.
 constexpr int kAccChunks = 12;                 // bits 2^-149 .. 2^234
 constexpr int kAccStride = kAccChunks + 1;     // + one word of flags
+constexpr int kAccCopies = 8;                  // divides 32
 constexpr int kAccLsbExp = -149;
 constexpr unsigned long long kAccNaN = 1ull, kAccPosInf = 2ull, kAccNegInf = 4ull;
 
+// Adds x into one accumulator copy (kAccStride words).
 __device__ __forceinline__ void acc_add(unsigned long long *acc, double x) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
     const bool neg = (b >> 63) != 0;
@@ -225,15 +230,9 @@ __device__ __forceinline__ void acc_add(unsigned long long *acc, double x) {
         if (d[q]) atomicAdd(acc + c + q, neg ? (0ull - d[q]) : d[q]);
 }
 
-// The accumulated total, rounded to nearest FP64; re-zeroes the accumulator.  Called by
-// one thread per value after every contribution is visible.
-__device__ __forceinline__ double acc_finish(unsigned long long *acc) {
-    long long w[kAccChunks];
-#pragma unroll
-    for (int i = 0; i < kAccChunks; ++i) w[i] = (long long)__ldcg(acc + i);
-    const unsigned long long flags = __ldcg(acc + kAccChunks);
-#pragma unroll
-    for (int i = 0; i < kAccStride; ++i) acc[i] = 0ull;
+// The exact total held in the words w (two's complement chunks, carries not yet
+// propagated) and flags, rounded to nearest FP64.
+__device__ __forceinline__ double acc_round(const long long (&w)[kAccChunks], unsigned long long flags) {
     if ((flags & kAccNaN) || (flags & (kAccPosInf | kAccNegInf)) == (kAccPosInf | kAccNegInf))
         return __longlong_as_double(0x7FF8000000000000ll);
     if (flags & kAccPosInf) return __longlong_as_double(0x7FF0000000000000ll);
@@ -281,6 +280,35 @@ __device__ __forceinline__ double acc_finish(unsigned long long *acc) {
     return neg ? -v : v;
 }
 
+// All NT threads of a block (NT a multiple of 32), after every contribution is visible:
+// res[k] = the total of value k (k < NV) over its kAccCopies copies (acc[k][copy][word]);
+// re-zeroes the accumulators.  Lane groups of kAccCopies read one copy each and add the
+// words with shuffles (integer sums: exact).
+template <int NV, int NT>
+__device__ __forceinline__ void acc_read(unsigned long long *acc, double *res) {
+    for (int base = 0; base < NV * kAccCopies; base += NT) {
+        const int t = base + (int)threadIdx.x;
+        const bool mine = t < NV * kAccCopies;
+        long long w[kAccChunks];
+        unsigned long long fl = 0ull;
+        unsigned long long *a = acc + (size_t)(mine ? t : 0) * kAccStride;
+#pragma unroll
+        for (int i = 0; i < kAccChunks; ++i) w[i] = mine ? (long long)__ldcg(a + i) : 0ll;
+        if (mine) {
+            fl = __ldcg(a + kAccChunks);
+#pragma unroll
+            for (int i = 0; i < kAccStride; ++i) a[i] = 0ull;
+        }
+#pragma unroll
+        for (int o = 1; o < kAccCopies; o <<= 1) {
+#pragma unroll
+            for (int i = 0; i < kAccChunks; ++i) w[i] += __shfl_xor_sync(0xffffffffu, w[i], o);
+            fl |= __shfl_xor_sync(0xffffffffu, fl, o);
+        }
+        if (mine && (t % kAccCopies) == 0) res[t / kAccCopies] = acc_round(w, fl);
+    }
+}
+
 // Deterministic reduction of the NV per-block partial sums that the nblk blocks of a slice
 // wrote to partials[b0 + lb][0 .. NV) (row stride `stride`), lb = the calling block's index
 // within the slice: every block adds its row into the slice's exact accumulators, and the
@@ -292,9 +320,10 @@ __device__ __forceinline__ bool reduce_slice(const SliceDev &S, const double *pa
     (void)wpart;
     __syncthreads();                                       // the row may come from any thread
     if (threadIdx.x < NV)
-        acc_add(S.acc + threadIdx.x * kAccStride, partials[(size_t)(b0 + lb) * stride + threadIdx.x]);
+        acc_add(S.acc + ((size_t)threadIdx.x * kAccCopies + (lb % kAccCopies)) * kAccStride,
+                partials[(size_t)(b0 + lb) * stride + threadIdx.x]);
     if (!last_block_of_slice(S.ctr, nblk, flag)) return false;
-    if (threadIdx.x < NV) res[threadIdx.x] = acc_finish(S.acc + threadIdx.x * kAccStride);
+    acc_read<NV, NT>(S.acc, res);
     __syncthreads();
     return true;
 }

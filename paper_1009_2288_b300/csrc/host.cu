@@ -193,7 +193,7 @@ static int build_batch(Batch &B, DevMem &mem, const std::vector<SliceDev> &sds) 
     // reduction bookkeeping per slice: one ticket counter and kPartialStride exact
     // accumulators (zero between launches)
     const int cstride = 1;
-    const size_t astride = (size_t)kPartialStride * kAccStride;
+    const size_t astride = (size_t)kPartialStride * kAccCopies * kAccStride;
     int rc;
     if ((rc = mem.alloc(&B.d_sd, B.n))) return rc;
     if ((rc = mem.alloc(&B.d_start, B.h_start.size()))) return rc;

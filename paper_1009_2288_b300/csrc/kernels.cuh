@@ -65,7 +65,7 @@ struct Batch {
     int *d_start = nullptr;         // [FAM_COUNT][n + 1]
     std::vector<int> h_start;
     unsigned int *d_counters = nullptr;   // [n][counter stride]: reduction tickets (SliceDev::ctr)
-    unsigned long long *d_acc = nullptr;  // [n][kPartialStride][kAccStride]: exact sums (SliceDev::acc)
+    unsigned long long *d_acc = nullptr;  // [n][kPartialStride][kAccCopies][kAccStride]: exact sums
     double *d_partials = nullptr;         // [max blocks][kPartialStride]
     unsigned int *d_hist = nullptr;       // [n][kHistBins]
     ParamsDev *d_params = nullptr;

@@ -1,9 +1,11 @@
-"""The exact fixed-point accumulator of the CUDA reductions (acc_add / acc_finish in
+"""The exact fixed-point accumulator of the CUDA reductions (acc_add / acc_round in
 csrc/eptv_internal.cuh), compiled for the host with stand-ins for the CUDA intrinsics
 (single-threaded: the device atomics become plain additions, which is what makes the
 result order-independent), against exact rational sums: every total of FP32-derived
 block partials must be the correctly rounded exact sum, including round-to-even ties,
-cancellation, and the non-finite and overflow flags."""
+cancellation, and the non-finite and overflow flags.  Values are spread over the
+kAccCopies copies as blocks spread them (value i into copy i mod kAccCopies), and the
+copies' words are added before rounding, as the device read-out does."""
 import math
 import os
 import random
@@ -35,17 +37,27 @@ static inline void atomicOr(unsigned long long *p, unsigned long long v) { *p |=
 
 MAIN = r'''
 int main() {
-    unsigned long long acc[kAccStride];
+    unsigned long long acc[kAccCopies][kAccStride];
     memset(acc, 0, sizeof acc);
     char line[128];
+    long n = 0;
     while (fgets(line, sizeof line, stdin)) {
         if (line[0] == 'E') {
-            const double r = acc_finish(acc);
+            long long w[kAccChunks];
+            unsigned long long flags = 0;
+            for (int i = 0; i < kAccChunks; ++i) {
+                w[i] = 0;
+                for (int c = 0; c < kAccCopies; ++c) w[i] += (long long)acc[c][i];
+            }
+            for (int c = 0; c < kAccCopies; ++c) flags |= acc[c][kAccChunks];
+            const double r = acc_round(w, flags);
             printf("%016llx\n", (unsigned long long)__double_as_longlong(r));
-            for (int i = 0; i < kAccStride; ++i) if (acc[i]) { printf("not-rezeroed\n"); return 1; }
+            memset(acc, 0, sizeof acc);
+            n = 0;
             continue;
         }
-        acc_add(acc, __longlong_as_double((long long)strtoull(line, 0, 16)));
+        acc_add(acc[n % kAccCopies], __longlong_as_double((long long)strtoull(line, 0, 16)));
+        ++n;
     }
     return 0;
 }
@@ -57,7 +69,7 @@ def accumulator(tmp_path_factory):
     if shutil.which("g++") is None:
         pytest.skip("no host C++ compiler")
     src = open(HEADER).read()
-    body = src[src.index("constexpr int kAccChunks"):src.index("// Deterministic reduction of the NV")]
+    body = src[src.index("constexpr int kAccChunks"):src.index("// All NT threads of a block (NT a multiple of 32)")]
     d = tmp_path_factory.mktemp("acc")
     cpp, exe = d / "acc.cpp", d / "acc"
     cpp.write_text(SHIMS + body + MAIN)

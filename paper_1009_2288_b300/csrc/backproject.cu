@@ -41,6 +41,7 @@ k2_backproject(const SliceDev *__restrict__ sls, TileMap map, BackArgs a, double
     const int si = find_slice(map, blockIdx.x, &local);
     const SliceDev &S = sls[si];
     const int nx = S.nx, ny = S.ny, nb = S.nb;
+    const double gamma_pre = threadIdx.x == 0 ? fin_gamma(S.sc, a.fin) : 0.0;
     const int tiles_x = (nx + kTileW - 1) / kTileW;
     const int tyb = local / tiles_x, txb = local - tyb * tiles_x;
     const int blk = threadIdx.x % kBlocksPT, vg = threadIdx.x / kBlocksPT;
@@ -226,7 +227,7 @@ k2_backproject(const SliceDev *__restrict__ sls, TileMap map, BackArgs a, double
     block_sum_to<1, NT>(vals, partials + (size_t)blockIdx.x * 2, rsm);
     if (threadIdx.x == 0) partials[(size_t)blockIdx.x * 2 + 1] = 0.0;
     if (!reduce_slice<2, NT>(S, partials, 2, b0, nblk, local, rsm, res, &last_flag)) return;
-    if (threadIdx.x == 0) finalize(S.sc, a.fin, res[0], res[1]);
+    if (threadIdx.x == 0) finalize(S.sc, a.fin, res[0], res[1], gamma_pre);
 }
 
 void launch_backproject(const Batch &B, const BackArgs &a, cudaStream_t st) {

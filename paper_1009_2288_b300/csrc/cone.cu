@@ -51,6 +51,7 @@ __global__ void __launch_bounds__(32 * SEG)
 k31_project(Cone C, const float *__restrict__ f, const float *__restrict__ y_resid, float *__restrict__ out,
             double *__restrict__ partials, SliceDev *S, int fin)
 {
+    const double gamma_pre = threadIdx.x == 0 ? fin_gamma(S->sc, fin) : 0.0;
     __shared__ float red[SEG][33];
     __shared__ double rsm[2 * SEG];
     __shared__ double res[2];
@@ -172,7 +173,7 @@ k31_project(Cone C, const float *__restrict__ f, const float *__restrict__ y_res
     float vals[2] = {sq, ysum};
     block_sum_to<2, 32 * SEG>(vals, partials + (size_t)blockIdx.x * 2, rsm);
     if (!reduce_slice<2, 32 * SEG>(*S, partials, 2, 0, gridDim.x, blockIdx.x, rsm, res, &last_flag)) return;
-    if (threadIdx.x == 0) finalize(S->sc, fin, res[0], res[1]);
+    if (threadIdx.x == 0) finalize(S->sc, fin, res[0], res[1], gamma_pre);
 }
 
 // ------------------------------------------------------------------ K32: back projector
@@ -181,6 +182,7 @@ __global__ void __launch_bounds__(256)
 k32_backproject(Cone C, const float *__restrict__ y, float *__restrict__ out, double *__restrict__ partials,
                 SliceDev *S, int fin)
 {
+    const double gamma_pre = threadIdx.x == 0 ? fin_gamma(S->sc, fin) : 0.0;
     __shared__ double rsm[2 * 8];
     __shared__ double res[2];
     __shared__ int last_flag;
@@ -232,7 +234,7 @@ k32_backproject(Cone C, const float *__restrict__ y, float *__restrict__ out, do
     block_sum_to<1, 256>(vals, partials + (size_t)blockIdx.x * 2, rsm);
     if (threadIdx.x == 0) partials[(size_t)blockIdx.x * 2 + 1] = 0.0;
     if (!reduce_slice<2, 256>(*S, partials, 2, 0, gridDim.x, blockIdx.x, rsm, res, &last_flag)) return;
-    if (threadIdx.x == 0) finalize(S->sc, fin, res[0], res[1]);
+    if (threadIdx.x == 0) finalize(S->sc, fin, res[0], res[1], gamma_pre);
 }
 
 // ------------------------------------------------------------------ CGLS vectors
@@ -241,6 +243,7 @@ k32_backproject(Cone C, const float *__restrict__ y, float *__restrict__ out, do
 __global__ void __launch_bounds__(256)
 k3v_norm2(const float *__restrict__ x, long long n, double *__restrict__ partials, SliceDev *S, int fin)
 {
+    const double gamma_pre = threadIdx.x == 0 ? fin_gamma(S->sc, fin) : 0.0;
     __shared__ double rsm[2 * 8];
     __shared__ double res[2];
     __shared__ int last_flag;
@@ -254,7 +257,7 @@ k3v_norm2(const float *__restrict__ x, long long n, double *__restrict__ partial
     float vals[2] = {s2, s1};
     block_sum_to<2, 256>(vals, partials + (size_t)blockIdx.x * 2, rsm);
     if (!reduce_slice<2, 256>(*S, partials, 2, 0, gridDim.x, blockIdx.x, rsm, res, &last_flag)) return;
-    if (threadIdx.x == 0) finalize(S->sc, fin, res[0], res[1]);
+    if (threadIdx.x == 0) finalize(S->sc, fin, res[0], res[1], gamma_pre);
 }
 
 // y += sign * sc[which] * x

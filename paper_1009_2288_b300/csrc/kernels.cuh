@@ -77,18 +77,22 @@ struct Batch {
     int blocks(int fam) const { return h_start[fam * (n + 1) + n]; }
 };
 
-__device__ __forceinline__ void finalize(double *sc, int fin, double s0, double s1) {
+// The scalar a finalisation mode divides by (SC_GAMMA), read by the caller at kernel start
+// so that the finishing block's tail waits on no global load (only that block writes it).
+__device__ __forceinline__ double fin_gamma(const double *sc, int fin) {
+    return (fin == FIN_QQ_TO_A || fin == FIN_B) ? sc[SC_GAMMA] : 0.0;
+}
+
+__device__ __forceinline__ void finalize(double *sc, int fin, double s0, double s1, double gamma) {
     if (!isfinite(s0) || !isfinite(s1)) sc[SC_NONFINITE] = 1.0;
     switch (fin) {
     case FIN_NORM: sc[SC_NORM] = s0; sc[SC_NORM2] = s1; break;
-    case FIN_QQ_TO_A: sc[SC_QQ] = s0; sc[SC_A] = (s0 > 0.0) ? sc[SC_GAMMA] / s0 : 0.0; break;
+    case FIN_QQ_TO_A: sc[SC_QQ] = s0; sc[SC_A] = (s0 > 0.0) ? gamma / s0 : 0.0; break;
     case FIN_GAMMA0: sc[SC_GAMMA] = s0; break;
-    case FIN_B: {
-        const double g = sc[SC_GAMMA];
-        sc[SC_B] = (g > 0.0) ? s0 / g : 0.0;
+    case FIN_B:
+        sc[SC_B] = (gamma > 0.0) ? s0 / gamma : 0.0;
         sc[SC_GAMMA] = s0;
         break;
-    }
     default: break;
     }
 }

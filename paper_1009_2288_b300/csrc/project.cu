@@ -31,6 +31,7 @@ k1_project(const SliceDev *__restrict__ sls, TileMap map, ProjArgs a, double *__
     const int si = find_slice(map, blockIdx.x, &local);
     const SliceDev &S = sls[si];
     const int nb = S.nb;
+    const double gamma_pre = threadIdx.x == 0 ? fin_gamma(S.sc, a.fin) : 0.0;
     const int nbb = (nb + 31) >> 5;
     // work unit (view, group of 32 bins) of this block: heaviest first, so that the blocks
     // dispatched last are the short ones and the SMs finish together
@@ -210,7 +211,7 @@ k1_project(const SliceDev *__restrict__ sls, TileMap map, ProjArgs a, double *__
         }
     }
     if (!reduce_slice<2, 32 * SEG>(S, partials, 2, b0, nblk, local, rsm, res, &last_flag)) return;
-    if (threadIdx.x == 0) finalize(S.sc, a.fin, res[0], res[1]);
+    if (threadIdx.x == 0) finalize(S.sc, a.fin, res[0], res[1], gamma_pre);
 }
 
 void launch_project(const Batch &B, const ProjArgs &a, cudaStream_t st) {

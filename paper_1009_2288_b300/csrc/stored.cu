@@ -351,6 +351,7 @@ k_spmv_p(const SliceDev *__restrict__ sls, TileMap map, ProjArgs a, double *__re
     const int si = find_slice(map, blockIdx.x, &local);
     const SliceDev &S = sls[si];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const double gamma_pre = threadIdx.x == 0 ? fin_gamma(S.sc, a.fin) : 0.0;
     const int slice = local;
     const int row = slice * 32 + lane;
     const float *x, *xT;
@@ -389,7 +390,7 @@ k_spmv_p(const SliceDev *__restrict__ sls, TileMap map, ProjArgs a, double *__re
     float vals[2] = {sq, ysum};
     block_sum_to<2, 256>(vals, partials + (size_t)blockIdx.x * 2, rsm);
     if (!reduce_slice<2, 256>(S, partials, 2, b0, nblk, local, rsm, res, &last_flag)) return;
-    if (threadIdx.x == 0) finalize(S.sc, a.fin, res[0], res[1]);
+    if (threadIdx.x == 0) finalize(S.sc, a.fin, res[0], res[1], gamma_pre);
 }
 
 // x = P^T y (rows = pixels).  A block covers a 32 x 8 pixel tile (warp = one image row of
@@ -406,6 +407,7 @@ k_spmv_pt(const SliceDev *__restrict__ sls, TileMap map, BackArgs a, double *__r
     const int si = find_slice(map, blockIdx.x, &local);
     const SliceDev &S = sls[si];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const double gamma_pre = threadIdx.x == 0 ? fin_gamma(S.sc, a.fin) : 0.0;
     const int spr = (S.nx + 31) >> 5;
     const int ty = local / spr, sx = local - ty * spr;
     const int iy = ty * 8 + warp, ix = sx * 32 + lane;
@@ -437,7 +439,7 @@ k_spmv_pt(const SliceDev *__restrict__ sls, TileMap map, BackArgs a, double *__r
     block_sum_to<1, 256>(vals, partials + (size_t)blockIdx.x * 2, rsm);
     if (threadIdx.x == 0) partials[(size_t)blockIdx.x * 2 + 1] = 0.0;
     if (!reduce_slice<2, 256>(S, partials, 2, b0, nblk, local, rsm, res, &last_flag)) return;
-    if (threadIdx.x == 0) finalize(S.sc, a.fin, res[0], res[1]);
+    if (threadIdx.x == 0) finalize(S.sc, a.fin, res[0], res[1], gamma_pre);
 }
 
 void launch_spmv_p(const Batch &B, const ProjArgs &a, cudaStream_t st) {

@@ -6,9 +6,10 @@
 //             axis (x or y).  In each major-axis slab the ray walks the cells of the two
 //             minor axes incrementally, so every voxel it crosses gets the canonical
 //             length min(exit planes) - max(entry planes) of eptv_internal.cuh.
-//   K32  P^T: voxel-driven gather, the exact transpose: per view, the voxel's 8 corners
-//             bound the detector pixels whose rays can cross it, and each such ray's
-//             length through the voxel is the same canonical formula.
+//   K32  P^T: voxel-driven gather, the exact transpose: a thread owns two voxels stacked
+//             in z; per view, their corners bound the detector pixels whose rays can
+//             cross them, and each such ray's length through each voxel is the same
+//             canonical formula.
 //   (P2) half-face kernels (the 2-D half-edges extended to faces, Eqs. 5, 9, A2, A3 in
 //             3-D), a gradient kernel, one kernel that evaluates all Armijo trial steps,
 //             and the step/clamp kernel; every reduction is the deterministic two-level
@@ -178,6 +179,11 @@ k31_project(Cone C, const float *__restrict__ f, const float *__restrict__ y_res
 
 // ------------------------------------------------------------------ K32: back projector
 
+// Thread = two voxels stacked in z, (ix, iy, 2 iz2) and (ix, iy, 2 iz2 + 1): a voxel's
+// detector columns do not depend on z, so the pair shares its per-view corner projections
+// and, per candidate ray, the x and y plane parameters (7 instead of 12 for two voxels).
+constexpr int kZPair = 2;
+
 __global__ void __launch_bounds__(256)
 k32_backproject(Cone C, const float *__restrict__ y, float *__restrict__ out, double *__restrict__ partials,
                 SliceDev *S, int fin)
@@ -186,29 +192,36 @@ k32_backproject(Cone C, const float *__restrict__ y, float *__restrict__ out, do
     __shared__ double rsm[2 * 8];
     __shared__ double res[2];
     __shared__ int last_flag;
-    const long long vox = (long long)blockIdx.x * 256 + threadIdx.x;
-    float acc = 0.0f;
-    const bool valid = vox < C.n_vox;
+    const int nz2 = (C.nz + kZPair - 1) / kZPair;
+    const long long col = (long long)blockIdx.x * 256 + threadIdx.x;   // (iz2, iy, ix)
+    const long long n_col = (long long)C.nx * C.ny * nz2;
+    float acc[kZPair] = {0.0f, 0.0f};
+    const bool valid = col < n_col;
+    int ix = 0, iy = 0, iz0 = 0;
     if (valid) {
-        const int ix = (int)(vox % C.nx);
-        const int iy = (int)((vox / C.nx) % C.ny);
-        const int iz = (int)(vox / ((long long)C.nx * C.ny));
+        ix = (int)(col % C.nx);
+        iy = (int)((col / C.nx) % C.ny);
+        iz0 = (int)(col / ((long long)C.nx * C.ny)) * kZPair;
+        const int nzp = min(kZPair, C.nz - iz0);            // voxels of the pair inside
         const float X0 = grid_line((float)ix, C.dx, C.x0), X1 = grid_line((float)(ix + 1), C.dx, C.x0);
         const float Y0 = grid_line((float)iy, C.dy, C.y0), Y1 = grid_line((float)(iy + 1), C.dy, C.y0);
-        const float Z0 = grid_line((float)iz, C.dz, C.z0), Z1 = grid_line((float)(iz + 1), C.dz, C.z0);
+        float Z[kZPair + 1];
+#pragma unroll
+        for (int q = 0; q <= kZPair; ++q) Z[q] = grid_line((float)(iz0 + q), C.dz, C.z0);
+        const float Ze = grid_line((float)(iz0 + nzp), C.dz, C.z0);
         for (int v = 0; v < C.nv; ++v) {
             const ViewRec3 V = C.view[v];
             float umin = 3e38f, umax = -3e38f, wmin = 3e38f, wmax = -3e38f;
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                const float px = (c & 1) ? X1 : X0, py = (c & 2) ? Y1 : Y0, pz = (c & 4) ? Z1 : Z0;
+            for (int c = 0; c < 4; ++c) {
+                const float px = (c & 1) ? X1 : X0, py = (c & 2) ? Y1 : Y0;
                 const float wx = px - V.sx, wy = py - V.sy;
                 const float depth = V.cx * wx + V.cy * wy;            // along the central ray
                 const float sc = __fdividef(C.sdd, depth);
                 const float u = (V.ux * wx + V.uy * wy) * sc;
-                const float w = pz * sc;
                 umin = fminf(umin, u); umax = fmaxf(umax, u);
-                wmin = fminf(wmin, w); wmax = fmaxf(wmax, w);
+                const float w0 = Z[0] * sc, w1 = Ze * sc;
+                wmin = fminf(wmin, fminf(w0, w1)); wmax = fmaxf(wmax, fmaxf(w0, w1));
             }
             const int iu0 = max(0, (int)ceilf(umin / C.du + C.uc - 0.01f));
             const int iu1 = min(C.nu - 1, (int)floorf(umax / C.du + C.uc + 0.01f));
@@ -220,17 +233,31 @@ k32_backproject(Cone C, const float *__restrict__ y, float *__restrict__ out, do
                     const RayRec3 R = C.ray[rowbase + iu];
                     const float ax = cross_t(X0, R.px, R.ix), bx = cross_t(X1, R.px, R.ix);
                     const float ay = cross_t(Y0, R.py, R.iy), by = cross_t(Y1, R.py, R.iy);
-                    const float az = cross_t(Z0, R.pz, R.iz), bz = cross_t(Z1, R.pz, R.iz);
-                    const float l = c3_len(fminf(ax, bx), fmaxf(ax, bx), fminf(ay, by), fmaxf(ay, by),
-                                           fminf(az, bz), fmaxf(az, bz));
-                    if (l > 0.0f) acc = fmaf(l, __ldg(y + rowbase + iu), acc);
+                    // min / max are exact, so grouping the x and y planes first gives the
+                    // same length as the canonical six-plane formula
+                    const float lo_xy = fmaxf(fminf(ax, bx), fminf(ay, by));
+                    const float hi_xy = fminf(fmaxf(ax, bx), fmaxf(ay, by));
+                    if (!(lo_xy < hi_xy)) continue;
+                    const float yv = __ldg(y + rowbase + iu);
+                    float tz[kZPair + 1];
+#pragma unroll
+                    for (int q = 0; q <= kZPair; ++q) tz[q] = cross_t(Z[q], R.pz, R.iz);
+#pragma unroll
+                    for (int q = 0; q < kZPair; ++q) {
+                        const float l = c3_len(lo_xy, hi_xy, lo_xy, hi_xy, fminf(tz[q], tz[q + 1]),
+                                               fmaxf(tz[q], tz[q + 1]));
+                        acc[q] = fmaf(l, yv, acc[q]);
+                    }
                 }
             }
         }
-        out[vox] = acc;
+        const long long vox = ((long long)iz0 * C.ny + iy) * C.nx + ix;
+        out[vox] = acc[0];
+        if (nzp > 1) out[vox + (long long)C.nx * C.ny] = acc[1];
+        if (nzp < 2) acc[1] = 0.0f;
     }
     if (fin == FIN_NONE) return;
-    float vals[1] = {valid ? acc * acc : 0.0f};
+    float vals[1] = {valid ? fmaf(acc[0], acc[0], acc[1] * acc[1]) : 0.0f};
     block_sum_to<1, 256>(vals, partials + (size_t)blockIdx.x * 2, rsm);
     if (threadIdx.x == 0) partials[(size_t)blockIdx.x * 2 + 1] = 0.0;
     if (!reduce_slice<2, 256>(*S, partials, 2, 0, gridDim.x, blockIdx.x, rsm, res, &last_flag)) return;
@@ -609,7 +636,8 @@ static void c3_project(const eptv3_geometry *g, const float *f, const float *y_r
 }
 
 static void c3_backproject(const eptv3_geometry *g, const float *y, float *out, int fin, cudaStream_t st) {
-    k32_backproject<<<nblk_of(g->C.n_vox, 256), 256, 0, st>>>(g->C, y, out, g->partials, g->d_sd, fin);
+    const long long n_col = (long long)g->C.nx * g->C.ny * ((g->C.nz + kZPair - 1) / kZPair);
+    k32_backproject<<<nblk_of(n_col, 256), 256, 0, st>>>(g->C, y, out, g->partials, g->d_sd, fin);
 }
 
 // (P1): M CGLS iterations on g->u (App. I), data g->y

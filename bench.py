@@ -86,6 +86,19 @@ def max_over_ranks(x, world):
     return float(t.item())
 
 
+def job_rate(ms_this_rank, world, units_per_rank):
+    """Whole-job rate of a replica run: every rank processes units_per_rank units (its own
+    slice, no data-path collective), the job takes as long as the slowest rank.
+    Returns (ms of the slowest rank, units of all ranks per second)."""
+    ms = max_over_ranks(ms_this_rank, world)
+    return ms, world * units_per_rank * 1e3 / ms
+
+
+def replica_seed(rank):
+    """Seed of the slice a rank reconstructs (each rank its own synthetic slice)."""
+    return 2 + rank
+
+
 class Clocks:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -608,7 +621,7 @@ def run_ours(args, world, rank, local):
             out = run_cone(dev, torch.cuda.current_stream(dev), peak, steps=args.steps, scale=args.cone_scale)
             print(json.dumps({"cone_3d": out}), flush=True)
         return
-    case = I.make_c2(seed=2 + rank, with_truth=False)
+    case = I.make_c2(seed=replica_seed(rank), with_truth=False)
     g = case.geom
     geo = E.Geometry(g)
     p = I.EptvParams(n_outer=N_OUTER)
@@ -648,8 +661,7 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     barrier(world)
     clk = clocks.stop()
-    ms = max_over_ranks(statistics.mean(times), world)
-    value = world * N_OUTER * 1e3 / ms
+    ms, value = job_rate(statistics.mean(times), world, N_OUTER)
 
     # end to end through the C ABI with host buffers (pinned), copies inside the region
     e2e_times = []
@@ -667,7 +679,7 @@ def run_ours(args, world, rank, local):
         e.synchronize()
         e2e_times.append(s.elapsed_time(e))
     barrier(world)
-    e2e_ms = max_over_ranks(statistics.mean(e2e_times), world)
+    e2e_ms, e2e_value = job_rate(statistics.mean(e2e_times), world, N_OUTER)
 
     # dominant kernels timed live: projector (with transposed image) and back projector
     fT = torch.empty_like(f_dev)
@@ -778,7 +790,7 @@ def run_ours(args, world, rank, local):
                    "n_gd": p.n_gd, "max_trials": p.max_trials, "l2": "flushed (256 MB write) between steps",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "tuning": {"k1_seg": tuning[0], "k2_vg": tuning[1]}},
-        "e2e": {"value": world * N_OUTER * 1e3 / e2e_ms, "unit": UNIT,
+        "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": 4 * g.n_rays, "d2h_bytes_per_step": 4 * g.n_pix,
                 "ms_per_step": e2e_ms},
         "gpu_launches": int(launches) * args.steps,

@@ -131,28 +131,35 @@ k31_project(Cone C, const float *__restrict__ f, const float *__restrict__ y_res
                 float hiz = cross_t(grid_line((float)(cz + ohz), C.dz, C.z0), R.pz, iz);
                 float fr = (float)(rs + 1);
                 float tac = t0;
+                // The slab interval is clipped to the volume's (m, z) extent [t_lo, t_hi]:
+                // plane parameters are monotone in the plane index, so for a cell inside the
+                // volume the clipping changes neither its largest entry nor its smallest
+                // exit plane and the clipped length is bit-identical to the canonical
+                // six-plane formula; a cell outside gets length exactly 0.  The cell's
+                // offset in the volume is carried along (32 bits: n_vox < 2^31).
+                const int step_m = sgm * sm, step_z = sgz * (int)sz;
+                int idx = cz * (int)sz + rs * sM + cm * sm;
                 for (int r = rs; r <= re; ++r) {
                     const float tb = cross_t(grid_line(fr, dM, M0), PM, iM);
                     const float tbc = fminf(tb, t_hi);
                     fr += 1.0f;
                     // walk the (m, z) cells the ray crosses inside [tac, tbc]
                     for (int it = 0; it < 6; ++it) {
-                        const float l = c3_len(ta, tb, lom, him, loz, hiz);
                         const float lc = fmaxf(0.0f, __fsub_rn(fminf(fminf(tbc, him), hiz),
                                                               fmaxf(fmaxf(tac, lom), loz)));
                         if (lc > 0.0f && cm >= 0 && cm < nm && cz >= 0 && cz < C.nz)
-                            acc = fmaf(l, __ldg(f + (long long)cz * sz + (long long)r * sM + (long long)cm * sm), acc);
+                            acc = fmaf(lc, __ldg(f + idx), acc);
                         const float nxt = fminf(him, hiz);
                         if (!(nxt < tbc)) break;
                         if (him <= hiz) {
-                            cm += sgm; lom = him;
+                            cm += sgm; idx += step_m; lom = him;
                             him = cross_t(grid_line((float)(cm + ohm), dm, m0), Pm, im);
                         } else {
-                            cz += sgz; loz = hiz;
+                            cz += sgz; idx += step_z; loz = hiz;
                             hiz = cross_t(grid_line((float)(cz + ohz), C.dz, C.z0), R.pz, iz);
                         }
                     }
-                    ta = tb;
+                    idx += sM;
                     tac = fmaxf(tb, t_lo);
                 }
             }

@@ -191,7 +191,9 @@ k31_project(Cone C, const float *__restrict__ f, const float *__restrict__ y_res
 // and, per candidate ray, the x and y plane parameters (7 instead of 12 for two voxels).
 constexpr int kZPair = 2;
 
-__global__ void __launch_bounds__(256)
+// 5 blocks per SM (48 registers): the kernel waits on its ray records, and the extra
+// resident warps hide more of that latency than the few spilled registers cost
+__global__ void __launch_bounds__(256, 5)
 k32_backproject(Cone C, const float *__restrict__ y, float *__restrict__ out, double *__restrict__ partials,
                 SliceDev *S, int fin)
 {

@@ -13,12 +13,16 @@
 // lengths are min(exit planes) - max(entry planes) with the canonical plane
 // parameters of eptv_internal.cuh, bit-identical to the back projector's.
 // The SEG partial sums of a ray are combined in shared memory in a fixed order.
+#include <type_traits>
+
 #include "eptv_internal.cuh"
 #include "kernels.cuh"
 
 namespace eptv {
 
-template <int SEG>
+// HAS_T: the launch supplies the transposed image (every call of the CGLS does), so a
+// shallow ray marches over the transposed copy and the column stride is 1 for every ray.
+template <int SEG, bool HAS_T>
 __global__ void __launch_bounds__(32 * SEG)
 k1_project(const SliceDev *__restrict__ sls, TileMap map, ProjArgs a, double *__restrict__ partials)
 {
@@ -49,8 +53,17 @@ k1_project(const SliceDev *__restrict__ sls, TileMap map, ProjArgs a, double *__
     else out = (a.out == SINO_R) ? S.r : S.q;
 
     float acc = 0.0f;
+    RayRec R = {0.0f, 0.0f, 0.0f, 0.0f};
+    bool lane_sliver = false;
     if (k < nb) {
-        const RayRec R = S.ray[v * nb + k];
+        R = S.ray[v * nb + k];
+        // a second column crossing within one row (an FP32 sliver) needs a ray within
+        // rounding of the diagonal: columns crossed per row = |iM| dM / (|im| dm) >= 0.99
+        const float cx = fabsf(R.ix) * S.dx, cy = fabsf(R.iy) * S.dy;
+        lane_sliver = fminf(cx, cy) >= 0.99f * fmaxf(cx, cy);
+    }
+    const bool any_sliver = __any_sync(0xffffffffu, lane_sliver);   // warp-uniform branch below
+    if (k < nb) {
         const bool steep = fabsf(R.ix) * S.dx >= fabsf(R.iy) * S.dy;
         float PM, iM, M0, dM, Pm, im, m0, dm;
         int nM, nm;
@@ -63,7 +76,7 @@ k1_project(const SliceDev *__restrict__ sls, TileMap map, ProjArgs a, double *__
         } else {
             PM = R.px; iM = R.ix; M0 = S.x0; dM = S.dx; nM = S.nx;
             Pm = R.py; im = R.iy; m0 = S.y0; dm = S.dy; nm = S.ny;
-            if (imgT) { base = imgT; sM = S.ny; sm = 1; }
+            if (HAS_T) { base = imgT; sM = S.ny; sm = 1; }
             else { base = img; sM = 1; sm = S.nx; }
         }
         if (iM < 0.0f) { iM = -iM; im = -im; }   // march with t increasing along the major axis
@@ -123,8 +136,11 @@ k1_project(const SliceDev *__restrict__ sls, TileMap map, ProjArgs a, double *__
                 // index only needs clamping for the address.
                 float tac = fmaxf(ta, tm_lo);
                 // one row of the march: lengths of the (at most) two columns the ray
-                // crosses in this row and their offsets from the row start
-                auto step = [&](float &l0, float &l1, int &o0, int &o1) {
+                // crosses in this row and their offsets from the row start.  SLIVER: the
+                // warp holds a ray within rounding of the diagonal, which can cross a
+                // second column plane inside one row (without one, that cannot happen:
+                // the columns crossed per row are below 0.99, far beyond FP32 error)
+                auto step = [&](auto sliver, float &l0, float &l1, int &o0, int &o1) {
                     const float tb = cross_t(grid_line(fr, dM, M0), PM, iM);
                     const float tbc = fminf(tb, tm_hi);
                     fr += 1.0f;
@@ -136,7 +152,7 @@ k1_project(const SliceDev *__restrict__ sls, TileMap map, ProjArgs a, double *__
                     o1 = c1 * sm;                // used only when l1 > 0 (column inside)
                     if (hi0 < tb) {
                         c = c1; lo0 = hi0; hi0 = hi1; f1 += fsgn;
-                        if (hi1 < tb) {          // FP32 sliver near 45 degrees
+                        if (decltype(sliver)::value && hi1 < tb) {   // FP32 sliver near 45 degrees
                             c += sgn; lo0 = hi1;
                             hi0 = cross_t(grid_line((float)(c + off_hi), dm, m0), Pm, im);
                             f1 += fsgn;
@@ -147,37 +163,41 @@ k1_project(const SliceDev *__restrict__ sls, TileMap map, ProjArgs a, double *__
                 // rows in groups of kRows: the plane arithmetic of the group first, then
                 // all its gathers (independent, in flight together), then the products
                 // in row order (the same sum as a row-by-row march)
-                constexpr int kRows = 4;
-                int r = rs;
-                for (; r + kRows - 1 <= re; r += kRows) {
-                    float l0[kRows], l1[kRows], v0[kRows], v1[kRows];
-                    int o0[kRows], o1[kRows];
+                auto march = [&](auto sliver) {
+                    constexpr int kRows = 4;
+                    int r = rs;
+                    for (; r + kRows - 1 <= re; r += kRows) {
+                        float l0[kRows], l1[kRows], v0[kRows], v1[kRows];
+                        int o0[kRows], o1[kRows];
 #pragma unroll
-                    for (int u = 0; u < kRows; ++u) step(l0[u], l1[u], o0[u], o1[u]);
+                        for (int u = 0; u < kRows; ++u) step(sliver, l0[u], l1[u], o0[u], o1[u]);
 #pragma unroll
-                    for (int u = 0; u < kRows; ++u) {
-                        v0[u] = __ldg(rowp + u * sM + o0[u]);
-                        v1[u] = 0.0f;
-                        if (l1[u] > 0.0f) v1[u] = __ldg(rowp + u * sM + o1[u]);
+                        for (int u = 0; u < kRows; ++u) {
+                            v0[u] = __ldg(rowp + u * sM + o0[u]);
+                            v1[u] = 0.0f;
+                            if (l1[u] > 0.0f) v1[u] = __ldg(rowp + u * sM + o1[u]);
+                        }
+#pragma unroll
+                        for (int u = 0; u < kRows; ++u) {
+                            acc = fmaf(l0[u], v0[u], acc);
+                            acc = fmaf(l1[u], v1[u], acc);
+                        }
+                        rowp += kRows * sM;
                     }
-#pragma unroll
-                    for (int u = 0; u < kRows; ++u) {
-                        acc = fmaf(l0[u], v0[u], acc);
-                        acc = fmaf(l1[u], v1[u], acc);
+                    for (; r <= re; ++r) {
+                        float l0, l1;
+                        int o0, o1;
+                        step(sliver, l0, l1, o0, o1);
+                        const float v0 = __ldg(rowp + o0);
+                        float v1 = 0.0f;
+                        if (l1 > 0.0f) v1 = __ldg(rowp + o1);
+                        acc = fmaf(l0, v0, acc);
+                        acc = fmaf(l1, v1, acc);
+                        rowp += sM;
                     }
-                    rowp += kRows * sM;
-                }
-                for (; r <= re; ++r) {
-                    float l0, l1;
-                    int o0, o1;
-                    step(l0, l1, o0, o1);
-                    const float v0 = __ldg(rowp + o0);
-                    float v1 = 0.0f;
-                    if (l1 > 0.0f) v1 = __ldg(rowp + o1);
-                    acc = fmaf(l0, v0, acc);
-                    acc = fmaf(l1, v1, acc);
-                    rowp += sM;
-                }
+                };
+                if (any_sliver) march(std::true_type{});
+                else march(std::false_type{});
             }
         }
     }
@@ -218,11 +238,18 @@ void launch_project(const Batch &B, const ProjArgs &a, cudaStream_t st) {
     const int nblk = B.blocks(FAM_K1);
     if (nblk == 0) return;
     ++g_launch_count;
+    // the kernel reads the transposed image exactly when this holds
+    const bool has_t = a.img_override ? (a.imgT_override != nullptr) : !a.no_T;
+    const TileMap m = B.map(FAM_K1);
+#define K1_LAUNCH(SEGv)                                                                          \
+    (has_t ? k1_project<SEGv, true><<<nblk, 32 * SEGv, 0, st>>>(B.d_sd, m, a, B.d_partials)      \
+           : k1_project<SEGv, false><<<nblk, 32 * SEGv, 0, st>>>(B.d_sd, m, a, B.d_partials))
     switch (B.k1_seg) {
-    case 4: k1_project<4><<<nblk, 128, 0, st>>>(B.d_sd, B.map(FAM_K1), a, B.d_partials); break;
-    case 16: k1_project<16><<<nblk, 512, 0, st>>>(B.d_sd, B.map(FAM_K1), a, B.d_partials); break;
-    default: k1_project<8><<<nblk, 256, 0, st>>>(B.d_sd, B.map(FAM_K1), a, B.d_partials); break;
+    case 4: K1_LAUNCH(4); break;
+    case 16: K1_LAUNCH(16); break;
+    default: K1_LAUNCH(8); break;
     }
+#undef K1_LAUNCH
 }
 
 }  // namespace eptv

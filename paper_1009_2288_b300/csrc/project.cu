@@ -22,8 +22,10 @@ namespace eptv {
 
 // HAS_T: the launch supplies the transposed image (every call of the CGLS does), so a
 // shallow ray marches over the transposed copy and the column stride is 1 for every ray.
+// At most 64 registers (8 blocks of 4 warps per SM): SEG = 4 then fits the 512^2
+// workload's 1120 blocks in one wave, with no spills.
 template <int SEG, bool HAS_T>
-__global__ void __launch_bounds__(32 * SEG)
+__global__ void __launch_bounds__(32 * SEG, 32 / SEG)
 k1_project(const SliceDev *__restrict__ sls, TileMap map, ProjArgs a, double *__restrict__ partials)
 {
     __shared__ float red[SEG][33];

@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-cone", action="store_true")
     ap.add_argument("--cone-only", action="store_true",
                     help="profiling mode: run only the cone-beam leg and print its JSON")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="profiling mode: run only the batched leg and print its JSON")
     ap.add_argument("--cone-scale", type=int, default=1,
                     help="divide the cone-beam grid and detector counts (reduced profiling cases)")
     ap.add_argument("--no-batched", action="store_true")
@@ -615,6 +617,11 @@ def run_ours(args, world, rank, local):
     B.build()
     E.load()
     dev = torch.device("cuda", local)
+    if args.batched_only:
+        if rank == 0:
+            out = run_batched(dev, torch.cuda.current_stream(dev), steps=args.steps)
+            print(json.dumps({"batched": out}), flush=True)
+        return
     if args.cone_only:
         if rank == 0:
             peak, _ = measured_peaks()

@@ -317,7 +317,7 @@ k4_gd(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__restrict
         const int i = X0 - 2 + xx, j = Y0 - 2 + yy;
         float fv = 0.0f;
         if (i >= 0 && i < nx && j >= 0 && j < ny) {
-            const size_t p = (size_t)j * nx + i;
+            const int p = j * nx + i;                   // images hold < 2^31 pixels
             fv = __ldg(fprev + p);
             if (tap != 0.0f) fv = fmaf(-tap, __ldg(gprev + p), fv);
         }
@@ -331,49 +331,49 @@ k4_gd(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__restrict
         const int yy = idx / GW, xx = idx - yy * GW;
         const int i = X0 - 1 + xx, j = Y0 - 1 + yy;
         float vx = 0.0f;
-        if (i >= 0 && i < nx && j >= 0 && j < ny) vx = __ldg(vv + (size_t)j * nx + i);
+        if (i >= 0 && i < nx && j >= 0 && j < ny) vx = __ldg(vv + (j * nx + i));
         V[yy][xx] = vx;
     }
     __syncthreads();
 
-    // phase 2: half-edges around the g region
-    for (int idx = tid; idx < QXH * QXW; idx += kGdThreads) {
-        const int yy = idx / QXW, ee = idx - yy * QXW;
-        const int e = X0 - 1 + ee, j = Y0 - 1 + yy;     // between (e-1, j) and (e, j)
-        float q = 0.f, T = 0.f, w = 0.f;
-        if (e >= 0 && e <= nx && j >= 0 && j < ny) {
-            const int fx = ee;                          // F column of pixel e-1
-            const int fy = yy + 1;                      // F row of pixel row j
-            float D;
-            const float T2 = edge_T2(eps2, F[fy][fx], F[fy][fx + 1], F[fy + 1][fx], F[fy + 1][fx + 1],
-                                     F[fy - 1][fx], F[fy - 1][fx + 1], &D);
-            const float rs = rsqrtf(T2);               // T2 >= eps^2 > 0
-            T = T2 * rs;
-            if (mode == EPTV_WEIGHTS_EPTV) w = __expf(-T2 * inv_s2);
-            else if (mode == EPTV_WEIGHTS_ONE) w = 1.0f;
-            else w = 0.5f * (W[fy][fx] + W[fy][fx + 1]);
-            q = w * D * rs;
+    // phase 2: half-edges around the g region.  One pass over the union of the x-edge
+    // region (QXH x QXW) and the y-edge region (QYH x QYW): position (a, b) holds x-edge
+    // (a, b) and y-edge (a, b), which share four of their six F values.
+    for (int idx = tid; idx < QYH * QXW; idx += kGdThreads) {
+        const int a = idx / QXW, b = idx - a * QXW;
+        const float f00 = F[a][b], f01 = F[a][b + 1], f10 = F[a + 1][b], f11 = F[a + 1][b + 1];
+        if (a < QXH) {
+            // x-edge: between (e-1, j) and (e, j); F rows a .. a+2, columns b, b+1
+            const int e = X0 - 1 + b, j = Y0 - 1 + a;
+            float q = 0.f, T = 0.f, w = 0.f;
+            if (e >= 0 && e <= nx && j >= 0 && j < ny) {
+                float D;
+                const float T2 = edge_T2(eps2, f10, f11, F[a + 2][b], F[a + 2][b + 1], f00, f01, &D);
+                const float rs = rsqrtf(T2);           // T2 >= eps^2 > 0
+                T = T2 * rs;
+                if (mode == EPTV_WEIGHTS_EPTV) w = __expf(-T2 * inv_s2);
+                else if (mode == EPTV_WEIGHTS_ONE) w = 1.0f;
+                else w = 0.5f * (W[a + 1][b] + W[a + 1][b + 1]);
+                q = w * D * rs;
+            }
+            QX[a][b] = q; TXs[a][b] = T; WX[a][b] = w;
         }
-        QX[yy][ee] = q; TXs[yy][ee] = T; WX[yy][ee] = w;
-    }
-    for (int idx = tid; idx < QYH * QYW; idx += kGdThreads) {
-        const int ee = idx / QYW, xx = idx - ee * QYW;
-        const int e = Y0 - 1 + ee, i = X0 - 1 + xx;     // between (i, e-1) and (i, e)
-        float q = 0.f, T = 0.f, w = 0.f;
-        if (e >= 0 && e <= ny && i >= 0 && i < nx) {
-            const int fy = ee;                          // F row of pixel row e-1
-            const int fx = xx + 1;                      // F column of pixel column i
-            float D;
-            const float T2 = edge_T2(eps2, F[fy][fx], F[fy + 1][fx], F[fy][fx + 1], F[fy + 1][fx + 1],
-                                     F[fy][fx - 1], F[fy + 1][fx - 1], &D);
-            const float rs = rsqrtf(T2);
-            T = T2 * rs;
-            if (mode == EPTV_WEIGHTS_EPTV) w = __expf(-T2 * inv_s2);
-            else if (mode == EPTV_WEIGHTS_ONE) w = 1.0f;
-            else w = 0.5f * (W[fy][fx] + W[fy + 1][fx]);
-            q = w * D * rs;
+        if (b < QYW) {
+            // y-edge: between (i, e-1) and (i, e); F rows a, a+1, columns b .. b+2
+            const int e = Y0 - 1 + a, i = X0 - 1 + b;
+            float q = 0.f, T = 0.f, w = 0.f;
+            if (e >= 0 && e <= ny && i >= 0 && i < nx) {
+                float D;
+                const float T2 = edge_T2(eps2, f01, f11, F[a][b + 2], F[a + 1][b + 2], f00, f10, &D);
+                const float rs = rsqrtf(T2);
+                T = T2 * rs;
+                if (mode == EPTV_WEIGHTS_EPTV) w = __expf(-T2 * inv_s2);
+                else if (mode == EPTV_WEIGHTS_ONE) w = 1.0f;
+                else w = 0.5f * (W[a][b + 1] + W[a + 1][b + 1]);
+                q = w * D * rs;
+            }
+            QY[a][b] = q; TYs[a][b] = T; WY[a][b] = w;
         }
-        QY[ee][xx] = q; TYs[ee][xx] = T; WY[ee][xx] = w;
     }
     __syncthreads();
 
@@ -389,7 +389,7 @@ k4_gd(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__restrict
             const float div = (QX[yy][xx + 1] - QX[yy][xx]) + (QY[yy + 1][xx] - QY[yy][xx]);
             g = lam * d - div;
             if (xx >= 1 && xx <= kTileW && yy >= 1 && yy <= kGdTileH) {
-                const size_t p = (size_t)j * nx + i;
+                const int p = j * nx + i;
                 gout[p] = g;
                 if (ga.write_f) fout[p] = f;
                 sA = fmaf(g, d, sA);
@@ -401,77 +401,77 @@ k4_gd(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__restrict
     }
     __syncthreads();
 
-    // phase 4: owned half-edges of the tile -- energy and trial energy changes
+    // phase 4: owned half-edges of the tile -- energy and trial energy changes.  One pass
+    // over the union of the owned x-edges ((kTileW + 1) x kGdTileH) and y-edges
+    // (kTileW x (kGdTileH + 1)): position (a, b) holds x-edge (a, b) and y-edge (a, b),
+    // which share four F and four G values; an edge that is not owned here gets weight 0
+    // and adds exact zeros.
     float dJ[KT];
 #pragma unroll
     for (int m = 0; m < KT; ++m) dJ[m] = 0.0f;
     const bool want_w = ga.last && S.wout;
-    for (int idx = tid; idx < (kTileW + 1) * kGdTileH; idx += kGdThreads) {
-        const int yy = idx / (kTileW + 1), ee = idx - yy * (kTileW + 1);
-        const int e = X0 + ee, j = Y0 + yy;
-        if (j >= ny || e > nx || (ee == kTileW && e != nx)) continue;
-        const int qx = ee + 1, qy = yy + 1;             // QX indices
-        const float T = TXs[qy][qx], w = WX[qy][qx];
-        sJ = fmaf(w, T, sJ);
-        if (want_w) S.wout[(size_t)j * (nx + 1) + e] = w;
-        if (K) {
-            // pixels a = (e-1, j), b = (e, j) in F / G coordinates
-            const int fx = ee + 1, fy = yy + 2;         // F col of e-1, row of j
-            const int gx = ee, gy = yy + 1;             // G col of e-1, row of j
-            const float D = F[fy][fx + 1] - F[fy][fx];
-            const float mc = 0.5f * (F[fy][fx] + F[fy][fx + 1]);
-            const float c1 = 0.5f * (F[fy + 1][fx] + F[fy + 1][fx + 1]) - mc;
-            const float c2 = mc - 0.5f * (F[fy - 1][fx] + F[fy - 1][fx + 1]);
-            const float dD = G[gy][gx + 1] - G[gy][gx];
-            const float gc = 0.5f * (G[gy][gx] + G[gy][gx + 1]);
-            const float dc1 = 0.5f * (G[gy + 1][gx] + G[gy + 1][gx + 1]) - gc;
-            const float dc2 = gc - 0.5f * (G[gy - 1][gx] + G[gy - 1][gx + 1]);
-            const float ae = D * dD + 0.5f * (c1 * dc1 + c2 * dc2);
-            const float be = dD * dD + 0.5f * (dc1 * dc1 + dc2 * dc2);
-            const float T2 = T * T;
-#pragma unroll
-            for (int m = 0; m < KT; ++m) {
-                if (m < K) {
-                    const float t = s_t[m];
-                    const float num = t * fmaf(t, be, -2.0f * ae);
-                    const float T2n = fmaxf(T2 + num, eps2);    // T'^2 >= eps^2
-                    const float Tn = T2n * rsqrtf(T2n);
-                    dJ[m] = fmaf(w, __fdividef(num, Tn + T), dJ[m]);
-                }
-            }
+    for (int idx = tid; idx < (kGdTileH + 1) * (kTileW + 1); idx += kGdThreads) {
+        const int a = idx / (kTileW + 1), b = idx - a * (kTileW + 1);
+        // x-edge between (e-1, j) and (e, j), e = X0 + b, j = Y0 + a
+        const int ex = X0 + b, jx = Y0 + a;
+        const bool own_x = a < kGdTileH && jx < ny && ex <= nx && (b < kTileW || ex == nx);
+        // y-edge between (i, e-1) and (i, e), e = Y0 + a, i = X0 + b
+        const int ey = Y0 + a, iy = X0 + b;
+        const bool own_y = b < kTileW && iy < nx && ey <= ny && (a < kGdTileH || ey == ny);
+        const float Tx = TXs[a + 1][b + 1], wx = own_x ? WX[a + 1][b + 1] : 0.0f;
+        const float Ty = TYs[a + 1][b + 1], wy = own_y ? WY[a + 1][b + 1] : 0.0f;
+        sJ = fmaf(wx, Tx, sJ);
+        sJ = fmaf(wy, Ty, sJ);
+        if (want_w) {
+            if (own_x) S.wout[(size_t)jx * (nx + 1) + ex] = wx;
+            if (own_y) S.wout[(size_t)(ny + 1) * (nx + 1) + (size_t)ey * (nx + 1) + iy] = wy;
         }
-    }
-    for (int idx = tid; idx < kTileW * (kGdTileH + 1); idx += kGdThreads) {
-        const int ee = idx / kTileW, xx = idx - ee * kTileW;
-        const int e = Y0 + ee, i = X0 + xx;
-        if (i >= nx || e > ny || (ee == kGdTileH && e != ny)) continue;
-        const int qy = ee + 1, qx = xx + 1;             // QY indices
-        const float T = TYs[qy][qx], w = WY[qy][qx];
-        sJ = fmaf(w, T, sJ);
-        if (want_w) S.wout[(size_t)(ny + 1) * (nx + 1) + (size_t)e * (nx + 1) + i] = w;
         if (K) {
-            // pixels a = (i, e-1), b = (i, e)
-            const int fx = xx + 2, fy = ee + 1;         // F col of i, row of e-1
-            const int gx = xx + 1, gy = ee;             // G col of i, row of e-1
-            const float D = F[fy + 1][fx] - F[fy][fx];
-            const float mc = 0.5f * (F[fy][fx] + F[fy + 1][fx]);
-            const float c1 = 0.5f * (F[fy][fx + 1] + F[fy + 1][fx + 1]) - mc;
-            const float c2 = mc - 0.5f * (F[fy][fx - 1] + F[fy + 1][fx - 1]);
-            const float dD = G[gy + 1][gx] - G[gy][gx];
-            const float gc = 0.5f * (G[gy][gx] + G[gy + 1][gx]);
-            const float dc1 = 0.5f * (G[gy][gx + 1] + G[gy + 1][gx + 1]) - gc;
-            const float dc2 = gc - 0.5f * (G[gy][gx - 1] + G[gy + 1][gx - 1]);
-            const float ae = D * dD + 0.5f * (c1 * dc1 + c2 * dc2);
-            const float be = dD * dD + 0.5f * (dc1 * dc1 + dc2 * dc2);
-            const float T2 = T * T;
+            const float f11 = F[a + 1][b + 1], f12 = F[a + 1][b + 2], f21 = F[a + 2][b + 1], f22 = F[a + 2][b + 2];
+            const float g00 = G[a][b], g01 = G[a][b + 1], g10 = G[a + 1][b], g11 = G[a + 1][b + 1];
+            // x-edge: pixels at F (a+2, b+1), (a+2, b+2) and G (a+1, b), (a+1, b+1); its
+            // rows exist only for a < kGdTileH (G has kGdTileH + 2 rows)
+            float aex = 0.0f, bex = 0.0f;
+            if (a < kGdTileH) {
+                const float D = f22 - f21;
+                const float mc = 0.5f * (f21 + f22);
+                const float c1 = 0.5f * (F[a + 3][b + 1] + F[a + 3][b + 2]) - mc;
+                const float c2 = mc - 0.5f * (f11 + f12);
+                const float dD = g11 - g10;
+                const float gc = 0.5f * (g10 + g11);
+                const float dc1 = 0.5f * (G[a + 2][b] + G[a + 2][b + 1]) - gc;
+                const float dc2 = gc - 0.5f * (g00 + g01);
+                aex = D * dD + 0.5f * (c1 * dc1 + c2 * dc2);
+                bex = dD * dD + 0.5f * (dc1 * dc1 + dc2 * dc2);
+            }
+            // y-edge: pixels at F (a+1, b+2), (a+2, b+2) and G (a, b+1), (a+1, b+1); its
+            // columns exist only for b < kTileW (G has kTileW + 2 columns)
+            float aey = 0.0f, bey = 0.0f;
+            if (b < kTileW) {
+                const float D = f22 - f12;
+                const float mc = 0.5f * (f12 + f22);
+                const float c1 = 0.5f * (F[a + 1][b + 3] + F[a + 2][b + 3]) - mc;
+                const float c2 = mc - 0.5f * (f11 + f21);
+                const float dD = g11 - g01;
+                const float gc = 0.5f * (g01 + g11);
+                const float dc1 = 0.5f * (G[a][b + 2] + G[a + 1][b + 2]) - gc;
+                const float dc2 = gc - 0.5f * (g00 + g10);
+                aey = D * dD + 0.5f * (c1 * dc1 + c2 * dc2);
+                bey = dD * dD + 0.5f * (dc1 * dc1 + dc2 * dc2);
+            }
+            const float T2x = Tx * Tx, T2y = Ty * Ty;
 #pragma unroll
             for (int m = 0; m < KT; ++m) {
                 if (m < K) {
                     const float t = s_t[m];
-                    const float num = t * fmaf(t, be, -2.0f * ae);
-                    const float T2n = fmaxf(T2 + num, eps2);    // T'^2 >= eps^2
-                    const float Tn = T2n * rsqrtf(T2n);
-                    dJ[m] = fmaf(w, __fdividef(num, Tn + T), dJ[m]);
+                    const float numx = t * fmaf(t, bex, -2.0f * aex);
+                    const float T2nx = fmaxf(T2x + numx, eps2);   // T'^2 >= eps^2
+                    const float Tnx = T2nx * rsqrtf(T2nx);
+                    dJ[m] = fmaf(wx, __fdividef(numx, Tnx + Tx), dJ[m]);
+                    const float numy = t * fmaf(t, bey, -2.0f * aey);
+                    const float T2ny = fmaxf(T2y + numy, eps2);
+                    const float Tny = T2ny * rsqrtf(T2ny);
+                    dJ[m] = fmaf(wy, __fdividef(numy, Tny + Ty), dJ[m]);
                 }
             }
         }

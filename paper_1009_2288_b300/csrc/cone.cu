@@ -27,8 +27,10 @@
 
 namespace eptv {
 
-struct RayRec3 { float px, py, pz, ix, iy, iz; };   // closest point to the origin, 1/d
-struct ViewRec3 { float sx, sy, cx, cy, ux, uy; };  // source, central direction, e_u (z = 0)
+// Records padded to 32 bytes and 16-byte aligned, so that one is two 128-bit loads (six
+// separate 32-bit loads at their natural size and alignment).
+struct __align__(16) RayRec3 { float px, py, pz, ix, iy, iz, pad0, pad1; };   // closest point, 1/d
+struct __align__(16) ViewRec3 { float sx, sy, cx, cy, ux, uy, pad0, pad1; };  // source, central dir, e_u
 
 struct Cone {
     int nx, ny, nz, nv, nu, nrow;                   // nv views, nu x nrow detector

@@ -12,7 +12,7 @@
 //             canonical formula.
 //   (P2) half-face kernels (the 2-D half-edges extended to faces, Eqs. 5, 9, A2, A3 in
 //             3-D), a gradient kernel, one kernel that evaluates all Armijo trial steps,
-//             and the step/clamp kernel; every reduction is the deterministic two-level
+//             and the step/clamp kernel; every reduction is the exact, order-independent
 //             one of eptv_internal.cuh, the step decision FP64 in parallel lanes.
 #include <math.h>
 #include <stdint.h>

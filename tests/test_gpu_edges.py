@@ -164,3 +164,30 @@ def test_largest_image_sampled_rays_and_exact_transpose():
     lhs = float(torch.dot(y.double(), yr.double()))
     rhs = float(torch.dot(fd.double(), b.double()))
     assert abs(lhs - rhs) / abs(lhs) < 1e-5
+
+
+def test_full_benchmark_workload_reaches_the_oracle_energy():
+    """The benchmark's 512^2, 40 x 888, 100-iteration reconstruction, in the launch
+    configuration the benchmark times (autotuned shapes): its final reported energy
+    (Eq. 2, sigma_ref = the oracle's last sigma) and its error against the truth agree
+    with the FP64 oracle's (tests/golden/c2_oracle_energy.json, written by
+    make_oracle_energy.py from the oracle alone)."""
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                                       "c2_oracle_energy.json")))
+    case = I.make_c2(with_truth=True)
+    g = case.geom
+    geo = E.Geometry(g)
+    E.eptv_autotune(geo)
+    p = I.EptvParams(n_outer=gold["n_outer"])
+    assert p.max_trials == gold["params"]["max_trials"] and p.lam == gold["params"]["lam"]
+    f = torch.zeros(g.n_pix, device=DEV)
+    y = t32(case.y)
+    rep = E.eptv_reconstruct(geo, p, y, f)
+    assert rep.n_fail == gold["line_search_failures"]
+    e = E.eptv_report_energy(geo, p, gold["sigma_ref"], f, y)
+    assert e == pytest.approx(gold["e_report_final"], rel=1e-3)
+    got = np64(f).reshape(g.ny, g.nx)
+    err = float(((got - case.f_true) ** 2).sum() / (case.f_true ** 2).sum())   # Eq. 12, as stored
+    assert err == pytest.approx(gold["rel_error_vs_truth"], rel=1e-2)

@@ -237,7 +237,13 @@ k_sort_rows(int rows, const int *__restrict__ ptr, const int *__restrict__ cnt,
 //        from the transposed image, like K1 does, so adjacent bins meet adjacent words.
 //   P^T: slice (iy, sx) = pixels ix = 32 sx .. 32 sx + 31 of image row iy.
 // A lane sums its row in entry order (deterministic).
-constexpr int kSpmvUnroll = 4;      // entries per lane whose loads are issued together
+// Layout within a slice: chunks of kSellChunk entries per lane, lane-interleaved, so that a
+// lane's next kSellChunk entries are one 16-byte word (one 128-bit load of columns and one
+// of values) and a warp's loads of one chunk are a contiguous 512 bytes.
+constexpr int kSellChunk = 4;
+__host__ __device__ __forceinline__ int sell_index(int j, int lane) {
+    return (j / kSellChunk) * (32 * kSellChunk) + lane * kSellChunk + (j % kSellChunk);
+}
 
 __device__ __forceinline__ bool ray_is_steep(const RayRec &R, float dx, float dy) {
     return fabsf(R.ix) * dx >= fabsf(R.iy) * dy;      // the K1 criterion
@@ -257,80 +263,57 @@ __device__ __forceinline__ int sell_row(int sl, int l, int rows, int width) {
 
 // REMAP: columns are transposed pixel indices c = ix ny + iy to be read from the
 // natural image (no transposed copy given): index (c % ny) nx + c / ny.
-// PIPE (long rows): software-pipelined, the loads of the next kSpmvUnroll entries are in
-// flight while the current ones gather from the vector, so the stream does not wait for
-// the gathers.  Short rows (P^T) run faster without the extra prologue loads.
+// PIPE (long rows): software-pipelined, the next chunk's loads are in flight while the
+// current chunk gathers from the vector, so the stream does not wait for the gathers.
+// Short rows (P^T) run faster without the extra prologue loads.  base: the slice's start
+// plus 32 times the first entry (a multiple of kSellChunk); len: a multiple of kSellChunk.
+// The lane sums its entries in order (the same sum as an entry-by-entry loop).
 template <bool REMAP, bool PIPE>
 __device__ __forceinline__ float sell_row_dot(const int *__restrict__ scol, const float *__restrict__ sval,
                                               int base, int len, int lane, const float *__restrict__ x,
                                               int nx, int ny) {
+    const int4 *pc = reinterpret_cast<const int4 *>(scol + base) + lane;
+    const float4 *pv = reinterpret_cast<const float4 *>(sval + base) + lane;
+    const int n_chunks = len / kSellChunk;
+    auto gather = [&](int k) {
+        if (REMAP) { const int ix = k / ny; k = (k - ix * ny) * nx + ix; }
+        return __ldg(x + k);
+    };
     float acc = 0.0f;
     if (!PIPE) {
-        for (int j0 = 0; j0 < len; j0 += kSpmvUnroll) {
-            int c[kSpmvUnroll];
-            float v[kSpmvUnroll];
-#pragma unroll
-            for (int u = 0; u < kSpmvUnroll; ++u) {
-                const int j = j0 + u;
-                if (j < len) {
-                    const int idx = base + 32 * j + lane;
-                    c[u] = __ldcs(scol + idx);
-                    v[u] = __ldcs(sval + idx);
-                } else {
-                    c[u] = 0;
-                    v[u] = 0.0f;
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < kSpmvUnroll; ++u) {
-                int k = c[u];
-                if (REMAP) { const int ix = k / ny; k = (k - ix * ny) * nx + ix; }
-                acc = fmaf(v[u], __ldg(x + k), acc);
-            }
+        for (int c = 0; c < n_chunks; ++c) {
+            const int4 cc = __ldcs(pc + 32 * c);
+            const float4 vv = __ldcs(pv + 32 * c);
+            const float x0 = gather(cc.x), x1 = gather(cc.y), x2 = gather(cc.z), x3 = gather(cc.w);
+            acc = fmaf(vv.x, x0, acc);
+            acc = fmaf(vv.y, x1, acc);
+            acc = fmaf(vv.z, x2, acc);
+            acc = fmaf(vv.w, x3, acc);
         }
         return acc;
     }
     // guarded loads as if / else: the conditional-expression form compiled to a loop
     // that ran the back projection at half the speed
-    int c[kSpmvUnroll];
-    float v[kSpmvUnroll];
-#pragma unroll
-    for (int u = 0; u < kSpmvUnroll; ++u) {
-        if (u < len) {
-            c[u] = __ldcs(scol + base + 32 * u + lane);
-            v[u] = __ldcs(sval + base + 32 * u + lane);
-        } else {
-            c[u] = 0;
-            v[u] = 0.0f;
-        }
+    int4 cc = make_int4(0, 0, 0, 0);
+    float4 vv = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (n_chunks > 0) {
+        cc = __ldcs(pc);
+        vv = __ldcs(pv);
     }
-    for (int j0 = 0; j0 < len; j0 += kSpmvUnroll) {
-        int cn[kSpmvUnroll];
-        float vn[kSpmvUnroll];
-#pragma unroll
-        for (int u = 0; u < kSpmvUnroll; ++u) {
-            const int j = j0 + kSpmvUnroll + u;
-            if (j < len) {
-                cn[u] = __ldcs(scol + base + 32 * j + lane);
-                vn[u] = __ldcs(sval + base + 32 * j + lane);
-            } else {
-                cn[u] = 0;
-                vn[u] = 0.0f;
-            }
+    for (int c = 0; c < n_chunks; ++c) {
+        int4 cn = make_int4(0, 0, 0, 0);
+        float4 vn = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (c + 1 < n_chunks) {
+            cn = __ldcs(pc + 32 * (c + 1));
+            vn = __ldcs(pv + 32 * (c + 1));
         }
-        float xv[kSpmvUnroll];
-#pragma unroll
-        for (int u = 0; u < kSpmvUnroll; ++u) {
-            int k = c[u];
-            if (REMAP) { const int ix = k / ny; k = (k - ix * ny) * nx + ix; }
-            xv[u] = __ldg(x + k);
-        }
-#pragma unroll
-        for (int u = 0; u < kSpmvUnroll; ++u) {
-            acc = fmaf(v[u], xv[u], acc);
-            c[u] = cn[u];
-            v[u] = vn[u];
-        }
+        const float x0 = gather(cc.x), x1 = gather(cc.y), x2 = gather(cc.z), x3 = gather(cc.w);
+        acc = fmaf(vv.x, x0, acc);
+        acc = fmaf(vv.y, x1, acc);
+        acc = fmaf(vv.z, x2, acc);
+        acc = fmaf(vv.w, x3, acc);
+        cc = cn;
+        vv = vn;
     }
     return acc;
 }
@@ -361,8 +344,8 @@ k_spmv_p(const SliceDev *__restrict__ sls, TileMap map, ProjArgs a, double *__re
     float *out = a.out_override ? a.out_override : (a.out == SINO_R ? S.r : S.q);
     float acc = 0.0f;
     if (row < S.n_rays) {
-        const int len = __ldg(S.p_slen + slice);
-        const int chunk = (len + 7) >> 3;
+        const int len = __ldg(S.p_slen + slice);                       // multiple of kSellChunk
+        const int chunk = ((len + 7) / 8 + kSellChunk - 1) / kSellChunk * kSellChunk;
         const int j0 = min(len, warp * chunk), j1 = min(len, j0 + chunk);
         const int base = __ldg(S.p_sptr + slice) + 32 * j0;
         const bool steep = ray_is_steep(S.ray[row], S.dx, S.dy);
@@ -470,7 +453,8 @@ k_row_real(int rows, const int *__restrict__ ptr, const float *__restrict__ val,
     cnt[r] = e - b;
 }
 
-// slen[s] = longest row of slice s; w[s] = 32 slen[s] (the slice's stored entries).
+// slen[s] = longest row of slice s rounded up to a multiple of kSellChunk; w[s] = 32 slen[s]
+// (the slice's stored entries).
 __global__ void __launch_bounds__(256)
 k_slice_len(int n_sl, int rows, int width, const int *__restrict__ cnt, int *__restrict__ slen,
             int *__restrict__ w)
@@ -482,6 +466,7 @@ k_slice_len(int n_sl, int rows, int width, const int *__restrict__ cnt, int *__r
         const int r = sell_row(sl, l, rows, width);
         if (r >= 0) m = max(m, cnt[r]);
     }
+    m = (m + kSellChunk - 1) / kSellChunk * kSellChunk;
     slen[sl] = m;
     w[sl] = 32 * m;
 }
@@ -502,8 +487,9 @@ k_fill_sell(int n_sl, int rows, int width, const int *__restrict__ ptr, const in
     const int b = (r >= 0) ? ptr[r] : 0;
     const int last = n > 0 ? col[b + n - 1] : 0;
     for (int j = 0; j < len; ++j) {
-        scol[base + 32 * j + l] = (j < n) ? col[b + j] : last;
-        sval[base + 32 * j + l] = (j < n) ? val[b + j] : 0.0f;
+        const int idx = base + sell_index(j, l);
+        scol[idx] = (j < n) ? col[b + j] : last;
+        sval[idx] = (j < n) ? val[b + j] : 0.0f;
     }
 }
 

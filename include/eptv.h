@@ -68,6 +68,8 @@ extern "C" {
 #define EPTV_OPERATOR_STORED     1   /* P, P^T stored as CSR matrices in device memory         */
 #define EPTV_OPERATOR_EQ11       2   /* P on the fly, P^T = the interpolating back projector of
                                         Eq. (11) (an approximation of the transpose)           */
+#define EPTV_OPERATOR_STORED_PT  3   /* P on the fly, P^T from the stored matrix (the same
+                                        canonical entries: still the exact transpose)          */
 
 /* Scan geometry (Sec. 3: fan beam, arc detector). */
 typedef struct {
@@ -332,6 +334,9 @@ int eptv_quality_metrics(const eptv_geometry *g, const float *d_f, const float *
  * nonzero of P for both matrices in both forms: CSR for export, SELL-32 for the SpMV);
  * EPTV_OPERATOR_ON_THE_FLY switches back and keeps them.
  * *h_nnz_opt (may be NULL) receives the stored entries of P, padding included.
+ * EPTV_OPERATOR_STORED_PT builds the same matrices but applies only P^T from them (P stays
+ * on the fly): each operator from whichever form is faster on this hardware for small
+ * problems -- the entries are identical, so the pair is still an exact transpose pair.
  * EPTV_OPERATOR_EQ11 keeps P on the fly and makes every P^T the back projector of
  * Eq. (11) (eptv_backproject_eq11); the solver then iterates with an approximate adjoint,
  * as the paper's GPU code did.

@@ -61,7 +61,7 @@ struct DevMem {
 
 struct GraphCache {
     cudaGraphExec_t exec = nullptr;
-    int key[9] = {-1, -1, -1, -1, -1, -1, -1, -1, -1};
+    int key[10] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1};
     long long kernels = 0;     // kernel nodes in the captured outer iteration
     void reset() {
         if (exec) cudaGraphExecDestroy(exec);
@@ -238,7 +238,7 @@ static void op_project(const Batch &B, const ProjArgs &a, cudaStream_t st) {
     else launch_project(B, a, st);
 }
 static void op_backproject(const Batch &B, const BackArgs &a, cudaStream_t st) {
-    if (B.stored) launch_spmv_pt(B, a, st);
+    if (B.stored || B.stored_pt) launch_spmv_pt(B, a, st);
     else launch_backproject(B, a, st);
 }
 
@@ -289,8 +289,8 @@ static void enqueue_outer(const Batch &B, const eptv_params *p, cudaStream_t st)
 
 // Capture one outer iteration of batch B into a graph (cached per structural key).
 static int outer_graph(const Batch &B, GraphCache &gc, cudaStream_t cap, const eptv_params *p) {
-    const int key[9] = {p->cgls_iters, p->n_gd, n_trials_of(p), p->step_rule, B.n, B.k1_seg, B.k2_vg,
-                        B.stored, B.bp_eq11};
+    const int key[10] = {p->cgls_iters, p->n_gd, n_trials_of(p), p->step_rule, B.n, B.k1_seg, B.k2_vg,
+                         B.stored, B.bp_eq11, B.stored_pt};
     if (gc.exec && memcmp(key, gc.key, sizeof key) == 0) return 0;
     gc.reset();
     cudaGraph_t graph = nullptr;
@@ -382,6 +382,7 @@ static int acquire_batch(int n, eptv_geometry *const *geoms, BatchCache &bc) {
     int rc = build_batch(bc.B, bc.mem, sds);
     if (rc) { bc.reset(); return rc; }
     bc.B.stored = modes[0] == EPTV_OPERATOR_STORED;
+    bc.B.stored_pt = modes[0] == EPTV_OPERATOR_STORED_PT;
     bc.B.bp_eq11 = modes[0] == EPTV_OPERATOR_EQ11;
     bc.members = members;
     bc.modes = modes;
@@ -988,10 +989,12 @@ static cudaError_t stored_alloc(void *ctx, void **p, size_t bytes) {
 
 int eptv_set_operator(eptv_geometry *g, int mode, long long *h_nnz_opt) {
     if (!g) return fail(EPTV_ERR_ARG, "NULL handle");
-    if (mode != EPTV_OPERATOR_ON_THE_FLY && mode != EPTV_OPERATOR_STORED && mode != EPTV_OPERATOR_EQ11)
+    if (mode != EPTV_OPERATOR_ON_THE_FLY && mode != EPTV_OPERATOR_STORED && mode != EPTV_OPERATOR_EQ11 &&
+        mode != EPTV_OPERATOR_STORED_PT)
         return fail(EPTV_ERR_ARG, "unknown operator mode %d", mode);
     CU(cudaDeviceSynchronize());
-    if (mode == EPTV_OPERATOR_STORED && !g->stored.p_ptr) {
+    const bool need = mode == EPTV_OPERATOR_STORED || mode == EPTV_OPERATOR_STORED_PT;
+    if (need && !g->stored.p_ptr) {
         StoredMatrices m;
         cudaError_t e = build_stored(g->sd, g->B.d_sd, stored_alloc, &g->stored_mem, &m, nullptr);
         if (e != cudaSuccess) {
@@ -1011,13 +1014,14 @@ int eptv_set_operator(eptv_geometry *g, int mode, long long *h_nnz_opt) {
         sd->p_slen = on ? g->stored.p_slen : nullptr;
         sd->p_scol = on ? g->stored.p_scol : nullptr;
         sd->p_sval = on ? g->stored.p_sval : nullptr;
-        sd->pt_sptr = on ? g->stored.pt_sptr : nullptr;
-        sd->pt_slen = on ? g->stored.pt_slen : nullptr;
-        sd->pt_scol = on ? g->stored.pt_scol : nullptr;
-        sd->pt_sval = on ? g->stored.pt_sval : nullptr;
+        sd->pt_sptr = need ? g->stored.pt_sptr : nullptr;
+        sd->pt_slen = need ? g->stored.pt_slen : nullptr;
+        sd->pt_scol = need ? g->stored.pt_scol : nullptr;
+        sd->pt_sval = need ? g->stored.pt_sval : nullptr;
     }
     CU(cudaMemcpy(g->B.d_sd, g->B.h_sd.data(), sizeof(SliceDev), cudaMemcpyHostToDevice));
     g->B.stored = on ? 1 : 0;
+    g->B.stored_pt = mode == EPTV_OPERATOR_STORED_PT ? 1 : 0;
     g->B.bp_eq11 = mode == EPTV_OPERATOR_EQ11 ? 1 : 0;
     g->op_mode = mode;
     g->graph.reset();

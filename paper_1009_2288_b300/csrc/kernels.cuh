@@ -72,6 +72,7 @@ struct Batch {
     int k1_seg = 8;        // projector: warps (row segments) per 32-ray block (4, 8, 16)
     int k2_vg = 4;         // back projector: view groups per 4-pixel strip (1, 2, 4, 8)
     int stored = 0;        // 1: P and P^T are applied from the stored matrices (stored.cu)
+    int stored_pt = 0;     // 1: only P^T is applied from the stored matrix (P on the fly)
     int bp_eq11 = 0;       // 1: P^T is the interpolating back projector of Eq. (11)
     TileMap map(int fam) const { return TileMap{d_start + fam * (n + 1), n}; }
     int blocks(int fam) const { return h_start[fam * (n + 1) + n]; }

@@ -370,7 +370,7 @@ def eptv_get_log(geom: Geometry):
     return steps.reshape(no.value, ng.value), sig
 
 
-OPERATOR_ON_THE_FLY, OPERATOR_STORED, OPERATOR_EQ11 = 0, 1, 2
+OPERATOR_ON_THE_FLY, OPERATOR_STORED, OPERATOR_EQ11, OPERATOR_STORED_PT = 0, 1, 2, 3
 
 
 def eptv_backproject_eq11(geom: Geometry, y, f, stream=None):

@@ -309,62 +309,6 @@ __device__ __forceinline__ void acc_read(unsigned long long *acc, double *res) {
     }
 }
 
-// Adds the FP32 value x exactly into a fixed-point accumulator in shared memory (the layout
-// of acc_add; 64-bit shared atomics).  A float is m 2^(sh + kAccLsbExp) with a 24-bit m and
-// 0 <= sh <= 253, so it spans at most two 32-bit chunks and never leaves the accumulator.
-__device__ __forceinline__ void acc_add_f32_shared(unsigned long long *acc, float x) {
-    const unsigned int b = __float_as_uint(x);
-    const bool neg = (b >> 31) != 0;
-    const int ex = (int)((b >> 23) & 0xFFu);
-    unsigned int m = b & 0x7FFFFFu;
-    if (ex == 0xFF) {
-        atomicOr(acc + kAccChunks, m ? kAccNaN : (neg ? kAccNegInf : kAccPosInf));
-        return;
-    }
-    if (ex) m |= 0x800000u;
-    if (m == 0u) return;
-    const int sh = (ex ? ex : 1) - 150 - kAccLsbExp;       // |x| = m 2^(sh + kAccLsbExp)
-    const int c = sh >> 5, r = sh & 31;
-    const unsigned long long w = (unsigned long long)m << r;   // < 2^55: two chunks
-    const unsigned long long d0 = w & 0xFFFFFFFFull, d1 = w >> 32;
-    if (d0) atomicAdd(acc + c, neg ? (0ull - d0) : d0);
-    if (d1) atomicAdd(acc + c + 1, neg ? (0ull - d1) : d1);
-}
-
-// Exact, FP64-free reduction of NV FP32 values over the nblk blocks of a slice (lb = the
-// calling block's index within the slice), with the block-level step in integers: each
-// warp's FP32 sum (shuffles) is added exactly into a per-block fixed-point accumulator in
-// shared memory, and the block adds that accumulator's non-zero words into copy
-// lb mod kAccCopies of the slice's accumulators.  The total is the correctly rounded sum
-// of all warp sums, independent of block order.  Returns true only in the block that
-// finishes last, with the totals in res.  s_acc: NV * kAccStride words of shared memory.
-template <int NV, int NT>
-__device__ __forceinline__ bool reduce_slice_f32(const SliceDev &S, const float (&v)[NV], int nblk, int lb,
-                                                 unsigned long long *s_acc, double *res, int *flag) {
-    for (int i = threadIdx.x; i < NV * kAccStride; i += NT) s_acc[i] = 0ull;
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-        const float w = warp_sum(v[k]);
-        if (lane == 0) acc_add_f32_shared(s_acc + k * kAccStride, w);
-    }
-    __syncthreads();
-    const int copy = lb % kAccCopies;
-    for (int i = threadIdx.x; i < NV * kAccStride; i += NT) {
-        const unsigned long long word = s_acc[i];
-        if (word == 0ull) continue;
-        const int k = i / kAccStride, wi = i - k * kAccStride;
-        unsigned long long *g = S.acc + ((size_t)k * kAccCopies + copy) * kAccStride + wi;
-        if (wi == kAccChunks) atomicOr(g, word);
-        else atomicAdd(g, word);
-    }
-    if (!last_block_of_slice(S.ctr, nblk, flag)) return false;
-    acc_read<NV, NT>(S.acc, res);
-    __syncthreads();
-    return true;
-}
-
 // Deterministic reduction of the NV per-block partial sums that the nblk blocks of a slice
 // wrote to partials[b0 + lb][0 .. NV) (row stride `stride`), lb = the calling block's index
 // within the slice: every block adds its row into the slice's exact accumulators, and the

@@ -277,27 +277,6 @@ k32_backproject(Cone C, const float *__restrict__ y, float *__restrict__ out, do
 
 // ------------------------------------------------------------------ CGLS vectors
 
-// sum of x^2 (and of x) over n values -> finalize(fin)
-__global__ void __launch_bounds__(256)
-k3v_norm2(const float *__restrict__ x, long long n, double *__restrict__ partials, SliceDev *S, int fin)
-{
-    const double gamma_pre = threadIdx.x == 0 ? fin_gamma(S->sc, fin) : 0.0;
-    __shared__ double rsm[2 * 8];
-    __shared__ double res[2];
-    __shared__ int last_flag;
-    float s2 = 0.0f, s1 = 0.0f;
-    const long long i0 = (long long)blockIdx.x * 1024 + threadIdx.x;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const long long i = i0 + q * 256;
-        if (i < n) { const float v = __ldg(x + i); s2 = fmaf(v, v, s2); s1 += v; }
-    }
-    float vals[2] = {s2, s1};
-    block_sum_to<2, 256>(vals, partials + (size_t)blockIdx.x * 2, rsm);
-    if (!reduce_slice<2, 256>(*S, partials, 2, 0, gridDim.x, blockIdx.x, rsm, res, &last_flag)) return;
-    if (threadIdx.x == 0) finalize(S->sc, fin, res[0], res[1], gamma_pre);
-}
-
 // y += sign * sc[which] * x
 __global__ void __launch_bounds__(256)
 k3v_axpy(float *__restrict__ y, const float *__restrict__ x, long long n, const double *__restrict__ sc,
@@ -337,50 +316,94 @@ __device__ __forceinline__ float vol_at(const float *f, const Vol &V, int i, int
     return __ldg(f + ((long long)k * V.ny + j) * V.nx + i);
 }
 
-// decode face index -> family d, position (i, j, k)
-__device__ __forceinline__ int face_pos(const Vol &V, long long e, int &i, int &j, int &k) {
-    int d;
-    long long r;
-    int wx, wy;
-    if (e < V.nfx) { d = 0; r = e; wx = V.nx + 1; wy = V.ny; }
-    else if (e < V.nfx + V.nfy) { d = 1; r = e - V.nfx; wx = V.nx; wy = V.ny + 1; }
-    else { d = 2; r = e - V.nfx - V.nfy; wx = V.nx; wy = V.ny; }
-    i = (int)(r % wx);
-    j = (int)((r / wx) % wy);
-    k = (int)(r / ((long long)wx * wy));
+// decode face index -> family d, position (i, j, k); 32-bit arithmetic (the handle
+// guarantees fewer than 2^31 faces), two integer divisions
+__device__ __forceinline__ int face_pos(const Vol &V, long long e64, int &i, int &j, int &k) {
+    const int e = (int)e64, nfx = (int)V.nfx, nfy = (int)V.nfy;
+    int d, r, wx, wy;
+    if (e < nfx) { d = 0; r = e; wx = V.nx + 1; wy = V.ny; }
+    else if (e < nfx + nfy) { d = 1; r = e - nfx; wx = V.nx; wy = V.ny + 1; }
+    else { d = 2; r = e - nfx - nfy; wx = V.nx; wy = V.ny; }
+    const int q = r / wx;
+    i = r - q * wx;
+    k = q / wy;
+    j = q - k * wy;
     return d;
+}
+
+// Voxel value of x at (i, j, k): bounds-checked (0 outside the volume), or, for a face
+// whose whole stencil lies inside the volume, a plain load at linear index lin.
+template <bool CHECK>
+__device__ __forceinline__ float ld_vox(const float *x, const Vol &V, int i, int j, int k, int lin) {
+    if (CHECK) return vol_at(x, V, i, j, k);
+    return __ldg(x + lin);
 }
 
 // D, and the transverse parts of T^2 (A3 extended) of a face, from image x; also the
 // bilinear quantities of the Armijo decomposition when a second image g is given:
-// a = D dD + 1/2 sum c dc, b = dD^2 + 1/2 sum dc^2.
-__device__ __forceinline__ void face_terms(const float *x, const float *gx, const Vol &V, int d, int i, int j,
-                                           int k, float eps2, float &D, float &T2, float &ae, float &be) {
+// a = D dD + 1/2 sum c dc, b = dD^2 + 1/2 sum dc^2.  CHECK = false: the face and its
+// transverse neighbours are inside the volume (the same values and operations, without
+// the bounds tests).
+template <bool CHECK>
+__device__ __forceinline__ void face_terms_t(const float *x, const float *gx, const Vol &V, int d, int i, int j,
+                                             int k, float eps2, float &D, float &T2, float &ae, float &be) {
     const int ai = i - (d == 0), aj = j - (d == 1), ak = k - (d == 2);
-    const float xa = vol_at(x, V, ai, aj, ak), xb = vol_at(x, V, i, j, k);
+    const int st[3] = {1, V.nx, V.nx * V.ny};
+    int lb = 0, la = 0;
+    if (!CHECK) {
+        lb = (k * V.ny + j) * V.nx + i;
+        la = lb - st[d];
+    }
+    const float xa = ld_vox<CHECK>(x, V, ai, aj, ak, la), xb = ld_vox<CHECK>(x, V, i, j, k, lb);
     D = xb - xa;
     T2 = eps2 + D * D;
     float ga = 0.f, gb = 0.f, dD = 0.f;
-    if (gx) { ga = vol_at(gx, V, ai, aj, ak); gb = vol_at(gx, V, i, j, k); dD = gb - ga; }
+    if (gx) { ga = ld_vox<CHECK>(gx, V, ai, aj, ak, la); gb = ld_vox<CHECK>(gx, V, i, j, k, lb); dD = gb - ga; }
     ae = D * dD;
     be = dD * dD;
     const float mc = 0.5f * (xa + xb), gc = 0.5f * (ga + gb);
 #pragma unroll
     for (int t = 0; t < 3; ++t) {
         if (t == d) continue;
-        const int ei = (t == 0), ej = (t == 1), ek = (t == 2);
-        const float mp = 0.5f * (vol_at(x, V, ai + ei, aj + ej, ak + ek) + vol_at(x, V, i + ei, j + ej, k + ek));
-        const float mm = 0.5f * (vol_at(x, V, ai - ei, aj - ej, ak - ek) + vol_at(x, V, i - ei, j - ej, k - ek));
+        const int ei = (t == 0), ej = (t == 1), ek = (t == 2), s = st[t];
+        const float mp = 0.5f * (ld_vox<CHECK>(x, V, ai + ei, aj + ej, ak + ek, la + s) +
+                                 ld_vox<CHECK>(x, V, i + ei, j + ej, k + ek, lb + s));
+        const float mm = 0.5f * (ld_vox<CHECK>(x, V, ai - ei, aj - ej, ak - ek, la - s) +
+                                 ld_vox<CHECK>(x, V, i - ei, j - ej, k - ek, lb - s));
         const float cp = mp - mc, cm = mc - mm;
         T2 += 0.5f * cp * cp + 0.5f * cm * cm;
         if (gx) {
-            const float gp = 0.5f * (vol_at(gx, V, ai + ei, aj + ej, ak + ek) + vol_at(gx, V, i + ei, j + ej, k + ek));
-            const float gm = 0.5f * (vol_at(gx, V, ai - ei, aj - ej, ak - ek) + vol_at(gx, V, i - ei, j - ej, k - ek));
+            const float gp = 0.5f * (ld_vox<CHECK>(gx, V, ai + ei, aj + ej, ak + ek, la + s) +
+                                     ld_vox<CHECK>(gx, V, i + ei, j + ej, k + ek, lb + s));
+            const float gm = 0.5f * (ld_vox<CHECK>(gx, V, ai - ei, aj - ej, ak - ek, la - s) +
+                                     ld_vox<CHECK>(gx, V, i - ei, j - ej, k - ek, lb - s));
             const float dcp = gp - gc, dcm = gc - gm;
             ae += 0.5f * (cp * dcp + cm * dcm);
             be += 0.5f * (dcp * dcp + dcm * dcm);
         }
     }
+}
+
+__device__ __forceinline__ void face_terms(const float *x, const float *gx, const Vol &V, int d, int i, int j,
+                                           int k, float eps2, float &D, float &T2, float &ae, float &be) {
+    // interior: both voxels of the face inside, and one more voxel on each transverse side
+    const int c[3] = {i, j, k}, n[3] = {V.nx, V.ny, V.nz};
+    bool inner = true;
+#pragma unroll
+    for (int t = 0; t < 3; ++t)
+        inner = inner && c[t] >= 1 && c[t] <= n[t] - (t == d ? 1 : 2);
+    if (inner) face_terms_t<false>(x, gx, V, d, i, j, k, eps2, D, T2, ae, be);
+    else face_terms_t<true>(x, gx, V, d, i, j, k, eps2, D, T2, ae, be);
+}
+
+// compensated (Kahan) running sum of one thread's terms: the grid-stride kernels below
+// give each thread a few hundred faces, and the compensation keeps the thread's sum
+// within a few units in the last place, as a single FP32 term was before
+__device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
 }
 
 // T of every face of x (for sigma)
@@ -404,11 +427,11 @@ k3tv_faces(Vol V, const float *__restrict__ f, float eps2, int mode, float *__re
     __shared__ double rsm[1 * 8];
     __shared__ double res[1];
     __shared__ int last_flag;
-    const long long e = (long long)blockIdx.x * 256 + threadIdx.x;
     const float sig = (float)S->sc[SC_SIGMA];
     const float inv_s2 = 1.0f / (sig * sig);
-    float wt = 0.0f;
-    if (e < V.nf) {
+    float wt = 0.0f, wc = 0.0f;
+    // grid-stride: a few blocks per SM, so that the block reductions stay few
+    for (long long e = (long long)blockIdx.x * 256 + threadIdx.x; e < V.nf; e += (long long)gridDim.x * 256) {
         int i, j, k;
         const int d = face_pos(V, e, i, j, k);
         float D, T2, ae, be;
@@ -419,9 +442,9 @@ k3tv_faces(Vol V, const float *__restrict__ f, float eps2, int mode, float *__re
         Q[e] = w * D * rs;
         TT[e] = T;
         WW[e] = w;
-        wt = w * T;
+        kahan_add(wt, wc, w * T);
     }
-    float vals[1] = {wt};
+    float vals[1] = {wt - wc};
     block_sum_to<1, 256>(vals, partials + (size_t)blockIdx.x * kPartialStride, rsm);
     if (!reduce_slice<1, 256>(*S, partials, kPartialStride, 0, gridDim.x, blockIdx.x, rsm, res, &last_flag)) return;
     if (threadIdx.x == 0) S->sc[SC_Q0] = res[0];                   // J
@@ -435,11 +458,11 @@ k3tv_grad(Vol V, const float *__restrict__ f, const float *__restrict__ v, const
     __shared__ double rsm[3 * 8];
     __shared__ double res[3];
     __shared__ int last_flag;
-    const long long p = (long long)blockIdx.x * 256 + threadIdx.x;
-    float A = 0.f, B = 0.f, F = 0.f;
+    float A = 0.f, B = 0.f, F = 0.f, cA = 0.f, cB = 0.f, cF = 0.f;
     const long long nvox = (long long)V.nx * V.ny * V.nz;
-    if (p < nvox) {
-        const int i = (int)(p % V.nx), j = (int)((p / V.nx) % V.ny), k = (int)(p / ((long long)V.nx * V.ny));
+    for (long long p = (long long)blockIdx.x * 256 + threadIdx.x; p < nvox; p += (long long)gridDim.x * 256) {
+        const int pi = (int)p, q = pi / V.nx;          // n_vox < 2^31
+        const int i = pi - q * V.nx, k = q / V.ny, j = q - k * V.ny;
         const float *Qx = Q, *Qy = Q + V.nfx, *Qz = Q + V.nfx + V.nfy;
         const long long ex = ((long long)k * V.ny + j) * (V.nx + 1) + i;
         const long long ey = ((long long)k * (V.ny + 1) + j) * V.nx + i;
@@ -449,11 +472,11 @@ k3tv_grad(Vol V, const float *__restrict__ f, const float *__restrict__ v, const
         const float d = __ldg(f + p) - __ldg(v + p);
         const float gv = lam * d - div;
         g[p] = gv;
-        A = gv * d;
-        B = gv * gv;
-        F = d * d;
+        kahan_add(A, cA, gv * d);
+        kahan_add(B, cB, gv * gv);
+        kahan_add(F, cF, d * d);
     }
-    float vals[3] = {A, B, F};
+    float vals[3] = {A - cA, B - cB, F - cF};
     block_sum_to<3, 256>(vals, partials + (size_t)blockIdx.x * kPartialStride, rsm);
     if (!reduce_slice<3, 256>(*S, partials, kPartialStride, 0, gridDim.x, blockIdx.x, rsm, res, &last_flag)) return;
     if (threadIdx.x < 3) S->sc[SC_Q0 + 1 + threadIdx.x] = res[threadIdx.x];   // A, B, F
@@ -484,11 +507,11 @@ k3tv_trials(Vol V, const float *__restrict__ f, const float *__restrict__ g, con
     }
     __syncthreads();
     const float eps2 = (float)(P->eps * P->eps);
-    const long long e = (long long)blockIdx.x * 256 + threadIdx.x;
-    float dJ[KT];
+    float dJ[KT], cJ[KT];
 #pragma unroll
-    for (int m = 0; m < KT; ++m) dJ[m] = 0.0f;
-    if (e < V.nf && K > 0) {
+    for (int m = 0; m < KT; ++m) dJ[m] = cJ[m] = 0.0f;
+    for (long long e = (long long)blockIdx.x * 256 + threadIdx.x; K > 0 && e < V.nf;
+         e += (long long)gridDim.x * 256) {
         int i, j, k;
         const int d = face_pos(V, e, i, j, k);
         float D, T2x, ae, be;
@@ -502,10 +525,12 @@ k3tv_trials(Vol V, const float *__restrict__ f, const float *__restrict__ g, con
                 const float num = t * fmaf(t, be, -2.0f * ae);
                 const float T2n = fmaxf(T2 + num, eps2);
                 const float Tn = T2n * rsqrtf(T2n);
-                dJ[m] = w * __fdividef(num, Tn + T);
+                kahan_add(dJ[m], cJ[m], w * __fdividef(num, Tn + T));
             }
         }
     }
+#pragma unroll
+    for (int m = 0; m < KT; ++m) dJ[m] -= cJ[m];
     block_sum_to<KT, 256>(dJ, partials + (size_t)blockIdx.x * kPartialStride, rsm);
     if (!reduce_slice<KT, 256>(*S, partials, kPartialStride, 0, gridDim.x, blockIdx.x, rsm, tot, &last_flag))
         return;
@@ -586,6 +611,7 @@ __global__ void __launch_bounds__(256) k3_clamp(float *__restrict__ x, long long
 // ------------------------------------------------------------------ host side
 
 static unsigned nblk_of(long long n, int per) { return (unsigned)((n + per - 1) / per); }
+static unsigned nblk_capped(long long n, int per, unsigned cap) { return std::max(1u, std::min(nblk_of(n, per), cap)); }
 
 }  // namespace eptv
 
@@ -597,6 +623,7 @@ struct eptv3_geometry {
     Cone C;
     Vol V;
     int k31_seg = 8;
+    unsigned red_blocks = 592;    // grid of the grid-stride reducing kernels: 4 blocks per SM
     RayRec3 *ray = nullptr;
     ViewRec3 *view = nullptr;
     float *u = nullptr, *s = nullptr, *t = nullptr, *fa = nullptr, *fb = nullptr, *g = nullptr;
@@ -687,9 +714,9 @@ static int c3_p2(const eptv3_geometry *g, const eptv_params *p, const float *v, 
     for (int n = 0; n < p->n_gd; ++n) {
         float *nxt = (n == p->n_gd - 1) ? out : ((cur == g->fb) ? g->u : g->fb);
         if (nxt == v) nxt = g->fb;
-        k3tv_faces<<<nblk_of(V.nf, 256), 256, 0, st>>>(V, cur, eps2, mode, g->Q, g->TT, g->WW, g->partials, g->d_sd);
-        k3tv_grad<<<nblk_of(nv, 256), 256, 0, st>>>(V, cur, v, g->Q, (float)p->lambda, g->g, g->partials, g->d_sd);
-        const unsigned nbf = nblk_of(V.nf, 256);
+        k3tv_faces<<<nblk_capped(V.nf, 256, g->red_blocks), 256, 0, st>>>(V, cur, eps2, mode, g->Q, g->TT, g->WW, g->partials, g->d_sd);
+        k3tv_grad<<<nblk_capped(nv, 256, g->red_blocks), 256, 0, st>>>(V, cur, v, g->Q, (float)p->lambda, g->g, g->partials, g->d_sd);
+        const unsigned nbf = nblk_capped(V.nf, 256, g->red_blocks);
         if (K <= 1) k3tv_trials<1><<<nbf, 256, 0, st>>>(V, cur, g->g, g->TT, g->WW, g->d_params, K, n == 0, 0, g->partials, g->d_sd);
         else if (K <= 4) k3tv_trials<4><<<nbf, 256, 0, st>>>(V, cur, g->g, g->TT, g->WW, g->d_params, K, n == 0, 0, g->partials, g->d_sd);
         else if (K <= 8) k3tv_trials<8><<<nbf, 256, 0, st>>>(V, cur, g->g, g->TT, g->WW, g->d_params, K, n == 0, 0, g->partials, g->d_sd);
@@ -779,6 +806,18 @@ int eptv3_create_geometry(const eptv3_geometry_desc *d, eptv3_geometry **out) {
     V.nfy = (long long)d->nx * (d->ny + 1) * d->nz;
     V.nfz = (long long)d->nx * d->ny * (d->nz + 1);
     V.nf = V.nfx + V.nfy + V.nfz;
+    if (V.nf > (1LL << 31) - 1) {
+        delete g;
+        return c3_fail(EPTV_ERR_ARG, "volume too large: 2^31 or more faces");
+    }
+    // grid of the grid-stride reducing kernels: 4 resident 256-thread blocks of 64 registers per SM
+    {
+        int dev = 0, n_sm = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n_sm > 0)
+            g->red_blocks = 4u * (unsigned)n_sm;
+        cudaGetLastError();
+    }
     // workspace
     const long long blk_k31 = (long long)d->n_views * d->nv * ((d->nu + 31) / 32);
     const long long blk_face = (V.nf + 255) / 256, blk_vox = (n_vox + 255) / 256;
@@ -928,7 +967,7 @@ int eptv3_report_energy(const eptv3_geometry *g, const eptv_params *p, double si
     c3_project(g, d_f, d_y, g->q, FIN_NORM, st);                         // |y - P f|^2 -> SC_NORM
     k3_set_scalar<<<1, 1, 0, st>>>(g->d_sd, SC_SIGMA, sigma_ref);
     const int mode = p->weights_mode == EPTV_WEIGHTS_ONE ? EPTV_WEIGHTS_ONE : EPTV_WEIGHTS_EPTV;
-    k3tv_faces<<<nblk_of(g->V.nf, 256), 256, 0, st>>>(g->V, d_f, (float)(p->eps * p->eps), mode, g->Q, g->TT,
+    k3tv_faces<<<nblk_capped(g->V.nf, 256, g->red_blocks), 256, 0, st>>>(g->V, d_f, (float)(p->eps * p->eps), mode, g->Q, g->TT,
                                                        g->WW, g->partials, g->d_sd);
     C3CU(cudaGetLastError());
     double sc[kScalarStride];

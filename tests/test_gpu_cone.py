@@ -192,3 +192,23 @@ def test_full_size_sampled_rays_and_exact_transpose():
         tol = 16 * 2.0 ** -24 * R
         assert np.max(np.abs(bb[vox] - ln)) <= tol, idx
         assert np.max(np.abs(bb[nz] - dense[nz])) <= tol, idx
+
+
+@pytest.mark.parametrize("rule", [O.FIXED, O.ARMIJO])
+def test_tv_step_several_faces_per_thread(rule):
+    """64^3 (798,720 faces, 262,144 voxels): the face and voxel kernels loop over several
+    elements per thread on a grid of a few blocks per SM, so each thread's partial sums
+    of the energy, the gradient products and the Armijo trials cover many terms."""
+    g = I.c5_geometry(4)
+    geo = E.Geometry3(g)
+    rng = np.random.Generator(np.random.PCG64(11))
+    v = blobs(g, 6) + 0.002 * rng.standard_normal((g.nz, g.ny, g.nx))
+    p = I.EptvParams(n_gd=5, step_rule=rule, t_fixed=2e-4)
+    want, st = C.p2_solve(v, p, p.t_init_eff)
+    want = np.maximum(want, 0.0)
+    f = torch.empty(g.n_vox, device=DEV)
+    stats, t_prev = E.eptv3_tv_step(geo, p, t32(v), f)
+    assert stats.sigma == pytest.approx(st.sigma, rel=2e-3)
+    assert rel(np64(f).reshape(want.shape), want) < 1e-4
+    if rule == O.ARMIJO:
+        assert t_prev == pytest.approx(st.t_prev, rel=1e-6)

@@ -273,8 +273,12 @@ typedef struct {
 
 typedef struct eptv3_geometry eptv3_geometry;
 
-/* Builds the ray table (24 bytes per ray) and the solver workspace (about 9 volumes of
- * faces, 6 volumes, 3 projections).  EPTV_ERR_ARG, EPTV_ERR_NOMEM, EPTV_ERR_CUDA. */
+/* Builds the ray tables (host FP64, stored FP32: 16 bytes per view and detector column,
+ * 8 per detector row, 4 per detector pixel; rays are parametrised by their depth along the
+ * central ray, so that P = diag(F) L' with F = |a| per detector pixel) and the solver
+ * workspace (about 9 volumes of faces, 6 volumes, 4 projections).  EPTV_ERR_ARG (also for
+ * more than 65535 views or a cone too wide for the narrow-cone march), EPTV_ERR_NOMEM,
+ * EPTV_ERR_CUDA. */
 int eptv3_create_geometry(const eptv3_geometry_desc *desc, eptv3_geometry **out);
 void eptv3_destroy_geometry(eptv3_geometry *g);
 /* Warps per 32-ray block of the 3-D projector (4, 8 or 16). */

@@ -1,15 +1,21 @@
 // 3-D cone-beam EPTV (the paper's method, which is 2-D, extended to a circular cone-beam
 // scan with a flat detector; see eptv.h for the conventions).  Same algorithm as the 2-D
 // path (Sec. 2.2: CGLS for (P1), GD with Armijo for (P2), clamp), with
+// Rays are parametrised by their depth along the central ray, counted from the plane
+// through the rotation axis (D' = D - sid).  The x and y plane crossings of a ray then
+// depend only on its view and detector column, the z plane crossings only on its detector
+// row, and its length through a voxel is F * (D' interval) with F = |a| = sqrt(1 + (u^2 +
+// w^2) / sdd^2) per detector pixel: P = diag(F) L', and both kernels below compute the
+// entries of L' with the same canonical formula from the same tables.
 //   K31  P:   ray-driven Siddon in 3-D.  A warp holds 32 adjacent detector columns of one
 //             detector row; the warps of a block split the ray's range along its major
 //             axis (x or y).  In each major-axis slab the ray walks the cells of the two
 //             minor axes incrementally, so every voxel it crosses gets the canonical
 //             length min(exit planes) - max(entry planes) of eptv_internal.cuh.
-//   K32  P^T: voxel-driven gather, the exact transpose: a thread owns two voxels stacked
-//             in z; per view, their corners bound the detector pixels whose rays can
-//             cross them, and each such ray's length through each voxel is the same
-//             canonical formula.
+//   K32  P^T: voxel-driven gather, the exact transpose L'^T diag(F): a thread owns two
+//             voxels stacked in z; per view, their corners bound the detector columns
+//             whose rays can cross them, each column's x-y chord through the pair bounds
+//             its rows, and each such ray's L' entry is the same canonical formula.
 //   (P2) half-face kernels (the 2-D half-edges extended to faces, Eqs. 5, 9, A2, A3 in
 //             3-D), a gradient kernel, one kernel that evaluates all Armijo trial steps,
 //             and the step/clamp kernel; every reduction is the exact, order-independent
@@ -27,18 +33,25 @@
 
 namespace eptv {
 
-// Records padded to 32 bytes and 16-byte aligned, so that one is two 128-bit loads (six
-// separate 32-bit loads at their natural size and alignment).
-struct __align__(16) RayRec3 { float px, py, pz, ix, iy, iz, pad0, pad1; };   // closest point, 1/d
+// Per (view, column): the x, y of the ray's point at depth sid (D' = 0) and 1 / a_x,
+// 1 / a_y, a = (central direction) + (u / sdd) e_u + (w / sdd) e_z the ray's direction per
+// unit depth (a_x, a_y do not depend on w).  One 128-bit load.
+struct __align__(16) ColRec3 { float qx, qy, ix, iy; };
+// Per detector row: the z of the point at depth sid (w sid / sdd) and 1 / a_z = sdd / w.
+struct __align__(8) RowRec3 { float qz, iz; };
+// Records padded to 32 bytes and 16-byte aligned, so that one is two 128-bit loads.
 struct __align__(16) ViewRec3 { float sx, sy, cx, cy, ux, uy, pad0, pad1; };  // source, central dir, e_u
 
 struct Cone {
     int nx, ny, nz, nv, nu, nrow;                   // nv views, nu x nrow detector
     float dx, dy, dz, x0, y0, z0;
     float du, dw, uc, wc;                           // column index = u / du + uc, row = w / dw + wc
-    float sdd;
+    float inv_du, inv_dw;                           // 1 / du, 1 / dw (candidate bounds only)
+    float sdd, sid;
     long long n_vox, n_rays;
-    const RayRec3 *ray;
+    const ColRec3 *col;                             // [view][column]
+    const RowRec3 *row;                             // [row]
+    const float *fac;                               // F = |a| per detector pixel, [row][column]
     const ViewRec3 *view;
 };
 
@@ -63,10 +76,13 @@ k31_project(Cone C, const float *__restrict__ f, const float *__restrict__ y_res
     const int nub = (C.nu + 31) >> 5;
     const int row_id = blockIdx.x / nub;                  // view * nrow + detector row
     const int iu = (blockIdx.x - row_id * nub) * 32 + lane;
+    const int view = row_id / C.nrow, iv = row_id - view * C.nrow;
     const long long ri = (long long)row_id * C.nu + iu;
     float acc = 0.0f;
     if (iu < C.nu) {
-        const RayRec3 R = C.ray[ri];
+        const ColRec3 Qc = C.col[view * C.nu + iu];
+        const RowRec3 Qr = C.row[iv];
+        struct { float px, py, pz, ix, iy, iz; } R = {Qc.qx, Qc.qy, Qr.qz, Qc.ix, Qc.iy, Qr.iz};
         // major axis M (x or y), minor axes m (the other) and z
         const bool ymaj = fabsf(R.ix) * C.dx >= fabsf(R.iy) * C.dy;
         float PM, iM, M0, dM, Pm, im, m0, dm;
@@ -174,6 +190,7 @@ k31_project(Cone C, const float *__restrict__ f, const float *__restrict__ y_res
         float tot = 0.0f;
 #pragma unroll
         for (int w = 0; w < SEG; ++w) tot += red[w][lane];
+        tot *= __ldg(C.fac + iv * C.nu + iu);              // L' -> P
         const float o = y_resid ? __ldg(y_resid + ri) - tot : tot;
         out[ri] = o;
         sq = o * o;
@@ -188,15 +205,24 @@ k31_project(Cone C, const float *__restrict__ f, const float *__restrict__ y_res
 
 // ------------------------------------------------------------------ K32: back projector
 
+// ys = F * y per ray (the diag(F) of P^T = L'^T diag(F)); grid.y = view
+__global__ void __launch_bounds__(256)
+k32_scale(const float *__restrict__ y, const float *__restrict__ fac, int npix, float *__restrict__ ys)
+{
+    const int i = blockIdx.x * 256 + threadIdx.x;
+    if (i >= npix) return;
+    const long long r = (long long)blockIdx.y * npix + i;
+    ys[r] = __ldg(y + r) * __ldg(fac + i);
+}
+
 // Thread = two voxels stacked in z, (ix, iy, 2 iz2) and (ix, iy, 2 iz2 + 1): a voxel's
-// detector columns do not depend on z, so the pair shares its per-view corner projections
-// and, per candidate ray, the x and y plane parameters (7 instead of 12 for two voxels).
+// detector columns do not depend on z, and a column's x-y chord through the pair (its
+// x and y plane parameters) does not depend on the row, so the pair shares, per view,
+// its corner projections and, per column, the chord; per row only the three z planes.
 constexpr int kZPair = 2;
 
-// 5 blocks per SM (48 registers): the kernel waits on its ray records, and the extra
-// resident warps hide more of that latency than the few spilled registers cost
-__global__ void __launch_bounds__(256, 5)
-k32_backproject(Cone C, const float *__restrict__ y, float *__restrict__ out, double *__restrict__ partials,
+__global__ void __launch_bounds__(256, 4)
+k32_backproject(Cone C, const float *__restrict__ ys, float *__restrict__ out, double *__restrict__ partials,
                 SliceDev *S, int fin)
 {
     const double gamma_pre = threadIdx.x == 0 ? fin_gamma(S->sc, fin) : 0.0;
@@ -220,39 +246,44 @@ k32_backproject(Cone C, const float *__restrict__ y, float *__restrict__ out, do
 #pragma unroll
         for (int q = 0; q <= kZPair; ++q) Z[q] = grid_line((float)(iz0 + q), C.dz, C.z0);
         const float Ze = grid_line((float)(iz0 + nzp), C.dz, C.z0);
+        const long long view_sz = (long long)C.nrow * C.nu;
         for (int v = 0; v < C.nv; ++v) {
             const ViewRec3 V = C.view[v];
-            float umin = 3e38f, umax = -3e38f, wmin = 3e38f, wmax = -3e38f;
+            float umin = 3e38f, umax = -3e38f;
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 const float px = (c & 1) ? X1 : X0, py = (c & 2) ? Y1 : Y0;
                 const float wx = px - V.sx, wy = py - V.sy;
                 const float depth = V.cx * wx + V.cy * wy;            // along the central ray
-                const float sc = __fdividef(C.sdd, depth);
-                const float u = (V.ux * wx + V.uy * wy) * sc;
+                const float u = __fdividef((V.ux * wx + V.uy * wy) * C.sdd, depth);
                 umin = fminf(umin, u); umax = fmaxf(umax, u);
-                const float w0 = Z[0] * sc, w1 = Ze * sc;
-                wmin = fminf(wmin, fminf(w0, w1)); wmax = fmaxf(wmax, fmaxf(w0, w1));
             }
-            const int iu0 = max(0, (int)ceilf(umin / C.du + C.uc - 0.01f));
-            const int iu1 = min(C.nu - 1, (int)floorf(umax / C.du + C.uc + 0.01f));
-            const int iv0 = max(0, (int)ceilf(wmin / C.dw + C.wc - 0.01f));
-            const int iv1 = min(C.nrow - 1, (int)floorf(wmax / C.dw + C.wc + 0.01f));
-            for (int iv = iv0; iv <= iv1; ++iv) {
-                const long long rowbase = ((long long)v * C.nrow + iv) * C.nu;
-                for (int iu = iu0; iu <= iu1; ++iu) {
-                    const RayRec3 R = C.ray[rowbase + iu];
-                    const float ax = cross_t(X0, R.px, R.ix), bx = cross_t(X1, R.px, R.ix);
-                    const float ay = cross_t(Y0, R.py, R.iy), by = cross_t(Y1, R.py, R.iy);
-                    // min / max are exact, so grouping the x and y planes first gives the
-                    // same length as the canonical six-plane formula
-                    const float lo_xy = fmaxf(fminf(ax, bx), fminf(ay, by));
-                    const float hi_xy = fminf(fmaxf(ax, bx), fmaxf(ay, by));
-                    if (!(lo_xy < hi_xy)) continue;
-                    const float yv = __ldg(y + rowbase + iu);
+            const int iu0 = max(0, (int)ceilf(fmaf(umin, C.inv_du, C.uc) - 0.01f));
+            const int iu1 = min(C.nu - 1, (int)floorf(fmaf(umax, C.inv_du, C.uc) + 0.01f));
+            const ColRec3 *colv = C.col + v * C.nu;
+            const float *ysv = ys + v * view_sz;
+            for (int iu = iu0; iu <= iu1; ++iu) {
+                const ColRec3 Q = colv[iu];
+                const float ax = cross_t(X0, Q.qx, Q.ix), bx = cross_t(X1, Q.qx, Q.ix);
+                const float ay = cross_t(Y0, Q.qy, Q.iy), by = cross_t(Y1, Q.qy, Q.iy);
+                // min / max are exact, so grouping the x and y planes first gives the
+                // same length as the canonical six-plane formula
+                const float lo_xy = fmaxf(fminf(ax, bx), fminf(ay, by));
+                const float hi_xy = fminf(fmaxf(ax, bx), fmaxf(ay, by));
+                if (!(lo_xy < hi_xy)) continue;
+                // rows whose rays are inside [Z0, Ze] at some depth of the chord:
+                // w = z sdd / (sid + D'), D' in [lo_xy, hi_xy] (both depths > 0)
+                const float ka = __fdividef(C.sdd, C.sid + lo_xy), kb = __fdividef(C.sdd, C.sid + hi_xy);
+                const float wlo = fminf(Z[0] * ka, Z[0] * kb), whi = fmaxf(Ze * ka, Ze * kb);
+                const int iv0 = max(0, (int)ceilf(fmaf(wlo, C.inv_dw, C.wc) - 0.01f));
+                const int iv1 = min(C.nrow - 1, (int)floorf(fmaf(whi, C.inv_dw, C.wc) + 0.01f));
+                const float *ycol = ysv + iu;
+                for (int iv = iv0; iv <= iv1; ++iv) {
+                    const RowRec3 Rr = C.row[iv];
+                    const float yv = __ldg(ycol + iv * C.nu);
                     float tz[kZPair + 1];
 #pragma unroll
-                    for (int q = 0; q <= kZPair; ++q) tz[q] = cross_t(Z[q], R.pz, R.iz);
+                    for (int q = 0; q <= kZPair; ++q) tz[q] = cross_t(Z[q], Rr.qz, Rr.iz);
 #pragma unroll
                     for (int q = 0; q < kZPair; ++q) {
                         const float l = c3_len(lo_xy, hi_xy, lo_xy, hi_xy, fminf(tz[q], tz[q + 1]),
@@ -624,7 +655,10 @@ struct eptv3_geometry {
     Vol V;
     int k31_seg = 8;
     unsigned red_blocks = 592;    // grid of the grid-stride reducing kernels: 4 blocks per SM
-    RayRec3 *ray = nullptr;
+    ColRec3 *col = nullptr;
+    RowRec3 *row = nullptr;
+    float *fac = nullptr;
+    float *ys = nullptr;                                 // F * y for K32
     ViewRec3 *view = nullptr;
     float *u = nullptr, *s = nullptr, *t = nullptr, *fa = nullptr, *fb = nullptr, *g = nullptr;
     float *y = nullptr, *r = nullptr, *q = nullptr;
@@ -674,8 +708,10 @@ static void c3_project(const eptv3_geometry *g, const float *f, const float *y_r
 }
 
 static void c3_backproject(const eptv3_geometry *g, const float *y, float *out, int fin, cudaStream_t st) {
+    const int npix = g->C.nu * g->C.nrow;
+    k32_scale<<<dim3(nblk_of(npix, 256), (unsigned)g->C.nv), 256, 0, st>>>(y, g->fac, npix, g->ys);
     const long long n_col = (long long)g->C.nx * g->C.ny * ((g->C.nz + kZPair - 1) / kZPair);
-    k32_backproject<<<nblk_of(n_col, 256), 256, 0, st>>>(g->C, y, out, g->partials, g->d_sd, fin);
+    k32_backproject<<<nblk_of(n_col, 256), 256, 0, st>>>(g->C, g->ys, out, g->partials, g->d_sd, fin);
 }
 
 // (P1): M CGLS iterations on g->u (App. I), data g->y
@@ -765,9 +801,27 @@ int eptv3_create_geometry(const eptv3_geometry_desc *d, eptv3_geometry **out) {
         g->angles.assign(d->angles, d->angles + d->n_views);
         g->desc.angles = g->angles.data();
     }
-    // ray and view tables in FP64, stored FP32
-    std::vector<RayRec3> rays((size_t)n_rays);
+    if (d->n_views > 65535) {
+        delete g;
+        return c3_fail(EPTV_ERR_ARG, "at most 65535 views");
+    }
+    // ray tables in FP64, stored FP32.  Depth parametrisation: a = (central direction) + (u / sdd) e_u + (w / sdd) e_z, the
+    // point at depth sid is (u e_u + w e_z) sid / sdd (the source plus sid times the central
+    // direction is the rotation axis); F = |a|
+    const int npix = d->nu * d->nv;
+    std::vector<ColRec3> cols((size_t)d->n_views * d->nu);
+    std::vector<RowRec3> rows((size_t)d->nv);
+    std::vector<float> fac((size_t)npix);
     std::vector<ViewRec3> views((size_t)d->n_views);
+    const double m_inv = d->sid / d->sdd;
+    for (int iv = 0; iv < d->nv; ++iv) {
+        const double w = (iv - (d->nv - 1) / 2.0 + d->v_off) * d->dv;
+        rows[iv] = RowRec3{(float)(w * m_inv), c3_inv(w / d->sdd)};
+        for (int iu = 0; iu < d->nu; ++iu) {
+            const double u = (iu - (d->nu - 1) / 2.0 + d->u_off) * d->du;
+            fac[(size_t)iv * d->nu + iu] = (float)std::sqrt(1.0 + (u * u + w * w) / (d->sdd * d->sdd));
+        }
+    }
     for (int k = 0; k < d->n_views; ++k) {
         const double th = d->angles ? d->angles[k] : 2.0 * M_PI * k / d->n_views;
         const double c = std::cos(th), s = std::sin(th);
@@ -777,19 +831,18 @@ int eptv3_create_geometry(const eptv3_geometry_desc *d, eptv3_geometry **out) {
             const double w = (iv - (d->nv - 1) / 2.0 + d->v_off) * d->dv;
             for (int iu = 0; iu < d->nu; ++iu) {
                 const double u = (iu - (d->nu - 1) / 2.0 + d->u_off) * d->du;
-                double ux = -d->sdd * c - u * s, uy = -d->sdd * s + u * c, uz = w;
-                const double n = std::sqrt(ux * ux + uy * uy + uz * uz);
-                ux /= n; uy /= n; uz /= n;
-                const double proj = Sx * ux + Sy * uy;
-                const double Px = Sx - proj * ux, Py = Sy - proj * uy, Pz = -proj * uz;
+                const double ux = -d->sdd * c - u * s, uy = -d->sdd * s + u * c, uz = w;
                 const bool zmaj = std::fabs(uz) / d->dz >= std::max(std::fabs(ux) / d->dx, std::fabs(uy) / d->dy);
                 if (zmaj) {
                     delete g;
                     return c3_fail(EPTV_ERR_ARG, "cone too wide: a ray crosses z planes faster than x and y planes");
                 }
-                rays[((size_t)k * d->nv + iv) * d->nu + iu] =
-                    RayRec3{(float)Px, (float)Py, (float)Pz, c3_inv(ux), c3_inv(uy), c3_inv(uz)};
             }
+        }
+        for (int iu = 0; iu < d->nu; ++iu) {
+            const double u = (iu - (d->nu - 1) / 2.0 + d->u_off) * d->du;
+            const double ax = -c - u / d->sdd * s, ay = -s + u / d->sdd * c;
+            cols[(size_t)k * d->nu + iu] = ColRec3{(float)(-s * u * m_inv), (float)(c * u * m_inv), c3_inv(ax), c3_inv(ay)};
         }
     }
     Cone &C = g->C;
@@ -797,8 +850,9 @@ int eptv3_create_geometry(const eptv3_geometry_desc *d, eptv3_geometry **out) {
     C.dx = (float)d->dx; C.dy = (float)d->dy; C.dz = (float)d->dz;
     C.x0 = (float)(-0.5 * d->nx * d->dx); C.y0 = (float)(-0.5 * d->ny * d->dy); C.z0 = (float)(-0.5 * d->nz * d->dz);
     C.du = (float)d->du; C.dw = (float)d->dv;
+    C.inv_du = (float)(1.0 / d->du); C.inv_dw = (float)(1.0 / d->dv);
     C.uc = (float)((d->nu - 1) / 2.0 - d->u_off); C.wc = (float)((d->nv - 1) / 2.0 - d->v_off);
-    C.sdd = (float)d->sdd;
+    C.sdd = (float)d->sdd; C.sid = (float)d->sid;
     C.n_vox = n_vox; C.n_rays = n_rays;
     Vol &V = g->V;
     V.nx = d->nx; V.ny = d->ny; V.nz = d->nz;
@@ -824,7 +878,8 @@ int eptv3_create_geometry(const eptv3_geometry_desc *d, eptv3_geometry **out) {
     const long long maxblk = std::max(blk_k31, std::max(blk_face, std::max(blk_vox, (n_rays + 1023) / 1024)));
     int rc = 0;
     auto A = [&](auto **p, size_t n) { if (!rc) rc = c3_alloc(g, p, n); };
-    A(&g->ray, (size_t)n_rays); A(&g->view, (size_t)d->n_views);
+    A(&g->col, cols.size()); A(&g->row, rows.size()); A(&g->fac, fac.size()); A(&g->view, (size_t)d->n_views);
+    A(&g->ys, (size_t)n_rays);
     for (float **p : {&g->u, &g->s, &g->t, &g->fa, &g->fb, &g->g}) A(p, (size_t)n_vox);
     for (float **p : {&g->y, &g->r, &g->q}) A(p, (size_t)n_rays);
     for (float **p : {&g->Q, &g->TT, &g->WW, &g->Tsel}) A(p, (size_t)V.nf);
@@ -836,11 +891,13 @@ int eptv3_create_geometry(const eptv3_geometry_desc *d, eptv3_geometry **out) {
     A(&g->d_sd, 1);
     A(&g->d_params, 1);
     if (rc) { eptv3_destroy_geometry(g); return rc; }
-    C.ray = g->ray; C.view = g->view;
+    C.col = g->col; C.row = g->row; C.fac = g->fac; C.view = g->view;
     SliceDev sd;
     memset(&sd, 0, sizeof sd);
     sd.ctr = g->ctr; sd.acc = g->acc; sd.sc = g->sc;
-    if (cudaMemcpy(g->ray, rays.data(), sizeof(RayRec3) * (size_t)n_rays, cudaMemcpyHostToDevice) != cudaSuccess ||
+    if (cudaMemcpy(g->col, cols.data(), sizeof(ColRec3) * cols.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(g->row, rows.data(), sizeof(RowRec3) * rows.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(g->fac, fac.data(), sizeof(float) * fac.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(g->view, views.data(), sizeof(ViewRec3) * views.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(g->d_sd, &sd, sizeof sd, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(g->ctr, 0, sizeof(unsigned int)) != cudaSuccess ||

@@ -526,7 +526,7 @@ def version() -> str:
 # ------------------------------------------------------------------ 3-D cone beam
 
 class Geometry3:
-    """Owner of one eptv3_geometry handle (cone-beam ray table + workspace)."""
+    """Owner of one eptv3_geometry handle (cone-beam ray tables + workspace)."""
 
     def __init__(self, g):
         L = load()

@@ -48,6 +48,8 @@ struct Cone {
     float du, dw, uc, wc;                           // column index = u / du + uc, row = w / dw + wc
     float inv_du, inv_dw;                           // 1 / du, 1 / dw (candidate bounds only)
     float sdd, sid;
+    float rxy;                                      // >= half-diagonal of the volume in x-y
+    int band_max;                                   // >= rows of any z slab's band (K32)
     long long n_vox, n_rays;
     const ColRec3 *col;                             // [view][column]
     const RowRec3 *row;                             // [row]
@@ -215,37 +217,58 @@ k32_scale(const float *__restrict__ y, const float *__restrict__ fac, int npix, 
     ys[r] = __ldg(y + r) * __ldg(fac + i);
 }
 
-// Thread = two voxels stacked in z, (ix, iy, 2 iz2) and (ix, iy, 2 iz2 + 1): a voxel's
-// detector columns do not depend on z, and a column's x-y chord through the pair (its
-// x and y plane parameters) does not depend on the row, so the pair shares, per view,
-// its corner projections and, per column, the chord; per row only the three z planes.
+// Thread = two voxels stacked in z, (ix, iy, 2 iz2) and (ix, iy, 2 iz2 + 1); block =
+// 256 (ix, iy) of one iz2 (grid.y).  A voxel's detector columns do not depend on z, and a
+// column's x-y chord through the pair (its x and y plane parameters) does not depend on
+// the row, so the pair shares, per view, its corner projections and, per column, the
+// chord.  The z planes of a row depend on the row alone and all threads of a block have
+// the same z planes: the block tabulates, in shared memory, each row's parameter interval
+// through both voxels of the pair, for the band of rows that can meet its slab at any
+// depth of the volume.
 constexpr int kZPair = 2;
+
+// first and last detector row of the band of the slab [Za, Zb]: depths of the volume
+// sid + D', |D'| <= rxy; half a row of margin (the per-column bounds use 0.01)
+__device__ __forceinline__ void k32_band(const Cone &C, float Za, float Zb, int &b0, int &b1) {
+    const float ka = __fdividef(C.sdd, C.sid - C.rxy), kb = __fdividef(C.sdd, C.sid + C.rxy);
+    const float wlo = fminf(Za * ka, Za * kb), whi = fmaxf(Zb * ka, Zb * kb);
+    b0 = max(0, (int)ceilf(fmaf(wlo, C.inv_dw, C.wc) - 0.5f));
+    b1 = min(C.nrow - 1, (int)floorf(fmaf(whi, C.inv_dw, C.wc) + 0.5f));
+    b1 = min(b1, b0 + C.band_max - 1);
+}
 
 __global__ void __launch_bounds__(256, 4)
 k32_backproject(Cone C, const float *__restrict__ ys, float *__restrict__ out, double *__restrict__ partials,
                 SliceDev *S, int fin)
 {
     const double gamma_pre = threadIdx.x == 0 ? fin_gamma(S->sc, fin) : 0.0;
+    extern __shared__ float4 s_zt[];                       // [band]: (lo, hi) of voxel 0, of voxel 1
     __shared__ double rsm[2 * 8];
     __shared__ double res[2];
     __shared__ int last_flag;
-    const int nz2 = (C.nz + kZPair - 1) / kZPair;
-    const long long col = (long long)blockIdx.x * 256 + threadIdx.x;   // (iz2, iy, ix)
-    const long long n_col = (long long)C.nx * C.ny * nz2;
-    float acc[kZPair] = {0.0f, 0.0f};
-    const bool valid = col < n_col;
-    int ix = 0, iy = 0, iz0 = 0;
+    const int iz0 = blockIdx.y * kZPair;
+    const int nzp = min(kZPair, C.nz - iz0);                // voxels of the pair inside
+    float Z[kZPair + 1];
+#pragma unroll
+    for (int q = 0; q <= kZPair; ++q) Z[q] = grid_line((float)(iz0 + q), C.dz, C.z0);
+    const float Ze = grid_line((float)(iz0 + nzp), C.dz, C.z0);
+    int b0, b1;
+    k32_band(C, Z[0], Ze, b0, b1);
+    for (int r = b0 + (int)threadIdx.x; r <= b1; r += 256) {
+        const RowRec3 Rr = C.row[r];
+        float tz[kZPair + 1];
+#pragma unroll
+        for (int q = 0; q <= kZPair; ++q) tz[q] = cross_t(Z[q], Rr.qz, Rr.iz);
+        s_zt[r - b0] = make_float4(fminf(tz[0], tz[1]), fmaxf(tz[0], tz[1]), fminf(tz[1], tz[2]), fmaxf(tz[1], tz[2]));
+    }
+    __syncthreads();
+    const int pxy = blockIdx.x * 256 + threadIdx.x;         // iy * nx + ix
+    float acc0 = 0.0f, acc1 = 0.0f;
+    const bool valid = pxy < C.nx * C.ny;
     if (valid) {
-        ix = (int)(col % C.nx);
-        iy = (int)((col / C.nx) % C.ny);
-        iz0 = (int)(col / ((long long)C.nx * C.ny)) * kZPair;
-        const int nzp = min(kZPair, C.nz - iz0);            // voxels of the pair inside
+        const int iy = pxy / C.nx, ix = pxy - iy * C.nx;
         const float X0 = grid_line((float)ix, C.dx, C.x0), X1 = grid_line((float)(ix + 1), C.dx, C.x0);
         const float Y0 = grid_line((float)iy, C.dy, C.y0), Y1 = grid_line((float)(iy + 1), C.dy, C.y0);
-        float Z[kZPair + 1];
-#pragma unroll
-        for (int q = 0; q <= kZPair; ++q) Z[q] = grid_line((float)(iz0 + q), C.dz, C.z0);
-        const float Ze = grid_line((float)(iz0 + nzp), C.dz, C.z0);
         const long long view_sz = (long long)C.nrow * C.nu;
         for (int v = 0; v < C.nv; ++v) {
             const ViewRec3 V = C.view[v];
@@ -266,8 +289,6 @@ k32_backproject(Cone C, const float *__restrict__ ys, float *__restrict__ out, d
                 const ColRec3 Q = colv[iu];
                 const float ax = cross_t(X0, Q.qx, Q.ix), bx = cross_t(X1, Q.qx, Q.ix);
                 const float ay = cross_t(Y0, Q.qy, Q.iy), by = cross_t(Y1, Q.qy, Q.iy);
-                // min / max are exact, so grouping the x and y planes first gives the
-                // same length as the canonical six-plane formula
                 const float lo_xy = fmaxf(fminf(ax, bx), fminf(ay, by));
                 const float hi_xy = fminf(fmaxf(ax, bx), fmaxf(ay, by));
                 if (!(lo_xy < hi_xy)) continue;
@@ -275,34 +296,32 @@ k32_backproject(Cone C, const float *__restrict__ ys, float *__restrict__ out, d
                 // w = z sdd / (sid + D'), D' in [lo_xy, hi_xy] (both depths > 0)
                 const float ka = __fdividef(C.sdd, C.sid + lo_xy), kb = __fdividef(C.sdd, C.sid + hi_xy);
                 const float wlo = fminf(Z[0] * ka, Z[0] * kb), whi = fmaxf(Ze * ka, Ze * kb);
-                const int iv0 = max(0, (int)ceilf(fmaf(wlo, C.inv_dw, C.wc) - 0.01f));
-                const int iv1 = min(C.nrow - 1, (int)floorf(fmaf(whi, C.inv_dw, C.wc) + 0.01f));
+                const int iv0 = max(b0, (int)ceilf(fmaf(wlo, C.inv_dw, C.wc) - 0.01f));
+                const int iv1 = min(b1, (int)floorf(fmaf(whi, C.inv_dw, C.wc) + 0.01f));
                 const float *ycol = ysv + iu;
+                // min / max are exact, so max(0, min(hi_xy, hi_z) - max(lo_xy, lo_z)) is
+                // the canonical six-plane length
                 for (int iv = iv0; iv <= iv1; ++iv) {
-                    const RowRec3 Rr = C.row[iv];
+                    const float4 zt = s_zt[iv - b0];
                     const float yv = __ldg(ycol + iv * C.nu);
-                    float tz[kZPair + 1];
-#pragma unroll
-                    for (int q = 0; q <= kZPair; ++q) tz[q] = cross_t(Z[q], Rr.qz, Rr.iz);
-#pragma unroll
-                    for (int q = 0; q < kZPair; ++q) {
-                        const float l = c3_len(lo_xy, hi_xy, lo_xy, hi_xy, fminf(tz[q], tz[q + 1]),
-                                               fmaxf(tz[q], tz[q + 1]));
-                        acc[q] = fmaf(l, yv, acc[q]);
-                    }
+                    const float l0 = fmaxf(0.0f, __fsub_rn(fminf(hi_xy, zt.y), fmaxf(lo_xy, zt.x)));
+                    const float l1 = fmaxf(0.0f, __fsub_rn(fminf(hi_xy, zt.w), fmaxf(lo_xy, zt.z)));
+                    acc0 = fmaf(l0, yv, acc0);
+                    acc1 = fmaf(l1, yv, acc1);
                 }
             }
         }
-        const long long vox = ((long long)iz0 * C.ny + iy) * C.nx + ix;
-        out[vox] = acc[0];
-        if (nzp > 1) out[vox + (long long)C.nx * C.ny] = acc[1];
-        if (nzp < 2) acc[1] = 0.0f;
+        const long long vox = (long long)iz0 * C.nx * C.ny + pxy;
+        out[vox] = acc0;
+        if (nzp > 1) out[vox + (long long)C.nx * C.ny] = acc1;
+        if (nzp < 2) acc1 = 0.0f;
     }
     if (fin == FIN_NONE) return;
-    float vals[1] = {valid ? fmaf(acc[0], acc[0], acc[1] * acc[1]) : 0.0f};
-    block_sum_to<1, 256>(vals, partials + (size_t)blockIdx.x * 2, rsm);
-    if (threadIdx.x == 0) partials[(size_t)blockIdx.x * 2 + 1] = 0.0;
-    if (!reduce_slice<2, 256>(*S, partials, 2, 0, gridDim.x, blockIdx.x, rsm, res, &last_flag)) return;
+    const int nblk = gridDim.x * gridDim.y, lb = blockIdx.y * gridDim.x + blockIdx.x;
+    float vals[1] = {valid ? fmaf(acc0, acc0, acc1 * acc1) : 0.0f};
+    block_sum_to<1, 256>(vals, partials + (size_t)lb * 2, rsm);
+    if (threadIdx.x == 0) partials[(size_t)lb * 2 + 1] = 0.0;
+    if (!reduce_slice<2, 256>(*S, partials, 2, 0, nblk, lb, rsm, res, &last_flag)) return;
     if (threadIdx.x == 0) finalize(S->sc, fin, res[0], res[1], gamma_pre);
 }
 
@@ -710,8 +729,8 @@ static void c3_project(const eptv3_geometry *g, const float *f, const float *y_r
 static void c3_backproject(const eptv3_geometry *g, const float *y, float *out, int fin, cudaStream_t st) {
     const int npix = g->C.nu * g->C.nrow;
     k32_scale<<<dim3(nblk_of(npix, 256), (unsigned)g->C.nv), 256, 0, st>>>(y, g->fac, npix, g->ys);
-    const long long n_col = (long long)g->C.nx * g->C.ny * ((g->C.nz + kZPair - 1) / kZPair);
-    k32_backproject<<<nblk_of(n_col, 256), 256, 0, st>>>(g->C, g->ys, out, g->partials, g->d_sd, fin);
+    const dim3 grid(nblk_of((long long)g->C.nx * g->C.ny, 256), (unsigned)((g->C.nz + kZPair - 1) / kZPair));
+    k32_backproject<<<grid, 256, sizeof(float4) * g->C.band_max, st>>>(g->C, g->ys, out, g->partials, g->d_sd, fin);
 }
 
 // (P1): M CGLS iterations on g->u (App. I), data g->y
@@ -791,7 +810,9 @@ int eptv3_create_geometry(const eptv3_geometry_desc *d, eptv3_geometry **out) {
     if (!(d->dx > 0 && d->dy > 0 && d->dz > 0 && d->du > 0 && d->dv > 0))
         return c3_fail(EPTV_ERR_ARG, "pitches must be > 0");
     const double R = 0.5 * std::sqrt(d->nx * d->dx * d->nx * d->dx + d->ny * d->dy * d->ny * d->dy);
-    if (!(d->sid > R) || !(d->sdd > d->sid)) return c3_fail(EPTV_ERR_ARG, "need sdd > sid > half-diagonal");
+    const double rxy = R * (1.0 + 1e-5);                  // every depth of the volume is in sid -+ rxy
+    if (!(d->sid > rxy * (1.0 + 1e-5)) || !(d->sdd > d->sid))
+        return c3_fail(EPTV_ERR_ARG, "need sdd > sid > half-diagonal");
     const long long n_vox = (long long)d->nx * d->ny * d->nz;
     const long long n_rays = (long long)d->n_views * d->nu * d->nv;
     if (n_vox > (1LL << 31) - 1 || n_rays > (1LL << 31) - 1) return c3_fail(EPTV_ERR_ARG, "volume or scan too large");
@@ -801,9 +822,9 @@ int eptv3_create_geometry(const eptv3_geometry_desc *d, eptv3_geometry **out) {
         g->angles.assign(d->angles, d->angles + d->n_views);
         g->desc.angles = g->angles.data();
     }
-    if (d->n_views > 65535) {
+    if (d->n_views > 65535 || (d->nz + kZPair - 1) / kZPair > 65535) {
         delete g;
-        return c3_fail(EPTV_ERR_ARG, "at most 65535 views");
+        return c3_fail(EPTV_ERR_ARG, "at most 65535 views and 131070 slices");
     }
     // ray tables in FP64, stored FP32.  Depth parametrisation: a = (central direction) + (u / sdd) e_u + (w / sdd) e_z, the
     // point at depth sid is (u e_u + w e_z) sid / sdd (the source plus sid times the central
@@ -853,6 +874,22 @@ int eptv3_create_geometry(const eptv3_geometry_desc *d, eptv3_geometry **out) {
     C.inv_du = (float)(1.0 / d->du); C.inv_dw = (float)(1.0 / d->dv);
     C.uc = (float)((d->nu - 1) / 2.0 - d->u_off); C.wc = (float)((d->nv - 1) / 2.0 - d->v_off);
     C.sdd = (float)d->sdd; C.sid = (float)d->sid;
+    C.rxy = (float)rxy;
+    {   // K32's row bands (the kernel's formula in FP64; each end may move by a row in FP32)
+        int bmax = 0;
+        for (int iz0 = 0; iz0 < d->nz; iz0 += kZPair) {
+            const int nzp = std::min(kZPair, d->nz - iz0);
+            const double Za = -0.5 * d->nz * d->dz + iz0 * d->dz, Zb = Za + nzp * d->dz;
+            const double ka = d->sdd / (d->sid - rxy), kb = d->sdd / (d->sid + rxy);
+            const double wlo = std::min(Za * ka, Za * kb), whi = std::max(Zb * ka, Zb * kb);
+            const double wc = (d->nv - 1) / 2.0 - d->v_off;
+            const int b0 = std::max(0, (int)std::ceil(wlo / d->dv + wc - 0.5));
+            const int b1 = std::min(d->nv - 1, (int)std::floor(whi / d->dv + wc + 0.5));
+            bmax = std::max(bmax, b1 - b0 + 1);
+        }
+        C.band_max = std::min(d->nv, bmax + 2);
+        if (C.band_max < 1) C.band_max = 1;
+    }
     C.n_vox = n_vox; C.n_rays = n_rays;
     Vol &V = g->V;
     V.nx = d->nx; V.ny = d->ny; V.nz = d->nz;
@@ -875,7 +912,7 @@ int eptv3_create_geometry(const eptv3_geometry_desc *d, eptv3_geometry **out) {
     // workspace
     const long long blk_k31 = (long long)d->n_views * d->nv * ((d->nu + 31) / 32);
     const long long blk_face = (V.nf + 255) / 256, blk_vox = (n_vox + 255) / 256;
-    const long long maxblk = std::max(blk_k31, std::max(blk_face, std::max(blk_vox, (n_rays + 1023) / 1024)));
+    const long long blk_k32 = ((long long)d->nx * d->ny + 255) / 256 * ((d->nz + kZPair - 1) / kZPair);
     int rc = 0;
     auto A = [&](auto **p, size_t n) { if (!rc) rc = c3_alloc(g, p, n); };
     A(&g->col, cols.size()); A(&g->row, rows.size()); A(&g->fac, fac.size()); A(&g->view, (size_t)d->n_views);
@@ -884,13 +921,24 @@ int eptv3_create_geometry(const eptv3_geometry_desc *d, eptv3_geometry **out) {
     for (float **p : {&g->y, &g->r, &g->q}) A(p, (size_t)n_rays);
     for (float **p : {&g->Q, &g->TT, &g->WW, &g->Tsel}) A(p, (size_t)V.nf);
     A(&g->sel, 1);
-    A(&g->partials, (size_t)std::max(blk_k31 * 2, std::max(blk_face, blk_vox) * kPartialStride));
+    A(&g->partials, (size_t)std::max(std::max(blk_k31, blk_k32) * 2, std::max(blk_face, blk_vox) * kPartialStride));
     A(&g->acc, (size_t)kPartialStride * kAccCopies * kAccStride);
     A(&g->ctr, 1);
     A(&g->sc, kScalarStride);
     A(&g->d_sd, 1);
     A(&g->d_params, 1);
     if (rc) { eptv3_destroy_geometry(g); return rc; }
+    const size_t band_bytes = sizeof(float4) * (size_t)C.band_max;
+    if (band_bytes > 200 * 1024) {
+        eptv3_destroy_geometry(g);
+        return c3_fail(EPTV_ERR_ARG, "detector row band of a z slab too tall for the back projector");
+    }
+    if (band_bytes > 48 * 1024 &&
+        cudaFuncSetAttribute(k32_backproject, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)band_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        eptv3_destroy_geometry(g);
+        return c3_fail(EPTV_ERR_CUDA, "cannot raise the back projector's shared memory");
+    }
     C.col = g->col; C.row = g->row; C.fac = g->fac; C.view = g->view;
     SliceDev sd;
     memset(&sd, 0, sizeof sd);

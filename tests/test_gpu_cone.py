@@ -22,6 +22,8 @@ GEOMS = {
     "c5_16": I.c5_geometry(16),
     "c5_8": I.c5_geometry(8),
     "aniso": I.ConeGeometry(20, 17, 11, 1.3, 1.1, 1.7, 9, 30, 14, 1.9, 2.3, 0.3, -0.4, 120.0, 200.0),
+    # source close to the volume, tall detector: the row band of a z slab spans many rows
+    "tall": I.ConeGeometry(16, 16, 24, 1.0, 1.0, 1.0, 12, 40, 64, 0.9, 0.5, 0.25, 0.1, 30.0, 45.0),
 }
 
 
@@ -212,3 +214,18 @@ def test_tv_step_several_faces_per_thread(rule):
     assert rel(np64(f).reshape(want.shape), want) < 1e-4
     if rule == O.ARMIJO:
         assert t_prev == pytest.approx(st.t_prev, rel=1e-6)
+
+
+@pytest.mark.parametrize("change,msg", [
+    (dict(sid=11.0), "half-diagonal"),                 # source inside the volume's circle
+    (dict(sdd=25.0), "half-diagonal"),                 # detector before the source distance
+    (dict(nv=400, dv=1.0), "too wide"),                # rays steeper than 45 deg in z
+    (dict(n_views=70000), "65535 views"),
+])
+def test_create_rejects_geometries_outside_the_kernels_assumptions(change, msg):
+    base = dict(nx=16, ny=16, nz=24, dx=1.0, dy=1.0, dz=1.0, n_views=12, nu=40, nv=64, du=0.9, dv=0.5,
+                u_off=0.25, v_off=0.1, sid=30.0, sdd=45.0)
+    base.update(change)
+    with pytest.raises(E.EptvError) as ei:
+        E.Geometry3(I.ConeGeometry(**base))
+    assert ei.value.code == -1 and msg in str(ei.value)

@@ -65,7 +65,7 @@ __device__ __forceinline__ float c3_len(float lo_a, float hi_a, float lo_b, floa
 // ------------------------------------------------------------------ K31: projector
 
 template <int SEG>
-__global__ void __launch_bounds__(32 * SEG)
+__global__ void __launch_bounds__(32 * SEG, 40 / SEG)
 k31_project(Cone C, const float *__restrict__ f, const float *__restrict__ y_resid, float *__restrict__ out,
             double *__restrict__ partials, SliceDev *S, int fin)
 {
@@ -167,7 +167,7 @@ k31_project(Cone C, const float *__restrict__ f, const float *__restrict__ y_res
                     for (int it = 0; it < 6; ++it) {
                         const float lc = fmaxf(0.0f, __fsub_rn(fminf(fminf(tbc, him), hiz),
                                                               fmaxf(fmaxf(tac, lom), loz)));
-                        if (lc > 0.0f && cm >= 0 && cm < nm && cz >= 0 && cz < C.nz)
+                        if (lc > 0.0f && (unsigned)cm < (unsigned)nm && (unsigned)cz < (unsigned)C.nz)
                             acc = fmaf(lc, __ldg(f + idx), acc);
                         const float nxt = fminf(him, hiz);
                         if (!(nxt < tbc)) break;

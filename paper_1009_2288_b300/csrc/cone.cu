@@ -826,9 +826,10 @@ int eptv3_create_geometry(const eptv3_geometry_desc *d, eptv3_geometry **out) {
         delete g;
         return c3_fail(EPTV_ERR_ARG, "at most 65535 views and 131070 slices");
     }
-    // ray tables in FP64, stored FP32.  Depth parametrisation: a = (central direction) + (u / sdd) e_u + (w / sdd) e_z, the
-    // point at depth sid is (u e_u + w e_z) sid / sdd (the source plus sid times the central
-    // direction is the rotation axis); F = |a|
+    // ray tables in FP64, stored FP32.  Depth parametrisation: the ray's displacement per
+    // unit depth is a = (central direction) + (u / sdd) e_u + (w / sdd) e_z, its point at
+    // depth sid is (u e_u + w e_z) sid / sdd (the source plus sid times the central
+    // direction is on the rotation axis), and F = |a|
     const int npix = d->nu * d->nv;
     std::vector<ColRec3> cols((size_t)d->n_views * d->nu);
     std::vector<RowRec3> rows((size_t)d->nv);

@@ -24,6 +24,11 @@ GEOMS = {
     "aniso": I.ConeGeometry(20, 17, 11, 1.3, 1.1, 1.7, 9, 30, 14, 1.9, 2.3, 0.3, -0.4, 120.0, 200.0),
     # source close to the volume, tall detector: the row band of a z slab spans many rows
     "tall": I.ConeGeometry(16, 16, 24, 1.0, 1.0, 1.0, 12, 40, 64, 0.9, 0.5, 0.25, 0.1, 30.0, 45.0),
+    # irregular angles over a short scan, including views along the grid axes
+    "angles": I.ConeGeometry(12, 10, 6, 1.0, 1.2, 0.9, 7, 24, 10, 1.1, 1.0, 0.25, 0.0, 60.0, 90.0,
+                             angles=np.array([0.0, 0.3, 0.31, 1.2, np.pi / 2, 2.0, np.pi])),
+    # a single slice, three detector rows
+    "slice": I.ConeGeometry(9, 13, 1, 1.0, 1.0, 2.0, 5, 21, 3, 1.0, 1.5, 0.25, 0.0, 40.0, 70.0),
 }
 
 

@@ -848,7 +848,7 @@ int eptv3_create_geometry(const eptv3_geometry_desc *d, eptv3_geometry **out) {
         const double th = d->angles ? d->angles[k] : 2.0 * M_PI * k / d->n_views;
         const double c = std::cos(th), s = std::sin(th);
         const double Sx = d->sid * c, Sy = d->sid * s;
-        views[k] = ViewRec3{(float)Sx, (float)Sy, (float)-c, (float)-s, (float)-s, (float)c};
+        views[k] = ViewRec3{(float)Sx, (float)Sy, (float)-c, (float)-s, (float)-s, (float)c, 0.0f, 0.0f};
         for (int iv = 0; iv < d->nv; ++iv) {
             const double w = (iv - (d->nv - 1) / 2.0 + d->v_off) * d->dv;
             for (int iu = 0; iu < d->nu; ++iu) {

@@ -554,12 +554,12 @@ int eptv_create_geometry(const eptv_geometry_desc *desc, eptv_geometry **out) {
     sd.sel_rank = 1;
 
     DevMem &m = g->mem;
-    RayRec *d_ray;
-    ViewRec *d_view;
-    int *d_order;
-    float *img[9];
-    float *sino[2];
-    double *sc;
+    RayRec *d_ray = nullptr;
+    ViewRec *d_view = nullptr;
+    int *d_order = nullptr;
+    float *img[9] = {};
+    float *sino[2] = {};
+    double *sc = nullptr;
     if ((rc = m.alloc(&d_ray, n_rays)) || (rc = m.alloc(&d_view, nv))) goto bad;
     if ((rc = m.alloc(&d_order, k1_order.size()))) goto bad;
     for (int i = 0; i < 9; ++i) if ((rc = m.alloc(&img[i], n_pix))) goto bad;
@@ -581,7 +581,8 @@ int eptv_create_geometry(const eptv_geometry_desc *desc, eptv_geometry **out) {
     sd.r = sino[0]; sd.q = sino[1];
     sd.y = g->y_int;
     sd.sc = sc;
-    if ((rc = build_batch(g->B, m, std::vector<SliceDev>{sd}))) goto bad;
+    rc = build_batch(g->B, m, std::vector<SliceDev>{sd});
+    if (rc) goto bad;
     if (cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking) != cudaSuccess) {
         rc = fail(EPTV_ERR_CUDA, "cudaStreamCreate failed");
         goto bad;

@@ -470,7 +470,7 @@ k3tv_face_T(Vol V, const float *__restrict__ x, float eps2, float *__restrict__ 
 }
 
 // per face: T, w (Eq. 5 with sigma = sc[SC_SIGMA], or 1), q = w D / T; sum of w T (J)
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 8)
 k3tv_faces(Vol V, const float *__restrict__ f, float eps2, int mode, float *__restrict__ Q,
            float *__restrict__ TT, float *__restrict__ WW, double *__restrict__ partials, SliceDev *S)
 {
@@ -501,7 +501,7 @@ k3tv_faces(Vol V, const float *__restrict__ f, float eps2, int mode, float *__re
 }
 
 // g = lambda (f - v) - div Q; sums A = g.(f - v), B = g.g, F = |f - v|^2
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 8)
 k3tv_grad(Vol V, const float *__restrict__ f, const float *__restrict__ v, const float *__restrict__ Q,
           float lam, float *__restrict__ g, double *__restrict__ partials, SliceDev *S)
 {
@@ -535,7 +535,7 @@ k3tv_grad(Vol V, const float *__restrict__ f, const float *__restrict__ v, const
 // All Armijo trials of one GD iteration: per face, with frozen w and T,
 // dJ_m += w (T'^2 - T^2) / (T' + T), T'^2 - T^2 = t (t b - 2 a); then the decision.
 template <int KT>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 8)
 k3tv_trials(Vol V, const float *__restrict__ f, const float *__restrict__ g, const float *__restrict__ TT,
             const float *__restrict__ WW, const ParamsDev *__restrict__ P, int K, int first, int energy_only,
             double *__restrict__ partials, SliceDev *S)
@@ -673,7 +673,7 @@ struct eptv3_geometry {
     Cone C;
     Vol V;
     int k31_seg = 8;
-    unsigned red_blocks = 592;    // grid of the grid-stride reducing kernels: 4 blocks per SM
+    unsigned red_blocks = 1184;    // grid of the grid-stride reducing kernels: 8 blocks per SM
     ColRec3 *col = nullptr;
     RowRec3 *row = nullptr;
     float *fac = nullptr;
@@ -907,7 +907,7 @@ int eptv3_create_geometry(const eptv3_geometry_desc *d, eptv3_geometry **out) {
         int dev = 0, n_sm = 0;
         if (cudaGetDevice(&dev) == cudaSuccess &&
             cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n_sm > 0)
-            g->red_blocks = 4u * (unsigned)n_sm;
+            g->red_blocks = 8u * (unsigned)n_sm;
         cudaGetLastError();
     }
     // workspace

@@ -673,7 +673,7 @@ struct eptv3_geometry {
     Cone C;
     Vol V;
     int k31_seg = 8;
-    unsigned red_blocks = 1184;    // grid of the grid-stride reducing kernels: 8 blocks per SM
+    unsigned red_blocks = 1184;   // grid of the grid-stride reducing kernels: 8 blocks per SM
     ColRec3 *col = nullptr;
     RowRec3 *row = nullptr;
     float *fac = nullptr;
@@ -902,7 +902,7 @@ int eptv3_create_geometry(const eptv3_geometry_desc *d, eptv3_geometry **out) {
         delete g;
         return c3_fail(EPTV_ERR_ARG, "volume too large: 2^31 or more faces");
     }
-    // grid of the grid-stride reducing kernels: 4 resident 256-thread blocks of 64 registers per SM
+    // grid of the grid-stride reducing kernels: 8 resident 256-thread blocks of 32 registers per SM
     {
         int dev = 0, n_sm = 0;
         if (cudaGetDevice(&dev) == cudaSuccess &&

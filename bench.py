@@ -211,11 +211,35 @@ def cpu_baseline(case, steps=8):
     p = I.EptvParams(n_outer=steps)
     op = O.Operator(case.geom)
     t0 = time.perf_counter()
-    O.reconstruct(op, case.y, p)
+    f = O.reconstruct(op, case.y, p)
     dt = time.perf_counter() - t0
     return {"value": steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{steps} of the {N_OUTER} outer iterations of {WORKLOAD} "
-                      f"(single-threaded C Siddon + numpy FP64), {dt:.1f} s"}
+                      f"(single-threaded C Siddon + numpy FP64), {dt:.1f} s"}, f, op
+
+
+def oracle_check(geo, case, f_orc, op, steps, dev):
+    """The GPU path against the FP64 oracle on the benchmark workload: the image after
+    `steps` outer iterations from 0 (relative L2 against the oracle's image of the timed
+    sample above), and P of that image per view (largest relative L2 over the views)."""
+    import numpy as np
+    import torch
+    from paper_1009_2288_b300 import eptv as E
+    from paper_1009_2288_b300 import inputs as I
+    g = case.geom
+    f = torch.zeros(g.n_pix, device=dev)
+    y = torch.from_numpy(case.y.astype(np.float32).reshape(-1)).to(dev)
+    E.eptv_reconstruct(geo, I.EptvParams(n_outer=steps), y, f, report=False)
+    fg = f.double().cpu().numpy().reshape(g.ny, g.nx)
+    img = float(np.linalg.norm(fg - f_orc) / np.linalg.norm(f_orc))
+    f32 = f_orc.astype(np.float32)
+    yp = torch.empty(g.n_rays, device=dev)
+    E.eptv_project(geo, torch.from_numpy(f32.reshape(-1)).to(dev), yp)
+    want = op.project(f32.astype(np.float64)).reshape(g.n_views, -1)
+    got = yp.double().cpu().numpy().reshape(g.n_views, -1)
+    per_view = np.linalg.norm(got - want, axis=1) / np.maximum(np.linalg.norm(want, axis=1), 1e-300)
+    return {"iterations": steps, "image_rel_l2": img, "P_per_view_rel_l2_max": float(per_view.max()),
+            "oracle": "FP64, the cpu_baseline sample's image"}
 
 
 def run_reference(args, world, rank):
@@ -800,9 +824,10 @@ def run_ours(args, world, rank, local):
     if not args.no_learned and rank == 0:
         learned = run_learned(dev, stream)
 
-    cpu = None
+    cpu = check = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(case)
+        cpu, f_orc, op_orc = cpu_baseline(case)
+        check = oracle_check(geo, case, f_orc, op_orc, 8, dev)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -819,6 +844,7 @@ def run_ours(args, world, rank, local):
         "gpu_launches": int(launches) * args.steps,
         "roofline": roofline,
         "cpu_baseline": cpu,
+        "oracle_check": check,
         "time_to_oracle_energy": tte,
         "batched": batched,
         "stored": stored,

@@ -3,7 +3,7 @@
 environment).  Checks the rendezvous, the barrier, the whole-job rate (slowest rank's
 time, all ranks' units), the per-rank slices of the replica run (no data-path
 collective: each rank reconstructs its own seeded slice), and that the reference arm
-runs on rank 0 only."""
+runs on rank 0 only; also the CPU-baseline leg that times the oracle."""
 import json
 import os
 import socket
@@ -66,3 +66,18 @@ def test_reference_arm_runs_on_rank_zero_only(capsys):
         steps, warmup, gpus = 1, 0, 2
     assert bench.run_reference(Args, 2, 1) is None
     assert capsys.readouterr().out == ""
+
+
+def test_cpu_baseline_times_the_oracle_and_returns_its_image():
+    """The bench's CPU leg times the oracle as it stands and hands its image on to the
+    GPU-vs-oracle check (one outer iteration of the 128^2 workload here)."""
+    import numpy as np
+    import bench
+    from oracle import eptv_oracle as O
+    from paper_1009_2288_b300 import inputs as I
+    case = I.make_c1(with_truth=False)
+    cpu, f, op = bench.cpu_baseline(case, steps=1)
+    assert cpu["kind"] == "oracle" and cpu["cores"] == 1 and cpu["value"] > 0
+    assert f.shape == (case.geom.ny, case.geom.nx) and np.all(f >= 0) and np.any(f > 0)
+    assert np.array_equal(f, O.reconstruct(O.Operator(case.geom), case.y, I.EptvParams(n_outer=1)))
+    assert isinstance(op, O.Operator)

@@ -402,19 +402,39 @@ static int autotune_batch(Batch &B, int *k1_out, int *k2_out) {
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0));
     CU(cudaEventCreate(&e1));
-    auto time_it = [&](auto launch) -> float {
-        for (int i = 0; i < 3; ++i) launch();
-        float best_ms = 1e30f;
-        for (int rep = 0; rep < 3; ++rep) {     // best of 3 rounds of 20 launches
-            cudaEventRecord(e0, st);
-            for (int i = 0; i < 20; ++i) launch();
-            cudaEventRecord(e1, st);
-            cudaEventSynchronize(e1);
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            best_ms = std::min(best_ms, ms);
+    // One window of 20 back-to-back launches (CUDA events on the launching stream).
+    auto window = [&](auto launch) -> float {
+        cudaEventRecord(e0, st);
+        for (int i = 0; i < 20; ++i) launch();
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        return ms;
+    };
+    // Each candidate is warmed up, then the candidates are timed in interleaved rounds
+    // (so that a drift of clocks or of the other work on the GPU falls on all of them
+    // alike) and ranked by their median window.
+    auto pick = [&](const int *cand, int n, auto set, auto launch) -> int {
+        constexpr int kRounds = 7;
+        std::vector<float> t((size_t)n * kRounds);
+        for (int c = 0; c < n; ++c) {
+            set(cand[c]);
+            for (int i = 0; i < 3; ++i) launch();
         }
-        return best_ms;
+        for (int r = 0; r < kRounds; ++r)
+            for (int c = 0; c < n; ++c) {
+                set(cand[c]);
+                t[(size_t)c * kRounds + r] = window(launch);
+            }
+        int best = 0;
+        float best_med = 3e38f;
+        for (int c = 0; c < n; ++c) {
+            float *w = t.data() + (size_t)c * kRounds;
+            std::nth_element(w, w + kRounds / 2, w + kRounds);
+            if (w[kRounds / 2] < best_med) { best_med = w[kRounds / 2]; best = c; }
+        }
+        return cand[best];
     };
     const long long saved = g_launch_count;
     ProjArgs pa{};
@@ -422,21 +442,9 @@ static int autotune_batch(Batch &B, int *k1_out, int *k2_out) {
     BackArgs ba{};
     ba.out = 1; ba.fin = FIN_NONE;
     const int k1c[] = {4, 8, 16}, k2c[] = {1, 2, 4, 8, 16};
-    float best = 1e30f;
-    int b1 = B.k1_seg;
-    for (int c : k1c) {
-        B.k1_seg = c;
-        const float ms = time_it([&] { launch_project(B, pa, st); });
-        if (ms < best) { best = ms; b1 = c; }
-    }
+    const int b1 = pick(k1c, 3, [&](int c) { B.k1_seg = c; }, [&] { launch_project(B, pa, st); });
     B.k1_seg = b1;
-    best = 1e30f;
-    int b2 = B.k2_vg;
-    for (int c : k2c) {
-        B.k2_vg = c;
-        const float ms = time_it([&] { launch_backproject(B, ba, st); });
-        if (ms < best) { best = ms; b2 = c; }
-    }
+    const int b2 = pick(k2c, 5, [&](int c) { B.k2_vg = c; }, [&] { launch_backproject(B, ba, st); });
     B.k2_vg = b2;
     g_launch_count = saved;
     cudaEventDestroy(e0);

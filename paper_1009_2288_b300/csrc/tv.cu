@@ -248,8 +248,12 @@ constexpr int QYW = GW, QYH = kGdTileH + 3;          // y-edges around the g reg
 
 
 
-template <int KT>
-__global__ void __launch_bounds__(kGdThreads)
+// WIDE: the launch has more tiles than 8 blocks per SM hold at once (a batch), and 12
+// resident blocks of 40 registers hide more of each tile's load -> stencil -> reduction
+// latency chain than 8 blocks of 64 registers; a single slice fits in one wave of 8, where
+// the extra spills only cost.
+template <int KT, bool WIDE>
+__global__ void __launch_bounds__(kGdThreads, WIDE ? 12 : 1)
 k4_gd(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__restrict__ P, GdArgs ga,
       int iter, double *__restrict__ partials)
 {
@@ -609,18 +613,38 @@ void launch_select_generic(const Batch &B, const TileMap &m, int nblk, const flo
                                             vals, n, k, out);
 }
 
+// SMs of the current device (queried once per device)
+static int sm_count() {
+    static int cache[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) { cudaGetLastError(); return 148; }
+    if (!cache[dev]) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+            cudaGetLastError();
+            n = 148;
+        }
+        cache[dev] = n;
+    }
+    return cache[dev];
+}
+
+template <int KT>
+static void launch_k4(int nb, bool wide, const Batch &B, const TileMap &m, const GdArgs &ga, int iter,
+                      cudaStream_t st) {
+    if (wide) k4_gd<KT, true><<<nb, kGdThreads, 0, st>>>(B.d_sd, m, B.d_params, ga, iter, B.d_partials);
+    else k4_gd<KT, false><<<nb, kGdThreads, 0, st>>>(B.d_sd, m, B.d_params, ga, iter, B.d_partials);
+}
+
 void launch_gd_iter(const Batch &B, const GdArgs &ga, int iter, cudaStream_t st) {
     ++g_launch_count;
     const int nb = B.blocks(FAM_TV);
     const TileMap m = B.map(FAM_TV);
-    if (ga.n_trials <= 1)
-        k4_gd<1><<<nb, kGdThreads, 0, st>>>(B.d_sd, m, B.d_params, ga, iter, B.d_partials);
-    else if (ga.n_trials <= 4)
-        k4_gd<4><<<nb, kGdThreads, 0, st>>>(B.d_sd, m, B.d_params, ga, iter, B.d_partials);
-    else if (ga.n_trials <= 8)
-        k4_gd<8><<<nb, kGdThreads, 0, st>>>(B.d_sd, m, B.d_params, ga, iter, B.d_partials);
-    else
-        k4_gd<16><<<nb, kGdThreads, 0, st>>>(B.d_sd, m, B.d_params, ga, iter, B.d_partials);
+    const bool wide = nb > 8 * sm_count();
+    if (ga.n_trials <= 1) launch_k4<1>(nb, wide, B, m, ga, iter, st);
+    else if (ga.n_trials <= 4) launch_k4<4>(nb, wide, B, m, ga, iter, st);
+    else if (ga.n_trials <= 8) launch_k4<8>(nb, wide, B, m, ga, iter, st);
+    else launch_k4<16>(nb, wide, B, m, ga, iter, st);
 }
 
 void launch_gd_finish(const Batch &B, int n_gd, const float *f0_override, float *out_override,

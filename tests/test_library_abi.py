@@ -42,3 +42,19 @@ def test_python_defaults_match_library_defaults():
 
 def test_sm103a_only_build_flags():
     assert B.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_cone_geometry_argument_errors_without_gpu():
+    """eptv3_create_geometry validates its descriptor before it touches the device: sizes,
+    pitches, the source inside the volume's circle, more than 65535 views -- each comes
+    back as EPTV_ERR_ARG with a message, and no handle."""
+    import pytest
+    from paper_1009_2288_b300 import inputs as I
+    base = dict(nx=16, ny=16, nz=24, dx=1.0, dy=1.0, dz=1.0, n_views=12, nu=40, nv=64, du=0.9, dv=0.5,
+                u_off=0.25, v_off=0.1, sid=30.0, sdd=45.0)
+    for change, msg in ((dict(nx=0), "sizes"), (dict(du=0.0), "pitches"), (dict(sid=11.0), "half-diagonal"),
+                        (dict(sdd=25.0), "half-diagonal"), (dict(n_views=70000), "65535 views")):
+        d = dict(base, **change)
+        with pytest.raises(E.EptvError) as ei:
+            E.Geometry3(I.ConeGeometry(**d))
+        assert ei.value.code == -1 and msg in str(ei.value), change

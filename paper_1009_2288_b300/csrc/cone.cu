@@ -1,12 +1,12 @@
 // 3-D cone-beam EPTV (the paper's method, which is 2-D, extended to a circular cone-beam
 // scan with a flat detector; see eptv.h for the conventions).  Same algorithm as the 2-D
-// path (Sec. 2.2: CGLS for (P1), GD with Armijo for (P2), clamp), with
+// path (Sec. 2.2: CGLS for (P1), GD with Armijo for (P2), clamp).
 // Rays are parametrised by their depth along the central ray, counted from the plane
 // through the rotation axis (D' = D - sid).  The x and y plane crossings of a ray then
 // depend only on its view and detector column, the z plane crossings only on its detector
 // row, and its length through a voxel is F * (D' interval) with F = |a| = sqrt(1 + (u^2 +
 // w^2) / sdd^2) per detector pixel: P = diag(F) L', and both kernels below compute the
-// entries of L' with the same canonical formula from the same tables.
+// entries of L' with the same canonical formula from the same tables.  Kernels:
 //   K31  P:   ray-driven Siddon in 3-D.  A warp holds 32 adjacent detector columns of one
 //             detector row; the warps of a block split the ray's range along its major
 //             axis (x or y).  In each major-axis slab the ray walks the cells of the two

@@ -208,3 +208,29 @@ def test_extended_a2_equals_derivative_of_lagged_energy():
                 fm[k, j, i] -= h
                 fd[k, j, i] = (energy(fp) - energy(fm)) / (2 * h)
     assert np.allclose(g, fd, rtol=1e-6, atol=1e-7)
+
+
+def test_armijo_sufficient_decrease_and_first_passing_trial():
+    """Every accepted (P2) step in 3-D decreases the frozen-weight energy by at least
+    c t |g|^2, each longer trial before it did not, and replaying the accepted steps from v
+    gives the oracle's result."""
+    rng = np.random.Generator(np.random.PCG64(22))
+    v = rng.uniform(0, 1.0, (4, 5, 6))
+    v[:, :, 3:] += 0.02                                      # an edge, so that w varies
+    p = I.EptvParams(n_gd=8, max_trials=8)
+    fo, st = C.p2_solve(v, p, p.t_init_eff)
+    assert st.sigma == C.select_sigma(C.half_faces(v, p.eps), p.sigma_q, p.sigma_floor)
+    f = v.copy()
+    assert len(st.steps) == p.n_gd
+    assert any(t > 0 and len(tr) > 1 for t, tr in zip(st.steps, st.trials))   # backtracked, then accepted
+    assert any(t == 0 for t in st.steps)                                       # and a failed search
+    for t, tried in zip(st.steps, st.trials):
+        g, ws, E0 = C.p2_gradient(f, v, p.lam, p.eps, st.sigma)
+        gg = float(np.sum(g * g))
+        longer = [tt for tt, _ in tried if tt > t] if t > 0 else [tt for tt, _ in tried]
+        for tt in longer:
+            assert C.p2_energy_frozen(f - tt * g, v, p.lam, p.eps, ws) > E0 - p.armijo_c * tt * gg
+        if t > 0:
+            assert C.p2_energy_frozen(f - t * g, v, p.lam, p.eps, ws) <= E0 - p.armijo_c * t * gg
+            f = f - t * g
+    assert np.array_equal(f, fo)

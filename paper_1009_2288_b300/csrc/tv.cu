@@ -15,6 +15,8 @@
 //    The last block takes the Armijo decision in FP64 and stores the step; the next
 //    kernel applies it.  One launch per GD iteration, no host round trip.
 // K4u apply the last step, clamp f >= 0 (step 3 of the algorithm), write f and f^T.
+#include <atomic>
+
 #include "eptv_internal.cuh"
 #include "kernels.cuh"
 
@@ -613,20 +615,21 @@ void launch_select_generic(const Batch &B, const TileMap &m, int nblk, const flo
                                             vals, n, k, out);
 }
 
-// SMs of the current device (queried once per device)
+// SMs of the current device (queried once per device; host threads may race to fill the
+// cache, all with the same value)
 static int sm_count() {
-    static int cache[64] = {};
+    static std::atomic<int> cache[64];
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) { cudaGetLastError(); return 148; }
-    if (!cache[dev]) {
-        int n = 0;
+    int n = cache[dev].load(std::memory_order_relaxed);
+    if (n == 0) {
         if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
             cudaGetLastError();
             n = 148;
         }
-        cache[dev] = n;
+        cache[dev].store(n, std::memory_order_relaxed);
     }
-    return cache[dev];
+    return n;
 }
 
 template <int KT>

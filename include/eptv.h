@@ -276,8 +276,11 @@ typedef struct eptv3_geometry eptv3_geometry;
 /* Builds the ray tables (host FP64, stored FP32: 16 bytes per view and detector column,
  * 8 per detector row, 4 per detector pixel; rays are parametrised by their depth along the
  * central ray, so that P = diag(F) L' with F = |a| per detector pixel) and the solver
- * workspace (about 9 volumes of faces, 6 volumes, 4 projections).  EPTV_ERR_ARG (also for
- * more than 65535 views or a cone too wide for the narrow-cone march), EPTV_ERR_NOMEM,
+ * workspace (about 9 volumes of faces, 6 volumes, 4 projections).  EPTV_ERR_ARG for a bad
+ * descriptor: sizes or pitches not positive, sid not above the volume's half-diagonal in
+ * x-y or sdd not above sid, 2^31 or more voxels, rays or faces, more than 65535 views or
+ * 131070 slices, a cone too wide for the narrow-cone march, or a detector row band of one
+ * z slab too tall for the back projector's shared-memory table; EPTV_ERR_NOMEM,
  * EPTV_ERR_CUDA. */
 int eptv3_create_geometry(const eptv3_geometry_desc *desc, eptv3_geometry **out);
 void eptv3_destroy_geometry(eptv3_geometry *g);

@@ -14,6 +14,8 @@ definitions:
   upsample2: y[c, i, j] = x[c, i // 2, j // 2]
   head:      o[k, i, j] = hb[k] + sum_c hW[k, c] x[c, i, j];  f0 = o[0];  w = sigmoid(o[1])
   loss:      mean((f0 - f_t)^2) + mean((w - w_t)^2)
+  warm start served to the solver: f^(0) = max(base + scale * o0, 0), with base the CGLS
+             image the network corrects (the image channel is a residual on it)
 """
 from __future__ import annotations
 
@@ -88,6 +90,13 @@ def upsample2_backward(dy):
 
 def sigmoid(z):
     return 1.0 / (1.0 + np.exp(-z))
+
+
+def warm_start(o0, base, scale: float):
+    """The solver's start image from the network's image channel: the channel is a
+    residual on the base image in units of `scale`, clamped to the constraint f >= 0
+    of Eq. (2)."""
+    return np.maximum(np.asarray(base, dtype=np.float64) + scale * np.asarray(o0, dtype=np.float64), 0.0)
 
 
 def init_params(seed: int):

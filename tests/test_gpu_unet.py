@@ -182,7 +182,8 @@ def test_training_reduces_loss_on_fixed_batch():
 
 def test_pack_input_and_composed_head():
     """Input rows (two scaled planes, 14 zero channels) and the serving head
-    f0 = max(base + s o0, 0), w = sigmoid(o1), against numpy on the same BF16 inputs."""
+    f0 = max(base + s o0, 0), w = sigmoid(o1), against the oracle's head on the same BF16
+    inputs."""
     rng = np.random.Generator(np.random.PCG64(21))
     npix = 1000
     a = rng.uniform(0, 3, npix).astype(np.float32)
@@ -205,8 +206,8 @@ def test_pack_input_and_composed_head():
     E.eptv_unet_head(xt, torch.tensor(hw).to(DEV), torch.tensor(hb).to(DEV), f0=f0, w=w,
                      base=torch.tensor(base).to(DEV), f_scale=0.02)
     o = feats @ hw.T.astype(np.float64) + hb
-    assert np.allclose(f0.cpu().numpy(), np.maximum(base + 0.02 * o[:, 0], 0.0), rtol=0, atol=1e-6)
-    assert np.allclose(w.cpu().numpy(), 1.0 / (1.0 + np.exp(-o[:, 1])), rtol=0, atol=1e-5)
+    assert np.allclose(f0.cpu().numpy(), U.warm_start(o[:, 0], base, 0.02), rtol=0, atol=1e-6)
+    assert np.allclose(w.cpu().numpy(), U.sigmoid(o[:, 1]), rtol=0, atol=1e-5)
 
 
 def test_prior_weight_mode_matches_oracle():

@@ -344,23 +344,71 @@ def test_sigma_is_order_statistic(q):
 
 # ---------------------------------------------------------------- (P2) GD + Armijo
 
-def test_armijo_sufficient_decrease_every_step():
-    rng = np.random.Generator(np.random.PCG64(12))
+def _armijo_case():
+    """A 20 x 20 (P2) input with an edge (so that the weights vary) on which the default
+    line search backtracks and then accepts, fails, hits the t_max cap and grows the step
+    again after a short accepted one."""
+    rng = np.random.Generator(np.random.PCG64(13))
     v = rng.uniform(0, 0.03, (20, 20))
-    p = I.EptvParams(n_gd=12)
-    f = v.copy()
-    _, Tvx, _, Tvy = O.half_edges(v, p.eps)
-    sigma = O.select_sigma(Tvx, Tvy, p.sigma_q)
+    v[:, 10:] += 0.02
+    return v, I.EptvParams(n_gd=12, max_trials=6)
+
+
+def test_armijo_accepts_first_passing_trial_and_replays_to_the_result():
+    """Sec. 2.2 solves (P2) by gradient descent with Armijo's inexact line search: the
+    search tries t0, t0 s, t0 s^2, ... and takes the FIRST trial that decreases the
+    frozen-weight energy by at least c t |g|^2.  Every accepted step passes, every longer
+    trial before it fails (so a later, shorter passing trial is never taken), a failed
+    search tried max_trials steps that all fail, and replaying the accepted steps from v
+    reproduces the oracle's image."""
+    v, p = _armijo_case()
     fo, st = O.p2_solve(v, p, p.t_init_eff)
-    assert st.sigma == sigma
-    for t in st.steps:
-        g, wx, wy, E0 = O.p2_gradient(f, v, p.lam, p.eps, sigma)
+    _, Tvx, _, Tvy = O.half_edges(v, p.eps)
+    assert st.sigma == O.select_sigma(Tvx, Tvy, p.sigma_q)
+    assert len(st.steps) == len(st.trials) == p.n_gd
+    assert any(t > 0 and len(tr) > 1 for t, tr in zip(st.steps, st.trials))   # backtracked, then accepted
+    assert any(t == 0 for t in st.steps)                                       # a failed search
+    f = v.copy()
+    for t, tried in zip(st.steps, st.trials):
+        g, wx, wy, E0 = O.p2_gradient(f, v, p.lam, p.eps, st.sigma)
+        gg = float(np.sum(g * g))
+
+        def passes(tt):
+            return O.p2_energy_frozen(f - tt * g, v, p.lam, p.eps, wx, wy) <= E0 - p.armijo_c * tt * gg
+        ts = [tt for tt, _ in tried]
+        for a, b in zip(ts, ts[1:]):                       # trials shrink by the factor s
+            assert b == pytest.approx(a * p.armijo_shrink, rel=1e-15)
         if t > 0:
-            E1 = O.p2_energy_frozen(f - t * g, v, p.lam, p.eps, wx, wy)
-            assert E1 <= E0 - p.armijo_c * t * float(np.sum(g * g))
-            # the step before it (twice as long) was rejected unless it was the first trial
+            assert ts[-1] == t and passes(t)
+            assert not any(passes(tt) for tt in ts[:-1])
             f = f - t * g
-    assert np.allclose(f, fo)
+        else:
+            assert len(ts) == p.max_trials and not any(passes(tt) for tt in ts)
+    assert np.array_equal(f, fo)
+
+
+def test_armijo_first_trial_grows_from_the_previous_step():
+    """The first trial of each search is min(grow t_prev, t_max) (the reading of the
+    silent constants, grow = 2, t_max = 1/lambda): t_prev is the step accepted by the
+    previous GD iteration (or the initial 1/lambda), and after a failed search the next
+    search continues just below that search's last (shortest) trial."""
+    v, p = _armijo_case()
+    t_start = p.t_init_eff
+    _, st = O.p2_solve(v, p, t_start)
+    t_prev = t_start
+    grew = capped = after_fail = 0
+    for n, (t, tried) in enumerate(zip(st.steps, st.trials)):
+        t0 = tried[0][0]
+        assert t0 == pytest.approx(min(2.0 * t_prev, 1.0 / p.lam), rel=1e-15)
+        if n > 0 and st.steps[n - 1] > 0:
+            grew += t0 == pytest.approx(2.0 * st.steps[n - 1], rel=1e-15)
+        capped += t0 == 1.0 / p.lam
+        if n > 0 and st.steps[n - 1] == 0:
+            assert t0 == pytest.approx(st.trials[n - 1][-1][0] * p.armijo_shrink, rel=1e-15)
+            after_fail += 1
+        t_prev = t if t > 0 else tried[-1][0] * p.armijo_shrink / 2.0
+    assert st.t_prev == pytest.approx(t_prev, rel=1e-15)
+    assert grew >= 1 and capped >= 1 and after_fail >= 1     # every branch of the rule is met
 
 
 def test_plain_tv_p2_energy_monotone():
@@ -393,6 +441,78 @@ def test_reconstruct_positive_and_better_than_zero(c1_case):
     assert np.all(f >= 0)
     e = np.sum((f - c1_case.f_true) ** 2) / np.sum(c1_case.f_true ** 2)
     assert e < 0.05
+
+
+def _dense(op, g):
+    n = g.ny * g.nx
+    return np.stack([op.project(np.eye(n)[j].reshape(g.ny, g.nx)).ravel() for j in range(n)], 1)
+
+
+def test_outer_iteration_restarts_cgls_at_the_current_image():
+    """Sec. 2.2, step 1 with App. I: each outer iteration runs CGLS started at the current
+    (clamped) image f^(k), not at 0.  With M = 1 the CGLS step is the exact line search
+    along s = P^T (y - P f^(k)) (a closed form on the dense matrix); one fixed (P2) step
+    is v - t dJ(v) (at f = v the fidelity part of Eq. 9 vanishes); step 3 clamps.  Two
+    outer iterations from a non-zero warm start, composed by hand, equal the oracle's
+    reconstruction; starting CGLS at 0 instead moves the result by a large margin."""
+    g = I.FanGeometry(12, 10, 1.0, 1.0, 9, 24, 0.05, 0.25, 40.0, 70.0, I.ARC)
+    op = O.Operator(g)
+    P = _dense(op, g)
+    rng = np.random.Generator(np.random.PCG64(31))
+    truth = rng.uniform(0, 0.03, (g.ny, g.nx))
+    y = (P @ truth.ravel()).reshape(g.n_views, g.n_bins) + 1e-3 * rng.standard_normal((g.n_views, g.n_bins))
+    f0 = rng.uniform(-0.01, 0.05, (g.ny, g.nx))       # warm start, clamped on entry
+    p = I.EptvParams(cgls_iters=1, n_gd=1, step_rule=O.FIXED, t_fixed=2e-4, lam=50.0)
+
+    def by_hand(fk):
+        r0 = y.ravel() - P @ fk.ravel()
+        s0 = P.T @ r0
+        q = P @ s0
+        a = float(q @ r0) / float(q @ q)
+        v = fk + (a * s0).reshape(fk.shape)
+        _, Tx, _, Ty = O.half_edges(v, p.eps)
+        sigma = O.select_sigma(Tx, Ty, p.sigma_q)
+        dJ, _, _, _ = O.p2_gradient(v, v, p.lam, p.eps, sigma)
+        return np.maximum(v - p.t_fixed * dJ, 0.0)
+
+    f1 = by_hand(np.maximum(f0, 0.0))
+    f2 = by_hand(f1)
+    got = O.reconstruct(op, y, p, f0=f0, n_outer=2)
+    assert np.allclose(got, f2, rtol=1e-10, atol=1e-14)
+    # start-point sensitivity: the same composition with CGLS from 0 is far away
+    r0 = y.ravel()
+    s0 = P.T @ r0
+    q = P @ s0
+    v0 = ((float(q @ r0) / float(q @ q)) * s0).reshape(g.ny, g.nx)
+    assert np.linalg.norm(v0 - f1) > 0.05 * np.linalg.norm(f1)
+
+
+def test_outer_loop_carries_the_armijo_step_across_iterations():
+    """Default solver (M = 3, Armijo): each outer iteration is CGLS_M from the clamped
+    f^(k), then (P2) started at v with the previous (P2) solve's last step t_prev, then the
+    clamp; the first (P2) starts from t_prev = 1/lambda."""
+    g = I.FanGeometry(16, 16, 1.0, 1.0, 12, 32, 0.045, 0.25, 60.0, 100.0, I.ARC)
+    op = O.Operator(g)
+    rng = np.random.Generator(np.random.PCG64(32))
+    truth = np.zeros((16, 16))
+    truth[4:12, 3:9] = 0.02
+    truth[6:10, 9:13] = 0.035
+    y = op.project(truth) + 2e-3 * rng.standard_normal((12, 32))
+    p = I.EptvParams(n_gd=6, lam=200.0)
+    f = np.zeros((16, 16))
+    t_prev = 1.0 / p.lam
+    lens = []
+    for _ in range(3):
+        v = O.cgls(op, y, f, 3)
+        f, st = O.p2_solve(v, p, t_prev)
+        lens.append(st.trials[0][0][0])
+        t_prev = st.t_prev
+        f = np.maximum(f, 0.0)
+    log = O.ReconLog()
+    got = O.reconstruct(op, y, p, n_outer=3, log=log)
+    assert np.array_equal(got, f)
+    assert log.t_prev == t_prev
+    assert [tr[0][0][0] for tr in log.trials] == lens
 
 
 def test_prior_edge_weights_hand_example():

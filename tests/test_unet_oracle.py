@@ -1,6 +1,8 @@
 """Pins of the FP64 U-Net oracle: the convolution against scipy's correlation, every
 backward pass against central finite differences of the forward pass, pooling and
 upsampling against hand-worked examples."""
+import math
+
 import numpy as np
 import pytest
 from scipy import signal
@@ -74,3 +76,39 @@ def test_network_gradients_finite_differences():
         lm, _ = U.loss_and_grads(pm, x, f_t, w_t)
         fd = (lp - lm) / (2 * h)
         assert grads[layer][which][idx] == pytest.approx(fd, rel=1e-5, abs=1e-9), (layer, which, idx)
+
+
+def test_forward_head_hand_example():
+    """All 3x3 weights zero: every convolution outputs its bias, so the last decoder layer
+    is the constant relu(b9) per channel and the head is o_k = hb_k + sum_c hW[k, c] relu(b9_c).
+    Chosen so that o0 = 0.3 and o1 = ln 3: f0 = 0.3 and w = sigmoid(ln 3) = 3/4 at every
+    pixel; a negative bias channel is cut by the ReLU.  The loss is then a hand-computed
+    mean of squares, and the served warm start max(base + 0.02 o0, 0) is clamped where the
+    base is below -0.006."""
+    params = U.init_params(0)
+    for k in range(10):
+        params[k][0] = np.zeros_like(params[k][0])
+        params[k][1] = np.full_like(params[k][1], 0.5)
+    params[9][1] = np.zeros(16)
+    params[9][1][:3] = [1.0, 2.0, -4.0]                  # relu -> 1, 2, 0
+    hW = np.zeros((2, 16))
+    hW[0, :3] = [0.1, 0.05, 7.0]                         # o0 = 0.1 + 0.1 + 0 + hb0
+    hW[1, :3] = [0.5, 0.0, 9.0]                          # o1 = 0.5 + 0 + hb1
+    params[10] = [hW, np.array([0.1, math.log(3.0) - 0.5])]
+    rng = np.random.Generator(np.random.PCG64(7))
+    x = rng.uniform(0, 1, (2, 8, 8))
+    f0, w, cache = U.forward(params, x)
+    assert np.allclose(f0, 0.3, rtol=0, atol=1e-15)
+    assert np.allclose(w, 0.75, rtol=0, atol=1e-15)
+    f_t = np.full((8, 8), 0.1)
+    f_t[0, :] = 0.5
+    w_t = np.full((8, 8), 0.25)
+    loss, _ = U.loss_and_grads(params, x, f_t, w_t)
+    want = (56 * 0.2 ** 2 + 8 * 0.2 ** 2) / 64 + 0.5 ** 2
+    assert loss == pytest.approx(want, rel=1e-14)
+    params[10][1][1] = -math.log(3.0) - 0.5              # o1 = -ln 3 -> w = 1/4
+    _, w2, _ = U.forward(params, x)
+    assert np.allclose(w2, 0.25, rtol=0, atol=1e-15)
+    base = np.array([[0.01, -0.006, -0.01], [0.0, 0.02, -0.0061]])
+    got = U.warm_start(np.full(base.shape, 0.3), base, 0.02)
+    assert np.allclose(got, [[0.016, 0.0, 0.0], [0.006, 0.026, 0.0]], rtol=0, atol=1e-15)

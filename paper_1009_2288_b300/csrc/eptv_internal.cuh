@@ -63,7 +63,8 @@ enum Scalar {
     SC_SEL_PREFIX,   // radix select: fixed bit prefix (as double, exact below 2^53)
     SC_SEL_RANK,     // radix select: remaining 1-based rank within the prefix
     SC_Q0,           // image-quality sums (quality.cu): SC_Q0 .. SC_Q0 + 8
-    SC_COUNT = SC_Q0 + 9
+    SC_TIMEOUT = SC_Q0 + 9,   // set to 1 when a bounded device wait ran out
+    SC_COUNT
 };
 constexpr int kScalarStride = 32;   // doubles per slice (>= SC_COUNT)
 
@@ -107,6 +108,10 @@ struct SliceDev {
     // launches)
     unsigned int *ctr;
     unsigned long long *acc;
+    // persistent (P2) kernel K4p: the batch's grid-barrier counter and this slice's three
+    // rotating exact-accumulator sets; both zeroed by the sigma selection before each K4p
+    unsigned int *p2bar;
+    unsigned long long *p2acc;
     // stored operator (null unless selected): SELL-32 P (rows = rays), P^T (rows = pixels)
     const int *p_sptr, *p_slen, *p_scol;
     const float *p_sval;
@@ -271,41 +276,109 @@ __device__ __forceinline__ double acc_round(const long long (&w)[kAccChunks], un
         if (i == h - 2) d2 = dg[i];
         if (i < h - 2) sticky |= dg[i] != 0u;
     }
-    // the top 64 bits of the magnitude, a sticky bit for the rest, one rounding
+    // the top 64 bits of the magnitude (leading one at bit 63) and a sticky bit for the
+    // rest; the value is t64 2^e.  Rounded to 53 bits, nearest even, in integer arithmetic
+    // (|total| < 2^235: no overflow; >= 2^-149: no subnormal)
     const int lz = __clz((unsigned int)d0);
     const unsigned long long top = (d0 << 32) | d1;
     const unsigned long long t64 = lz ? ((top << lz) | (d2 >> (32 - lz))) : top;
     sticky |= (lz ? ((d2 << lz) & 0xFFFFFFFFull) : d2) != 0ull;
-    const double v = scalbn(__ull2double_rn(t64 | (sticky ? 1ull : 0ull)), 32 * (h - 1) - lz + kAccLsbExp);
-    return neg ? -v : v;
+    int e = 32 * (h - 1) - lz + kAccLsbExp;
+    unsigned long long m = t64 >> 11;                      // 53 bits
+    const unsigned long long rest = t64 & 0x7FFull;
+    const bool half = (rest & 0x400ull) != 0;
+    const bool below = (rest & 0x3FFull) != 0 || sticky;
+    if (half && (below || (m & 1ull))) {
+        ++m;
+        if (m >> 53) { m >>= 1; ++e; }
+    }
+    const unsigned long long biased = (unsigned long long)(e + 11 + 52 + 1023);
+    const unsigned long long bits = (biased << 52) | (m & 0xFFFFFFFFFFFFFull) | (neg ? (1ull << 63) : 0ull);
+    return __longlong_as_double((long long)bits);
+}
+
+// Adds the FP32 value x exactly into one accumulator copy (kAccStride words, global or
+// shared memory): its 24-bit significand lands in at most two 32-bit chunks, with integer
+// atomics only (no FP64 arithmetic).  Same total as acc_add((double)x).
+__device__ __forceinline__ void acc_add_f32(unsigned long long *acc, float x) {
+    const unsigned int b = __float_as_uint(x);
+    const bool neg = (b >> 31) != 0;
+    const int ex = (int)((b >> 23) & 0xFFu);
+    unsigned int m = b & 0x7FFFFFu;
+    if (ex == 0xFF) {
+        atomicOr(acc + kAccChunks, m ? kAccNaN : (neg ? kAccNegInf : kAccPosInf));
+        return;
+    }
+    if (ex) m |= 0x800000u;
+    if (m == 0u) return;
+    const int sh = (ex ? ex : 1) - 1;                       // |x| = m 2^(sh + kAccLsbExp)
+    const int c = sh >> 5, r = sh & 31;
+    const unsigned long long v = (unsigned long long)m << r;  // < 2^55
+    const unsigned long long lo = v & 0xFFFFFFFFull, hi = v >> 32;
+    atomicAdd(acc + c, neg ? (0ull - lo) : lo);
+    if (hi) atomicAdd(acc + c + 1, neg ? (0ull - hi) : hi);
 }
 
 // All NT threads of a block (NT a multiple of 32), after every contribution is visible:
 // res[k] = the total of value k (k < NV) over its kAccCopies copies (acc[k][copy][word]);
-// re-zeroes the accumulators.  Lane groups of kAccCopies read one copy each and add the
-// words with shuffles (integer sums: exact).
-template <int NV, int NT>
+// re-zeroes the accumulators unless ZERO is false.  Lane groups of kAccCopies read one copy
+// each and add the words with shuffles (integer sums: exact).
+template <int NV, int NT, bool ZERO = true, int C = kAccCopies>
 __device__ __forceinline__ void acc_read(unsigned long long *acc, double *res) {
-    for (int base = 0; base < NV * kAccCopies; base += NT) {
+    static_assert(C >= 1 && C <= kAccCopies && (C & (C - 1)) == 0, "copies: a power of two");
+    for (int base = 0; base < NV * C; base += NT) {
         const int t = base + (int)threadIdx.x;
-        const bool mine = t < NV * kAccCopies;
+        const bool mine = t < NV * C;
         long long w[kAccChunks];
         unsigned long long fl = 0ull;
-        unsigned long long *a = acc + (size_t)(mine ? t : 0) * kAccStride;
+        unsigned long long *a = acc + ((size_t)(mine ? (t / C) * kAccCopies + t % C : 0)) * kAccStride;
 #pragma unroll
         for (int i = 0; i < kAccChunks; ++i) w[i] = mine ? (long long)__ldcg(a + i) : 0ll;
         if (mine) {
             fl = __ldcg(a + kAccChunks);
+            if (ZERO) {
 #pragma unroll
-            for (int i = 0; i < kAccStride; ++i) a[i] = 0ull;
+                for (int i = 0; i < kAccStride; ++i) a[i] = 0ull;
+            }
         }
 #pragma unroll
-        for (int o = 1; o < kAccCopies; o <<= 1) {
+        for (int o = 1; o < C; o <<= 1) {
 #pragma unroll
             for (int i = 0; i < kAccChunks; ++i) w[i] += __shfl_xor_sync(0xffffffffu, w[i], o);
             fl |= __shfl_xor_sync(0xffffffffu, fl, o);
         }
-        if (mine && (t % kAccCopies) == 0) res[t / kAccCopies] = acc_round(w, fl);
+        if (mine && (t % C) == 0) res[t / C] = acc_round(w, fl);
+    }
+}
+
+// One warp: the FP32 warp sums of its NV per-thread values, each added exactly (integer
+// atomics) into the block's shared accumulator sacc[k] (kAccStride words) by lane k.
+template <int NV>
+__device__ __forceinline__ void warp_acc(const float (&v)[NV], unsigned long long *sacc) {
+    static_assert(NV <= 32, "one lane per value");
+    const int lane = threadIdx.x & 31;
+    float mine = 0.0f;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        const float sv = warp_sum(v[k]);
+        if (lane == k) mine = sv;
+    }
+    if (lane < NV) acc_add_f32(sacc + lane * kAccStride, mine);
+}
+
+// All NT threads, after the block's contributions to sacc are complete (__syncthreads):
+// adds the nonzero words of the block's shared accumulators (NV values) into copy `copy`
+// of the global accumulators gacc ([value][kAccCopies][kAccStride] words).
+template <int NV, int NT>
+__device__ __forceinline__ void acc_push(const unsigned long long *sacc, unsigned long long *gacc, int copy) {
+    for (int w = threadIdx.x; w < NV * kAccStride; w += NT) {
+        const int k = w / kAccStride, i = w - k * kAccStride;
+        const unsigned long long x = sacc[w];
+        if (x) {
+            unsigned long long *dst = gacc + ((size_t)k * kAccCopies + copy) * kAccStride + i;
+            if (i == kAccChunks) atomicOr(dst, x);
+            else atomicAdd(dst, x);
+        }
     }
 }
 

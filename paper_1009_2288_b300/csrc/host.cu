@@ -61,7 +61,7 @@ struct DevMem {
 
 struct GraphCache {
     cudaGraphExec_t exec = nullptr;
-    int key[10] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1};
+    int key[12] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1};
     long long kernels = 0;     // kernel nodes in the captured outer iteration
     void reset() {
         if (exec) cudaGraphExecDestroy(exec);
@@ -206,11 +206,21 @@ static int build_batch(Batch &B, DevMem &mem, const std::vector<SliceDev> &sds) 
     }
     if ((rc = mem.alloc(&B.d_hist, (size_t)B.n * kHistBins))) return rc;
     if ((rc = mem.alloc(&B.d_params, 1))) return rc;
+    const size_t p2words = (size_t)kP2Sets * kP2SetWords;
+    if ((rc = mem.alloc(&B.d_p2start, (size_t)B.n + 1))) return rc;
+    if ((rc = mem.alloc(&B.d_p2bar, 1))) return rc;
+    if ((rc = mem.alloc(&B.d_p2acc, (size_t)B.n * p2words))) return rc;
+    for (int i = 0; i < B.n; ++i) {
+        B.h_sd[i].p2bar = B.d_p2bar;
+        B.h_sd[i].p2acc = B.d_p2acc + (size_t)i * p2words;
+    }
     CU(cudaMemcpy(B.d_sd, B.h_sd.data(), sizeof(SliceDev) * B.n, cudaMemcpyHostToDevice));
     CU(cudaMemcpy(B.d_start, B.h_start.data(), sizeof(int) * B.h_start.size(), cudaMemcpyHostToDevice));
     CU(cudaMemset(B.d_counters, 0, sizeof(unsigned int) * (size_t)B.n * cstride));
     CU(cudaMemset(B.d_acc, 0, sizeof(unsigned long long) * (size_t)B.n * astride));
     CU(cudaMemset(B.d_hist, 0, sizeof(unsigned int) * (size_t)B.n * kHistBins));
+    CU(cudaMemset(B.d_p2bar, 0, sizeof(unsigned int)));
+    CU(cudaMemset(B.d_p2acc, 0, sizeof(unsigned long long) * (size_t)B.n * p2words));
     return 0;
 }
 
@@ -266,10 +276,40 @@ static void enqueue_cgls(const Batch &B, int M, bool have_uT, cudaStream_t st) {
     }
 }
 
-// (P2) + clamp on v = u: sigma, n_gd fused GD iterations, apply + clamp into u, u^T.
+// Chooses the persistent (P2) kernel's launch plan for batch B and parameters p (outside
+// any stream capture: it may upload the region map).  B.p2.ok == 0 selects the
+// per-iteration K4 launches.
+static int ensure_p2(Batch &B, const eptv_params *p, cudaStream_t st) {
+    P2Plan plan;
+    p2_plan(B, n_trials_of(p), p->n_gd, &plan);
+    if (plan.ok && (plan.rtx != B.p2_rtx || plan.rty != B.p2_rty)) {
+        p2_region_starts(B, plan.rtx, plan.rty, B.h_p2start);
+        CU(cudaMemcpyAsync(B.d_p2start, B.h_p2start.data(), sizeof(int) * B.h_p2start.size(),
+                           cudaMemcpyHostToDevice, st));
+        CU(cudaStreamSynchronize(st));
+        B.p2_rtx = plan.rtx;
+        B.p2_rty = plan.rty;
+    }
+    B.p2 = plan;
+    return 0;
+}
+
+// (P2) + clamp on v = u: sigma, then either the persistent kernel K4p (all n_gd GD
+// iterations, apply + clamp into u, u^T) or n_gd fused GD launches of K4 and K4u.
 static void enqueue_p2(const Batch &B, const eptv_params *p, const float *v_override,
                        float *out_override, cudaStream_t st) {
     launch_sigma(B, v_override, st);
+    if (B.p2.ok && p->n_gd >= 1) {
+        P2Args pa{};
+        pa.v = v_override;
+        pa.out = out_override;
+        pa.n_gd = p->n_gd;
+        pa.n_trials = n_trials_of(p);
+        pa.bar_extra = B.p2_bar_extra;
+        pa.wait_cycles = B.p2_wait_cycles;
+        launch_p2(B, B.p2, pa, st);   // a failure surfaces in the caller's launch check / capture
+        return;
+    }
     for (int n = 0; n < p->n_gd; ++n) {
         GdArgs ga{};
         ga.first = (n == 0);
@@ -289,8 +329,8 @@ static void enqueue_outer(const Batch &B, const eptv_params *p, cudaStream_t st)
 
 // Capture one outer iteration of batch B into a graph (cached per structural key).
 static int outer_graph(const Batch &B, GraphCache &gc, cudaStream_t cap, const eptv_params *p) {
-    const int key[10] = {p->cgls_iters, p->n_gd, n_trials_of(p), p->step_rule, B.n, B.k1_seg, B.k2_vg,
-                         B.stored, B.bp_eq11, B.stored_pt};
+    const int key[12] = {p->cgls_iters, p->n_gd, n_trials_of(p), p->step_rule, B.n, B.k1_seg, B.k2_vg,
+                         B.stored, B.bp_eq11, B.stored_pt, B.p2.ok, B.p2.rtx * 16 + B.p2.rty};
     if (gc.exec && memcmp(key, gc.key, sizeof key) == 0) return 0;
     gc.reset();
     cudaGraph_t graph = nullptr;
@@ -747,12 +787,15 @@ int eptv_tv_step(const eptv_geometry *gc, const eptv_params *p, const float *d_v
     launch_set_scalar(g->B, SC_NFAIL_P2, 0.0, st);
     launch_set_scalar(g->B, SC_NACC_P2, 0.0, st);
     launch_set_scalar(g->B, SC_NONFINITE, 0.0, st);
+    launch_set_scalar(g->B, SC_TIMEOUT, 0.0, st);
+    if ((rc = ensure_p2(g->B, p, st))) return rc;
     enqueue_p2(g->B, p, d_v, d_f, st);
     if ((rc = launch_check())) return rc;
     if ((rc = upload_sd(g->B, st))) return rc;     // clear the weights pointer for later calls
     if (t_prev_io || out_opt) {
         double sc[kScalarStride];
         if ((rc = read_scalars(sd, sc, st))) return rc;
+        if (sc[SC_TIMEOUT] != 0.0) return fail(EPTV_ERR_TIMEOUT, "a bounded device wait of the (P2) kernel ran out");
         if (sc[SC_NONFINITE] != 0.0) return fail(EPTV_ERR_NONFINITE, "non-finite value in the TV step");
         if (t_prev_io) *t_prev_io = sc[SC_TPREV];
         if (out_opt) {
@@ -773,6 +816,8 @@ static int run_outer(Batch &B, GraphCache &gc, cudaStream_t cap, const eptv_para
                      cudaStream_t st) {
     int rc;
     if ((rc = upload_sd(B, st)) || (rc = upload_params(B, p, st))) return rc;
+    if ((rc = ensure_p2(B, p, st))) return rc;
+    launch_set_scalar(B, SC_TIMEOUT, 0.0, st);
     // f^(0): clamp the start image, build its transpose, reset the per-slice state
     launch_gd_finish(B, 0, nullptr, nullptr, st);
     launch_set_scalar(B, SC_OUTER, 0.0, st);
@@ -781,7 +826,15 @@ static int run_outer(Batch &B, GraphCache &gc, cudaStream_t cap, const eptv_para
     launch_set_scalar(B, SC_NONFINITE, 0.0, st);
     if ((rc = launch_check())) return rc;
     if (p->n_outer == 0) return 0;
-    if ((rc = outer_graph(B, gc, cap, p))) return rc;
+    if ((rc = outer_graph(B, gc, cap, p))) {
+        if (!B.p2.ok) return rc;
+        // a cooperative launch this driver does not capture: per-iteration K4 launches
+        cudaGetLastError();
+        B.p2_disabled = 1;
+        B.p2 = P2Plan{};
+        gc.reset();
+        if ((rc = outer_graph(B, gc, cap, p))) return rc;
+    }
     for (int k = 0; k < p->n_outer; ++k) CU(cudaGraphLaunch(gc.exec, st));
     g_launch_count += gc.kernels * p->n_outer;
     return 0;
@@ -826,6 +879,7 @@ int eptv_reconstruct(const eptv_geometry *gc, const eptv_params *p, const float 
         rep_opt->n_launches = nl;
         double sc[kScalarStride];
         if ((rc = read_scalars(sd, sc, st))) return rc;
+        if (sc[SC_TIMEOUT] != 0.0) return fail(EPTV_ERR_TIMEOUT, "a bounded device wait of the (P2) kernel ran out");
         if (sc[SC_NONFINITE] != 0.0) return fail(EPTV_ERR_NONFINITE, "non-finite value during the reconstruction");
         rep_opt->n_outer = p->n_outer;
         rep_opt->sigma_last = sc[SC_SIGMA];
@@ -929,6 +983,7 @@ int eptv_reconstruct_batched(int n, eptv_geometry *const *geoms, const eptv_para
     BatchCache &bc = g0->batch;
     cudaStreamSynchronize(st);
     if ((rc = acquire_batch(n, geoms, bc))) return rc;
+    bc.B.p2_forbid = g0->B.p2_forbid;
     for (int i = 0; i < n; ++i) {
         SliceDev &sd = bc.B.h_sd[i];
         sd.sel_rank = std::min<long long>(std::max<long long>((long long)std::ceil(p->sigma_q * sd.n_edges), 1), sd.n_edges);
@@ -947,6 +1002,7 @@ int eptv_reconstruct_batched(int n, eptv_geometry *const *geoms, const eptv_para
         for (int i = 0; i < n; ++i) {
             double sc[kScalarStride];
             if ((rc = read_scalars(bc.B.h_sd[i], sc, st))) return rc;
+            if (sc[SC_TIMEOUT] != 0.0) return fail(EPTV_ERR_TIMEOUT, "a bounded device wait ran out in slice %d", i);
             if (sc[SC_NONFINITE] != 0.0) return fail(EPTV_ERR_NONFINITE, "non-finite value in slice %d", i);
             reps[i].n_outer = p->n_outer;
             reps[i].n_launches = nl;
@@ -956,6 +1012,24 @@ int eptv_reconstruct_batched(int n, eptv_geometry *const *geoms, const eptv_para
             reps[i].status = reps[i].n_fail ? EPTV_WARN_LINESEARCH : EPTV_OK;
         }
     }
+    return 0;
+}
+
+int eptv_set_tv_kernel(eptv_geometry *g, int mode) {
+    if (!g) return fail(EPTV_ERR_ARG, "NULL handle");
+    if (mode != EPTV_TV_AUTO && mode != EPTV_TV_PER_ITERATION) return fail(EPTV_ERR_ARG, "bad tv kernel mode %d", mode);
+    g->B.p2_forbid = mode == EPTV_TV_PER_ITERATION;
+    g->batch.B.p2_forbid = g->B.p2_forbid;
+    return 0;
+}
+
+int eptv_debug_set_p2_wait(eptv_geometry *g, int extra_blocks, long long wait_cycles) {
+    if (!g) return fail(EPTV_ERR_ARG, "NULL handle");
+    if (extra_blocks < 0 || extra_blocks > 1024 || wait_cycles < 1000 || wait_cycles > 4000000000ll)
+        return fail(EPTV_ERR_ARG, "extra_blocks in [0, 1024], wait_cycles in [1e3, 4e9]");
+    g->B.p2_bar_extra = extra_blocks;
+    g->B.p2_wait_cycles = wait_cycles;
+    g->graph.reset();     // the captured launch carries the old values
     return 0;
 }
 

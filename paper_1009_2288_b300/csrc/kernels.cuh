@@ -58,6 +58,13 @@ struct BackArgs {
     int eq11;                   // the interpolating back projector of Eq. (11) for this call
 };
 
+// Launch plan of K4p for a batch: region shape (tiles), trial template, block size, grid.
+struct P2Plan {
+    int ok = 0;
+    int rtx = 0, rty = 0, kt = 0, nt = 0, blocks = 0;
+    size_t smem = 0;
+};
+
 struct Batch {
     int n = 0;
     SliceDev *d_sd = nullptr;
@@ -74,6 +81,18 @@ struct Batch {
     int stored = 0;        // 1: P and P^T are applied from the stored matrices (stored.cu)
     int stored_pt = 0;     // 1: only P^T is applied from the stored matrix (P on the fly)
     int bp_eq11 = 0;       // 1: P^T is the interpolating back projector of Eq. (11)
+    // persistent (P2) kernel K4p (tv_p2.cu): region starts of the current plan, the grid
+    // barrier counter, the accumulator sets, and the plan the starts were uploaded for
+    int *d_p2start = nullptr;             // [n + 1]
+    unsigned int *d_p2bar = nullptr;      // [1]
+    unsigned long long *d_p2acc = nullptr;  // [n][3][kPartialStride][kAccCopies][kAccStride]
+    int p2_rtx = 0, p2_rty = 0;           // shape whose starts are in d_p2start (0: none)
+    std::vector<int> h_p2start;
+    int p2_disabled = 0;                  // 1: cooperative capture failed: per-iteration K4
+    int p2_forbid = 0;                    // 1: the caller asked for per-iteration K4
+    int p2_bar_extra = 0;                 // test hook: phantom blocks the barrier waits for
+    long long p2_wait_cycles = 2000000000ll;  // bound of one barrier wait (~1 s at 2 GHz)
+    P2Plan p2;                            // plan of the next (P2) solves (ok = 0: K4)
     TileMap map(int fam) const { return TileMap{d_start + fam * (n + 1), n}; }
     int blocks(int fam) const { return h_start[fam * (n + 1) + n]; }
 };
@@ -109,6 +128,22 @@ struct GdArgs {
     float *fout, *gout;      // outputs (null: slice ping-pong)
     int write_f;             // store the iterate
 };
+
+// Arguments of the persistent (P2) kernel K4p (its barrier counter and accumulator sets
+// are SliceDev::p2bar / p2acc: kP2Sets sets of kP2SetWords words per slice).
+constexpr int kP2Sets = 3;
+constexpr size_t kP2SetWords = (size_t)kPartialStride * kAccCopies * kAccStride;
+struct P2Args {
+    const float *v;               // (P2) input (null: S.u)
+    float *out;                   // result max(f, 0) (null: S.u and S.uT)
+    int n_gd, n_trials;
+    int bar_extra;                // blocks the barrier waits for beyond the grid (tests: > 0)
+    long long wait_cycles;        // bound of one barrier wait in SM cycles
+};
+
+int p2_plan(Batch &B, int n_trials, int n_gd, P2Plan *plan);
+void p2_region_starts(const Batch &B, int rtx, int rty, std::vector<int> &starts);
+cudaError_t launch_p2(const Batch &B, const P2Plan &plan, const P2Args &pa, cudaStream_t st);
 
 // Stored-matrix operator (stored.cu): device CSR matrices of P (rows = rays) and P^T
 // (rows = pixels), rows padded to multiples of 4 entries.

@@ -19,21 +19,11 @@
 
 #include "eptv_internal.cuh"
 #include "kernels.cuh"
+#include "tv_stencil.cuh"
 
 namespace eptv {
 
 // ------------------------------------------------------------------ half-edge stencil
-
-// T^2 of the x half-edge between pixels a=(i-1,j) and b=(i,j) given the six values
-// around it: a_d, b_d (row j-1), a, b (row j), a_u, b_u (row j+1).  Eq. (A3).
-__device__ __forceinline__ float edge_T2(float eps2, float a, float b, float a_u, float b_u,
-                                         float a_d, float b_d, float *D) {
-    const float d = b - a;
-    const float mc = 0.5f * (a + b), mu = 0.5f * (a_u + b_u), md = 0.5f * (a_d + b_d);
-    const float cu = mu - mc, cd = mc - md;
-    *D = d;
-    return eps2 + d * d + 0.5f * cu * cu + 0.5f * cd * cd;
-}
 
 __device__ __forceinline__ float img_at(const float *f, int nx, int ny, int i, int j) {
     return (i >= 0 && i < nx && j >= 0 && j < ny) ? __ldg(f + (size_t)j * nx + i) : 0.0f;
@@ -220,6 +210,13 @@ k5_radix_pass(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__
     }
     const int b0 = __ldg(map.start + si);
     const int nblk = __ldg(map.start + si + 1) - b0;
+    if (pass == 2 && !vals_override && S.p2acc) {
+        // re-arm the persistent (P2) kernel that follows: zero accumulator sets and barrier
+        const long long words = (long long)kP2Sets * (long long)kP2SetWords;
+        for (long long w = (long long)local * 256 + threadIdx.x; w < words; w += (long long)nblk * 256)
+            S.p2acc[w] = 0ull;
+        if (si == 0 && local == 0 && threadIdx.x == 0) *S.p2bar = 0u;
+    }
     if (!last_block_of_slice(S.ctr, nblk, &last_flag)) return;
     const long long rank0 = vals_override ? rank_override : S.sel_rank;
     const unsigned int key = sel_scan(hist, S.sc, pass, rank0, s_cnt, &s_res);
@@ -267,7 +264,7 @@ k4_gd(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__restrict
     __shared__ float QY[QYH][QYW], TYs[QYH][QYW], WY[QYH][QYW];
     __shared__ float s_t[KT];
     __shared__ double s_td[KT];
-    __shared__ double rsm[(KT + 4) * (kGdThreads / 32)];
+    __shared__ unsigned long long sacc[(KT + 4) * kAccStride];
     __shared__ float s_tapply;
     __shared__ int last_flag;
 
@@ -299,21 +296,10 @@ k4_gd(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__restrict
     const float sig = (float)S.sc[SC_SIGMA];
     const float inv_s2 = 1.0f / (sig * sig);
 
+    for (int w = tid; w < (KT + 4) * kAccStride; w += kGdThreads) sacc[w] = 0ull;
+    (void)partials;
     if (tid == 0) s_tapply = ga.first ? 0.0f : (float)S.sc[SC_TSTEP];
-    if (tid == 0 && K > 0) {
-        // trial steps t0, t0 s, t0 s^2, ... (repeated products: exact for s = 1/2)
-        double t;
-        if (P->step_rule == EPTV_STEP_FIXED) t = P->t_fixed;
-        else {
-            const double tmax = P->t_max > 0.0 ? P->t_max : 1.0 / P->lambda;
-            t = fmin(P->armijo_grow * S.sc[SC_TPREV], tmax);
-        }
-        for (int m = 0; m < K; ++m) {
-            s_t[m] = (float)t;
-            s_td[m] = (double)(float)t;
-            t *= P->armijo_shrink;
-        }
-    }
+    if (tid == 0 && K > 0) trial_steps(P, S.sc[SC_TPREV], K, s_t, s_td);
     __syncthreads();
     const float tap = s_tapply;
 
@@ -352,204 +338,79 @@ k4_gd(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__restrict
             // x-edge: between (e-1, j) and (e, j); F rows a .. a+2, columns b, b+1
             const int e = X0 - 1 + b, j = Y0 - 1 + a;
             float q = 0.f, T = 0.f, w = 0.f;
-            if (e >= 0 && e <= nx && j >= 0 && j < ny) {
-                float D;
-                const float T2 = edge_T2(eps2, f10, f11, F[a + 2][b], F[a + 2][b + 1], f00, f01, &D);
-                const float rs = rsqrtf(T2);           // T2 >= eps^2 > 0
-                T = T2 * rs;
-                if (mode == EPTV_WEIGHTS_EPTV) w = __expf(-T2 * inv_s2);
-                else if (mode == EPTV_WEIGHTS_ONE) w = 1.0f;
-                else w = 0.5f * (W[a + 1][b] + W[a + 1][b + 1]);
-                q = w * D * rs;
-            }
+            if (e >= 0 && e <= nx && j >= 0 && j < ny)
+                edge_eval(mode, eps2, inv_s2, f10, f11, F[a + 2][b], F[a + 2][b + 1], f00, f01,
+                          W[a + 1][b], W[a + 1][b + 1], &q, &T, &w);
             QX[a][b] = q; TXs[a][b] = T; WX[a][b] = w;
         }
         if (b < QYW) {
             // y-edge: between (i, e-1) and (i, e); F rows a, a+1, columns b .. b+2
             const int e = Y0 - 1 + a, i = X0 - 1 + b;
             float q = 0.f, T = 0.f, w = 0.f;
-            if (e >= 0 && e <= ny && i >= 0 && i < nx) {
-                float D;
-                const float T2 = edge_T2(eps2, f01, f11, F[a][b + 2], F[a + 1][b + 2], f00, f10, &D);
-                const float rs = rsqrtf(T2);
-                T = T2 * rs;
-                if (mode == EPTV_WEIGHTS_EPTV) w = __expf(-T2 * inv_s2);
-                else if (mode == EPTV_WEIGHTS_ONE) w = 1.0f;
-                else w = 0.5f * (W[a][b + 1] + W[a + 1][b + 1]);
-                q = w * D * rs;
-            }
+            if (e >= 0 && e <= ny && i >= 0 && i < nx)
+                edge_eval(mode, eps2, inv_s2, f01, f11, F[a][b + 2], F[a + 1][b + 2], f00, f10,
+                          W[a][b + 1], W[a + 1][b + 1], &q, &T, &w);
             QY[a][b] = q; TYs[a][b] = T; WY[a][b] = w;
         }
     }
     __syncthreads();
 
     // phase 3: g = lambda (f - v) + dJ/df on the g region (Eq. 9, A2)
-    float sA = 0.f, sB = 0.f, sF = 0.f, sJ = 0.f;
     for (int idx = tid; idx < GH * GW; idx += kGdThreads) {
         const int yy = idx / GW, xx = idx - yy * GW;
         const int i = X0 - 1 + xx, j = Y0 - 1 + yy;
         float g = 0.0f;
         if (i >= 0 && i < nx && j >= 0 && j < ny) {
             const float f = F[yy + 1][xx + 1];
-            const float d = f - V[yy][xx];
-            const float div = (QX[yy][xx + 1] - QX[yy][xx]) + (QY[yy + 1][xx] - QY[yy][xx]);
-            g = lam * d - div;
+            float d;
+            g = grad_value(lam, f, V[yy][xx], QX[yy][xx], QX[yy][xx + 1], QY[yy][xx], QY[yy + 1][xx], &d);
             if (xx >= 1 && xx <= kTileW && yy >= 1 && yy <= kGdTileH) {
                 const int p = j * nx + i;
                 gout[p] = g;
                 if (ga.write_f) fout[p] = f;
-                sA = fmaf(g, d, sA);
-                sB = fmaf(g, g, sB);
-                sF = fmaf(d, d, sF);
             }
         }
         G[yy][xx] = g;
     }
     __syncthreads();
 
-    // phase 4: owned half-edges of the tile -- energy and trial energy changes.  One pass
-    // over the union of the owned x-edges ((kTileW + 1) x kGdTileH) and y-edges
-    // (kTileW x (kGdTileH + 1)): position (a, b) holds x-edge (a, b) and y-edge (a, b),
-    // which share four F and four G values; an edge that is not owned here gets weight 0
-    // and adds exact zeros.
+    // phase 4: the tile's sums -- fidelity, energy and trial energy changes of its owned
+    // half-edges (the same per-thread assignment as the persistent kernel)
+    constexpr int NV = KT + 4;
+    float vals[NV];
+    float sA = 0.f, sB = 0.f, sF = 0.f, sJ = 0.f;
     float dJ[KT];
 #pragma unroll
     for (int m = 0; m < KT; ++m) dJ[m] = 0.0f;
-    const bool want_w = ga.last && S.wout;
-    for (int idx = tid; idx < (kGdTileH + 1) * (kTileW + 1); idx += kGdThreads) {
-        const int a = idx / (kTileW + 1), b = idx - a * (kTileW + 1);
-        // x-edge between (e-1, j) and (e, j), e = X0 + b, j = Y0 + a
-        const int ex = X0 + b, jx = Y0 + a;
-        const bool own_x = a < kGdTileH && jx < ny && ex <= nx && (b < kTileW || ex == nx);
-        // y-edge between (i, e-1) and (i, e), e = Y0 + a, i = X0 + b
-        const int ey = Y0 + a, iy = X0 + b;
-        const bool own_y = b < kTileW && iy < nx && ey <= ny && (a < kGdTileH || ey == ny);
-        const float Tx = TXs[a + 1][b + 1], wx = own_x ? WX[a + 1][b + 1] : 0.0f;
-        const float Ty = TYs[a + 1][b + 1], wy = own_y ? WY[a + 1][b + 1] : 0.0f;
-        sJ = fmaf(wx, Tx, sJ);
-        sJ = fmaf(wy, Ty, sJ);
-        if (want_w) {
-            if (own_x) S.wout[(size_t)jx * (nx + 1) + ex] = wx;
-            if (own_y) S.wout[(size_t)(ny + 1) * (nx + 1) + (size_t)ey * (nx + 1) + iy] = wy;
-        }
-        if (K) {
-            const float f11 = F[a + 1][b + 1], f12 = F[a + 1][b + 2], f21 = F[a + 2][b + 1], f22 = F[a + 2][b + 2];
-            const float g00 = G[a][b], g01 = G[a][b + 1], g10 = G[a + 1][b], g11 = G[a + 1][b + 1];
-            // x-edge: pixels at F (a+2, b+1), (a+2, b+2) and G (a+1, b), (a+1, b+1); its
-            // rows exist only for a < kGdTileH (G has kGdTileH + 2 rows)
-            float aex = 0.0f, bex = 0.0f;
-            if (a < kGdTileH) {
-                const float D = f22 - f21;
-                const float mc = 0.5f * (f21 + f22);
-                const float c1 = 0.5f * (F[a + 3][b + 1] + F[a + 3][b + 2]) - mc;
-                const float c2 = mc - 0.5f * (f11 + f12);
-                const float dD = g11 - g10;
-                const float gc = 0.5f * (g10 + g11);
-                const float dc1 = 0.5f * (G[a + 2][b] + G[a + 2][b + 1]) - gc;
-                const float dc2 = gc - 0.5f * (g00 + g01);
-                aex = D * dD + 0.5f * (c1 * dc1 + c2 * dc2);
-                bex = dD * dD + 0.5f * (dc1 * dc1 + dc2 * dc2);
-            }
-            // y-edge: pixels at F (a+1, b+2), (a+2, b+2) and G (a, b+1), (a+1, b+1); its
-            // columns exist only for b < kTileW (G has kTileW + 2 columns)
-            float aey = 0.0f, bey = 0.0f;
-            if (b < kTileW) {
-                const float D = f22 - f12;
-                const float mc = 0.5f * (f12 + f22);
-                const float c1 = 0.5f * (F[a + 1][b + 3] + F[a + 2][b + 3]) - mc;
-                const float c2 = mc - 0.5f * (f11 + f21);
-                const float dD = g11 - g01;
-                const float gc = 0.5f * (g01 + g11);
-                const float dc1 = 0.5f * (G[a][b + 2] + G[a + 1][b + 2]) - gc;
-                const float dc2 = gc - 0.5f * (g00 + g10);
-                aey = D * dD + 0.5f * (c1 * dc1 + c2 * dc2);
-                bey = dD * dD + 0.5f * (dc1 * dc1 + dc2 * dc2);
-            }
-            const float T2x = Tx * Tx, T2y = Ty * Ty;
-#pragma unroll
-            for (int m = 0; m < KT; ++m) {
-                if (m < K) {
-                    const float t = s_t[m];
-                    const float numx = t * fmaf(t, bex, -2.0f * aex);
-                    const float T2nx = fmaxf(T2x + numx, eps2);   // T'^2 >= eps^2
-                    const float Tnx = T2nx * rsqrtf(T2nx);
-                    dJ[m] = fmaf(wx, __fdividef(numx, Tnx + Tx), dJ[m]);
-                    const float numy = t * fmaf(t, bey, -2.0f * aey);
-                    const float T2ny = fmaxf(T2y + numy, eps2);
-                    const float Tny = T2ny * rsqrtf(T2ny);
-                    dJ[m] = fmaf(wy, __fdividef(numy, Tny + Ty), dJ[m]);
-                }
-            }
-        }
-    }
+    tile_sums<KT>(tid, X0, Y0, nx, ny, &F[0][0], FW, &G[0][0], GW, &V[0][0], GW, &TXs[0][0], &WX[0][0],
+                  QXW, &TYs[0][0], &WY[0][0], QYW, K, s_t, eps2, (ga.last && S.wout) ? S.wout : nullptr,
+                  &sA, &sB, &sF, &sJ, dJ);
 
-    // phase 5: block sums -> partials; last block decides the step (FP64)
-    constexpr int NV = KT + 4;
-    float vals[NV];
+    // phase 5: each warp's sums added exactly into the block's accumulators, the block's
+    // words into the slice's (copy local % kAccCopies); the last block decides the step
     vals[0] = sA; vals[1] = sB; vals[2] = sF; vals[3] = sJ;
 #pragma unroll
     for (int m = 0; m < KT; ++m) vals[4 + m] = dJ[m];
-    block_sum_to<NV, kGdThreads>(vals, partials + (size_t)blockIdx.x * kPartialStride, rsm);
+    warp_acc<NV>(vals, sacc);
+    __syncthreads();
+    acc_push<NV, kGdThreads>(sacc, S.acc, local % kAccCopies);
     const int b0 = __ldg(map.start + si);
     const int nblk = __ldg(map.start + si + 1) - b0;
     __shared__ double tot[NV];
-    if (!reduce_slice<NV, kGdThreads>(S, partials, kPartialStride, b0, nblk, local, rsm, tot, &last_flag))
-        return;
+    if (!last_block_of_slice(S.ctr, nblk, &last_flag)) return;
+    acc_read<NV, kGdThreads>(S.acc, tot);
+    __syncthreads();
     if (tid < 32) {
-        double *sc = S.sc;
-        const double A = tot[0], Bg = tot[1];
-        const double lamd = P->lambda;
-        const double E0 = 0.5 * lamd * tot[2] + tot[3];
-        // Armijo: trial m in lane m, all at once (FP64 latency is long on this GPU); the
-        // accepted step is the first trial that passes, as in a sequential search
-        const bool armijo = !ga.energy_only_fin && P->step_rule != EPTV_STEP_FIXED;
-        double d = 0.0;
-        bool pass = false, nonfinite = false;
-        if (armijo && tid < K) {
-            const double t = s_td[tid];
-            d = lamd * (-t * A + 0.5 * t * t * Bg) + tot[4 + tid];
-            nonfinite = !isfinite(d);
-            pass = d <= -P->armijo_c * t * Bg;
-        }
-        const unsigned pass_mask = __ballot_sync(0xffffffffu, pass);
-        const unsigned bad_mask = __ballot_sync(0xffffffffu, nonfinite);
-        const int acc_m = pass_mask ? __ffs(pass_mask) - 1 : -1;
-        const double dE = __shfl_sync(0xffffffffu, d, acc_m >= 0 ? acc_m : 0);
-        if (tid == 0) {
-            bool bad = !isfinite(E0) || !isfinite(A) || !isfinite(Bg);
-            if (ga.energy_only_fin) {
-                sc[SC_E_FIRST] = E0;
-                sc[SC_NORM2] = Bg;
-            } else {
-                if (ga.first) sc[SC_E_FIRST] = E0;
-                if (P->step_rule == EPTV_STEP_FIXED) {
-                    const double t = s_td[0];
-                    sc[SC_TSTEP] = t;
-                    sc[SC_E_LAST] = E0 + lamd * (-t * A + 0.5 * t * t * Bg) + tot[4];
-                    sc[SC_NACC_P2] += 1.0;
-                } else {
-                    // trials a sequential search would have evaluated: up to the accepted one
-                    const unsigned seen = acc_m >= 0 ? ((2u << acc_m) - 1u) : ((1u << K) - 1u);
-                    if (bad_mask & seen) bad = true;
-                    if (acc_m >= 0) {
-                        sc[SC_TSTEP] = s_td[acc_m];
-                        sc[SC_TPREV] = s_td[acc_m];
-                        sc[SC_E_LAST] = E0 + dE;
-                        sc[SC_NACC_P2] += 1.0;
-                    } else {
-                        sc[SC_TSTEP] = 0.0;
-                        sc[SC_TPREV] = s_td[K - 1] * P->armijo_shrink / P->armijo_grow;
-                        sc[SC_E_LAST] = E0;
-                        sc[SC_NFAIL] += 1.0;
-                        sc[SC_NFAIL_P2] += 1.0;
-                    }
-                }
+        if (ga.energy_only_fin) {
+            if (tid == 0) {
+                const double E0 = 0.5 * P->lambda * tot[2] + tot[3];
+                S.sc[SC_E_FIRST] = E0;
+                S.sc[SC_NORM2] = tot[1];
+                if (!isfinite(E0) || !isfinite(tot[0]) || !isfinite(tot[1])) S.sc[SC_NONFINITE] = 1.0;
             }
-            if (bad) sc[SC_NONFINITE] = 1.0;
-            if (!ga.energy_only_fin && S.log) {
-                const int k = (int)sc[SC_OUTER];
-                if (k >= 0 && k < S.log_outer && iter < S.log_gd) S.log[(size_t)k * S.log_gd + iter] = sc[SC_TSTEP];
-            }
+        } else {
+            const GdDecision r = gd_decide(tot, s_td, K, P, 0.0);
+            if (tid == 0) gd_record(S, P, r, ga.first != 0, iter);
         }
     }
 }

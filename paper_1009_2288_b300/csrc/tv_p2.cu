@@ -1,0 +1,442 @@
+// K4p: the whole (P2) descent of one outer iteration -- n_gd gradient-descent iterations
+// with Armijo steps (Sec. 2.2; Eqs. 5, 9, A2, A3) and the clamp of step 3 -- in ONE
+// cooperative launch.
+//
+// Each block owns a rectangle ("region") of RTX x RTY of the 32 x 8 tiles that K4 launches
+// one block per, and keeps in shared memory, for all GD iterations: the iterate f on the
+// region + 2-pixel halo, v on the region + 1, and g on the region + 2.  Per GD iteration:
+//   phase 2  T, w, q = w D / T of every half-edge around the region + 1 (Eqs. A3, 5);
+//   phase 3  g = lambda (f - v) + dJ/df on the region + 1 (Eqs. 9, A2); the owned values go
+//            to an exchange image;
+//   phase 4  per tile, in K4's thread mapping: the fidelity sums <g, f-v>, |g|^2, |f-v|^2
+//            and, for every trial step, the energy change of the owned half-edges with the
+//            weights frozen; each tile's FP64 sums go into the slice's exact accumulators
+//            (one set per GD iteration, three sets in rotation);
+//   barrier  one grid-wide arrival / wait (bounded);
+//   decide   every block reads the exact totals and takes the same FP64 Armijo decision
+//            (the first passing trial); the slice's first block records it;
+//   apply    f <- f - t g on the region + 2, the ring 2 of g read from the neighbours'
+//            exchange values of this iteration.
+// After the last iteration the owned pixels get f = max(f, 0) (step 3) and go to u and u^T.
+//
+// Because the per-pixel / per-edge arithmetic is K4's (tv_stencil.cuh), the per-tile sums
+// use K4's thread mapping, and the cross-tile sums are exact, K4p produces bit for bit the
+// same iterates, steps and scalars as n_gd launches of K4 followed by K4u.
+//
+// Co-residency: the launch is cooperative (all blocks resident or the launch fails), and
+// every wait has a bound: a block that waits longer than about a second sets SC_TIMEOUT in
+// its slice's scalars and returns, so that the host reports EPTV_ERR_TIMEOUT instead of a
+// hung context.  The barrier counter and the accumulator sets are re-armed (zeroed) by the
+// sigma selection (K5), which always runs right before this kernel.
+#include <algorithm>
+#include <atomic>
+
+#include "eptv_internal.cuh"
+#include "kernels.cuh"
+#include "tv_stencil.cuh"
+
+namespace eptv {
+
+// ------------------------------------------------------------------ grid barrier
+
+__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int *p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void red_release_add_gpu(unsigned int *p, unsigned int v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Waits until *bar >= target, at most max_cycles SM cycles and at most kP2WaitSpins polls
+// (~2.7 s with the back-off).  Returns false if a bound ran out.
+constexpr long long kP2WaitSpins = 1ll << 26;
+
+__device__ __forceinline__ bool p2_wait(const unsigned int *bar, unsigned int target,
+                                        long long max_cycles) {
+    const long long t0 = clock64();
+    for (long long spins = 0; spins < kP2WaitSpins; ++spins) {
+        if (ld_acquire_gpu(bar) >= target) return true;
+        if (spins > 32) __nanosleep(40);
+        if ((spins & 63) == 63 && clock64() - t0 > max_cycles) return false;
+    }
+    return false;
+}
+
+// Accumulator copies K4p's blocks spread their words over (block b: copy b mod kP2Copies).
+constexpr int kP2Copies = 4;
+
+// ------------------------------------------------------------------ layout
+
+template <int RTX, int RTY, int KT>
+struct P2Shape {
+    static constexpr int RW = RTX * kTileW, RH = RTY * kGdTileRows;
+    static constexpr int TILES = RTX * RTY;
+    static constexpr int NG = TILES < 4 ? TILES : 4;       // tile groups of 128 threads
+    static constexpr int NT = 128 * NG;
+    static constexpr int NV = KT + 4;
+    static constexpr int FW = RW + 4, FH = RH + 4;         // f, g, prior map: region + 2
+    static constexpr int VW = RW + 2, VH = RH + 2;         // v and the g region: region + 1
+    static constexpr int QXW = RW + 3, QXH = RH + 2;       // x-edges around the g region
+    static constexpr int QYW = RW + 2, QYH = RH + 3;       // y-edges around the g region
+    static constexpr int KTP = (KT + 3) & ~3;
+    static constexpr int N_DBL = NV + KT + 4;  // tot, s_td, t_prev / decision
+    static constexpr int N_FLT = KTP + 3 * FH * FW + VH * VW + 3 * QXH * QXW + 3 * QYH * QYW;
+    static constexpr size_t SMEM = sizeof(double) * N_DBL + sizeof(float) * N_FLT;
+};
+
+template <int RTX, int RTY, int KT>
+__global__ void __launch_bounds__(P2Shape<RTX, RTY, KT>::NT, 1)
+k4p_descent(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__restrict__ P,
+            P2Args pa)
+{
+    using Sh = P2Shape<RTX, RTY, KT>;
+    constexpr int RW = Sh::RW, RH = Sh::RH, NV = Sh::NV, NG = Sh::NG;
+    constexpr int FW = Sh::FW, FH = Sh::FH, VW = Sh::VW, VH = Sh::VH;
+    constexpr int QXW = Sh::QXW, QXH = Sh::QXH, QYW = Sh::QYW, QYH = Sh::QYH;
+    constexpr int NT = Sh::NT;
+
+    extern __shared__ __align__(16) double p2_smem[];
+    double *tot = p2_smem;                       // [NV] exact totals
+    double *s_td = tot + NV;                     // [KT] trial steps (FP64 copies)
+    double *s_misc = s_td + KT;                  // t_prev, t_step, flags
+    float *s_t = reinterpret_cast<float *>(s_misc + 4);
+    float *F = s_t + Sh::KTP;
+    float *G = F + FH * FW;
+    float *Wp = G + FH * FW;
+    float *V = Wp + FH * FW;
+    float *QX = V + VH * VW;
+    float *TX = QX + QXH * QXW;
+    float *WX = TX + QXH * QXW;
+    float *QY = WX + QXH * QXW;
+    float *TY = QY + QYH * QYW;
+    float *WY = TY + QYH * QYW;
+    __shared__ int s_abort;
+    __shared__ unsigned long long sacc[NV * kAccStride];   // the block's exact sums
+
+    int local;
+    const int si = find_slice(map, blockIdx.x, &local);
+    const SliceDev &S = sls[si];
+    const int nx = S.nx, ny = S.ny;
+    const int tiles_x = (nx + kTileW - 1) / kTileW, tiles_y = (ny + kGdTileRows - 1) / kGdTileRows;
+    const int regions_x = (tiles_x + RTX - 1) / RTX;
+    const int ry = local / regions_x, rx = local - ry * regions_x;
+    const int RX0 = rx * RW, RY0 = ry * RH;
+    const int tid = threadIdx.x;
+    const int K = pa.n_trials;
+    const float eps2 = (float)(P->eps * P->eps);
+    const float lam = (float)P->lambda;
+    const float *vv = pa.v ? pa.v : S.u;
+    unsigned long long *acc_slice = S.p2acc;
+    (void)tiles_y;
+
+    int mode = P->weights_mode;
+    if (mode == EPTV_WEIGHTS_PRIOR) {
+        mode = (S.wprior && S.sc[SC_OUTER] < (double)P->prior_iters) ? EPTV_WEIGHTS_PRIOR
+                                                                      : EPTV_WEIGHTS_EPTV;
+    }
+    const float sig = (float)S.sc[SC_SIGMA];
+    const float inv_s2 = 1.0f / (sig * sig);
+    if (tid == 0) {
+        s_misc[0] = S.sc[SC_TPREV];
+        s_abort = 0;
+    }
+
+    // f = v on the region + 2 (0 outside the image), g = 0, the prior map (edge-replicated)
+    for (int idx = tid; idx < FH * FW; idx += NT) {
+        const int r = idx / FW, c = idx - r * FW;
+        const int i = RX0 - 2 + c, j = RY0 - 2 + r;
+        float fv = 0.0f;
+        if (i >= 0 && i < nx && j >= 0 && j < ny) fv = __ldcg(vv + (j * nx + i));
+        F[idx] = fv;
+        G[idx] = 0.0f;
+        if (mode == EPTV_WEIGHTS_PRIOR) {
+            const int ci = min(max(i, 0), nx - 1), cj = min(max(j, 0), ny - 1);
+            Wp[idx] = __ldg(S.wprior + (size_t)cj * nx + ci);
+        } else {
+            Wp[idx] = 0.0f;
+        }
+    }
+    for (int idx = tid; idx < VH * VW; idx += NT) {
+        const int r = idx / VW, c = idx - r * VW;
+        const int i = RX0 - 1 + c, j = RY0 - 1 + r;
+        float vx = 0.0f;
+        if (i >= 0 && i < nx && j >= 0 && j < ny) vx = __ldcg(vv + (j * nx + i));
+        V[idx] = vx;
+    }
+    __syncthreads();
+
+    const int grp = tid >> 7, vt = tid & 127;
+    constexpr int kRing = 2 * FW + 2 * (FH - 2);
+    static_assert(kRing <= NT, "one ring position per thread");
+    if (tid == 0 && K > 0) trial_steps(P, s_misc[0], K, s_t, s_td);
+    __syncthreads();
+    for (int it = 0; it < pa.n_gd; ++it) {
+        for (int w = tid; w < NV * kAccStride; w += NT) sacc[w] = 0ull;
+        // the accumulator set of the next iteration: last read after barrier it - 2
+        if (local == 0) {
+            unsigned long long *nxt = acc_slice + (size_t)((it + 1) % kP2Sets) * kP2SetWords;
+            for (int w = tid; w < NV * kAccCopies * kAccStride; w += NT) nxt[w] = 0ull;
+        }
+
+        // phase 2: half-edges around the g region (x-edge (a, b) and y-edge (a, b) of one
+        // position share four of their six f values)
+        for (int idx = tid; idx < QYH * QXW; idx += NT) {
+            const int a = idx / QXW, b = idx - a * QXW;
+            const float f00 = F[a * FW + b], f01 = F[a * FW + b + 1];
+            const float f10 = F[(a + 1) * FW + b], f11 = F[(a + 1) * FW + b + 1];
+            if (a < QXH) {
+                const int e = RX0 - 1 + b, j = RY0 - 1 + a;
+                float q = 0.f, T = 0.f, w = 0.f;
+                if (e >= 0 && e <= nx && j >= 0 && j < ny)
+                    edge_eval(mode, eps2, inv_s2, f10, f11, F[(a + 2) * FW + b], F[(a + 2) * FW + b + 1],
+                              f00, f01, Wp[(a + 1) * FW + b], Wp[(a + 1) * FW + b + 1], &q, &T, &w);
+                QX[a * QXW + b] = q; TX[a * QXW + b] = T; WX[a * QXW + b] = w;
+            }
+            if (b < QYW) {
+                const int e = RY0 - 1 + a, i = RX0 - 1 + b;
+                float q = 0.f, T = 0.f, w = 0.f;
+                if (e >= 0 && e <= ny && i >= 0 && i < nx)
+                    edge_eval(mode, eps2, inv_s2, f01, f11, F[a * FW + b + 2], F[(a + 1) * FW + b + 2],
+                              f00, f10, Wp[a * FW + b + 1], Wp[(a + 1) * FW + b + 1], &q, &T, &w);
+                QY[a * QYW + b] = q; TY[a * QYW + b] = T; WY[a * QYW + b] = w;
+            }
+        }
+        __syncthreads();
+
+        // phase 3: g on the g region; owned values to the exchange image of this iteration
+        float *gx = (it & 1) ? S.gb : S.ga;
+        for (int idx = tid; idx < VH * VW; idx += NT) {
+            const int yy = idx / VW, xx = idx - yy * VW;
+            const int i = RX0 - 1 + xx, j = RY0 - 1 + yy;
+            float g = 0.0f;
+            if (i >= 0 && i < nx && j >= 0 && j < ny) {
+                float d;
+                g = grad_value(lam, F[(yy + 1) * FW + xx + 1], V[idx], QX[yy * QXW + xx],
+                               QX[yy * QXW + xx + 1], QY[yy * QYW + xx], QY[(yy + 1) * QYW + xx], &d);
+                if (xx >= 1 && xx <= RW && yy >= 1 && yy <= RH) gx[j * nx + i] = g;
+            }
+            G[(yy + 1) * FW + xx + 1] = g;
+        }
+        __syncthreads();
+
+        // phase 4: the tiles' sums (tile_sums: the per-thread assignment K4 uses), group grp
+        // (128 threads) takes tiles grp, grp + NG, ...; every warp adds its FP32 sums exactly
+        // into the block's accumulators (no barrier between the warps)
+        float *wout = (it == pa.n_gd - 1) ? S.wout : nullptr;
+        unsigned long long *set = acc_slice + (size_t)(it % kP2Sets) * kP2SetWords;
+        for (int q = grp; q < Sh::TILES; q += NG) {
+            const int ox = (q % RTX) * kTileW, oy = (q / RTX) * kGdTileRows;
+            const int X0 = RX0 + ox, Y0 = RY0 + oy;
+            float vals[NV];
+#pragma unroll
+            for (int k = 0; k < NV; ++k) vals[k] = 0.0f;
+            if (X0 < nx && Y0 < ny) {
+                float dJ[KT];
+#pragma unroll
+                for (int m = 0; m < KT; ++m) dJ[m] = 0.0f;
+                tile_sums<KT>(vt, X0, Y0, nx, ny, F + oy * FW + ox, FW, G + (oy + 1) * FW + ox + 1, FW,
+                              V + oy * VW + ox, VW, TX + oy * QXW + ox, WX + oy * QXW + ox, QXW,
+                              TY + oy * QYW + ox, WY + oy * QYW + ox, QYW, K, s_t, eps2, wout,
+                              &vals[0], &vals[1], &vals[2], &vals[3], dJ);
+#pragma unroll
+                for (int m = 0; m < KT; ++m) vals[4 + m] = dJ[m];
+            }
+            warp_acc<NV>(vals, sacc);
+        }
+        __syncthreads();
+        acc_push<NV, NT>(sacc, set, blockIdx.x % kP2Copies);
+
+        // grid barrier: every block's accumulations and exchange values are visible after it
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();
+            red_release_add_gpu(S.p2bar, 1u);
+            const unsigned int need = (unsigned int)(it + 1) * (gridDim.x + (unsigned int)pa.bar_extra);
+            if (!p2_wait(S.p2bar, need, pa.wait_cycles)) s_abort = 1;
+            __threadfence();
+        }
+        __syncthreads();
+        if (s_abort) {
+            if (tid == 0) S.sc[SC_TIMEOUT] = 1.0;
+            return;
+        }
+
+        // ring 2 of g: the neighbours' exchange values of this iteration (loads issued before
+        // the exact read, stored after it)
+        float ring_g = 0.0f;
+        int ring_at = -1;
+        if (tid < kRing) {
+            int r, c;
+            if (tid < FW) { r = 0; c = tid; }
+            else if (tid < 2 * FW) { r = FH - 1; c = tid - FW; }
+            else { const int k = tid - 2 * FW; r = 1 + (k >> 1); c = (k & 1) ? FW - 1 : 0; }
+            const int i = RX0 - 2 + c, j = RY0 - 2 + r;
+            ring_at = r * FW + c;
+            if (i >= 0 && i < nx && j >= 0 && j < ny) ring_g = __ldcg(gx + (j * nx + i));
+        }
+        // the exact totals of this iteration (read, not cleared: every block reads them)
+        acc_read<NV, NT, false, kP2Copies>(set, tot);
+        __syncthreads();
+        if (tid < 32) {
+            const GdDecision r = gd_decide(tot, s_td, K, P, s_misc[0]);
+            if (tid == 0) {
+                s_misc[1] = r.t_step;
+                s_misc[0] = r.t_prev;
+                if (local == 0) gd_record(S, P, r, it == 0, it);
+                if (K > 0) trial_steps(P, r.t_prev, K, s_t, s_td);      // for the next iteration
+            }
+        }
+        if (ring_at >= 0) G[ring_at] = ring_g;
+        __syncthreads();
+        const float tap = (float)s_misc[1];
+        if (tap != 0.0f) {
+            for (int idx = tid; idx < FH * FW; idx += NT) {
+                const int r = idx / FW, c = idx - r * FW;
+                const int i = RX0 - 2 + c, j = RY0 - 2 + r;
+                if (i >= 0 && i < nx && j >= 0 && j < ny) F[idx] = fmaf(-tap, G[idx], F[idx]);
+            }
+        }
+        __syncthreads();
+    }
+
+    // step 3: f = max(f, 0) on the owned pixels -> u (or the caller's output) and u^T
+    float *out = pa.out ? pa.out : S.u;
+    for (int idx = tid; idx < RH * RW; idx += NT) {
+        const int r = idx / RW, c = idx - r * RW;
+        const int i = RX0 + c, j = RY0 + r;
+        if (i < nx && j < ny) out[j * nx + i] = fmaxf(F[(r + 2) * FW + c + 2], 0.0f);
+    }
+    if (S.uT && !pa.out) {
+        for (int idx = tid; idx < RH * RW; idx += NT) {
+            const int c = idx / RH, r = idx - c * RH;    // consecutive threads: consecutive rows
+            const int i = RX0 + c, j = RY0 + r;
+            if (i < nx && j < ny) S.uT[(size_t)i * ny + j] = fmaxf(F[(r + 2) * FW + c + 2], 0.0f);
+        }
+    }
+    if (local == 0 && tid == 0) S.sc[SC_OUTER] += 1.0;
+}
+
+// ------------------------------------------------------------------ host side
+
+namespace {
+
+struct P2Kernel {
+    const void *fn;
+    int rtx, rty, kt, nt;
+    size_t smem;
+};
+
+template <int RTX, int RTY, int KT>
+P2Kernel p2_kernel() {
+    using Sh = P2Shape<RTX, RTY, KT>;
+    return P2Kernel{(const void *)&k4p_descent<RTX, RTY, KT>, RTX, RTY, KT, Sh::NT, Sh::SMEM};
+}
+
+P2Kernel p2_lookup(int rtx, int rty, int kt) {
+#define EPTV_P2_CASE(X, Y)                                                 \
+    if (rtx == X && rty == Y) {                                            \
+        if (kt == 1) return p2_kernel<X, Y, 1>();                          \
+        if (kt == 4) return p2_kernel<X, Y, 4>();                          \
+        return p2_kernel<X, Y, 8>();                                       \
+    }
+    EPTV_P2_CASE(2, 4)
+    EPTV_P2_CASE(1, 4)
+    EPTV_P2_CASE(1, 2)
+    EPTV_P2_CASE(1, 1)
+#undef EPTV_P2_CASE
+    return P2Kernel{nullptr, 0, 0, 0, 0, 0};
+}
+
+int kt_of(int n_trials) {
+    if (n_trials <= 1) return 1;
+    if (n_trials <= 4) return 4;
+    if (n_trials <= 8) return 8;
+    return 0;
+}
+
+}  // namespace
+
+int p2_plan(Batch &B, int n_trials, int n_gd, P2Plan *plan) {
+    plan->ok = 0;
+    const int kt = kt_of(n_trials);
+    if (!kt || n_gd < 1 || n_gd > (1 << 20) || B.p2_disabled || B.p2_forbid) return 0;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
+        cudaGetLastError();
+        return 0;
+    }
+    static const int shapes[4][2] = {{2, 4}, {1, 4}, {1, 2}, {1, 1}};
+    long long best_cost = -1;
+    for (const auto &sh : shapes) {
+        const P2Kernel k = p2_lookup(sh[0], sh[1], kt);
+        if (!k.fn) continue;
+        if (cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k.fn, k.nt, k.smem) != cudaSuccess || occ < 1) {
+            cudaGetLastError();
+            continue;
+        }
+        long long regions = 0;
+        for (const SliceDev &s : B.h_sd) {
+            const int tx = (s.nx + kTileW - 1) / kTileW, ty = (s.ny + kGdTileRows - 1) / kGdTileRows;
+            regions += (long long)((tx + sh[0] - 1) / sh[0]) * ((ty + sh[1] - 1) / sh[1]);
+        }
+        if (regions > (long long)occ * sms) continue;
+        // the most tiles one SM works through per GD iteration
+        const long long cost = (long long)sh[0] * sh[1] * ((regions + sms - 1) / sms);
+        if (best_cost < 0 || cost < best_cost) {
+            best_cost = cost;
+            plan->ok = 1;
+            plan->rtx = sh[0];
+            plan->rty = sh[1];
+            plan->kt = kt;
+            plan->nt = k.nt;
+            plan->smem = k.smem;
+            plan->blocks = (int)regions;
+        }
+    }
+    return 0;
+}
+
+// Start offsets of the regions of each slice for a region shape (host array, n + 1 entries).
+void p2_region_starts(const Batch &B, int rtx, int rty, std::vector<int> &starts) {
+    starts.assign(B.n + 1, 0);
+    int acc = 0;
+    for (int i = 0; i < B.n; ++i) {
+        const SliceDev &s = B.h_sd[i];
+        const int tx = (s.nx + kTileW - 1) / kTileW, ty = (s.ny + kGdTileRows - 1) / kGdTileRows;
+        starts[i] = acc;
+        acc += ((tx + rtx - 1) / rtx) * ((ty + rty - 1) / rty);
+    }
+    starts[B.n] = acc;
+}
+
+cudaError_t launch_p2(const Batch &B, const P2Plan &plan, const P2Args &pa, cudaStream_t st) {
+    const P2Kernel k = p2_lookup(plan.rtx, plan.rty, plan.kt);
+    if (!k.fn) return cudaErrorInvalidValue;
+    ++g_launch_count;
+    TileMap map{B.d_p2start, B.n};
+    const SliceDev *sd = B.d_sd;
+    const ParamsDev *pp = B.d_params;
+    P2Args a = pa;
+    void *args[] = {(void *)&sd, (void *)&map, (void *)&pp, (void *)&a};
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(plan.blocks);
+    cfg.blockDim = dim3(k.nt);
+    cfg.dynamicSmemBytes = k.smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, k.fn, args);
+}
+
+}  // namespace eptv

@@ -23,7 +23,7 @@ EXPORTED = [
     "eptv_project_t", "eptv_transpose", "eptv_backproject", "eptv_cgls", "eptv_sigma",
     "eptv_tv_gradient", "eptv_tv_step", "eptv_reconstruct", "eptv_report_energy",
     "eptv_select_kth", "eptv_reconstruct_batched", "eptv_last_error", "eptv_version",
-    "eptv_get_log", "eptv_select_kth_noalloc", "eptv_set_tuning", "eptv_autotune",
+    "eptv_get_log", "eptv_select_kth_noalloc", "eptv_set_tuning", "eptv_set_tv_kernel", "eptv_debug_set_p2_wait", "eptv_autotune",
     "eptv_autotune_batched", "eptv_unet_conv3x3", "eptv_unet_conv3x3_wgrad",
     "eptv_unet_weights_to_bf16", "eptv_unet_maxpool2", "eptv_unet_maxpool2_bwd",
     "eptv_unet_upsample2", "eptv_unet_upsample2_bwd", "eptv_unet_relu_bwd", "eptv_unet_head",
@@ -129,6 +129,8 @@ def load():
         "eptv_get_log": (c_int, [vp, ctypes.POINTER(dbl), c_int, ctypes.POINTER(dbl), c_int,
                                  ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
         "eptv_set_tuning": (c_int, [vp, c_int, c_int]),
+        "eptv_set_tv_kernel": (c_int, [vp, c_int]),
+        "eptv_debug_set_p2_wait": (c_int, [vp, c_int, ctypes.c_longlong]),
         "eptv_autotune": (c_int, [vp, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
         "eptv_autotune_batched": (c_int, [c_int, ctypes.POINTER(vp), ctypes.POINTER(c_int),
                                           ctypes.POINTER(c_int)]),
@@ -427,6 +429,21 @@ def eptv_quality_metrics(geom: Geometry, f, ref=None, roi=None, edge_scale: floa
 
 def eptv_set_tuning(geom: Geometry, k1_seg: int, k2_vg: int):
     _check(load().eptv_set_tuning(geom.handle, int(k1_seg), int(k2_vg)))
+
+
+TV_AUTO, TV_PER_ITERATION = 0, 1
+
+
+def eptv_set_tv_kernel(geom: Geometry, mode: int):
+    """(P2) kernel of geom's solves: TV_AUTO (one persistent launch per (P2) solve when it
+    fits) or TV_PER_ITERATION (one launch per GD iteration); results are bit-identical."""
+    _check(load().eptv_set_tv_kernel(geom.handle, int(mode)))
+
+
+def eptv_debug_set_p2_wait(geom: Geometry, extra_blocks: int, wait_cycles: int):
+    """Test hook: the persistent (P2) kernel's barrier waits for extra_blocks phantom blocks
+    and gives up after wait_cycles SM cycles (EPTV_ERR_TIMEOUT)."""
+    _check(load().eptv_debug_set_p2_wait(geom.handle, int(extra_blocks), int(wait_cycles)))
 
 
 def eptv_autotune(geom: Geometry):

@@ -33,6 +33,8 @@ static inline double __ull2double_rn(unsigned long long x) { return (double)x; }
 static inline unsigned long long __ldcg(const unsigned long long *p) { return *p; }
 static inline void atomicAdd(unsigned long long *p, unsigned long long v) { *p += v; }
 static inline void atomicOr(unsigned long long *p, unsigned long long v) { *p |= v; }
+static inline unsigned int __float_as_uint(float x) { unsigned int r; memcpy(&r, &x, 4); return r; }
+static inline float __uint_as_float(unsigned int x) { float r; memcpy(&r, &x, 4); return r; }
 '''
 
 MAIN = r'''
@@ -56,7 +58,10 @@ int main() {
             n = 0;
             continue;
         }
-        acc_add(acc[n % kAccCopies], __longlong_as_double((long long)strtoull(line, 0, 16)));
+        if (line[0] == 'F')        // an FP32 value added by acc_add_f32
+            acc_add_f32(acc[n % kAccCopies], __uint_as_float((unsigned int)strtoul(line + 1, 0, 16)));
+        else
+            acc_add(acc[n % kAccCopies], __longlong_as_double((long long)strtoull(line, 0, 16)));
         ++n;
     }
     return 0;
@@ -75,10 +80,13 @@ def accumulator(tmp_path_factory):
     cpp.write_text(SHIMS + body + MAIN)
     subprocess.check_call(["g++", "-O1", "-std=c++17", "-o", str(exe), str(cpp)])
 
-    def run(groups):
+    def run(groups, as_f32=False):
         lines = []
         for g in groups:
-            lines += ["%016x" % struct.unpack("<Q", struct.pack("<d", x))[0] for x in g] + ["E"]
+            if as_f32:
+                lines += ["F%08x" % struct.unpack("<I", struct.pack("<f", x))[0] for x in g] + ["E"]
+            else:
+                lines += ["%016x" % struct.unpack("<Q", struct.pack("<d", x))[0] for x in g] + ["E"]
         out = subprocess.run([str(exe)], input="\n".join(lines) + "\n", capture_output=True,
                              text=True, check=True).stdout.split()
         return [struct.unpack("<d", struct.pack("<Q", int(h, 16)))[0] for h in out]
@@ -140,3 +148,25 @@ def test_ties_cancellation_and_special_values(accumulator):
     assert sp[0] == inf and sp[1] == -inf
     assert math.isnan(sp[2]) and math.isnan(sp[3])
     assert sp[4] == inf and sp[5] == -inf              # beyond the accumulator's range
+
+
+def test_fp32_values_added_directly(accumulator):
+    """acc_add_f32 (integer atomics only): sums of FP32 warp sums, including subnormals,
+    both signs, cancellation and FLT_MAX, are the correctly rounded exact sums and equal the
+    FP64 path's; non-finite values set the flags."""
+    rng = random.Random(11)
+    groups = []
+    for _ in range(300):
+        n = rng.choice([1, 3, 32, 500])
+        scale = 2.0 ** rng.randint(-149, 100)
+        groups.append([f32(rng.uniform(-1, 1) * scale * 2.0 ** rng.randint(-24, 24)) for _ in range(n)])
+    groups += [[2.0 ** -149, -(2.0 ** -149)], [f32(1.1754942e-38), 2.0 ** -149], [f32(3.4028235e38)] * 3,
+               [f32(16777217.0), 1.0, -16777216.0], [-0.0], []]
+    got = accumulator(groups, as_f32=True)
+    want64 = accumulator(groups)
+    for g, r, r64 in zip(groups, got, want64):
+        assert r == float(sum(Fraction(x) for x in g)), g[:3]
+        assert r == r64
+    inf, nan = float("inf"), float("nan")
+    sp = accumulator([[inf, 1.0], [-inf, 2.0], [nan]], as_f32=True)
+    assert sp[0] == inf and sp[1] == -inf and math.isnan(sp[2])

@@ -351,12 +351,12 @@ def test_reconstruct_armijo_matches_oracle(c1, n_outer):
     Armijo trial can land within that noise of the acceptance threshold; after such a
     decision the two runs follow different (equally valid) paths, and late in the run the
     reported energy swings by 5-10 % from one iteration to the next (also in the oracle).
-    Checked: the GPU's step log equals the oracle's until the first differing decision,
-    where the oracle's own decision must have been marginal (|rho - c| < 1e-2, rho =
-    achieved decrease / (t |g|^2)); the image agrees within max(1e-4, 3x the oracle's own
-    change under 1e-6 perturbations of P and P^T, worst of two seeds) -- under 1e-7
-    perturbations that change is 4e-6 at 3 iterations but already 1.4e-4 at 5, where
-    marginal decisions start to appear;
+    Checked: without a differing decision (identical step logs) the image agrees within
+    1e-4; otherwise the GPU's step log equals the oracle's until the first differing
+    decision, where the oracle's own decision must have been marginal (|rho - c| < 1e-2,
+    rho = achieved decrease / (t |g|^2)), and the image agrees within max(1e-4, 3x the
+    oracle's own change under 1e-6 perturbations of P and P^T, worst of two seeds), the
+    floor printed with the result;
     the mean reported energy (Eq. 2) over the last 20 % of the iterations agrees within
     2 % (1e-7 perturbations of P and P^T move the oracle's own by <= 0.4 %); chaining
     one-iteration calls (previous step carried in t_init) reproduces the single call."""
@@ -418,8 +418,85 @@ def test_reconstruct_armijo_matches_oracle(c1, n_outer):
             x = op.backproject(yv)
             return x * (1 + 1e-6 * self.rng.standard_normal(x.shape))
 
+    err = rel(got, want)
+    if flip is None:
+        print(f"armijo n_outer={n_outer}: identical step logs, image rel L2 {err:.3e} (bound 1e-4)")
+        assert err < 1e-4
+        return
     floor = max(rel(O.reconstruct(Perturbed(seed), c1.y, p), want) for seed in (77, 78))
-    assert rel(got, want) <= max(1e-4, 3 * floor)
+    bound = max(1e-4, 3 * floor)
+    print(f"armijo n_outer={n_outer}: first differing decision {flip}, image rel L2 {err:.3e}, "
+          f"oracle's own change under 1e-6 perturbations {floor:.3e}, bound {bound:.3e}")
+    assert err <= bound
+
+
+@pytest.fixture(scope="module")
+def c2_bench():
+    """The benchmark's workload (512^2 at 0.8 mm, 40 views x 888 bins) in the benchmark's
+    launch configuration (autotuned K1 / K2 shapes), with the oracle's operator."""
+    c = I.make_c2(with_truth=False)
+    geo = E.Geometry(c.geom)
+    E.eptv_autotune(geo)
+    return c, geo, O.Operator(c.geom)
+
+
+def _perturbed(op, seed, amp):
+    """The FP64 operator with relative noise of size amp on its outputs (the size of FP32
+    summation differences is ~1e-6): how far the method itself moves under it."""
+    class Perturbed:
+        g = op.g
+        rng = np.random.Generator(np.random.PCG64(seed))
+
+        def project(self, x):
+            yv = op.project(x)
+            return yv * (1 + amp * self.rng.standard_normal(yv.shape))
+
+        def backproject(self, yv):
+            x = op.backproject(yv)
+            return x * (1 + amp * self.rng.standard_normal(x.shape))
+    return Perturbed()
+
+
+def test_benchmark_workload_fixed_steps_image_parity(c2_bench):
+    """Stated target on the benchmark workload: 1e-4 relative L2 on the image after N
+    iterations; 10 outer iterations with a fixed (P2) step of 2e-5 (no discrete decisions;
+    the FP64 oracle itself moves by 3.6e-7 under 1e-7 perturbations of P and P^T there,
+    while with a step of 1e-4 the lagged TV step chatters in flat regions and the oracle
+    moves by 1.2e-3 under the same perturbations)."""
+    c, geo, op = c2_bench
+    g = c.geom
+    p = I.EptvParams(n_outer=10, step_rule=O.FIXED, t_fixed=2e-5)
+    want = O.reconstruct(op, c.y, p)
+    f = torch.zeros(g.n_pix, device=DEV)
+    E.eptv_reconstruct(geo, p, t32(c.y).reshape(-1), f)
+    err = rel(np64(f).reshape(g.ny, g.nx), want)
+    print(f"benchmark workload, 10 fixed-step iterations: image rel L2 {err:.3e}")
+    assert err < 1e-4
+
+
+def test_benchmark_workload_armijo_image_parity(c2_bench):
+    """The benchmark workload with the default Armijo (P2): 8 outer iterations, the GPU's
+    accepted steps equal the oracle's (no decision differs), and the image within
+    max(1e-4, 3x the oracle's own change under 1e-6 perturbations of P and P^T) -- that
+    change is 9.4e-5 here (3.4e-5 under 1e-7), the floor of any FP32 evaluation of the
+    operators; both numbers are printed."""
+    c, geo, op = c2_bench
+    g = c.geom
+    p = I.EptvParams(n_outer=8)
+    log = O.ReconLog()
+    want = O.reconstruct(op, c.y, p, log=log)
+    f = torch.zeros(g.n_pix, device=DEV)
+    rep = E.eptv_reconstruct(geo, p, t32(c.y).reshape(-1), f)
+    steps, sigmas = E.eptv_get_log(geo)
+    assert _first_flip(steps, log.steps) is None
+    assert rep.n_fail == log.fails
+    assert np.allclose(sigmas, log.sigmas, rtol=2e-3)
+    err = rel(np64(f).reshape(g.ny, g.nx), want)
+    floor = rel(O.reconstruct(_perturbed(op, 77, 1e-6), c.y, p), want)
+    bound = max(1e-4, 3 * floor)
+    print(f"benchmark workload, 8 Armijo iterations: image rel L2 {err:.3e}, oracle's own change "
+          f"under 1e-6 perturbations {floor:.3e}, bound {bound:.3e}")
+    assert err <= bound
 
 
 def test_reconstruct_deterministic_and_warm_start(c1):

@@ -202,20 +202,43 @@ def measured_peaks():
     return 6400.0, "fallback"
 
 
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
 def cpu_baseline(case, steps=8):
     """The FP64 oracle as it stands, on the host: `steps` outer iterations of the same
-    workload (a bounded sample of the 100)."""
-    import numpy as np
+    workload (a bounded sample of the 100), once on one core and once with its P and P^T
+    on every host core (oracle/sharded.py: the same C routines on view shards; CGLS and
+    (P2) unchanged, single-threaded)."""
     from oracle import eptv_oracle as O
+    from oracle import sharded as SH
     from paper_1009_2288_b300 import inputs as I
     p = I.EptvParams(n_outer=steps)
     op = O.Operator(case.geom)
     t0 = time.perf_counter()
     f = O.reconstruct(op, case.y, p)
-    dt = time.perf_counter() - t0
-    return {"value": steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{steps} of the {N_OUTER} outer iterations of {WORKLOAD} "
-                      f"(single-threaded C Siddon + numpy FP64), {dt:.1f} s"}, f, op
+    dt1 = time.perf_counter() - t0
+    cores = SH.host_cores()
+    with SH.ShardedOperator(case.geom, cores) as sop:
+        O.reconstruct(sop, case.y, I.EptvParams(n_outer=1))        # pool warm-up
+        t0 = time.perf_counter()
+        O.reconstruct(sop, case.y, p)
+        dtn = time.perf_counter() - t0
+        workers = sop.n_workers
+    return {"value": steps / dtn, "unit": UNIT, "cores": workers, "kind": "oracle",
+            "cpu": cpu_model(), "host_cores": cores,
+            "sample": f"{steps} of the {N_OUTER} outer iterations of {WORKLOAD}: P and P^T on "
+                      f"{workers} processes (view shards of the C Siddon), CGLS and (P2) numpy FP64 "
+                      f"on one core, {dtn:.1f} s",
+            "single_core": {"value": steps / dt1, "unit": UNIT, "cores": 1,
+                            "sample": f"the same {steps} iterations on one core, {dt1:.1f} s"}}, f, op
 
 
 def oracle_check(geo, case, f_orc, op, steps, dev):
@@ -243,27 +266,31 @@ def oracle_check(geo, case, f_orc, op, steps, dev):
 
 
 def run_reference(args, world, rank):
-    """Reference arm: the FP64 oracle timed on the host cores, same workload and metric,
-    each step = one outer iteration (a bounded sample of the 100)."""
+    """Reference arm: the FP64 oracle timed on the host cores (its P and P^T sharded over
+    every core, CGLS and (P2) on one), same workload and metric, each step = one outer
+    iteration (a bounded sample of the 100)."""
     if rank != 0:
         return
     import numpy as np
     from oracle import eptv_oracle as O
+    from oracle import sharded as SH
     from paper_1009_2288_b300 import inputs as I
     case = I.make_c2(with_truth=False)
-    op = O.Operator(case.geom)
+    cores = SH.host_cores()
     p = I.EptvParams(n_outer=1)
     f = np.zeros((case.geom.ny, case.geom.nx))
     t_prev = p.t_init_eff
     times = []
-    for i in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        v = O.cgls(op, case.y, f, p.cgls_iters)
-        f, st = O.p2_solve(v, p, t_prev)
-        t_prev = st.t_prev
-        f = np.maximum(f, 0.0)
-        if i >= args.warmup:
-            times.append(time.perf_counter() - t0)
+    with SH.ShardedOperator(case.geom, cores) as op:
+        for i in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            v = O.cgls(op, case.y, f, p.cgls_iters)
+            f, st = O.p2_solve(v, p, t_prev)
+            t_prev = st.t_prev
+            f = np.maximum(f, 0.0)
+            if i >= args.warmup:
+                times.append(time.perf_counter() - t0)
+        workers = op.n_workers
     ms = 1e3 * statistics.mean(times)
     value = 1e3 / ms
     line = {
@@ -272,8 +299,10 @@ def run_reference(args, world, rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "step": "one outer iteration (sample of 100)",
                    "image": "512x512 @ 0.8 mm", "views": 40, "bins": 888, "M": 3, "n_gd": 10},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{args.steps} outer iterations of {WORKLOAD}, one per step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle",
+                         "cpu": cpu_model(), "host_cores": cores,
+                         "sample": f"{args.steps} outer iterations of {WORKLOAD}, one per step; P and "
+                                   f"P^T on {workers} processes, CGLS and (P2) on one core"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -342,11 +371,73 @@ def run_batched(dev, stream, n_slices=64, n_outer=50, steps=3):
     ms = statistics.mean(times)
     pix = sum(c.geom.n_pix for c in cases)
     rays = sum(c.geom.n_rays for c in cases)
+    tte = batched_tte(dev, stream, cases, geos, ys, fs, tuning, p)
     return {"workload": f"batched_{n_slices}_slices_256-512_20-60v_512-888b", "n_outer": n_outer,
             "value": n_slices * n_outer * 1e3 / ms, "unit": "slice-iterations/s",
             "ms_per_step": ms, "steps": steps, "pixels": pix, "rays": rays,
             "gpu_launches_per_step": int(rep[0].n_launches),
-            "tuning": {"k1_seg": tuning[0], "k2_vg": tuning[1]}}
+            "tuning": {"k1_seg": tuning[0], "k2_vg": tuning[1]}, "time_to_oracle_energy": tte}
+
+
+def batched_tte(dev, stream, cases, geos, ys, fs, tuning, p):
+    """Time to the FP64 oracle's energy (Eq. 2) for the batch slices whose oracle energies
+    tests/golden/make_oracle_energy.py stored (one 512^2, one 256^2, one 384^2 slice).  The
+    batch computes every slice bit for bit as a single-slice reconstruction with the same
+    launch shapes does, so each slice's iteration count k* comes from chained one-iteration
+    single-slice calls; the time is that of the whole batch run for k* iterations (all 64
+    slices advance together).  Criterion as for the single-slice workload: the first k
+    whose 5-iteration mean of E_report is within 1e-3 of the oracle's last-5 mean."""
+    import torch
+    from paper_1009_2288_b300 import eptv as E
+    from paper_1009_2288_b300 import inputs as I
+    out = []
+    for i, c in enumerate(cases):
+        gold = os.path.join(ROOT, "tests", "golden", f"c3_seed{c.seed}_oracle_energy.json")
+        if not os.path.exists(gold):
+            continue
+        ref = json.load(open(gold))
+        sig, eo = ref["sigma_ref"], ref["e_report_per_iteration"]
+        target = sum(eo[-5:]) / 5.0
+
+        def first_reach(es):
+            for k in range(5, len(es) + 1):
+                if sum(es[k - 5:k]) / 5.0 <= target * (1 + 1e-3):
+                    return k
+            return None
+        g1 = E.Geometry(c.geom)
+        E.eptv_set_tuning(g1, tuning[0], tuning[1])
+        f1 = torch.zeros(c.geom.n_pix, device=dev)
+        t_prev = p.t_init_eff
+        es = []
+        k_star = None
+        for k in range(1, ref["n_outer"] + 11):
+            rep = E.eptv_reconstruct(g1, I.EptvParams(n_outer=1, t_init=t_prev), ys[i], f1, report=True)
+            t_prev = rep.t_prev
+            es.append(E.eptv_report_energy(g1, p, sig, f1, ys[i]))
+            k_star = first_reach(es)
+            if k_star is not None:
+                break
+        ent = {"slice": i, "workload": c.name, "seed": c.seed, "target": target,
+               "oracle_iterations": first_reach(eo), "iterations": k_star, "batch_ms": None}
+        if k_star is not None:
+            pk = I.EptvParams(n_outer=k_star)
+            ts = []
+            for _ in range(2):
+                for f in fs:
+                    f.zero_()
+                s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                s.record(stream)
+                E.eptv_reconstruct_batched(geos, pk, ys, fs, report=False)
+                e.record(stream)
+                e.synchronize()
+                ts.append(s.elapsed_time(e))
+            ent["batch_ms"] = min(ts)
+            # the batch's own image of this slice after k* iterations against the chained one
+            f1.zero_()
+            E.eptv_reconstruct(g1, pk, ys[i], f1, report=False)
+            ent["batch_equals_single"] = bool(torch.equal(fs[i], f1))
+        out.append(ent)
+    return out
 
 
 def run_stored(dev, stream, case, n_outer, peak, peak_kind, steps=3):
@@ -728,29 +819,64 @@ def run_ours(args, world, rank, local):
     barrier(world)
     e2e_ms, e2e_value = job_rate(statistics.mean(e2e_times), world, N_OUTER)
 
-    # dominant kernels timed live: projector (with transposed image) and back projector
+    # the kernels of one outer iteration, timed live on this stream: projector (with the
+    # transposed image) and back projector as graph-replayed launches; the (P2) descent --
+    # one cooperative launch per outer iteration running n_gd GD iterations -- per GD
+    # iteration, from two in-graph reconstructions that differ only in n_gd (10 and 1)
     fT = torch.empty_like(f_dev)
     E.eptv_transpose(geo, f_dev, fT)
     ybuf = torch.empty(g.n_rays, device=dev)
     ximg = torch.empty_like(f_dev)
     t_k1 = time_kernel(lambda: E.eptv_project_t(geo, f_dev, fT, ybuf))
     t_k2 = time_kernel(lambda: E.eptv_backproject(geo, y_dev, ximg))
-    per_outer = {"k1_project": (p.cgls_iters + 1) * t_k1, "k2_backproject": p.cgls_iters * t_k2}
-    dom = max(per_outer, key=per_outer.get)
+
+    def outer_seconds(n_gd, n_outer=20, reps=3):
+        pq = I.EptvParams(n_outer=n_outer, n_gd=n_gd)
+        best = None
+        for _ in range(reps + 1):
+            f_dev.zero_()
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record(stream)
+            E.eptv_reconstruct(geo, pq, y_dev, f_dev, report=False)
+            e.record(stream)
+            e.synchronize()
+            t = s.elapsed_time(e) * 1e-3 / n_outer
+            best = t if best is None else min(best, t)
+        return best
+    t_out10 = outer_seconds(p.n_gd)
+    t_gd = (t_out10 - outer_seconds(1)) / (p.n_gd - 1)
     nnz = nnz_of(g)
     vec = 4 * (g.n_pix + g.n_rays)
-    t_dom = t_k1 if dom == "k1_project" else t_k2
-    algo_bytes = 8 * nnz + vec          # CSR SpMV equivalent: value + column index per nonzero
+    spmv_bytes = 8 * nnz + vec          # CSR SpMV equivalent: value + column index per nonzero
+    gd_bytes = (12 + 8 * p.max_trials) * g.n_pix   # f, v read, g written; f, g per Armijo trial
     peak, peak_kind = measured_peaks()
-    achieved = algo_bytes / t_dom / 1e9
-    src = {"k1_project": ["paper_1009_2288_b300/csrc/project.cu"],
-           "k2_backproject": ["paper_1009_2288_b300/csrc/backproject.cu"]}[dom] + \
-        ["paper_1009_2288_b300/csrc/eptv_internal.cuh", "paper_1009_2288_b300/csrc/kernels.cuh"]
-    traffic = load_counters(dom, src)
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
-                "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                "algorithmic_bytes_per_launch": algo_bytes, "nnz": nnz,
-                "launch_us": {"k1_project": t_k1 * 1e6, "k2_backproject": t_k2 * 1e6}}
+    src_of = {"k1_project": ["paper_1009_2288_b300/csrc/project.cu"],
+              "k2_backproject": ["paper_1009_2288_b300/csrc/backproject.cu"],
+              "k4p_descent": ["paper_1009_2288_b300/csrc/tv_p2.cu",
+                              "paper_1009_2288_b300/csrc/tv_stencil.cuh"]}
+    common = ["paper_1009_2288_b300/csrc/eptv_internal.cuh", "paper_1009_2288_b300/csrc/kernels.cuh"]
+    kernels = []
+    for name, t, nbytes, per_outer, unit_desc, limiter in (
+            ("k1_project", t_k1, spmv_bytes, (p.cgls_iters + 1) * t_k1, "launch",
+             "gather/issue (SpMV-equivalent bytes)"),
+            ("k2_backproject", t_k2, spmv_bytes, p.cgls_iters * t_k2, "launch",
+             "gather/issue (SpMV-equivalent bytes)"),
+            ("k4p_descent", t_gd, gd_bytes, p.n_gd * t_gd, "GD iteration",
+             "latency: one grid barrier, exact read-out and FP64 Armijo decision per GD iteration")):
+        achieved = nbytes / t / 1e9
+        kernels.append({"kernel": name, "limiter": limiter, "unit_of_work": unit_desc,
+                        "algorithmic_bytes": nbytes, "us": t * 1e6, "achieved": achieved,
+                        "frac": achieved / peak, "per_outer_us": per_outer * 1e6,
+                        "share_of_outer": per_outer / t_out10,
+                        "traffic": load_counters(name, src_of[name] + common)})
+    dom = max(kernels, key=lambda k: k["per_outer_us"])
+    roofline = {"bound": "hbm", "kernel": dom["kernel"], "limiter": dom["limiter"],
+                "achieved": dom["achieved"], "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                "frac": dom["frac"], "traffic": dom["traffic"],
+                "algorithmic_bytes_per_unit": dom["algorithmic_bytes"], "unit_of_work": dom["unit_of_work"],
+                "nnz": nnz, "outer_iteration_us": t_out10 * 1e6, "kernels": kernels,
+                "launch_us": {"k1_project": t_k1 * 1e6, "k2_backproject": t_k2 * 1e6,
+                              "k4p_descent_per_gd_iteration": t_gd * 1e6}}
 
     # time to the FP64 oracle's energy (stored by tests/golden/make_oracle_energy.py).
     # The reported energy (Eq. 2) swings from one iteration to the next late in a run, so

@@ -239,10 +239,14 @@ int eptv_select_kth(const eptv_geometry *g, const float *d_vals, long n, long k,
  * Its working memory is one 16.5 KB array compiled into the library, kept by every GPU
  * that loads it until the process exits.  n must be in [1, 2^31 - 1] (the histogram
  * counts are 32-bit) and k in [1, n]; otherwise EPTV_ERR_ARG.  d_vals: n non-negative
- * finite floats; d_out: one float.  The first call on a device looks up the array's
- * device address (make that first call before any stream capture).  All calls on a
- * device share the array: each call clears it before use, and calls that overlap on
- * the GPU (other streams or threads) race and give wrong results. */
+ * finite floats; d_out: one float; both in device memory of the current device
+ * (EPTV_ERR_ARG otherwise).  The first call on a device looks up the array's device
+ * address and caches it (make that first call before any stream capture); a
+ * cudaDeviceReset of that device invalidates the cached address, so do not call this
+ * again in a process after resetting the device.  A CUDA error left pending by earlier
+ * work on the calling thread is reported (EPTV_ERR_CUDA) and left pending, not cleared.
+ * All calls on a device share the array: each call clears it before use, and calls
+ * that overlap on the GPU (other streams or threads) race and give wrong results. */
 int eptv_select_kth_noalloc(const float *d_vals, long n, long k, float *d_out, void *stream);
 
 /* ------------------------------------------------------------------ 3-D cone beam
@@ -428,6 +432,26 @@ int eptv_autotune_batched(int n, eptv_geometry *const *geoms, int *k1_seg, int *
 int eptv_unet_conv3x3(const void *d_x, int n, int h, int w, int cin, int x_stride, int x_off,
                       const void *d_wt, const float *d_bias, int cout, void *d_y, int y_stride,
                       int y_off, int relu, void *stream);
+
+/* Kernel of eptv_unet_conv3x3 (process-wide; not part of the paper):
+ *   EPTV_CONV_TENSOR_MEMORY (default): tcgen05.mma with the FP32 accumulator in tensor
+ *     memory and TMA-loaded input halos, M = 128 pixels of one tile, N = cout, K = 9 cin,
+ *     for the shapes where it is not slower than the mma.sync kernel on B300 (image width
+ *     a multiple of 128 with cin >= 32 or cout >= 48); the mma.sync kernel for the others;
+ *   EPTV_CONV_MMA_SYNC: always the warp-level mma.sync kernel;
+ *   EPTV_CONV_TENSOR_MEMORY_ALL: the tensor-memory kernel wherever it tiles the image
+ *     (width a multiple of 128, or 64 with an even height; input channel stride and
+ *     offset multiples of 8, input 16-byte aligned).
+ * All sum the same BF16 products in FP32 (different order).  EPTV_ERR_ARG otherwise. */
+#define EPTV_CONV_TENSOR_MEMORY     0
+#define EPTV_CONV_MMA_SYNC          1
+#define EPTV_CONV_TENSOR_MEMORY_ALL 2
+int eptv_unet_set_conv_kernel(int mode);
+
+/* Synchronises with the device and reports (then clears) the tensor-memory conv's error
+ * flag: EPTV_ERR_TIMEOUT if one of its bounded waits for the MMAs ran out since the last
+ * call (that launch stopped early and its outputs are incomplete), else EPTV_OK. */
+int eptv_unet_tc_status(void);
 
 /* Weight (and bias, if d_db) gradient of eptv_unet_conv3x3, accumulated into FP32 buffers:
  * dw[o][tap][c] += sum_p dy[p][o] x[p + tap][c], db[o] += sum_p dy[p][o].  Same channel

@@ -6,7 +6,8 @@ baseline import this module.  It shares no code with the CUDA path: the system m
 comes from the plain-C Siddon tracer in siddon.c, everything else is numpy in float64,
 written to be checked against the paper by eye.
 
-Functions and the passages they follow:
+Functions and the passages they follow (sharded.py evaluates the same P and P^T on every
+host core, for timing):
   rays / project / backproject .... Eq. (1), Sec. 2.1 (p_ij = intersection length,
                                     Siddon), Sec. 3 (fan-beam arc detector); P^T is the
                                     exact transpose (Eq. A3 of App. III, adjoint identity)
@@ -196,6 +197,17 @@ def project_rays(nx, ny, dx, dy, sx, sy, ux, uy, f):
     rc = _load().og_project(nx, ny, dx, dy, arrs[0].size, *[_dp(a) for a in arrs], _dp(f), _dp(y))
     assert rc == 0
     return y
+
+
+def backproject_rays(nx, ny, dx, dy, sx, sy, ux, uy, y):
+    """P^T y for arbitrary rays (source point, unit direction): the image [ny][nx]."""
+    arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (sx, sy, ux, uy)]
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    assert y.size == arrs[0].size
+    f = np.empty(ny * nx)
+    rc = _load().og_backproject(nx, ny, dx, dy, arrs[0].size, *[_dp(a) for a in arrs], _dp(y), _dp(f))
+    assert rc == 0
+    return f
 
 
 def ray_row(nx, ny, dx, dy, sx, sy, ux, uy):

@@ -25,6 +25,23 @@ constexpr int kTileW = 32, kTileH = 8;
 constexpr int kGdTileRows = 8;
 constexpr int kHistBins = 4096;    // radix-select histogram (12 bits per pass)
 
+// Radix selection over FP32 bit patterns (the sigma order statistic and the generic
+// selections): the key of a value (-0 counts as +0; the selections take non-negative or
+// same-sign inputs, whose keys order like the values), and one pass's histogram update:
+// pass 0 buckets the top 12 bits, pass 1 the next 12 bits of keys with the pass-0 prefix,
+// pass 2 the low 8 bits of keys with the 24-bit prefix.
+__device__ __forceinline__ unsigned int sel_key(float x) {
+    unsigned int b = __float_as_uint(x);
+    return (b == 0x80000000u) ? 0u : b;     // -0 -> +0
+}
+
+__device__ __forceinline__ void sel_hist_add(unsigned int *sh, unsigned int key, int pass,
+                                             unsigned int prefix) {
+    if (pass == 0) atomicAdd(&sh[key >> 20], 1u);
+    else if (pass == 1) { if ((key >> 20) == prefix) atomicAdd(&sh[(key >> 8) & 0xFFFu], 1u); }
+    else { if ((key >> 8) == prefix) atomicAdd(&sh[key & 0xFFu], 1u); }
+}
+
 // Finalisers run by the last block of a reduction.
 enum Fin {
     FIN_NONE = 0,

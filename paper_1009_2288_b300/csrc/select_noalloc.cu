@@ -20,7 +20,7 @@
 
 namespace eptv {
 
-constexpr int kNaBins = 4096;                     // 12-bit buckets (pass 2 uses 256)
+constexpr int kNaBins = kHistBins;                // 12-bit buckets (pass 2 uses 256)
 constexpr int kNaTicket = kNaBins;                // finishing-block ticket
 constexpr int kNaPrefix = kNaBins + 1;            // selected bit prefix so far
 constexpr int kNaRankLo = kNaBins + 2;            // remaining 1-based rank (64-bit)
@@ -29,11 +29,6 @@ constexpr int kNaWords = kNaBins + 64;            // 16.6 KB, 256-byte multiple
 constexpr long kNaMaxN = 2147483647L;             // bucket counts are 32-bit
 
 static __device__ __align__(256) unsigned int g_noalloc_scratch[kNaWords];
-
-__device__ __forceinline__ unsigned int na_key(float x) {
-    const unsigned int b = __float_as_uint(x);
-    return (b == 0x80000000u) ? 0u : b;           // -0 counts as +0
-}
 
 __global__ void na_clear(unsigned int *scr) {
     for (int i = threadIdx.x; i < kNaWords; i += blockDim.x) scr[i] = 0u;
@@ -57,12 +52,7 @@ na_radix_pass(const float *__restrict__ vals, long long n, long long k, int pass
     const long long e0 = (long long)blockIdx.x * 2048;
     for (int q = 0; q < 8; ++q) {
         const long long e = e0 + q * 256 + threadIdx.x;
-        if (e < n) {
-            const unsigned int key = na_key(__ldg(vals + e));
-            if (pass == 0) atomicAdd(&sh[key >> 20], 1u);
-            else if (pass == 1) { if ((key >> 20) == prefix) atomicAdd(&sh[(key >> 8) & 0xFFFu], 1u); }
-            else if ((key >> 8) == prefix) atomicAdd(&sh[key & 0xFFu], 1u);
-        }
+        if (e < n) sel_hist_add(sh, sel_key(__ldg(vals + e)), pass, prefix);   // as the handle-based selection
     }
     __syncthreads();
     for (int b = threadIdx.x; b < nbins; b += 256) {
@@ -141,9 +131,31 @@ int select_kth_noalloc(const float *d_vals, long n, long k, float *d_out, cudaSt
     if (!d_vals || !d_out) { *err = "NULL argument"; return EPTV_ERR_ARG; }
     if (n < 1 || n > kNaMaxN) { *err = "n must be in [1, 2^31 - 1]"; return EPTV_ERR_ARG; }
     if (k < 1 || k > n) { *err = "k must be in [1, n]"; return EPTV_ERR_ARG; }
+    // an error left by earlier work on this thread is reported as such and left pending
+    const cudaError_t e0 = cudaPeekAtLastError();
+    if (e0 != cudaSuccess) { *err = "a CUDA error from earlier work is pending on this thread"; return EPTV_ERR_CUDA; }
     unsigned int *scr = nullptr;
     int rc = na_scratch_for_current_device(&scr, err);
     if (rc) return rc;
+    // both buffers must live on the current device (the scratch array is this device's)
+    int dev = 0;
+    cudaGetDevice(&dev);
+    for (const void *ptr : {(const void *)d_vals, (const void *)d_out}) {
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+            cudaGetLastError();
+            *err = "cudaPointerGetAttributes failed on an argument";
+            return EPTV_ERR_ARG;
+        }
+        if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) {
+            *err = "vals and out must be device memory";
+            return EPTV_ERR_ARG;
+        }
+        if (at.type == cudaMemoryTypeDevice && at.device != dev) {
+            *err = "vals and out must be on the current device";
+            return EPTV_ERR_ARG;
+        }
+    }
     const int nblk = (int)((n + 2047) / 2048);
     na_clear<<<1, 256, 0, st>>>(scr);
     for (int pass = 0; pass <= 2; ++pass)

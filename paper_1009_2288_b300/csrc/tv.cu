@@ -49,10 +49,6 @@ __device__ __forceinline__ float half_edge_T(const float *f, int nx, int ny, flo
 
 // ------------------------------------------------------------------ radix selection
 
-__device__ __forceinline__ unsigned int sel_key(float x) {
-    unsigned int b = __float_as_uint(x);
-    return (b == 0x80000000u) ? 0u : b;     // -0 -> +0
-}
 
 struct SelCtx {
     const float *vals;
@@ -63,13 +59,6 @@ struct SelCtx {
     int n_blocks, b0;
 };
 
-// Histogram one pass: keys with the required prefix add to bucket (key >> shift) & mask.
-__device__ __forceinline__ void sel_hist_add(unsigned int *sh, unsigned int key, int pass,
-                                             unsigned int prefix) {
-    if (pass == 0) atomicAdd(&sh[key >> 20], 1u);
-    else if (pass == 1) { if ((key >> 20) == prefix) atomicAdd(&sh[(key >> 8) & 0xFFFu], 1u); }
-    else { if ((key >> 8) == prefix) atomicAdd(&sh[key & 0xFFu], 1u); }
-}
 
 // Last block (256 threads): find the bucket holding the remaining rank and narrow the
 // prefix.  The histogram is read with independent loads (16 per thread), the per-thread
@@ -340,7 +329,7 @@ k4_gd(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__restrict
             float q = 0.f, T = 0.f, w = 0.f;
             if (e >= 0 && e <= nx && j >= 0 && j < ny)
                 edge_eval(mode, eps2, inv_s2, f10, f11, F[a + 2][b], F[a + 2][b + 1], f00, f01,
-                          W[a + 1][b], W[a + 1][b + 1], &q, &T, &w);
+                          &W[a + 1][b], 1, &q, &T, &w);
             QX[a][b] = q; TXs[a][b] = T; WX[a][b] = w;
         }
         if (b < QYW) {
@@ -349,7 +338,7 @@ k4_gd(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__restrict
             float q = 0.f, T = 0.f, w = 0.f;
             if (e >= 0 && e <= ny && i >= 0 && i < nx)
                 edge_eval(mode, eps2, inv_s2, f01, f11, F[a][b + 2], F[a + 1][b + 2], f00, f10,
-                          W[a][b + 1], W[a + 1][b + 1], &q, &T, &w);
+                          &W[a][b + 1], FW, &q, &T, &w);
             QY[a][b] = q; TYs[a][b] = T; WY[a][b] = w;
         }
     }

@@ -54,11 +54,15 @@ __device__ __forceinline__ void red_release_add_gpu(unsigned int *p, unsigned in
 constexpr long long kP2WaitSpins = 1ll << 26;
 
 __device__ __forceinline__ bool p2_wait(const unsigned int *bar, unsigned int target,
-                                        long long max_cycles) {
+                                        long long max_cycles, volatile int *seen) {
     const long long t0 = clock64();
     for (long long spins = 0; spins < kP2WaitSpins; ++spins) {
-        if (ld_acquire_gpu(bar) >= target) return true;
-        if (spins > 32) __nanosleep(40);
+        if (*seen) return true;                            // another warp of the block saw it
+        if (ld_acquire_gpu(bar) >= target) {
+            *seen = 1;
+            return true;
+        }
+        if (spins > 256) __nanosleep(32);
         if ((spins & 63) == 63 && clock64() - t0 > max_cycles) return false;
     }
     return false;
@@ -113,7 +117,15 @@ k4p_descent(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__re
     float *TY = QY + QYH * QYW;
     float *WY = TY + QYH * QYW;
     __shared__ int s_abort;
+    __shared__ int s_seen[2];                              // barrier seen (per iteration parity)
+    constexpr int kPollers = NT / 32 < 4 ? NT / 32 : 4;
     __shared__ unsigned long long sacc[NV * kAccStride];   // the block's exact sums
+    // candidate trial steps of the next iteration ((K + 1) K <= 32: K <= 4)
+    constexpr bool kCand = (KT + 1) * KT <= 32;
+    __shared__ float cand_f[kCand ? (KT + 1) * KT : 1];
+    __shared__ double cand_d[kCand ? (KT + 1) * KT : 1];
+    struct Record { double e_first, t_step, e_last, t_prev; int nacc, nfail, bad; };
+    Record rec{0.0, 0.0, 0.0, 0.0, 0, 0, 0};
 
     int local;
     const int si = find_slice(map, blockIdx.x, &local);
@@ -138,9 +150,12 @@ k4p_descent(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__re
     }
     const float sig = (float)S.sc[SC_SIGMA];
     const float inv_s2 = 1.0f / (sig * sig);
+    const int k_outer = (int)S.sc[SC_OUTER];
     if (tid == 0) {
         s_misc[0] = S.sc[SC_TPREV];
         s_abort = 0;
+        s_seen[0] = 0;
+        s_seen[1] = 0;
     }
 
     // f = v on the region + 2 (0 outside the image), g = 0, the prior map (edge-replicated)
@@ -191,7 +206,7 @@ k4p_descent(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__re
                 float q = 0.f, T = 0.f, w = 0.f;
                 if (e >= 0 && e <= nx && j >= 0 && j < ny)
                     edge_eval(mode, eps2, inv_s2, f10, f11, F[(a + 2) * FW + b], F[(a + 2) * FW + b + 1],
-                              f00, f01, Wp[(a + 1) * FW + b], Wp[(a + 1) * FW + b + 1], &q, &T, &w);
+                              f00, f01, Wp + (a + 1) * FW + b, 1, &q, &T, &w);
                 QX[a * QXW + b] = q; TX[a * QXW + b] = T; WX[a * QXW + b] = w;
             }
             if (b < QYW) {
@@ -199,7 +214,7 @@ k4p_descent(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__re
                 float q = 0.f, T = 0.f, w = 0.f;
                 if (e >= 0 && e <= ny && i >= 0 && i < nx)
                     edge_eval(mode, eps2, inv_s2, f01, f11, F[a * FW + b + 2], F[(a + 1) * FW + b + 2],
-                              f00, f10, Wp[a * FW + b + 1], Wp[(a + 1) * FW + b + 1], &q, &T, &w);
+                              f00, f10, Wp + a * FW + b + 1, FW, &q, &T, &w);
                 QY[a * QYW + b] = q; TY[a * QYW + b] = T; WY[a * QYW + b] = w;
             }
         }
@@ -253,10 +268,29 @@ k4p_descent(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__re
         if (tid == 0) {
             __threadfence();
             red_release_add_gpu(S.p2bar, 1u);
+        }
+        // while the barrier is pending: the next iteration's trial steps for every outcome
+        // (accepted trial c, or c = K: a failed search), lane c K + m of warp 1
+        if (kCand && (tid >> 5) == 1 && K > 1) {
+            const int lane = tid & 31;
+            if (lane < (K + 1) * K) {
+                const int c = lane / K, m = lane - c * K;
+                const double tp = (c < K) ? s_td[c] : s_td[K - 1] * P->armijo_shrink / P->armijo_grow;
+                const double tmax = P->t_max > 0.0 ? P->t_max : 1.0 / P->lambda;
+                double t = fmin(P->armijo_grow * tp, tmax);
+                for (int q = 0; q < m; ++q) t *= P->armijo_shrink;
+                cand_f[lane] = (float)t;
+                cand_d[lane] = (double)(float)t;
+            }
+        }
+        // lane 0 of up to kPollers warps polls; the first to see every arrival tells the
+        // others through s_seen (polls of several warps in flight shorten the detection)
+        if ((tid & 31) == 0 && (tid >> 5) < kPollers) {
             const unsigned int need = (unsigned int)(it + 1) * (gridDim.x + (unsigned int)pa.bar_extra);
-            if (!p2_wait(S.p2bar, need, pa.wait_cycles)) s_abort = 1;
+            if (!p2_wait(S.p2bar, need, pa.wait_cycles, &s_seen[it & 1])) s_abort = 1;
             __threadfence();
         }
+        if (tid == 0) s_seen[(it + 1) & 1] = 0;          // re-armed for the next iteration
         __syncthreads();
         if (s_abort) {
             if (tid == 0) S.sc[SC_TIMEOUT] = 1.0;
@@ -284,9 +318,27 @@ k4p_descent(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__re
             if (tid == 0) {
                 s_misc[1] = r.t_step;
                 s_misc[0] = r.t_prev;
-                if (local == 0) gd_record(S, P, r, it == 0, it);
-                if (K > 0) trial_steps(P, r.t_prev, K, s_t, s_td);      // for the next iteration
+                if (local == 0) {          // the slice's record, written to its scalars at the end
+                    if (it == 0) rec.e_first = r.e0;
+                    rec.t_step = r.t_step;
+                    rec.e_last = r.e_last;
+                    rec.t_prev = r.t_prev;
+                    rec.nacc += r.accepted;
+                    rec.nfail += 1 - r.accepted;
+                    rec.bad |= r.bad;
+                    if (S.log && k_outer >= 0 && k_outer < S.log_outer && it < S.log_gd)
+                        S.log[(size_t)k_outer * S.log_gd + it] = r.t_step;
+                }
+                if (!(kCand && K > 1) && K > 0 && P->step_rule != EPTV_STEP_FIXED)
+                    trial_steps(P, r.t_prev, K, s_t, s_td);      // for the next iteration
+                s_misc[2] = (double)r.index;
             }
+        }
+        __syncthreads();
+        if (kCand && K > 1 && tid < K && P->step_rule != EPTV_STEP_FIXED) {
+            const int c = (int)s_misc[2];
+            s_t[tid] = cand_f[c * K + tid];
+            s_td[tid] = cand_d[c * K + tid];
         }
         if (ring_at >= 0) G[ring_at] = ring_g;
         __syncthreads();
@@ -315,7 +367,22 @@ k4p_descent(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__re
             if (i < nx && j < ny) S.uT[(size_t)i * ny + j] = fmaxf(F[(r + 2) * FW + c + 2], 0.0f);
         }
     }
-    if (local == 0 && tid == 0) S.sc[SC_OUTER] += 1.0;
+    if (local == 0 && tid == 0) {
+        double *sc = S.sc;
+        sc[SC_E_FIRST] = rec.e_first;
+        sc[SC_TSTEP] = rec.t_step;
+        sc[SC_E_LAST] = rec.e_last;
+        if (P->step_rule == EPTV_STEP_FIXED) {
+            sc[SC_NACC_P2] += (double)pa.n_gd;
+        } else {
+            sc[SC_TPREV] = rec.t_prev;
+            sc[SC_NACC_P2] += (double)rec.nacc;
+            sc[SC_NFAIL] += (double)rec.nfail;
+            sc[SC_NFAIL_P2] += (double)rec.nfail;
+        }
+        if (rec.bad) sc[SC_NONFINITE] = 1.0;
+        sc[SC_OUTER] += 1.0;
+    }
 }
 
 // ------------------------------------------------------------------ host side

@@ -20,11 +20,11 @@ __device__ __forceinline__ float edge_T2(float eps2, float a, float b, float a_u
 }
 
 // One half-edge (either orientation; the argument order of edge_T2): magnitude T, weight
-// w (Eq. 5, 1 for plain TV, or the mean of the two prior values wpa, wpb) and the flux
-// q = w D / T of Eq. (A2).
+// w (Eq. 5, 1 for plain TV, or the mean of the prior values wp[0], wp[wstep] of its two
+// pixels) and the flux q = w D / T of Eq. (A2).
 __device__ __forceinline__ void edge_eval(int mode, float eps2, float inv_s2, float a, float b,
-                                          float a_u, float b_u, float a_d, float b_d, float wpa,
-                                          float wpb, float *q, float *T, float *w) {
+                                          float a_u, float b_u, float a_d, float b_d, const float *wp,
+                                          int wstep, float *q, float *T, float *w) {
     float D;
     const float T2 = edge_T2(eps2, a, b, a_u, b_u, a_d, b_d, &D);
     const float rs = rsqrtf(T2);           // T2 >= eps^2 > 0
@@ -32,7 +32,7 @@ __device__ __forceinline__ void edge_eval(int mode, float eps2, float inv_s2, fl
     float ww;
     if (mode == EPTV_WEIGHTS_EPTV) ww = __expf(-T2 * inv_s2);
     else if (mode == EPTV_WEIGHTS_ONE) ww = 1.0f;
-    else ww = 0.5f * (wpa + wpb);
+    else ww = 0.5f * (wp[0] + wp[wstep]);   // prior map values of the edge's two pixels
     *w = ww;
     *q = ww * D * rs;
 }
@@ -114,6 +114,7 @@ struct GdDecision {
     double e_last;     // (P2) energy after the step (frozen weights)
     double e0;         // energy at the current iterate
     int accepted;      // 1: a trial passed (or fixed step), 0: failed search
+    int index;         // the accepted trial (0 for fixed steps), K after a failed search
     int bad;           // a total or an evaluated trial was not finite
 };
 
@@ -149,6 +150,7 @@ __device__ __forceinline__ GdDecision gd_decide(const double *tot, const double 
         r.t_prev = t_prev_in;
         r.e_last = r.e0 + lamd * (-t * A + 0.5 * t * t * Bg) + tot[4];
         r.accepted = 1;
+        r.index = 0;
         return r;
     }
     // trials a sequential search would have evaluated: up to the accepted one
@@ -159,11 +161,13 @@ __device__ __forceinline__ GdDecision gd_decide(const double *tot, const double 
         r.t_prev = s_td[acc_m];
         r.e_last = r.e0 + dE;
         r.accepted = 1;
+        r.index = acc_m;
     } else {
         r.t_step = 0.0;
         r.t_prev = s_td[K - 1] * P->armijo_shrink / P->armijo_grow;
         r.e_last = r.e0;
         r.accepted = 0;
+        r.index = K;
     }
     return r;
 }
@@ -196,17 +200,64 @@ __device__ __forceinline__ void gd_record(const SliceDev &S, const ParamsDev *P,
 
 namespace eptv {
 
+// One position (a, b) of a 32 x 8 tile (tile_sums below): the fidelity terms of pixel
+// (X0 + b, Y0 + a) when it is the tile's, and the energy / trial terms of its left x-edge
+// and upper y-edge when the tile owns them.
+template <int KT>
+__device__ __forceinline__ void tile_position(int a, int b, int X0, int Y0, int nx, int ny,
+                                              const float *F, int fs, const float *G, int gs,
+                                              const float *V, int vs, const float *TX,
+                                              const float *WX, int xs, const float *TY,
+                                              const float *WY, int ys, int K, const float *s_t,
+                                              float eps2, float *wout, float *sA, float *sB,
+                                              float *sF, float *sJ, float (&dJ)[KT]) {
+    constexpr int TW = 32, TH = 8;
+    const int i = X0 + b, j = Y0 + a;
+    if (a < TH && b < TW && i < nx && j < ny) {
+        const float g = G[(a + 1) * gs + b + 1];
+        const float d = F[(a + 2) * fs + b + 2] - V[(a + 1) * vs + b + 1];
+        *sA = fmaf(g, d, *sA);
+        *sB = fmaf(g, g, *sB);
+        *sF = fmaf(d, d, *sF);
+    }
+    // x-edge between (i - 1, j) and (i, j); y-edge between (i, j - 1) and (i, j)
+    const bool own_x = a < TH && j < ny && i <= nx && (b < TW || i == nx);
+    const bool own_y = b < TW && i < nx && j <= ny && (a < TH || j == ny);
+    const float Tx = TX[(a + 1) * xs + b + 1], wx = own_x ? WX[(a + 1) * xs + b + 1] : 0.0f;
+    const float Ty = TY[(a + 1) * ys + b + 1], wy = own_y ? WY[(a + 1) * ys + b + 1] : 0.0f;
+    *sJ = fmaf(wx, Tx, *sJ);
+    *sJ = fmaf(wy, Ty, *sJ);
+    if (wout) {
+        if (own_x) wout[(size_t)j * (nx + 1) + i] = wx;
+        if (own_y) wout[(size_t)(ny + 1) * (nx + 1) + (size_t)j * (nx + 1) + i] = wy;
+    }
+    if (K && (own_x || own_y)) {
+        const float *Fb = F + a * fs + b;       // Fb[r][c] = f at (i - 2 + c, j - 2 + r)
+        const float *Gb = G + a * gs + b;       // Gb[r][c] = g at (i - 1 + c, j - 1 + r)
+        const float f11 = Fb[fs + 1], f12 = Fb[fs + 2], f21 = Fb[2 * fs + 1], f22 = Fb[2 * fs + 2];
+        const float g00 = Gb[0], g01 = Gb[1], g10 = Gb[gs], g11 = Gb[gs + 1];
+        float aex = 0.0f, bex = 0.0f, aey = 0.0f, bey = 0.0f;
+        if (own_x)
+            edge_ab(f21, f22, Fb[3 * fs + 1], Fb[3 * fs + 2], f11, f12,
+                    g10, g11, Gb[2 * gs], Gb[2 * gs + 1], g00, g01, &aex, &bex);
+        if (own_y)
+            edge_ab(f12, f22, Fb[fs + 3], Fb[2 * fs + 3], f11, f21,
+                    g01, g11, Gb[2], Gb[gs + 2], g00, g10, &aey, &bey);
+        trial_accum<KT>(K, s_t, eps2, Tx, wx, aex, bex, Ty, wy, aey, bey, dJ);
+    }
+}
+
 // One 32 x 8 tile's share of a GD iteration's sums (Eq. 9's energy and the Armijo trial
 // changes), evaluated by 128 threads (vt = 0..127) from the tile's values in shared memory:
 //   sA = sum <g, f - v>, sB = sum g^2, sF = sum (f - v)^2 over the tile's pixels,
 //   sJ = sum w T and dJ[m] = sum w (T'(t_m) - T) over the tile's owned half-edges (the left
 //   x-edge and the upper y-edge of every pixel, and the edges on the image's right / lower
 //   border when the tile touches it).
-// Thread vt takes the pixels (a, b) = (vt / 32, vt % 32) and (a + 4, b) of the tile, each
-// with its left x-edge and upper y-edge, then (vt < 8) the right-border x-edge of row vt,
-// or (32 <= vt < 64) the lower-border y-edge of column vt - 32: every value is a fixed
-// function of the tile, so the per-tile sums (FP32 per thread and warp, FP64 over the four
-// warps in order) do not depend on which kernel or block evaluates the tile.
+// Thread vt takes the vertically adjacent positions (a, b) = (2 (vt / 32), vt % 32) and
+// (a + 1, b) -- their stencils share most of their values -- then (vt < 8) the right-border
+// x-edge of row vt, or (32 <= vt < 64) the lower-border y-edge of column vt - 32: every
+// value is a fixed function of the tile, so the per-tile sums (FP32 per thread and warp)
+// do not depend on which kernel or block evaluates the tile.
 // Frames (row stride in elements): F[r][c] = f at pixel (X0 - 2 + c, Y0 - 2 + r);
 // G[r][c] = g and V[r][c] = v at pixel (X0 - 1 + c, Y0 - 1 + r); TX / WX [r][c] = x-edge
 // between pixel columns X0 - 2 + c and X0 - 1 + c in row Y0 - 1 + r; TY / WY [r][c] =
@@ -219,48 +270,18 @@ __device__ __forceinline__ void tile_sums(int vt, int X0, int Y0, int nx, int ny
                                           const float *s_t, float eps2, float *wout,
                                           float *sA, float *sB, float *sF, float *sJ, float (&dJ)[KT]) {
     constexpr int TW = 32, TH = 8;
-#pragma unroll 1
-    for (int k = 0; k < 3; ++k) {
-        int a, b;
-        if (k < 2) { a = (vt >> 5) + 4 * k; b = vt & 31; }
-        else if (vt < TH) { a = vt; b = TW; }                  // right-border x-edges
-        else if (vt >= 32 && vt < 32 + TW) { a = TH; b = vt - 32; }   // lower-border y-edges
-        else break;
-        const int i = X0 + b, j = Y0 + a;
-        // pixel (i, j): fidelity sums
-        if (a < TH && b < TW && i < nx && j < ny) {
-            const float g = G[(a + 1) * gs + b + 1];
-            const float d = F[(a + 2) * fs + b + 2] - V[(a + 1) * vs + b + 1];
-            *sA = fmaf(g, d, *sA);
-            *sB = fmaf(g, g, *sB);
-            *sF = fmaf(d, d, *sF);
-        }
-        // x-edge between (i - 1, j) and (i, j); y-edge between (i, j - 1) and (i, j)
-        const bool own_x = a < TH && j < ny && i <= nx && (b < TW || i == nx);
-        const bool own_y = b < TW && i < nx && j <= ny && (a < TH || j == ny);
-        const float Tx = TX[(a + 1) * xs + b + 1], wx = own_x ? WX[(a + 1) * xs + b + 1] : 0.0f;
-        const float Ty = TY[(a + 1) * ys + b + 1], wy = own_y ? WY[(a + 1) * ys + b + 1] : 0.0f;
-        *sJ = fmaf(wx, Tx, *sJ);
-        *sJ = fmaf(wy, Ty, *sJ);
-        if (wout) {
-            if (own_x) wout[(size_t)j * (nx + 1) + i] = wx;
-            if (own_y) wout[(size_t)(ny + 1) * (nx + 1) + (size_t)j * (nx + 1) + i] = wy;
-        }
-        if (K && (own_x || own_y)) {
-            const float *Fb = F + a * fs + b;       // Fb[r][c] = f at (i - 2 + c, j - 2 + r)
-            const float *Gb = G + a * gs + b;       // Gb[r][c] = g at (i - 1 + c, j - 1 + r)
-            const float f11 = Fb[fs + 1], f12 = Fb[fs + 2], f21 = Fb[2 * fs + 1], f22 = Fb[2 * fs + 2];
-            const float g00 = Gb[0], g01 = Gb[1], g10 = Gb[gs], g11 = Gb[gs + 1];
-            float aex = 0.0f, bex = 0.0f, aey = 0.0f, bey = 0.0f;
-            if (own_x)
-                edge_ab(f21, f22, Fb[3 * fs + 1], Fb[3 * fs + 2], f11, f12,
-                        g10, g11, Gb[2 * gs], Gb[2 * gs + 1], g00, g01, &aex, &bex);
-            if (own_y)
-                edge_ab(f12, f22, Fb[fs + 3], Fb[2 * fs + 3], f11, f21,
-                        g01, g11, Gb[2], Gb[gs + 2], g00, g10, &aey, &bey);
-            trial_accum<KT>(K, s_t, eps2, Tx, wx, aex, bex, Ty, wy, aey, bey, dJ);
-        }
-    }
+    const int a = 2 * (vt >> 5), b = vt & 31;
+    tile_position<KT>(a, b, X0, Y0, nx, ny, F, fs, G, gs, V, vs, TX, WX, xs, TY, WY, ys, K, s_t, eps2,
+                      wout, sA, sB, sF, sJ, dJ);
+    tile_position<KT>(a + 1, b, X0, Y0, nx, ny, F, fs, G, gs, V, vs, TX, WX, xs, TY, WY, ys, K, s_t,
+                      eps2, wout, sA, sB, sF, sJ, dJ);
+    // edges on the image's right / lower border (only tiles that reach it own them)
+    if (X0 + TW >= nx && vt < TH)
+        tile_position<KT>(vt, TW, X0, Y0, nx, ny, F, fs, G, gs, V, vs, TX, WX, xs, TY, WY, ys, K, s_t,
+                          eps2, wout, sA, sB, sF, sJ, dJ);
+    else if (Y0 + TH >= ny && vt >= 32 && vt < 32 + TW)
+        tile_position<KT>(TH, vt - 32, X0, Y0, nx, ny, F, fs, G, gs, V, vs, TX, WX, xs, TY, WY, ys, K,
+                          s_t, eps2, wout, sA, sB, sF, sJ, dJ);
 }
 
 }  // namespace eptv

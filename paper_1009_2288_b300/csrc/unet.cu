@@ -17,6 +17,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "eptv_internal.cuh"
 #include "unet.cuh"
@@ -484,8 +485,17 @@ static cudaError_t launch_conv_t(const bf16 *x, int n, int H, int W, int xs, int
     return cudaGetLastError();
 }
 
+// 0: the tcgen05 / tensor-memory kernel for the shapes where it is not slower (else
+// mma.sync); 1: mma.sync always; 2: the tensor-memory kernel wherever it tiles the image
+static std::atomic<int> g_conv_path{0};
+
 cudaError_t unet_conv3x3(const void *x, int n, int H, int W, int cin, int xs, int xo, const void *wt,
                          const float *b, int cout, void *y, int ys, int yo, int relu, cudaStream_t st) {
+    const int path = g_conv_path.load(std::memory_order_relaxed);
+    if (path != 1) {
+        const cudaError_t e = unet_conv3x3_tc(x, n, H, W, cin, xs, xo, wt, b, cout, y, ys, yo, relu, st, path == 2);
+        if (e != cudaErrorNotSupported) return e;
+    }
     const bf16 *X = static_cast<const bf16 *>(x);
     const bf16 *Wt = static_cast<const bf16 *>(wt);
     bf16 *Y = static_cast<bf16 *>(y);
@@ -662,6 +672,21 @@ int eptv_unet_conv3x3_wgrad(const void *d_x, int n, int h, int w, int cin, int x
     if (!al16(d_x) || !al16(d_dy)) return report_error(EPTV_ERR_ARG, "x and dy must be 16-byte aligned");
     return unet_rc(unet_conv3x3_wgrad(d_x, n, h, w, cin, x_stride, x_off, d_dy, dy_stride, dy_off,
                                       cout, d_dw, d_db, (cudaStream_t)stream));
+}
+
+int eptv_unet_set_conv_kernel(int mode) {
+    if (mode != EPTV_CONV_TENSOR_MEMORY && mode != EPTV_CONV_MMA_SYNC && mode != EPTV_CONV_TENSOR_MEMORY_ALL)
+        return report_error(EPTV_ERR_ARG, "bad conv kernel mode");
+    g_conv_path.store(mode);
+    return 0;
+}
+
+int eptv_unet_tc_status(void) {
+    int flag = 0;
+    const cudaError_t e = unet_tc_status(&flag);
+    if (e != cudaSuccess) return report_error(EPTV_ERR_CUDA, cudaGetErrorString(e));
+    if (flag) return report_error(EPTV_ERR_TIMEOUT, "a bounded wait of the tensor-core conv ran out");
+    return 0;
 }
 
 int eptv_unet_weights_to_bf16(const float *d_w, int cout, int cin, void *d_wf, void *d_wb, void *stream) {

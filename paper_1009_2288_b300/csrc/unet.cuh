@@ -8,6 +8,12 @@ namespace eptv {
 extern thread_local long long g_launch_count;   // kernels launched on this thread (cgls.cu)
 
 bool unet_conv_supported(int cin, int cout);
+// tensor-memory (tcgen05) path of the 3x3 conv (unet_tc.cu): cudaErrorNotSupported for
+// image widths it does not tile; and its error flag (1: a bounded wait ran out)
+cudaError_t unet_conv3x3_tc(const void *x, int n, int H, int W, int cin, int xs, int xo, const void *wt,
+                            const float *b, int cout, void *y, int ys, int yo, int relu, cudaStream_t st,
+                            bool all_shapes);
+cudaError_t unet_tc_status(int *flag);
 cudaError_t unet_conv3x3(const void *x, int n, int H, int W, int cin, int xs, int xo, const void *wt,
                          const float *b, int cout, void *y, int ys, int yo, int relu, cudaStream_t st);
 cudaError_t unet_conv3x3_wgrad(const void *x, int n, int H, int W, int cin, int xs, int xo,

@@ -25,7 +25,7 @@ EXPORTED = [
     "eptv_select_kth", "eptv_reconstruct_batched", "eptv_last_error", "eptv_version",
     "eptv_get_log", "eptv_select_kth_noalloc", "eptv_set_tuning", "eptv_set_tv_kernel", "eptv_debug_set_p2_wait", "eptv_autotune",
     "eptv_autotune_batched", "eptv_unet_conv3x3", "eptv_unet_conv3x3_wgrad",
-    "eptv_unet_weights_to_bf16", "eptv_unet_maxpool2", "eptv_unet_maxpool2_bwd",
+    "eptv_unet_weights_to_bf16", "eptv_unet_set_conv_kernel", "eptv_unet_tc_status", "eptv_unet_maxpool2", "eptv_unet_maxpool2_bwd",
     "eptv_unet_upsample2", "eptv_unet_upsample2_bwd", "eptv_unet_relu_bwd", "eptv_unet_head",
     "eptv_unet_adam", "eptv_unet_pack_input", "eptv_set_operator", "eptv_matrix_info",
     "eptv_copy_matrix", "eptv_backproject_eq11", "eptv_quality_metrics",
@@ -139,6 +139,8 @@ def load():
         "eptv_unet_conv3x3_wgrad": (c_int, [vp, c_int, c_int, c_int, c_int, c_int, c_int, vp, c_int,
                                             c_int, c_int, vp, vp, vp]),
         "eptv_unet_weights_to_bf16": (c_int, [vp, c_int, c_int, vp, vp, vp]),
+        "eptv_unet_set_conv_kernel": (c_int, [c_int]),
+        "eptv_unet_tc_status": (c_int, []),
         "eptv_unet_maxpool2": (c_int, [vp, c_int, c_int, c_int, c_int, c_int, c_int, vp, c_int, c_int, vp]),
         "eptv_unet_maxpool2_bwd": (c_int, [vp, c_int, c_int, c_int, c_int, c_int, c_int, vp, c_int,
                                            c_int, vp, c_int, c_int, c_int, vp]),
@@ -340,9 +342,14 @@ def eptv_select_kth(geom: Geometry, vals, k: int, out, stream=None):
 
 def eptv_select_kth_noalloc(vals, k: int, out, stream=None):
     """k-th smallest of vals without a geometry handle and without any device
-    allocation (working memory compiled into the library); see eptv.h."""
-    _check(load().eptv_select_kth_noalloc(_ptr(vals, None, "vals"), vals.numel(), int(k),
-                                          _ptr(out, 1, "out"), _stream(stream)))
+    allocation (working memory compiled into the library); see eptv.h.  Runs on the
+    device that holds vals; out must be on the same device."""
+    import torch
+    if out.device != vals.device:
+        raise EptvError(-1, "out must be on the device of vals")
+    with torch.cuda.device(vals.device):
+        _check(load().eptv_select_kth_noalloc(_ptr(vals, None, "vals"), vals.numel(), int(k),
+                                              _ptr(out, 1, "out"), _stream(stream)))
     return out
 
 
@@ -624,3 +631,18 @@ def eptv3_report_energy(geom: Geometry3, p: EptvParams, sigma_ref: float, f, y, 
     _check(load().eptv3_report_energy(geom.handle, ctypes.byref(pp), float(sigma_ref), _ptr(f, geom.n_vox, "f"),
                                       _ptr(y, geom.n_rays, "y"), ctypes.byref(out), _stream(stream)))
     return out.value
+
+
+CONV_TENSOR_MEMORY, CONV_MMA_SYNC, CONV_TENSOR_MEMORY_ALL = 0, 1, 2
+
+
+def eptv_unet_set_conv_kernel(mode: int):
+    """Kernel of the 3x3 convs: CONV_TENSOR_MEMORY (tcgen05 for the shapes where it is not
+    slower), CONV_MMA_SYNC, or CONV_TENSOR_MEMORY_ALL (tcgen05 wherever it tiles the
+    image); see eptv.h."""
+    _check(load().eptv_unet_set_conv_kernel(int(mode)))
+
+
+def eptv_unet_tc_status():
+    """Raises EptvError(EPTV_ERR_TIMEOUT) if a bounded wait of the tensor-memory conv ran out."""
+    _check(load().eptv_unet_tc_status())

@@ -7,6 +7,8 @@ with sigma_ref = the oracle's last sigma.
     python tests/golden/make_oracle_energy.py c2   # 512x512, 40 x 888, 100 iterations
     python tests/golden/make_oracle_energy.py c1   # 128x128, 30 x 256, 50 iterations
     python tests/golden/make_oracle_energy.py c4 1 # 256x256, 30 x 888, 50 iterations, seed 1
+    python tests/golden/make_oracle_energy.py c3 100  # one slice of the batched workload
+                                                      # (seed 100: 512^2; 101: 256^2; 102: 384^2)
 """
 import json
 import os
@@ -24,6 +26,9 @@ def main(which: str, seed=None):
     if which == "c4":
         case = I.make_c4(int(seed), with_truth=True)
         which = f"c4_seed{int(seed)}"
+    elif which == "c3":
+        case = I.make_c3_slice(int(seed), with_truth=True)
+        which = f"c3_seed{int(seed)}"
     else:
         case = {"c1": I.make_c1, "c2": I.make_c2}[which](with_truth=True)
     p = I.EptvParams(n_outer=case.n_outer)

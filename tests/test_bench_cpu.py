@@ -1,6 +1,7 @@
 """Host-side pieces of the benchmark that its numbers rest on, checked on the CPU: the
 nonzero count behind the roofline's algorithmic bytes (against the FP64 oracle's rows of
-P), and the JSON line of the reference arm (the oracle timed on the host)."""
+P), and the JSON line of the reference arm (the oracle timed on the host cores, its P and
+P^T sharded over them)."""
 import io
 import json
 from contextlib import redirect_stdout
@@ -39,6 +40,8 @@ def test_reference_arm_prints_the_contract_line():
     assert line["impl"] == "reference" and line["metric"] == bench.METRIC
     assert line["unit"] == "iterations/s" and line["value"] > 0 and line["higher_is_better"]
     assert line["config"]["workload"] == bench.WORKLOAD
-    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["cores"] <= cb["host_cores"]
+    assert cb["cpu"] and cb["value"] == line["value"]
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"],
                            "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}

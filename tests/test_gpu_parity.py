@@ -549,7 +549,10 @@ def test_batched_equals_single():
 def test_batched_uneven_slices_match_single_and_oracle():
     """Six slices of the batched workload (mixed sizes, view and bin counts) in one
     batch: identical to the single-slice path, and -- after the batch autotuner changed
-    the launch shapes -- still within 1e-4 of the oracle after 3 iterations."""
+    the launch shapes -- against the oracle after 3 iterations for one slice of each size
+    (512^2 x 54 views, 256^2 x 58, 384^2 x 26): within max(1e-4, 3x the oracle's own change
+    under 1e-6 perturbations of P and P^T), both printed (the 26-view slice is the least
+    well conditioned: the oracle itself moves by ~1.2e-4 there)."""
     cases = I.make_c3(6, with_truth=False)
     assert len({(c.geom.nx, c.geom.n_views, c.geom.n_bins) for c in cases}) > 1
     p = I.EptvParams(n_outer=3)
@@ -568,10 +571,16 @@ def test_batched_uneven_slices_match_single_and_oracle():
     assert k1 in (4, 8, 16) and k2 in (1, 2, 4, 8, 16)
     fs = [torch.zeros(c.geom.n_pix, device=DEV) for c in cases]
     E.eptv_reconstruct_batched(geos, p, ys, fs)
-    for i in (0, 3):
+    assert sorted(cases[i].geom.nx for i in (0, 1, 2)) == [256, 384, 512]
+    for i in (0, 1, 2):
         c = cases[i]
         want = O.reconstruct(O.Operator(c.geom), c.y, p)
-        assert rel(np64(fs[i]).reshape(c.geom.ny, c.geom.nx), want) < 1e-4
+        err = rel(np64(fs[i]).reshape(c.geom.ny, c.geom.nx), want)
+        floor = rel(O.reconstruct(_perturbed(O.Operator(c.geom), 77, 1e-6), c.y, p), want)
+        bound = max(1e-4, 3 * floor)
+        print(f"batched slice {c.name}: 3 iterations, image rel L2 {err:.3e}, oracle's own change "
+              f"under 1e-6 perturbations {floor:.3e}, bound {bound:.3e}")
+        assert err <= bound
 
 
 def test_bad_arguments_raise_without_gpu_work():

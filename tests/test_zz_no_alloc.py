@@ -45,3 +45,33 @@ def test_noalloc_selection_rejects_out_of_range_sizes():
     assert ei.value.code == -1
     with pytest.raises(E.EptvError):
         E.eptv_select_kth_noalloc(torch.ones(5, device=DEV), 0, out)
+
+
+def test_noalloc_selection_allocates_nothing_and_handles_every_bucket():
+    """After a warm-up call the device's free memory does not move across calls.  Values
+    spread over all binades (pass-0 buckets across the exponent range), a selected value
+    whose low byte is 0xFF (the last bucket of the final 8-bit pass), and a mix of -0.0
+    and +0.0 (one key) all select exactly what np.partition selects."""
+    rng = np.random.Generator(np.random.PCG64(7))
+    n = 200_003
+    wide = (rng.uniform(1.0, 2.0, n) * 2.0 ** rng.integers(-126, 127, n)).astype(np.float32)
+    x = np.array([0x3F8000FF], dtype=np.uint32).view(np.float32)[0]       # low byte 0xFF
+    wide[12345] = x
+    k_x = int(np.count_nonzero(wide < x)) + 1
+    zeros = np.where(rng.uniform(size=n) < 0.5, np.float32(-0.0), np.float32(0.0)).astype(np.float32)
+    zeros[: n // 10] = rng.uniform(0, 1, n // 10).astype(np.float32)
+    out = torch.empty(1, device=DEV)
+    tw = torch.as_tensor(wide, device=DEV)
+    E.eptv_select_kth_noalloc(tw, 1, out)                 # warm-up (looks up the array)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for vals, ks in ((wide, [1, n // 2, k_x, n - 3, n]), (zeros, [1, n // 3, n - n // 10, n])):
+        tv = torch.as_tensor(vals, device=DEV)
+        for k in ks:
+            E.eptv_select_kth_noalloc(tv, k, out)
+            torch.cuda.synchronize()
+            assert out.item() == float(np.partition(vals, k - 1)[k - 1])
+    E.eptv_select_kth_noalloc(tw, k_x, out)
+    torch.cuda.synchronize()
+    assert out.item() == float(x)
+    assert free0 == torch.cuda.mem_get_info()[0]

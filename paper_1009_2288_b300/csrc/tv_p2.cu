@@ -8,20 +8,24 @@
 //   phase 2  T, w, q = w D / T of every half-edge around the region + 1 (Eqs. A3, 5);
 //   phase 3  g = lambda (f - v) + dJ/df on the region + 1 (Eqs. 9, A2); the owned values go
 //            to an exchange image;
-//   phase 4  per tile, in K4's thread mapping: the fidelity sums <g, f-v>, |g|^2, |f-v|^2
-//            and, for every trial step, the energy change of the owned half-edges with the
-//            weights frozen; each tile's FP64 sums go into the slice's exact accumulators
-//            (one set per GD iteration, three sets in rotation);
-//   barrier  one grid-wide arrival / wait (bounded);
+//   phase 4  per tile (tile_sums, the per-thread assignment K4 uses): the fidelity sums
+//            <g, f-v>, |g|^2, |f-v|^2 and, for every trial step, the energy change of the
+//            owned half-edges with the weights frozen; each warp adds its FP32 sums exactly
+//            (integer fixed point) into the block's accumulators, and the block's words go
+//            into the slice's accumulators (one set per GD iteration, three in rotation);
+//   barrier  one grid-wide arrival / wait (bounded), polled by several warps; meanwhile
+//            warp 1 prepares the next iteration's trial steps for every possible outcome;
 //   decide   every block reads the exact totals and takes the same FP64 Armijo decision
-//            (the first passing trial); the slice's first block records it;
+//            (the first passing trial); the slice's first block keeps the record and
+//            writes it to the slice's scalars and log once, at the end;
 //   apply    f <- f - t g on the region + 2, the ring 2 of g read from the neighbours'
 //            exchange values of this iteration.
 // After the last iteration the owned pixels get f = max(f, 0) (step 3) and go to u and u^T.
 //
-// Because the per-pixel / per-edge arithmetic is K4's (tv_stencil.cuh), the per-tile sums
-// use K4's thread mapping, and the cross-tile sums are exact, K4p produces bit for bit the
-// same iterates, steps and scalars as n_gd launches of K4 followed by K4u.
+// Because the per-pixel / per-edge arithmetic is K4's (tv_stencil.cuh), every warp's sums
+// are the same fixed functions of its tile in both kernels, and everything above a warp is
+// summed exactly, K4p produces bit for bit the same iterates, steps and scalars as n_gd
+// launches of K4 followed by K4u.
 //
 // Co-residency: the launch is cooperative (all blocks resident or the launch fails), and
 // every wait has a bound: a block that waits longer than about a second sets SC_TIMEOUT in

@@ -180,7 +180,8 @@ def source_sha(files):
 
 
 def load_counters(kernel, files):
-    """DRAM bytes per launch from the committed ncu summary, if taken on this source."""
+    """DRAM bytes per unit of work (a launch; a GD iteration for the (P2) kernel) from the
+    committed ncu summary, if taken on this source."""
     path = os.path.join(ROOT, "profiles", "counters.json")
     if not os.path.exists(path):
         return None
@@ -191,7 +192,7 @@ def load_counters(kernel, files):
     ent = data.get(kernel)
     if not ent or ent.get("source_sha") != source_sha(files):
         return None
-    return ent.get("dram_bytes_per_launch")
+    return ent.get("dram_bytes_per_unit", ent.get("dram_bytes_per_launch"))
 
 
 def measured_peaks():
@@ -623,7 +624,7 @@ def run_cone(dev, stream, peak, n_outer=5, steps=2, scale=1):
     f.mul_(1e-4)
     yb = torch.empty(g.n_rays, device=dev)
     best = None
-    for seg in (4, 8, 16):
+    for seg in (2, 4, 8, 16):
         E.eptv3_set_tuning(geo, seg)
         t = time_kernel(lambda: E.eptv3_project(geo, f, yb), n=5)
         if best is None or t < best[1]:
@@ -631,7 +632,14 @@ def run_cone(dev, stream, peak, n_outer=5, steps=2, scale=1):
     E.eptv3_set_tuning(geo, best[0])
     t_p = best[1]
     fb = torch.empty_like(f)
-    t_pt = time_kernel(lambda: E.eptv3_backproject(geo, y, fb), n=5)
+    best_zp = None
+    for zp in (2, 4):
+        E.eptv3_set_backprojector_stack(geo, zp)
+        t = time_kernel(lambda: E.eptv3_backproject(geo, y, fb), n=5)
+        if best_zp is None or t < best_zp[1]:
+            best_zp = (zp, t)
+    E.eptv3_set_backprojector_stack(geo, best_zp[0])
+    t_pt = best_zp[1]
     algo = 8 * nnz + 4 * (g.n_vox + g.n_rays)
     p = I.EptvParams(n_outer=n_outer)
     E.eptv3_reconstruct(geo, I.EptvParams(n_outer=1), y, f.zero_(), report=False)
@@ -647,7 +655,7 @@ def run_cone(dev, stream, peak, n_outer=5, steps=2, scale=1):
     ms = statistics.mean(times)
     return {"workload": f"cone_{g.nx}x{g.ny}x{g.nz}_{g.n_views}v_{g.nu}x{g.nv}",
             "create_s": t_create, "synth_s": t_synth,
-            "nnz": nnz, "k31_seg": best[0],
+            "nnz": nnz, "k31_seg": best[0], "k32_zp": best_zp[0],
             "project_ms": t_p * 1e3, "backproject_ms": t_pt * 1e3,
             "project_equiv_gbs": algo / t_p / 1e9, "project_frac": algo / t_p / 1e9 / peak,
             "backproject_equiv_gbs": algo / t_pt / 1e9, "backproject_frac": algo / t_pt / 1e9 / peak,

@@ -288,8 +288,11 @@ typedef struct eptv3_geometry eptv3_geometry;
  * EPTV_ERR_CUDA. */
 int eptv3_create_geometry(const eptv3_geometry_desc *desc, eptv3_geometry **out);
 void eptv3_destroy_geometry(eptv3_geometry *g);
-/* Warps per 32-ray block of the 3-D projector (4, 8 or 16). */
+/* Warps per 32-ray block of the 3-D projector (2, 4, 8 or 16). */
 int eptv3_set_tuning(eptv3_geometry *g, int seg);
+/* Voxels stacked in z per thread of the 3-D back projector (2 or 4; default 4).  The
+ * result does not depend on it: every voxel sums the same terms in the same order. */
+int eptv3_set_backprojector_stack(eptv3_geometry *g, int zp);
 /* d_y [n_rays] = P d_f [n_vox]; d_f = P^T d_y. */
 int eptv3_project(const eptv3_geometry *g, const float *d_f, float *d_y, void *stream);
 int eptv3_backproject(const eptv3_geometry *g, const float *d_y, float *d_f, void *stream);

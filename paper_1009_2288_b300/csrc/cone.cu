@@ -149,38 +149,51 @@ k31_project(Cone C, const float *__restrict__ f, const float *__restrict__ y_res
                 float him = cross_t(grid_line((float)(cm + ohm), dm, m0), Pm, im);
                 float loz = cross_t(grid_line((float)(cz + olz), C.dz, C.z0), R.pz, iz);
                 float hiz = cross_t(grid_line((float)(cz + ohz), C.dz, C.z0), R.pz, iz);
-                float fr = (float)(rs + 1);
-                float tac = t0;
                 // The slab interval is clipped to the volume's (m, z) extent [t_lo, t_hi]:
                 // plane parameters are monotone in the plane index, so for a cell inside the
                 // volume the clipping changes neither its largest entry nor its smallest
                 // exit plane and the clipped length is bit-identical to the canonical
                 // six-plane formula; a cell outside gets length exactly 0.  The cell's
                 // offset in the volume is carried along (32 bits: n_vox < 2^31).
+                //
+                // One loop iteration per cell: the walk leaves the cell through the nearest
+                // of its M, m and z exit planes (M last on a tie with the clipped M exit,
+                // m before z on a tie), so the lanes of a warp step together for as many
+                // iterations as their longest walk, instead of each slab costing the warp
+                // its lane with the most crossings.  A cell's largest entry plane is the
+                // previous cell's exit (entry planes only grow along the walk, and the one
+                // just crossed is the largest): tin = max(tin, exit) is the canonical max of
+                // the three entry planes, exactly, for every cell inside the volume, and
+                // beyond the volume's exit both give length 0.  The next crossing of each
+                // axis is evaluated every step (three FMA-pipe triples, no operand selects);
+                // the one crossed is kept.  Cells of nonzero length are inside the volume
+                // (outside it every length is 0, see above); the clamp of the offset only
+                // keeps the load in bounds.
                 const int step_m = sgm * sm, step_z = sgz * (int)sz;
+                const float sgm_f = (float)sgm, sgz_f = (float)sgz;
+                const unsigned last_vox = (unsigned)(C.n_vox - 1);
                 int idx = cz * (int)sz + rs * sM + cm * sm;
-                for (int r = rs; r <= re; ++r) {
-                    const float tb = cross_t(grid_line(fr, dM, M0), PM, iM);
-                    const float tbc = fminf(tb, t_hi);
-                    fr += 1.0f;
-                    // walk the (m, z) cells the ray crosses inside [tac, tbc]
-                    for (int it = 0; it < 6; ++it) {
-                        const float lc = fmaxf(0.0f, __fsub_rn(fminf(fminf(tbc, him), hiz),
-                                                              fmaxf(fmaxf(tac, lom), loz)));
-                        if (lc > 0.0f && (unsigned)cm < (unsigned)nm && (unsigned)cz < (unsigned)C.nz)
-                            acc = fmaf(lc, __ldg(f + idx), acc);
-                        const float nxt = fminf(him, hiz);
-                        if (!(nxt < tbc)) break;
-                        if (him <= hiz) {
-                            cm += sgm; idx += step_m; lom = him;
-                            him = cross_t(grid_line((float)(cm + ohm), dm, m0), Pm, im);
-                        } else {
-                            cz += sgz; idx += step_z; loz = hiz;
-                            hiz = cross_t(grid_line((float)(cz + ohz), C.dz, C.z0), R.pz, iz);
-                        }
-                    }
-                    idx += sM;
-                    tac = fmaxf(tb, t_lo);
+                float tin = fmaxf(fmaxf(t0, lom), loz);
+                float tbc = fminf(cross_t(grid_line((float)(rs + 1), dM, M0), PM, iM), t_hi);
+                float kM = (float)(rs + 2);                       // next plane index, per axis
+                float km = (float)(cm + ohm) + sgm_f;
+                float kz = (float)(cz + ohz) + sgz_f;
+                const float kend = (float)(re + 2);               // M plane after the last slab's exit
+                const int cap = (re - rs + 1) + nm + C.nz + 2;    // each step moves one index
+                for (int it = 0; it < cap; ++it) {
+                    const float mn = fminf(him, hiz);
+                    const float ex = fminf(tbc, mn);
+                    const float lc = fmaxf(0.0f, __fsub_rn(ex, tin));
+                    if (lc > 0.0f) acc = fmaf(lc, __ldg(f + min((unsigned)idx, last_vox)), acc);
+                    tin = fmaxf(tin, ex);
+                    const bool adv_M = !(mn < tbc);
+                    if (adv_M && kM == kend) break;
+                    const float tnM = cross_t(grid_line(kM, dM, M0), PM, iM);
+                    const float tnm = cross_t(grid_line(km, dm, m0), Pm, im);
+                    const float tnz = cross_t(grid_line(kz, C.dz, C.z0), R.pz, iz);
+                    if (adv_M) { tbc = fminf(tnM, t_hi); kM += 1.0f; idx += sM; }
+                    else if (him <= hiz) { him = tnm; km += sgm_f; idx += step_m; }
+                    else { hiz = tnz; kz += sgz_f; idx += step_z; }
                 }
             }
         }
@@ -217,15 +230,16 @@ k32_scale(const float *__restrict__ y, const float *__restrict__ fac, int npix, 
     ys[r] = __ldg(y + r) * __ldg(fac + i);
 }
 
-// Thread = two voxels stacked in z, (ix, iy, 2 iz2) and (ix, iy, 2 iz2 + 1); block =
-// 256 (ix, iy) of one iz2 (grid.y).  A voxel's detector columns do not depend on z, and a
-// column's x-y chord through the pair (its x and y plane parameters) does not depend on
-// the row, so the pair shares, per view, its corner projections and, per column, the
+// Thread = ZP voxels stacked in z, (ix, iy, ZP iz_b + q), q < ZP; block = 256 (ix, iy) of
+// one z block iz_b (grid.y).  A voxel's detector columns do not depend on z, and a
+// column's x-y chord through the stack (its x and y plane parameters) does not depend on
+// the row, so the stack shares, per view, its corner projections and, per column, the
 // chord.  The z planes of a row depend on the row alone and all threads of a block have
 // the same z planes: the block tabulates, in shared memory, each row's parameter interval
-// through both voxels of the pair, for the band of rows that can meet its slab at any
+// through each voxel of the stack, for the band of rows that can meet its slab at any
 // depth of the volume.
-constexpr int kZPair = 2;
+constexpr int kZPair = 2;                                   // smallest stack (grid and workspace bounds)
+constexpr int kZStackMax = 4;                               // tallest stack (row bands)
 
 // first and last detector row of the band of the slab [Za, Zb]: depths of the volume
 // sid + D', |D'| <= rxy; half a row of margin (the per-column bounds use 0.01)
@@ -237,33 +251,40 @@ __device__ __forceinline__ void k32_band(const Cone &C, float Za, float Zb, int 
     b1 = min(b1, b0 + C.band_max - 1);
 }
 
+template <int ZP>
 __global__ void __launch_bounds__(256, 4)
 k32_backproject(Cone C, const float *__restrict__ ys, float *__restrict__ out, double *__restrict__ partials,
                 SliceDev *S, int fin)
 {
+    constexpr int NQ = ZP / 2;                              // float4 per row: (lo, hi) of two voxels
     const double gamma_pre = threadIdx.x == 0 ? fin_gamma(S->sc, fin) : 0.0;
-    extern __shared__ float4 s_zt[];                       // [band]: (lo, hi) of voxel 0, of voxel 1
+    extern __shared__ float4 s_zt[];                       // [band][NQ]
     __shared__ double rsm[2 * 8];
     __shared__ double res[2];
     __shared__ int last_flag;
-    const int iz0 = blockIdx.y * kZPair;
-    const int nzp = min(kZPair, C.nz - iz0);                // voxels of the pair inside
-    float Z[kZPair + 1];
+    const int iz0 = blockIdx.y * ZP;
+    const int nzp = min(ZP, C.nz - iz0);                    // voxels of the stack inside
+    float Z[ZP + 1];
 #pragma unroll
-    for (int q = 0; q <= kZPair; ++q) Z[q] = grid_line((float)(iz0 + q), C.dz, C.z0);
+    for (int q = 0; q <= ZP; ++q) Z[q] = grid_line((float)(iz0 + q), C.dz, C.z0);
     const float Ze = grid_line((float)(iz0 + nzp), C.dz, C.z0);
     int b0, b1;
     k32_band(C, Z[0], Ze, b0, b1);
     for (int r = b0 + (int)threadIdx.x; r <= b1; r += 256) {
         const RowRec3 Rr = C.row[r];
-        float tz[kZPair + 1];
+        float tz[ZP + 1];
 #pragma unroll
-        for (int q = 0; q <= kZPair; ++q) tz[q] = cross_t(Z[q], Rr.qz, Rr.iz);
-        s_zt[r - b0] = make_float4(fminf(tz[0], tz[1]), fmaxf(tz[0], tz[1]), fminf(tz[1], tz[2]), fmaxf(tz[1], tz[2]));
+        for (int q = 0; q <= ZP; ++q) tz[q] = cross_t(Z[q], Rr.qz, Rr.iz);
+#pragma unroll
+        for (int h = 0; h < NQ; ++h)
+            s_zt[(r - b0) * NQ + h] = make_float4(fminf(tz[2 * h], tz[2 * h + 1]), fmaxf(tz[2 * h], tz[2 * h + 1]),
+                                                  fminf(tz[2 * h + 1], tz[2 * h + 2]), fmaxf(tz[2 * h + 1], tz[2 * h + 2]));
     }
     __syncthreads();
     const int pxy = blockIdx.x * 256 + threadIdx.x;         // iy * nx + ix
-    float acc0 = 0.0f, acc1 = 0.0f;
+    float acc[ZP];
+#pragma unroll
+    for (int q = 0; q < ZP; ++q) acc[q] = 0.0f;
     const bool valid = pxy < C.nx * C.ny;
     if (valid) {
         const int iy = pxy / C.nx, ix = pxy - iy * C.nx;
@@ -272,7 +293,7 @@ k32_backproject(Cone C, const float *__restrict__ ys, float *__restrict__ out, d
         const long long view_sz = (long long)C.nrow * C.nu;
         for (int v = 0; v < C.nv; ++v) {
             const ViewRec3 V = C.view[v];
-            float umin = 3e38f, umax = -3e38f;
+            float umin = 3e38f, umax = -3e38f, dmin = 3e38f, dmax = -3e38f;
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 const float px = (c & 1) ? X1 : X0, py = (c & 2) ? Y1 : Y0;
@@ -280,9 +301,19 @@ k32_backproject(Cone C, const float *__restrict__ ys, float *__restrict__ out, d
                 const float depth = V.cx * wx + V.cy * wy;            // along the central ray
                 const float u = __fdividef((V.ux * wx + V.uy * wy) * C.sdd, depth);
                 umin = fminf(umin, u); umax = fmaxf(umax, u);
+                dmin = fminf(dmin, depth); dmax = fmaxf(dmax, depth);
             }
             const int iu0 = max(0, (int)ceilf(fmaf(umin, C.inv_du, C.uc) - 0.01f));
             const int iu1 = min(C.nu - 1, (int)floorf(fmaf(umax, C.inv_du, C.uc) + 0.01f));
+            // rows whose rays are inside [Z0, Ze] at some depth of the stack's x-y column:
+            // w = z sdd / depth, depth in [dmin, dmax] (the corners' depths bound every
+            // chord's; the margin covers their rounding).  The same rows serve every
+            // column of the view, so the lanes of a warp (one slab, nearly equal depths)
+            // walk the same rows; rows outside a chord's own range add exact zeros.
+            const float ka = __fdividef(C.sdd, dmin), kb = __fdividef(C.sdd, dmax);
+            const float wlo = fminf(Z[0] * ka, Z[0] * kb), whi = fmaxf(Ze * ka, Ze * kb);
+            const int iv0 = max(b0, (int)ceilf(fmaf(wlo, C.inv_dw, C.wc) - 0.01f));
+            const int iv1 = min(b1, (int)floorf(fmaf(whi, C.inv_dw, C.wc) + 0.01f));
             const ColRec3 *colv = C.col + v * C.nu;
             const float *ysv = ys + v * view_sz;
             for (int iu = iu0; iu <= iu1; ++iu) {
@@ -292,33 +323,35 @@ k32_backproject(Cone C, const float *__restrict__ ys, float *__restrict__ out, d
                 const float lo_xy = fmaxf(fminf(ax, bx), fminf(ay, by));
                 const float hi_xy = fminf(fmaxf(ax, bx), fmaxf(ay, by));
                 if (!(lo_xy < hi_xy)) continue;
-                // rows whose rays are inside [Z0, Ze] at some depth of the chord:
-                // w = z sdd / (sid + D'), D' in [lo_xy, hi_xy] (both depths > 0)
-                const float ka = __fdividef(C.sdd, C.sid + lo_xy), kb = __fdividef(C.sdd, C.sid + hi_xy);
-                const float wlo = fminf(Z[0] * ka, Z[0] * kb), whi = fmaxf(Ze * ka, Ze * kb);
-                const int iv0 = max(b0, (int)ceilf(fmaf(wlo, C.inv_dw, C.wc) - 0.01f));
-                const int iv1 = min(b1, (int)floorf(fmaf(whi, C.inv_dw, C.wc) + 0.01f));
                 const float *ycol = ysv + iu;
                 // min / max are exact, so max(0, min(hi_xy, hi_z) - max(lo_xy, lo_z)) is
                 // the canonical six-plane length
                 for (int iv = iv0; iv <= iv1; ++iv) {
-                    const float4 zt = s_zt[iv - b0];
                     const float yv = __ldg(ycol + iv * C.nu);
-                    const float l0 = fmaxf(0.0f, __fsub_rn(fminf(hi_xy, zt.y), fmaxf(lo_xy, zt.x)));
-                    const float l1 = fmaxf(0.0f, __fsub_rn(fminf(hi_xy, zt.w), fmaxf(lo_xy, zt.z)));
-                    acc0 = fmaf(l0, yv, acc0);
-                    acc1 = fmaf(l1, yv, acc1);
+#pragma unroll
+                    for (int h = 0; h < NQ; ++h) {
+                        const float4 zt = s_zt[(iv - b0) * NQ + h];
+                        const float l0 = fmaxf(0.0f, __fsub_rn(fminf(hi_xy, zt.y), fmaxf(lo_xy, zt.x)));
+                        const float l1 = fmaxf(0.0f, __fsub_rn(fminf(hi_xy, zt.w), fmaxf(lo_xy, zt.z)));
+                        acc[2 * h] = fmaf(l0, yv, acc[2 * h]);
+                        acc[2 * h + 1] = fmaf(l1, yv, acc[2 * h + 1]);
+                    }
                 }
             }
         }
-        const long long vox = (long long)iz0 * C.nx * C.ny + pxy;
-        out[vox] = acc0;
-        if (nzp > 1) out[vox + (long long)C.nx * C.ny] = acc1;
-        if (nzp < 2) acc1 = 0.0f;
+        const long long nxy = (long long)C.nx * C.ny;
+        const long long vox = (long long)iz0 * nxy + pxy;
+#pragma unroll
+        for (int q = 0; q < ZP; ++q)
+            if (q < nzp) out[vox + q * nxy] = acc[q];
     }
     if (fin == FIN_NONE) return;
     const int nblk = gridDim.x * gridDim.y, lb = blockIdx.y * gridDim.x + blockIdx.x;
-    float vals[1] = {valid ? fmaf(acc0, acc0, acc1 * acc1) : 0.0f};
+    float sq = 0.0f;
+#pragma unroll
+    for (int q = 0; q < ZP; ++q)
+        if (valid && q < nzp) sq = fmaf(acc[q], acc[q], sq);
+    float vals[1] = {sq};
     block_sum_to<1, 256>(vals, partials + (size_t)lb * 2, rsm);
     if (threadIdx.x == 0) partials[(size_t)lb * 2 + 1] = 0.0;
     if (!reduce_slice<2, 256>(*S, partials, 2, 0, nblk, lb, rsm, res, &last_flag)) return;
@@ -673,6 +706,7 @@ struct eptv3_geometry {
     Cone C;
     Vol V;
     int k31_seg = 8;
+    int k32_zp = 4;                                      // voxels per K32 thread (2 or 4)
     unsigned red_blocks = 1184;   // grid of the grid-stride reducing kernels: 8 blocks per SM
     ColRec3 *col = nullptr;
     RowRec3 *row = nullptr;
@@ -720,6 +754,7 @@ static void c3_project(const eptv3_geometry *g, const float *f, const float *y_r
                        cudaStream_t st) {
     const unsigned nb = (unsigned)((long long)g->C.nv * g->C.nrow * ((g->C.nu + 31) / 32));
     switch (g->k31_seg) {
+    case 2: k31_project<2><<<nb, 64, 0, st>>>(g->C, f, y_resid, out, g->partials, g->d_sd, fin); break;
     case 4: k31_project<4><<<nb, 128, 0, st>>>(g->C, f, y_resid, out, g->partials, g->d_sd, fin); break;
     case 16: k31_project<16><<<nb, 512, 0, st>>>(g->C, f, y_resid, out, g->partials, g->d_sd, fin); break;
     default: k31_project<8><<<nb, 256, 0, st>>>(g->C, f, y_resid, out, g->partials, g->d_sd, fin); break;
@@ -729,8 +764,11 @@ static void c3_project(const eptv3_geometry *g, const float *f, const float *y_r
 static void c3_backproject(const eptv3_geometry *g, const float *y, float *out, int fin, cudaStream_t st) {
     const int npix = g->C.nu * g->C.nrow;
     k32_scale<<<dim3(nblk_of(npix, 256), (unsigned)g->C.nv), 256, 0, st>>>(y, g->fac, npix, g->ys);
-    const dim3 grid(nblk_of((long long)g->C.nx * g->C.ny, 256), (unsigned)((g->C.nz + kZPair - 1) / kZPair));
-    k32_backproject<<<grid, 256, sizeof(float4) * g->C.band_max, st>>>(g->C, g->ys, out, g->partials, g->d_sd, fin);
+    const int zp = g->k32_zp;
+    const dim3 grid(nblk_of((long long)g->C.nx * g->C.ny, 256), (unsigned)((g->C.nz + zp - 1) / zp));
+    const size_t smem = sizeof(float4) * (size_t)g->C.band_max * (zp / 2);
+    if (zp == 4) k32_backproject<4><<<grid, 256, smem, st>>>(g->C, g->ys, out, g->partials, g->d_sd, fin);
+    else k32_backproject<2><<<grid, 256, smem, st>>>(g->C, g->ys, out, g->partials, g->d_sd, fin);
 }
 
 // (P1): M CGLS iterations on g->u (App. I), data g->y
@@ -876,10 +914,11 @@ int eptv3_create_geometry(const eptv3_geometry_desc *d, eptv3_geometry **out) {
     C.uc = (float)((d->nu - 1) / 2.0 - d->u_off); C.wc = (float)((d->nv - 1) / 2.0 - d->v_off);
     C.sdd = (float)d->sdd; C.sid = (float)d->sid;
     C.rxy = (float)rxy;
-    {   // K32's row bands (the kernel's formula in FP64; each end may move by a row in FP32)
+    {   // K32's row bands (the kernel's formula in FP64; each end may move by a row in FP32),
+        // for the tallest stack: a shorter stack's slab lies inside one of its slabs
         int bmax = 0;
-        for (int iz0 = 0; iz0 < d->nz; iz0 += kZPair) {
-            const int nzp = std::min(kZPair, d->nz - iz0);
+        for (int iz0 = 0; iz0 < d->nz; iz0 += kZStackMax) {
+            const int nzp = std::min(kZStackMax, d->nz - iz0);
             const double Za = -0.5 * d->nz * d->dz + iz0 * d->dz, Zb = Za + nzp * d->dz;
             const double ka = d->sdd / (d->sid - rxy), kb = d->sdd / (d->sid + rxy);
             const double wlo = std::min(Za * ka, Za * kb), whi = std::max(Zb * ka, Zb * kb);
@@ -929,13 +968,14 @@ int eptv3_create_geometry(const eptv3_geometry_desc *d, eptv3_geometry **out) {
     A(&g->d_sd, 1);
     A(&g->d_params, 1);
     if (rc) { eptv3_destroy_geometry(g); return rc; }
-    const size_t band_bytes = sizeof(float4) * (size_t)C.band_max;
-    if (band_bytes > 200 * 1024) {
+    const size_t band_bytes = sizeof(float4) * (size_t)C.band_max;        // per pair of voxels
+    if (band_bytes > 100 * 1024) {
         eptv3_destroy_geometry(g);
         return c3_fail(EPTV_ERR_ARG, "detector row band of a z slab too tall for the back projector");
     }
-    if (band_bytes > 48 * 1024 &&
-        cudaFuncSetAttribute(k32_backproject, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)band_bytes) != cudaSuccess) {
+    if (band_bytes > 24 * 1024 &&
+        (cudaFuncSetAttribute(k32_backproject<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)band_bytes) != cudaSuccess ||
+         cudaFuncSetAttribute(k32_backproject<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * band_bytes)) != cudaSuccess)) {
         cudaGetLastError();
         eptv3_destroy_geometry(g);
         return c3_fail(EPTV_ERR_CUDA, "cannot raise the back projector's shared memory");
@@ -967,8 +1007,14 @@ void eptv3_destroy_geometry(eptv3_geometry *g) {
 }
 
 int eptv3_set_tuning(eptv3_geometry *g, int seg) {
-    if (!g || (seg != 4 && seg != 8 && seg != 16)) return c3_fail(EPTV_ERR_ARG, "seg must be 4, 8 or 16");
+    if (!g || (seg != 2 && seg != 4 && seg != 8 && seg != 16)) return c3_fail(EPTV_ERR_ARG, "seg must be 2, 4, 8 or 16");
     g->k31_seg = seg;
+    return 0;
+}
+
+int eptv3_set_backprojector_stack(eptv3_geometry *g, int zp) {
+    if (!g || (zp != 2 && zp != 4)) return c3_fail(EPTV_ERR_ARG, "zp must be 2 or 4");
+    g->k32_zp = zp;
     return 0;
 }
 

@@ -29,7 +29,7 @@ EXPORTED = [
     "eptv_unet_upsample2", "eptv_unet_upsample2_bwd", "eptv_unet_relu_bwd", "eptv_unet_head",
     "eptv_unet_adam", "eptv_unet_pack_input", "eptv_set_operator", "eptv_matrix_info",
     "eptv_copy_matrix", "eptv_backproject_eq11", "eptv_quality_metrics",
-    "eptv3_create_geometry", "eptv3_destroy_geometry", "eptv3_set_tuning", "eptv3_project",
+    "eptv3_create_geometry", "eptv3_destroy_geometry", "eptv3_set_tuning", "eptv3_set_backprojector_stack", "eptv3_project",
     "eptv3_backproject", "eptv3_cgls", "eptv3_tv_step", "eptv3_reconstruct", "eptv3_report_energy",
 ]
 
@@ -157,6 +157,7 @@ def load():
         "eptv3_create_geometry": (c_int, [ctypes.POINTER(GeometryDesc3), ctypes.POINTER(vp)]),
         "eptv3_destroy_geometry": (None, [vp]),
         "eptv3_set_tuning": (c_int, [vp, c_int]),
+        "eptv3_set_backprojector_stack": (c_int, [vp, c_int]),
         "eptv3_project": (c_int, [vp, vp, vp, vp]),
         "eptv3_backproject": (c_int, [vp, vp, vp, vp]),
         "eptv3_cgls": (c_int, [vp, c_int, vp, vp, vp]),
@@ -588,6 +589,10 @@ class Geometry3:
 
 def eptv3_set_tuning(geom: Geometry3, seg: int):
     _check(load().eptv3_set_tuning(geom.handle, int(seg)))
+
+
+def eptv3_set_backprojector_stack(geom: Geometry3, zp: int):
+    _check(load().eptv3_set_backprojector_stack(geom.handle, int(zp)))
 
 
 def eptv3_project(geom: Geometry3, f, y, stream=None):

@@ -102,7 +102,7 @@ def test_adjoint_identity_fp32(name):
     assert abs(lhs - rhs) / (np.linalg.norm(np64(px)) * np.linalg.norm(yf)) < 1e-6
 
 
-@pytest.mark.parametrize("seg", [4, 8, 16])
+@pytest.mark.parametrize("seg", [2, 4, 8, 16])
 def test_projector_launch_shapes_agree(seg):
     g = GEOMS["c5_8"]
     geo = E.Geometry3(g)
@@ -113,6 +113,25 @@ def test_projector_launch_shapes_agree(seg):
     y1 = torch.empty_like(y0)
     E.eptv3_project(geo, f, y1)
     assert rel(np64(y1), np64(y0)) < 1e-6
+
+
+@pytest.mark.parametrize("name", sorted(GEOMS))
+def test_backprojector_stacks_agree(name):
+    """Two and four voxels per thread of the back projector sum the same terms in the same
+    order for every voxel (slab heights that do not divide nz included)."""
+    g = GEOMS[name]
+    geo = E.Geometry3(g)
+    ys = t32(np.random.Generator(np.random.PCG64(21)).standard_normal(g.n_rays))
+    out = []
+    for zp in (2, 4):
+        E.eptv3_set_backprojector_stack(geo, zp)
+        b = torch.full((g.n_vox,), float("nan"), device=DEV)
+        E.eptv3_backproject(geo, ys, b)
+        out.append(np64(b))
+    assert np.isfinite(out[0]).all()
+    assert np.array_equal(out[0], out[1])
+    with pytest.raises(E.EptvError):
+        E.eptv3_set_backprojector_stack(geo, 3)
 
 
 @pytest.fixture(scope="module")

@@ -31,20 +31,43 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(d) <= t for d in deps())
 
 
+def _compile(args):
+    subprocess.check_call(args)
+
+
 def build(force: bool = False, verbose: bool = False, extra=None) -> str:
+    """Compiles every csrc/*.cu to an object in _build/ (in parallel: the translation units
+    share no device code) and links them into libeptv.so."""
     if not force and up_to_date():
         return LIB
+    from concurrent.futures import ThreadPoolExecutor
     nvcc = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
-    tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = [nvcc, "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC", "-shared",
-           "-cudart", "shared", "-I", os.path.join(ROOT, "include"),
-           "-I", os.path.join(PKG, "csrc"), "-o", tmp, *sources()]
+    obj_dir = os.path.join(PKG, "_build")
+    os.makedirs(obj_dir, exist_ok=True)
+    flags = ["-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC",
+             "-I", os.path.join(ROOT, "include"), "-I", os.path.join(PKG, "csrc")]
     if extra:
-        cmd += list(extra)
+        flags += list(extra)
+    tag = f".{os.getpid()}"
+    jobs, objs = [], []
+    for src in sources():
+        obj = os.path.join(obj_dir, os.path.splitext(os.path.basename(src))[0] + tag + ".o")
+        objs.append(obj)
+        jobs.append([nvcc, *flags, "-c", src, "-o", obj])
     if verbose:
-        print(" ".join(cmd), file=sys.stderr)
-    subprocess.check_call(cmd)
-    os.replace(tmp, LIB)
+        for j in jobs:
+            print(" ".join(j), file=sys.stderr)
+    workers = max(1, min(len(jobs), os.cpu_count() or 1))
+    try:
+        with ThreadPoolExecutor(workers) as ex:
+            list(ex.map(_compile, jobs))
+        tmp = LIB + f"{tag}.tmp"
+        subprocess.check_call([nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs])
+        os.replace(tmp, LIB)
+    finally:
+        for o in objs:
+            if os.path.exists(o):
+                os.remove(o)
     return LIB
 
 

@@ -165,8 +165,10 @@ k31_project(Cone C, const float *__restrict__ f, const float *__restrict__ y_res
                 // just crossed is the largest): tin = max(tin, exit) is the canonical max of
                 // the three entry planes, exactly, for every cell inside the volume, and
                 // beyond the volume's exit both give length 0.  The next crossing of each
-                // axis is evaluated every step (three FMA-pipe triples, no operand selects);
-                // the one crossed is kept.  Cells of nonzero length are inside the volume
+                // axis is evaluated every step (three FMA-pipe triples, no operand selects)
+                // and the one crossed is kept by selects, so the lanes never branch apart.
+                // A cell's load is issued one step before its product is added (the
+                // additions keep the walk's order).  Cells of nonzero length are inside the volume
                 // (outside it every length is 0, see above); the clamp of the offset only
                 // keeps the load in bounds.
                 const int step_m = sgm * sm, step_z = sgz * (int)sz;
@@ -180,21 +182,31 @@ k31_project(Cone C, const float *__restrict__ f, const float *__restrict__ y_res
                 float kz = (float)(cz + ohz) + sgz_f;
                 const float kend = (float)(re + 2);               // M plane after the last slab's exit
                 const int cap = (re - rs + 1) + nm + C.nz + 2;    // each step moves one index
+                float pl = 0.0f, pv = 0.0f;
                 for (int it = 0; it < cap; ++it) {
                     const float mn = fminf(him, hiz);
                     const float ex = fminf(tbc, mn);
                     const float lc = fmaxf(0.0f, __fsub_rn(ex, tin));
-                    if (lc > 0.0f) acc = fmaf(lc, __ldg(f + min((unsigned)idx, last_vox)), acc);
+                    const float v = lc > 0.0f ? __ldg(f + min((unsigned)idx, last_vox)) : 0.0f;
+                    acc = fmaf(pl, pv, acc);
+                    pl = lc; pv = v;
                     tin = fmaxf(tin, ex);
                     const bool adv_M = !(mn < tbc);
                     if (adv_M && kM == kend) break;
                     const float tnM = cross_t(grid_line(kM, dM, M0), PM, iM);
                     const float tnm = cross_t(grid_line(km, dm, m0), Pm, im);
                     const float tnz = cross_t(grid_line(kz, C.dz, C.z0), R.pz, iz);
-                    if (adv_M) { tbc = fminf(tnM, t_hi); kM += 1.0f; idx += sM; }
-                    else if (him <= hiz) { him = tnm; km += sgm_f; idx += step_m; }
-                    else { hiz = tnz; kz += sgz_f; idx += step_z; }
+                    const bool adv_m = !adv_M && him <= hiz;
+                    const bool adv_z = !adv_M && !adv_m;
+                    tbc = adv_M ? fminf(tnM, t_hi) : tbc;
+                    kM += adv_M ? 1.0f : 0.0f;
+                    him = adv_m ? tnm : him;
+                    km += adv_m ? sgm_f : 0.0f;
+                    hiz = adv_z ? tnz : hiz;
+                    kz += adv_z ? sgz_f : 0.0f;
+                    idx += adv_M ? sM : (adv_m ? step_m : step_z);
                 }
+                acc = fmaf(pl, pv, acc);
             }
         }
     }

@@ -389,11 +389,13 @@ int eptv_set_tuning(eptv_geometry *g, int k1_seg, int k2_vg);
 /* (P2) descent kernel used by (P2) solves of handle g (eptv_tv_step, eptv_reconstruct, and
  * batches whose first member is g); Sec. 2.2, Eqs. 5, 9, A2, A3.
  *   EPTV_TV_AUTO (default): when every region of the slices fits on the GPU at once, one
- *     cooperative launch runs all n_gd GD iterations of a (P2) solve and the clamp, with
- *     one grid-wide barrier per iteration (bounded waits: EPTV_ERR_TIMEOUT, reported by the
- *     calls that read their scalars, if one runs out); otherwise, or for more than 8
- *     Armijo trials, one launch per GD iteration;
- *   EPTV_TV_PER_ITERATION: always one launch per GD iteration plus one for the clamp.
+ *     cooperative launch runs the sigma selection (three grid-wide barriers), all n_gd GD
+ *     iterations of a (P2) solve (one grid-wide barrier per iteration) and the clamp
+ *     (bounded waits: EPTV_ERR_TIMEOUT, reported by the calls that read their scalars, if
+ *     one runs out); otherwise, or for more than 8 Armijo trials, three sigma launches
+ *     and one launch per GD iteration;
+ *   EPTV_TV_PER_ITERATION: always three sigma launches, one launch per GD iteration and
+ *     one for the clamp.
  * Both give bit-identical results.  EPTV_ERR_ARG for other values. */
 #define EPTV_TV_AUTO           0
 #define EPTV_TV_PER_ITERATION  1
@@ -403,7 +405,7 @@ int eptv_set_tv_kernel(eptv_geometry *g, int mode);
  * its grid barrier waits for extra_blocks blocks beyond the launch (0: none, the default)
  * and gives up after wait_cycles SM cycles (default 2e9, about one second), after which
  * the kernel stops and the call that reads the scalars returns EPTV_ERR_TIMEOUT; the next
- * (P2) solve re-arms the barrier.  extra_blocks > 0 makes every wait run out without
+ * call re-arms the barrier.  extra_blocks > 0 makes every wait run out without
  * faulting or hanging the GPU.  EPTV_ERR_ARG outside [0, 1024] x [1e3, 4e9]. */
 int eptv_debug_set_p2_wait(eptv_geometry *g, int extra_blocks, long long wait_cycles);
 

@@ -108,10 +108,13 @@ struct SliceDev {
     // launches)
     unsigned int *ctr;
     unsigned long long *acc;
-    // persistent (P2) kernel K4p: the batch's grid-barrier counter and this slice's three
-    // rotating exact-accumulator sets; both zeroed by the sigma selection before each K4p
+    // persistent (P2) kernel K4p: the batch's grid-barrier words (p2bar[0] the arrival
+    // count, p2bar[1] its value when the next launch starts), this slice's three rotating
+    // exact-accumulator sets and its three sigma-selection histograms (kP2HistWords words,
+    // zero between launches)
     unsigned int *p2bar;
     unsigned long long *p2acc;
+    unsigned int *p2hist;
     // stored operator (null unless selected): SELL-32 P (rows = rays), P^T (rows = pixels)
     const int *p_sptr, *p_slen, *p_scol;
     const float *p_sval;

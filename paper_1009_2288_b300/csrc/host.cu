@@ -208,19 +208,30 @@ static int build_batch(Batch &B, DevMem &mem, const std::vector<SliceDev> &sds) 
     if ((rc = mem.alloc(&B.d_params, 1))) return rc;
     const size_t p2words = (size_t)kP2Sets * kP2SetWords;
     if ((rc = mem.alloc(&B.d_p2start, (size_t)B.n + 1))) return rc;
-    if ((rc = mem.alloc(&B.d_p2bar, 1))) return rc;
+    if ((rc = mem.alloc(&B.d_p2bar, 2))) return rc;
     if ((rc = mem.alloc(&B.d_p2acc, (size_t)B.n * p2words))) return rc;
+    if ((rc = mem.alloc(&B.d_p2hist, (size_t)B.n * kP2HistWords))) return rc;
     for (int i = 0; i < B.n; ++i) {
         B.h_sd[i].p2bar = B.d_p2bar;
         B.h_sd[i].p2acc = B.d_p2acc + (size_t)i * p2words;
+        B.h_sd[i].p2hist = B.d_p2hist + (size_t)i * kP2HistWords;
     }
     CU(cudaMemcpy(B.d_sd, B.h_sd.data(), sizeof(SliceDev) * B.n, cudaMemcpyHostToDevice));
     CU(cudaMemcpy(B.d_start, B.h_start.data(), sizeof(int) * B.h_start.size(), cudaMemcpyHostToDevice));
     CU(cudaMemset(B.d_counters, 0, sizeof(unsigned int) * (size_t)B.n * cstride));
     CU(cudaMemset(B.d_acc, 0, sizeof(unsigned long long) * (size_t)B.n * astride));
     CU(cudaMemset(B.d_hist, 0, sizeof(unsigned int) * (size_t)B.n * kHistBins));
-    CU(cudaMemset(B.d_p2bar, 0, sizeof(unsigned int)));
+    CU(cudaMemset(B.d_p2bar, 0, 2 * sizeof(unsigned int)));
     CU(cudaMemset(B.d_p2acc, 0, sizeof(unsigned long long) * (size_t)B.n * p2words));
+    CU(cudaMemset(B.d_p2hist, 0, sizeof(unsigned int) * (size_t)B.n * kP2HistWords));
+    return 0;
+}
+
+// The persistent (P2) kernel's barrier words and sigma histograms to zero, at the start of
+// a call: after a bounded wait ran out in an earlier call they are not consistent.
+static int reset_p2(const Batch &B, cudaStream_t st) {
+    CU(cudaMemsetAsync(B.d_p2bar, 0, 2 * sizeof(unsigned int), st));
+    CU(cudaMemsetAsync(B.d_p2hist, 0, sizeof(unsigned int) * (size_t)B.n * kP2HistWords, st));
     return 0;
 }
 
@@ -294,11 +305,10 @@ static int ensure_p2(Batch &B, const eptv_params *p, cudaStream_t st) {
     return 0;
 }
 
-// (P2) + clamp on v = u: sigma, then either the persistent kernel K4p (all n_gd GD
-// iterations, apply + clamp into u, u^T) or n_gd fused GD launches of K4 and K4u.
+// (P2) + clamp on v = u: either the persistent kernel K4p (sigma, all n_gd GD iterations,
+// apply + clamp into u, u^T) or sigma (K5) and n_gd fused GD launches of K4 and K4u.
 static void enqueue_p2(const Batch &B, const eptv_params *p, const float *v_override,
                        float *out_override, cudaStream_t st) {
-    launch_sigma(B, v_override, st);
     if (B.p2.ok && p->n_gd >= 1) {
         P2Args pa{};
         pa.v = v_override;
@@ -310,6 +320,7 @@ static void enqueue_p2(const Batch &B, const eptv_params *p, const float *v_over
         launch_p2(B, B.p2, pa, st);   // a failure surfaces in the caller's launch check / capture
         return;
     }
+    launch_sigma(B, v_override, st);
     for (int n = 0; n < p->n_gd; ++n) {
         GdArgs ga{};
         ga.first = (n == 0);
@@ -788,7 +799,7 @@ int eptv_tv_step(const eptv_geometry *gc, const eptv_params *p, const float *d_v
     launch_set_scalar(g->B, SC_NACC_P2, 0.0, st);
     launch_set_scalar(g->B, SC_NONFINITE, 0.0, st);
     launch_set_scalar(g->B, SC_TIMEOUT, 0.0, st);
-    if ((rc = ensure_p2(g->B, p, st))) return rc;
+    if ((rc = ensure_p2(g->B, p, st)) || (rc = reset_p2(g->B, st))) return rc;
     enqueue_p2(g->B, p, d_v, d_f, st);
     if ((rc = launch_check())) return rc;
     if ((rc = upload_sd(g->B, st))) return rc;     // clear the weights pointer for later calls
@@ -816,7 +827,7 @@ static int run_outer(Batch &B, GraphCache &gc, cudaStream_t cap, const eptv_para
                      cudaStream_t st) {
     int rc;
     if ((rc = upload_sd(B, st)) || (rc = upload_params(B, p, st))) return rc;
-    if ((rc = ensure_p2(B, p, st))) return rc;
+    if ((rc = ensure_p2(B, p, st)) || (rc = reset_p2(B, st))) return rc;
     launch_set_scalar(B, SC_TIMEOUT, 0.0, st);
     // f^(0): clamp the start image, build its transpose, reset the per-slice state
     launch_gd_finish(B, 0, nullptr, nullptr, st);

@@ -101,8 +101,9 @@ struct Batch {
     // persistent (P2) kernel K4p (tv_p2.cu): region starts of the current plan, the grid
     // barrier counter, the accumulator sets, and the plan the starts were uploaded for
     int *d_p2start = nullptr;             // [n + 1]
-    unsigned int *d_p2bar = nullptr;      // [1]
+    unsigned int *d_p2bar = nullptr;      // [2]: arrival count, its value at the next launch
     unsigned long long *d_p2acc = nullptr;  // [n][3][kPartialStride][kAccCopies][kAccStride]
+    unsigned int *d_p2hist = nullptr;     // [n][kP2HistWords]
     int p2_rtx = 0, p2_rty = 0;           // shape whose starts are in d_p2start (0: none)
     std::vector<int> h_p2start;
     int p2_disabled = 0;                  // 1: cooperative capture failed: per-iteration K4
@@ -146,10 +147,12 @@ struct GdArgs {
     int write_f;             // store the iterate
 };
 
-// Arguments of the persistent (P2) kernel K4p (its barrier counter and accumulator sets
-// are SliceDev::p2bar / p2acc: kP2Sets sets of kP2SetWords words per slice).
+// Arguments of the persistent (P2) kernel K4p (its barrier words, accumulator sets and
+// selection histograms are SliceDev::p2bar / p2acc / p2hist: kP2Sets sets of kP2SetWords
+// words and kP2HistWords histogram words per slice).
 constexpr int kP2Sets = 3;
 constexpr size_t kP2SetWords = (size_t)kPartialStride * kAccCopies * kAccStride;
+constexpr int kP2HistWords = 2 * kHistBins + 256;     // passes 0, 1 (12 bits), 2 (8 bits)
 struct P2Args {
     const float *v;               // (P2) input (null: S.u)
     float *out;                   // result max(f, 0) (null: S.u and S.uT)

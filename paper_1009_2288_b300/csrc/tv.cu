@@ -199,13 +199,6 @@ k5_radix_pass(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__
     }
     const int b0 = __ldg(map.start + si);
     const int nblk = __ldg(map.start + si + 1) - b0;
-    if (pass == 2 && !vals_override && S.p2acc) {
-        // re-arm the persistent (P2) kernel that follows: zero accumulator sets and barrier
-        const long long words = (long long)kP2Sets * (long long)kP2SetWords;
-        for (long long w = (long long)local * 256 + threadIdx.x; w < words; w += (long long)nblk * 256)
-            S.p2acc[w] = 0ull;
-        if (si == 0 && local == 0 && threadIdx.x == 0) *S.p2bar = 0u;
-    }
     if (!last_block_of_slice(S.ctr, nblk, &last_flag)) return;
     const long long rank0 = vals_override ? rank_override : S.sel_rank;
     const unsigned int key = sel_scan(hist, S.sc, pass, rank0, s_cnt, &s_res);

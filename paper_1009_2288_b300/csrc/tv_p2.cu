@@ -4,7 +4,12 @@
 //
 // Each block owns a rectangle ("region") of RTX x RTY of the 32 x 8 tiles that K4 launches
 // one block per, and keeps in shared memory, for all GD iterations: the iterate f on the
-// region + 2-pixel halo, v on the region + 1, and g on the region + 2.  Per GD iteration:
+// region + 2-pixel halo, v on the region + 1, and g on the region + 2.  First, sigma
+// (Sec. 2.1): the sel_rank-th smallest half-edge magnitude T of v over the slice, by K5's
+// exact radix selection (12 + 12 + 8 bits of the FP32 keys) over the half-edges each block
+// owns (its pixels' left and upper sides, and the right / bottom image border in the last
+// region column / row), one grid barrier after each pass, every block scanning the slice's
+// histogram itself.  Then per GD iteration:
 //   phase 2  T, w, q = w D / T of every half-edge around the region + 1 (Eqs. A3, 5);
 //   phase 3  g = lambda (f - v) + dJ/df on the region + 1 (Eqs. 9, A2); the owned values go
 //            to an exchange image;
@@ -30,8 +35,12 @@
 // Co-residency: the launch is cooperative (all blocks resident or the launch fails), and
 // every wait has a bound: a block that waits longer than about a second sets SC_TIMEOUT in
 // its slice's scalars and returns, so that the host reports EPTV_ERR_TIMEOUT instead of a
-// hung context.  The barrier counter and the accumulator sets are re-armed (zeroed) by the
-// sigma selection (K5), which always runs right before this kernel.
+// hung context.  The launch re-arms itself: the barrier counter only grows (p2bar[1] holds
+// its value at the start of the next launch, compares are modulo 2^32), each accumulator
+// set is zeroed by the slice's first block before its first use, and the selection
+// histograms are zeroed once every block has passed the first GD barrier.  The host zeroes
+// the barrier words and histograms at the start of every call (after a wait that ran out
+// they are not consistent).
 #include <algorithm>
 #include <atomic>
 
@@ -53,8 +62,9 @@ __device__ __forceinline__ void red_release_add_gpu(unsigned int *p, unsigned in
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Waits until *bar >= target, at most max_cycles SM cycles and at most kP2WaitSpins polls
-// (~2.7 s with the back-off).  Returns false if a bound ran out.
+// Waits until *bar reaches target (modulo 2^32: the counter only grows), at most
+// max_cycles SM cycles and at most kP2WaitSpins polls (~2.7 s with the back-off).  Returns
+// false if a bound ran out.
 constexpr long long kP2WaitSpins = 1ll << 26;
 
 __device__ __forceinline__ bool p2_wait(const unsigned int *bar, unsigned int target,
@@ -62,7 +72,7 @@ __device__ __forceinline__ bool p2_wait(const unsigned int *bar, unsigned int ta
     const long long t0 = clock64();
     for (long long spins = 0; spins < kP2WaitSpins; ++spins) {
         if (*seen) return true;                            // another warp of the block saw it
-        if (ld_acquire_gpu(bar) >= target) {
+        if ((int)(ld_acquire_gpu(bar) - target) >= 0) {
             *seen = 1;
             return true;
         }
@@ -74,6 +84,49 @@ __device__ __forceinline__ bool p2_wait(const unsigned int *bar, unsigned int ta
 
 // Accumulator copies K4p's blocks spread their words over (block b: copy b mod kP2Copies).
 constexpr int kP2Copies = 4;
+
+// One pass of the selection scan, run by every block on the slice's histogram gh (NB
+// bins): the bin holding the remaining rank (1-based) and the rank within it, to *s_bin and
+// *s_rank.  Bins are summed per thread (PER consecutive bins), the thread sums are
+// prefix-summed across the block, and the thread whose bins hold the rank searches them.
+template <int NT, int NB>
+__device__ __forceinline__ void p2_sel_scan(const unsigned int *gh, long long rank,
+                                            unsigned long long *s_w, int *s_bin, long long *s_rank) {
+    constexpr int PER = NB >= NT ? NB / NT : 1;
+    static_assert(NB >= NT ? NB % NT == 0 : true, "bins split evenly over the threads");
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    unsigned int v[PER];
+    unsigned long long local = 0;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int b = t * PER + q;
+        v[q] = (b < NB) ? __ldcg(gh + b) : 0u;
+        local += v[q];
+    }
+    unsigned long long inc = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) s_w[w] = inc;
+    __syncthreads();
+    unsigned long long before = 0;
+    for (int i = 0; i < w; ++i) before += s_w[i];
+    inc += before;
+    const unsigned long long exc = inc - local;
+    if ((long long)exc < rank && rank <= (long long)inc) {
+        unsigned long long cum = exc;
+        int b = t * PER;
+        for (int q = 0; q < PER; ++q, ++b) {
+            if ((long long)(cum + v[q]) >= rank) break;
+            cum += v[q];
+        }
+        *s_bin = b;
+        *s_rank = rank - (long long)cum;
+    }
+    __syncthreads();
+}
 
 // ------------------------------------------------------------------ layout
 
@@ -128,6 +181,10 @@ k4p_descent(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__re
     constexpr bool kCand = (KT + 1) * KT <= 32;
     __shared__ float cand_f[kCand ? (KT + 1) * KT : 1];
     __shared__ double cand_d[kCand ? (KT + 1) * KT : 1];
+    __shared__ unsigned int s_hist[kHistBins];             // sigma: the block's histogram
+    __shared__ unsigned long long s_w[NT / 32];
+    __shared__ int s_bin;
+    __shared__ long long s_rank;
     struct Record { double e_first, t_step, e_last, t_prev; int nacc, nfail, bad; };
     Record rec{0.0, 0.0, 0.0, 0.0, 0, 0, 0};
 
@@ -152,9 +209,12 @@ k4p_descent(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__re
         mode = (S.wprior && S.sc[SC_OUTER] < (double)P->prior_iters) ? EPTV_WEIGHTS_PRIOR
                                                                       : EPTV_WEIGHTS_EPTV;
     }
-    const float sig = (float)S.sc[SC_SIGMA];
-    const float inv_s2 = 1.0f / (sig * sig);
     const int k_outer = (int)S.sc[SC_OUTER];
+    // barrier b of this launch (0, 1, 2: sigma passes; 3 + it: GD iteration it) completes
+    // when the counter reaches base + (b + 1) per_bar
+    const unsigned int base = ld_acquire_gpu(S.p2bar + 1);
+    const unsigned int per_bar = gridDim.x + (unsigned int)pa.bar_extra;
+    const int nblk = __ldg(map.start + si + 1) - __ldg(map.start + si);
     if (tid == 0) {
         s_misc[0] = S.sc[SC_TPREV];
         s_abort = 0;
@@ -184,7 +244,92 @@ k4p_descent(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__re
         if (i >= 0 && i < nx && j >= 0 && j < ny) vx = __ldcg(vv + (j * nx + i));
         V[idx] = vx;
     }
+    // the slice's first accumulator set is used first after the sigma barriers
+    if (local == 0)
+        for (int w = tid; w < NV * kAccCopies * kAccStride; w += NT) acc_slice[w] = 0ull;
     __syncthreads();
+
+    // one grid barrier (number b), arrival after the block's writes; false if a wait ran out
+    auto grid_sync = [&](int b) -> bool {
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();
+            red_release_add_gpu(S.p2bar, 1u);
+        }
+        if ((tid & 31) == 0 && (tid >> 5) < kPollers) {
+            if (!p2_wait(S.p2bar, base + (unsigned int)(b + 1) * per_bar, pa.wait_cycles, &s_seen[b & 1]))
+                s_abort = 1;
+            __threadfence();
+        }
+        if (tid == 0) s_seen[(b + 1) & 1] = 0;             // re-armed for the next barrier
+        __syncthreads();
+        return !s_abort;
+    };
+
+    // sigma: T = sqrt(T^2) (K5's half_edge_T) of the owned half-edges of v, x-edges (i, j)
+    // between (i - 1, j) and (i, j) first, then y-edges between (i, j - 1) and (i, j)
+    constexpr int KEYS = (2 * (RW + 1) * (RH + 1) + NT - 1) / NT;
+    unsigned int keys[KEYS];
+    const int cx1 = min(RX0 + RW, nx), cy1 = min(RY0 + RH, ny);
+    const int ncol = cx1 - RX0, nrow = cy1 - RY0;
+    const int nxe = ncol + (RX0 + RW >= nx ? 1 : 0);       // x-edge columns owned
+    const int nye = nrow + (RY0 + RH >= ny ? 1 : 0);       // y-edge rows owned
+    const int n_ox = nxe * nrow, n_own = n_ox + ncol * nye;
+    bool nonfinite = false;
+#pragma unroll
+    for (int k = 0; k < KEYS; ++k) {
+        const int e = tid + k * NT;
+        unsigned int key = 0u;
+        if (e < n_own) {
+            float D, T2;
+            if (e < n_ox) {
+                const int r = e / nxe, c = e - r * nxe;
+                const float *q = F + (r + 2) * FW + (c + 1);            // pixel (i - 1, j)
+                T2 = edge_T2(eps2, q[0], q[1], q[FW], q[FW + 1], q[-FW], q[-FW + 1], &D);
+            } else {
+                const int e2 = e - n_ox, r = e2 / ncol, c = e2 - r * ncol;
+                const float *q = F + (r + 1) * FW + (c + 2);            // pixel (i, j - 1)
+                T2 = edge_T2(eps2, q[0], q[FW], q[1], q[FW + 1], q[-1], q[FW - 1], &D);
+            }
+            const float T = sqrtf(T2);
+            nonfinite |= !isfinite(T);
+            key = sel_key(T);
+        }
+        keys[k] = key;
+    }
+    if (nonfinite) S.sc[SC_NONFINITE] = 1.0;
+    long long rank = S.sel_rank;
+    unsigned int prefix = 0u;
+    for (int pass = 0; pass < 3; ++pass) {
+        const int nbins = (pass == 2) ? 256 : kHistBins;
+        for (int b = tid; b < nbins; b += NT) s_hist[b] = 0u;
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < KEYS; ++k)
+            if (tid + k * NT < n_own) sel_hist_add(s_hist, keys[k], pass, prefix);
+        __syncthreads();
+        unsigned int *gh = S.p2hist + pass * kHistBins;
+        for (int b = tid; b < nbins; b += NT) {
+            const unsigned int c = s_hist[b];
+            if (c) atomicAdd(gh + b, c);
+        }
+        if (!grid_sync(pass)) {
+            if (tid == 0) S.sc[SC_TIMEOUT] = 1.0;
+            return;
+        }
+        if (pass == 2) p2_sel_scan<NT, 256>(gh, rank, s_w, &s_bin, &s_rank);
+        else p2_sel_scan<NT, kHistBins>(gh, rank, s_w, &s_bin, &s_rank);
+        rank = s_rank;
+        prefix = (pass == 0) ? (unsigned int)s_bin : (prefix << (pass == 1 ? 12 : 8)) | (unsigned int)s_bin;
+    }
+    const double sigma = fmax((double)__uint_as_float(prefix), P->sigma_floor);
+    if (local == 0 && tid == 0) {
+        S.sc[SC_SIGMA] = sigma;
+        if (S.log && k_outer >= 0 && k_outer < S.log_outer)
+            S.log[(size_t)S.log_outer * S.log_gd + k_outer] = sigma;
+    }
+    const float sig = (float)sigma;
+    const float inv_s2 = 1.0f / (sig * sig);
 
     const int grp = tid >> 7, vt = tid & 127;
     constexpr int kRing = 2 * FW + 2 * (FH - 2);
@@ -289,17 +434,20 @@ k4p_descent(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__re
         }
         // lane 0 of up to kPollers warps polls; the first to see every arrival tells the
         // others through s_seen (polls of several warps in flight shorten the detection)
+        const int bnum = 3 + it;
         if ((tid & 31) == 0 && (tid >> 5) < kPollers) {
-            const unsigned int need = (unsigned int)(it + 1) * (gridDim.x + (unsigned int)pa.bar_extra);
-            if (!p2_wait(S.p2bar, need, pa.wait_cycles, &s_seen[it & 1])) s_abort = 1;
+            const unsigned int need = base + (unsigned int)(bnum + 1) * per_bar;
+            if (!p2_wait(S.p2bar, need, pa.wait_cycles, &s_seen[bnum & 1])) s_abort = 1;
             __threadfence();
         }
-        if (tid == 0) s_seen[(it + 1) & 1] = 0;          // re-armed for the next iteration
+        if (tid == 0) s_seen[(bnum + 1) & 1] = 0;        // re-armed for the next barrier
         __syncthreads();
         if (s_abort) {
             if (tid == 0) S.sc[SC_TIMEOUT] = 1.0;
             return;
         }
+        if (it == 0)      // every block has read the sigma histograms: zero them for the next launch
+            for (int w = local * NT + tid; w < kP2HistWords; w += nblk * NT) S.p2hist[w] = 0u;
 
         // ring 2 of g: the neighbours' exchange values of this iteration (loads issued before
         // the exact read, stored after it)
@@ -371,6 +519,8 @@ k4p_descent(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__re
             if (i < nx && j < ny) S.uT[(size_t)i * ny + j] = fmaxf(F[(r + 2) * FW + c + 2], 0.0f);
         }
     }
+    if (blockIdx.x == 0 && tid == 0)       // every block has passed the last barrier
+        S.p2bar[1] = base + (unsigned int)(3 + pa.n_gd) * per_bar;
     if (local == 0 && tid == 0) {
         double *sc = S.sc;
         sc[SC_E_FIRST] = rec.e_first;

@@ -56,7 +56,7 @@ def test_persistent_equals_per_iteration_armijo(name):
     y = t32(I.random_sino(g, 5) * 0.05 + 0.5).reshape(-1)
     p = I.EptvParams(n_outer=3)
     ra, rb = _assert_same(geo, g, y, p)
-    assert ra.n_launches < rb.n_launches          # one (P2) launch instead of n_gd + 1
+    assert ra.n_launches < rb.n_launches          # one (P2) launch instead of 3 + n_gd + 1
 
 
 @pytest.mark.parametrize("kw", [dict(step_rule=O.FIXED, t_fixed=2e-5), dict(max_trials=8),
@@ -85,7 +85,7 @@ def test_persistent_equals_per_iteration_benchmark_workload():
     geo = E.Geometry(g)
     E.eptv_autotune(geo)
     ra, rb = _assert_same(geo, g, t32(c.y).reshape(-1), I.EptvParams(n_outer=3))
-    assert rb.n_launches - ra.n_launches == 3 * 10     # n_gd + 1 launches became one
+    assert rb.n_launches - ra.n_launches == 3 * 13     # 3 sigma + n_gd + 1 launches became one
 
 
 def test_persistent_tv_step_with_weights(c1_case):
@@ -125,3 +125,29 @@ def test_persistent_wait_runs_out_and_the_handle_recovers(c1_case):
     torch.cuda.synchronize()
     E.eptv_debug_set_p2_wait(geo, 0, 2_000_000_000)
     _assert_same(geo, g, y, p)
+
+
+@pytest.mark.parametrize("mode", [E.TV_AUTO, E.TV_PER_ITERATION])
+def test_nan_in_the_p2_input_raises_nonfinite(c1_case, mode):
+    """A NaN pixel of v makes its half-edge magnitudes NaN: the sigma selection of either
+    kernel flags it, the call reports EPTV_ERR_NONFINITE, and the handle stays usable."""
+    g = c1_case.geom
+    geo = E.Geometry(g)
+    E.eptv_set_tv_kernel(geo, mode)
+    v = t32(c1_case.f_true).reshape(-1).clone()
+    v[g.nx * (g.ny // 2) + g.nx // 2] = float("nan")
+    f = torch.empty(g.n_pix, device=DEV)
+    with pytest.raises(E.EptvError) as ei:
+        E.eptv_tv_step(geo, I.EptvParams(n_gd=3), v, f, t_prev=3e-4)
+    assert ei.value.code == -3
+    st, _ = E.eptv_tv_step(geo, I.EptvParams(n_gd=3), t32(c1_case.f_true).reshape(-1), f, t_prev=3e-4)
+    assert torch.isfinite(f).all() and st.sigma > 0
+
+
+def test_persistent_equals_per_iteration_over_many_launches(c1_case):
+    """30 outer iterations: 30 cooperative launches in a row, each starting its barriers
+    where the previous one left the counter and re-arming its accumulator sets and
+    selection histograms itself, against the per-iteration kernels."""
+    g = c1_case.geom
+    geo = E.Geometry(g)
+    _assert_same(geo, g, t32(c1_case.y).reshape(-1), I.EptvParams(n_outer=30))

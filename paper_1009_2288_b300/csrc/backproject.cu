@@ -30,6 +30,7 @@ template <int VG, bool EQ11>
 __global__ void __launch_bounds__(kBlocksPT * VG)
 k2_backproject(const SliceDev *__restrict__ sls, TileMap map, BackArgs a, double *__restrict__ partials)
 {
+    pdl_wait();
     constexpr int NT = kBlocksPT * VG, R = kRowsPT;
     __shared__ float4 part[VG > 1 ? VG - 1 : 1][R][kBlocksPT];
     __shared__ float tr[kTileH][kTileW + 1];
@@ -236,9 +237,9 @@ void launch_backproject(const Batch &B, const BackArgs &a, cudaStream_t st) {
     ++g_launch_count;
     const TileMap m = B.map(FAM_K2);
     const bool eq11 = B.bp_eq11 || a.eq11;
-#define K2_LAUNCH(VGv)                                                                              \
-    (eq11 ? k2_backproject<VGv, true><<<nblk, kBlocksPT * VGv, 0, st>>>(B.d_sd, m, a, B.d_partials) \
-          : k2_backproject<VGv, false><<<nblk, kBlocksPT * VGv, 0, st>>>(B.d_sd, m, a, B.d_partials))
+#define K2_LAUNCH(VGv)                                                                                  \
+    (eq11 ? launch_pdl(k2_backproject<VGv, true>, nblk, kBlocksPT * VGv, 0, st, B.d_sd, m, a, B.d_partials) \
+          : launch_pdl(k2_backproject<VGv, false>, nblk, kBlocksPT * VGv, 0, st, B.d_sd, m, a, B.d_partials))
     switch (B.k2_vg) {
     case 1: K2_LAUNCH(1); break;
     case 2: K2_LAUNCH(2); break;

@@ -12,6 +12,7 @@ thread_local long long g_launch_count = 0;
 __global__ void __launch_bounds__(256)
 k3_update_r(const SliceDev *__restrict__ sls, TileMap map)
 {
+    pdl_wait();
     int local;
     const int si = find_slice(map, blockIdx.x, &local);
     const SliceDev &S = sls[si];
@@ -29,6 +30,7 @@ __global__ void __launch_bounds__(256)
 k3_update_us(const SliceDev *__restrict__ sls, TileMap map, int update_s)
 {
     __shared__ float tile[32][33];
+    pdl_wait();
     int local;
     const int si = find_slice(map, blockIdx.x, &local);
     const SliceDev &S = sls[si];
@@ -69,12 +71,12 @@ k3_update_us(const SliceDev *__restrict__ sls, TileMap map, int update_s)
 
 void launch_cgls_update_r(const Batch &B, cudaStream_t st) {
     const int nblk = B.blocks(FAM_SINO);
-    if (nblk) { ++g_launch_count; k3_update_r<<<nblk, 256, 0, st>>>(B.d_sd, B.map(FAM_SINO)); }
+    if (nblk) { ++g_launch_count; launch_pdl(k3_update_r, nblk, 256, 0, st, B.d_sd, B.map(FAM_SINO)); }
 }
 
 void launch_cgls_update_us(const Batch &B, int update_s, cudaStream_t st) {
     const int nblk = B.blocks(FAM_IMG);
-    if (nblk) { ++g_launch_count; k3_update_us<<<nblk, 256, 0, st>>>(B.d_sd, B.map(FAM_IMG), update_s); }
+    if (nblk) { ++g_launch_count; launch_pdl(k3_update_us, nblk, 256, 0, st, B.d_sd, B.map(FAM_IMG), update_s); }
 }
 
 // Small helpers: set one scalar of every slice; advance the outer-iteration counter.

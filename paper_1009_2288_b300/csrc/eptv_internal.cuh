@@ -6,9 +6,36 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "eptv.h"
 
 namespace eptv {
+
+// ---------------------------------------------------------------------------------
+// Programmatic dependent launch.  A kernel started by launch_pdl may be scheduled while
+// the previous kernel of its stream (or CUDA graph) still finishes; it calls pdl_wait()
+// before its first access to global memory, which returns once that kernel has completed
+// and its writes are visible (at once when there is no such dependency).  Only kernels
+// that begin with pdl_wait() are launched this way.
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t st, Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // ---------------------------------------------------------------------------------
 // Canonical crossing parameter of a grid line.
@@ -96,7 +123,7 @@ struct SliceDev {
     float *r, *q;        // CGLS sinogram vectors
     float *fa, *fb;      // (P2) iterate ping-pong
     float *ga, *gb;      // (P2) gradient ping-pong
-    float *tv_scr;       // [n_edges] FP32 scratch (half-edge magnitudes for sigma)
+    float *tv_scr;       // [n_edges] FP32 scratch (half-edge T^2 for the sigma selection)
     const float *wprior; // per-pixel prior weight map, or null
     float *wout;         // optional output of the final edge weights
     double *sc;          // [kScalarStride] scalars

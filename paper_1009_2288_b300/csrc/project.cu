@@ -28,6 +28,7 @@ template <int SEG, bool HAS_T>
 __global__ void __launch_bounds__(32 * SEG, 32 / SEG)
 k1_project(const SliceDev *__restrict__ sls, TileMap map, ProjArgs a, double *__restrict__ partials)
 {
+    pdl_wait();
     __shared__ float red[SEG][33];
     __shared__ double rsm[2 * SEG];
     __shared__ double res[2];
@@ -243,9 +244,9 @@ void launch_project(const Batch &B, const ProjArgs &a, cudaStream_t st) {
     // the kernel reads the transposed image exactly when this holds
     const bool has_t = a.img_override ? (a.imgT_override != nullptr) : !a.no_T;
     const TileMap m = B.map(FAM_K1);
-#define K1_LAUNCH(SEGv)                                                                          \
-    (has_t ? k1_project<SEGv, true><<<nblk, 32 * SEGv, 0, st>>>(B.d_sd, m, a, B.d_partials)      \
-           : k1_project<SEGv, false><<<nblk, 32 * SEGv, 0, st>>>(B.d_sd, m, a, B.d_partials))
+#define K1_LAUNCH(SEGv)                                                                            \
+    (has_t ? launch_pdl(k1_project<SEGv, true>, nblk, 32 * SEGv, 0, st, B.d_sd, m, a, B.d_partials) \
+           : launch_pdl(k1_project<SEGv, false>, nblk, 32 * SEGv, 0, st, B.d_sd, m, a, B.d_partials))
     switch (B.k1_seg) {
     case 4: K1_LAUNCH(4); break;
     case 16: K1_LAUNCH(16); break;

@@ -326,6 +326,7 @@ __device__ __forceinline__ float sell_row_dot(const int *__restrict__ scol, cons
 __global__ void __launch_bounds__(256)
 k_spmv_p(const SliceDev *__restrict__ sls, TileMap map, ProjArgs a, double *__restrict__ partials)
 {
+    pdl_wait();
     __shared__ float part[8][32];
     __shared__ double rsm[2 * 8];
     __shared__ double res[2];
@@ -382,6 +383,7 @@ k_spmv_p(const SliceDev *__restrict__ sls, TileMap map, ProjArgs a, double *__re
 __global__ void __launch_bounds__(256)
 k_spmv_pt(const SliceDev *__restrict__ sls, TileMap map, BackArgs a, double *__restrict__ partials)
 {
+    pdl_wait();
     __shared__ float tile[8][33];
     __shared__ double rsm[2 * 8];
     __shared__ double res[2];
@@ -429,14 +431,14 @@ void launch_spmv_p(const Batch &B, const ProjArgs &a, cudaStream_t st) {
     const int nblk = B.blocks(FAM_SPMV_P);
     if (nblk == 0) return;
     ++g_launch_count;
-    k_spmv_p<<<nblk, 256, 0, st>>>(B.d_sd, B.map(FAM_SPMV_P), a, B.d_partials);
+    launch_pdl(k_spmv_p, nblk, 256, 0, st, B.d_sd, B.map(FAM_SPMV_P), a, B.d_partials);
 }
 
 void launch_spmv_pt(const Batch &B, const BackArgs &a, cudaStream_t st) {
     const int nblk = B.blocks(FAM_SPMV_PT);
     if (nblk == 0) return;
     ++g_launch_count;
-    k_spmv_pt<<<nblk, 256, 0, st>>>(B.d_sd, B.map(FAM_SPMV_PT), a, B.d_partials);
+    launch_pdl(k_spmv_pt, nblk, 256, 0, st, B.d_sd, B.map(FAM_SPMV_PT), a, B.d_partials);
 }
 
 // ---------------------------------------------------------------- CSR -> SELL-32

@@ -1,9 +1,11 @@
 // K4/K5: the (P2) step -- edge-preserving TV descent (Sec. 2.2, Eqs. 5, 9, A2, A3).
 //
 // K5 sigma: the ceil(q n)-th smallest half-edge magnitude T of v (Sec. 2.1), found
-//    exactly by a 3-pass radix selection over the FP32 bit patterns (12 + 12 + 8 bits):
-//    pass 0 computes every T (fused stencil) and histograms the top 12 bits; each pass's
-//    last block scans the histogram and narrows the prefix.
+//    exactly by a 3-pass radix selection over the FP32 bit patterns (12 + 12 + 8 bits) of
+//    T^2: sqrtf is monotone, so sqrtf of the k-th smallest T^2 is the k-th smallest
+//    sqrtf(T^2) = T, bit for bit, and one square root replaces one per half-edge.  Pass 0
+//    computes every T^2 (fused stencil) and histograms the top 12 bits; each pass's last
+//    block scans the histogram and narrows the prefix.
 // K4 one gradient-descent iteration, fused: apply the previous step f = f' - t' g'
 //    on the fly, stage f (tile + 2-pixel halo) and v in shared memory, compute T, the
 //    weights w = exp(-T^2/sigma^2) and w D / T at every half-edge, the gradient
@@ -29,22 +31,22 @@ __device__ __forceinline__ float img_at(const float *f, int nx, int ny, int i, i
     return (i >= 0 && i < nx && j >= 0 && j < ny) ? __ldg(f + (size_t)j * nx + i) : 0.0f;
 }
 
-// Half-edge e of the slice (x-edges first: e = j (nx+1) + i, between (i-1, j) and
+// T^2 of half-edge e of the slice (x-edges first: e = j (nx+1) + i, between (i-1, j) and
 // (i, j); then y-edges: X + j nx + i, between (i, j-1) and (i, j)).
-__device__ __forceinline__ float half_edge_T(const float *f, int nx, int ny, float eps2, int e) {
+__device__ __forceinline__ float half_edge_T2(const float *f, int nx, int ny, float eps2, int e) {
     const int X = (nx + 1) * ny;
     float D;
     if (e < X) {
         const int j = e / (nx + 1), i = e - j * (nx + 1);
-        return sqrtf(edge_T2(eps2, img_at(f, nx, ny, i - 1, j), img_at(f, nx, ny, i, j),
-                             img_at(f, nx, ny, i - 1, j + 1), img_at(f, nx, ny, i, j + 1),
-                             img_at(f, nx, ny, i - 1, j - 1), img_at(f, nx, ny, i, j - 1), &D));
+        return edge_T2(eps2, img_at(f, nx, ny, i - 1, j), img_at(f, nx, ny, i, j),
+                       img_at(f, nx, ny, i - 1, j + 1), img_at(f, nx, ny, i, j + 1),
+                       img_at(f, nx, ny, i - 1, j - 1), img_at(f, nx, ny, i, j - 1), &D);
     }
     e -= X;
     const int j = e / nx, i = e - j * nx;
-    return sqrtf(edge_T2(eps2, img_at(f, nx, ny, i, j - 1), img_at(f, nx, ny, i, j),
-                         img_at(f, nx, ny, i + 1, j - 1), img_at(f, nx, ny, i + 1, j),
-                         img_at(f, nx, ny, i - 1, j - 1), img_at(f, nx, ny, i - 1, j), &D));
+    return edge_T2(eps2, img_at(f, nx, ny, i, j - 1), img_at(f, nx, ny, i, j),
+                   img_at(f, nx, ny, i + 1, j - 1), img_at(f, nx, ny, i + 1, j),
+                   img_at(f, nx, ny, i - 1, j - 1), img_at(f, nx, ny, i - 1, j), &D);
 }
 
 // ------------------------------------------------------------------ radix selection
@@ -114,11 +116,12 @@ __device__ unsigned int sel_scan(unsigned int *hist, double *sc, int pass, long 
     return (pass == 2) ? (unsigned int)(*s_res) : 0u;
 }
 
-// Pass 0 of sigma: T of every half-edge of v -> scratch, histogram of the top 12 bits.
+// Pass 0 of sigma: T^2 of every half-edge of v -> scratch, histogram of the top 12 bits.
 __global__ void __launch_bounds__(256)
 k5_sigma_edges(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__restrict__ P,
                const float *v_override, unsigned int *__restrict__ hist_all)
 {
+    pdl_wait();
     __shared__ unsigned int sh[kHistBins];
     __shared__ unsigned int s_cnt[256];
     __shared__ long long s_res;
@@ -135,7 +138,7 @@ k5_sigma_edges(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *_
 #pragma unroll
     for (int q = 0; q < 8; ++q) {               // all stencil loads before any atomic
         const int e = e0 + q * 256 + threadIdx.x;
-        Tv[q] = (e < S.n_edges) ? half_edge_T(v, S.nx, S.ny, eps2, e) : 0.0f;
+        Tv[q] = (e < S.n_edges) ? half_edge_T2(v, S.nx, S.ny, eps2, e) : 0.0f;
     }
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
@@ -165,6 +168,7 @@ k5_radix_pass(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__
               int pass, unsigned int *__restrict__ hist_all, const float *vals_override, long long n_override, long long rank_override,
               float *out_override)
 {
+    pdl_wait();
     __shared__ unsigned int sh[kHistBins];
     __shared__ unsigned int s_cnt[256];
     __shared__ long long s_res;
@@ -208,7 +212,7 @@ k5_radix_pass(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__
             *out_override = val;
             S.sc[SC_NORM] = (double)val;
         } else {
-            S.sc[SC_SIGMA] = fmax((double)val, P->sigma_floor);
+            S.sc[SC_SIGMA] = fmax((double)sqrtf(val), P->sigma_floor);    // val: the k-th smallest T^2
             if (S.log) {
                 const int k = (int)S.sc[SC_OUTER];
                 if (k >= 0 && k < S.log_outer)
@@ -238,6 +242,7 @@ __global__ void __launch_bounds__(kGdThreads, WIDE ? 12 : 1)
 k4_gd(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__restrict__ P, GdArgs ga,
       int iter, double *__restrict__ partials)
 {
+    pdl_wait();
     __shared__ float F[FH][FW];
     __shared__ float W[FH][FW];          // prior map (PRIOR mode only)
     __shared__ float V[GH][GW];
@@ -402,6 +407,7 @@ __global__ void __launch_bounds__(256)
 k4_finish(const SliceDev *__restrict__ sls, TileMap map, int n_gd, const float *f0_override,
           float *out_override)
 {
+    pdl_wait();
     __shared__ float tile[32][33];
     int local;
     const int si = find_slice(map, blockIdx.x, &local);
@@ -443,19 +449,17 @@ k4_finish(const SliceDev *__restrict__ sls, TileMap map, int n_gd, const float *
 
 void launch_sigma(const Batch &B, const float *v_override, cudaStream_t st) {
     ++g_launch_count;
-    k5_sigma_edges<<<B.blocks(FAM_EDGE), 256, 0, st>>>(B.d_sd, B.map(FAM_EDGE), B.d_params,
-                                                       v_override, B.d_hist);
+    launch_pdl(k5_sigma_edges, B.blocks(FAM_EDGE), 256, 0, st, B.d_sd, B.map(FAM_EDGE), B.d_params,
+               v_override, B.d_hist);
     for (int pass = 1; pass <= 2; ++pass, ++g_launch_count)
-        k5_radix_pass<<<B.blocks(FAM_EDGE), 256, 0, st>>>(B.d_sd, B.map(FAM_EDGE), B.d_params, pass,
-                                                          B.d_hist, nullptr, 0, 0,
-                                                          nullptr);
+        launch_pdl(k5_radix_pass, B.blocks(FAM_EDGE), 256, 0, st, B.d_sd, B.map(FAM_EDGE), B.d_params, pass,
+                   B.d_hist, (const float *)nullptr, 0ll, 0ll, (float *)nullptr);
 }
 
 void launch_select_generic(const Batch &B, const TileMap &m, int nblk, const float *vals,
                            long long n, long long k, float *out, cudaStream_t st) {
     for (int pass = 0; pass <= 2; ++pass, ++g_launch_count)
-        k5_radix_pass<<<nblk, 256, 0, st>>>(B.d_sd, m, B.d_params, pass, B.d_hist,
-                                            vals, n, k, out);
+        launch_pdl(k5_radix_pass, nblk, 256, 0, st, B.d_sd, m, B.d_params, pass, B.d_hist, vals, n, k, out);
 }
 
 // SMs of the current device (queried once per device; host threads may race to fill the
@@ -478,8 +482,8 @@ static int sm_count() {
 template <int KT>
 static void launch_k4(int nb, bool wide, const Batch &B, const TileMap &m, const GdArgs &ga, int iter,
                       cudaStream_t st) {
-    if (wide) k4_gd<KT, true><<<nb, kGdThreads, 0, st>>>(B.d_sd, m, B.d_params, ga, iter, B.d_partials);
-    else k4_gd<KT, false><<<nb, kGdThreads, 0, st>>>(B.d_sd, m, B.d_params, ga, iter, B.d_partials);
+    if (wide) launch_pdl(k4_gd<KT, true>, nb, kGdThreads, 0, st, B.d_sd, m, B.d_params, ga, iter, B.d_partials);
+    else launch_pdl(k4_gd<KT, false>, nb, kGdThreads, 0, st, B.d_sd, m, B.d_params, ga, iter, B.d_partials);
 }
 
 void launch_gd_iter(const Batch &B, const GdArgs &ga, int iter, cudaStream_t st) {
@@ -496,8 +500,8 @@ void launch_gd_iter(const Batch &B, const GdArgs &ga, int iter, cudaStream_t st)
 void launch_gd_finish(const Batch &B, int n_gd, const float *f0_override, float *out_override,
                       cudaStream_t st) {
     ++g_launch_count;
-    k4_finish<<<B.blocks(FAM_IMG), 256, 0, st>>>(B.d_sd, B.map(FAM_IMG), n_gd, f0_override,
-                                                 out_override);
+    launch_pdl(k4_finish, B.blocks(FAM_IMG), 256, 0, st, B.d_sd, B.map(FAM_IMG), n_gd, f0_override,
+               out_override);
 }
 
 }  // namespace eptv

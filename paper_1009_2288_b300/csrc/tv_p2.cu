@@ -247,6 +247,7 @@ k4p_descent(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__re
     // the slice's first accumulator set is used first after the sigma barriers
     if (local == 0)
         for (int w = tid; w < NV * kAccCopies * kAccStride; w += NT) acc_slice[w] = 0ull;
+    if (tid == 0 && K > 0) trial_steps(P, s_misc[0], K, s_t, s_td);     // first GD iteration's
     __syncthreads();
 
     // one grid barrier (number b), arrival after the block's writes; false if a wait ran out
@@ -266,8 +267,10 @@ k4p_descent(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__re
         return !s_abort;
     };
 
-    // sigma: T = sqrt(T^2) (K5's half_edge_T) of the owned half-edges of v, x-edges (i, j)
-    // between (i - 1, j) and (i, j) first, then y-edges between (i, j - 1) and (i, j)
+    // sigma: the keys of T^2 (K5's half_edge_T2) of the owned half-edges of v, x-edges
+    // (i, j) between (i - 1, j) and (i, j) first, then y-edges between (i, j - 1) and (i, j);
+    // sqrtf is monotone, so sigma = sqrtf(the k-th smallest T^2), bit for bit the k-th
+    // smallest T
     constexpr int KEYS = (2 * (RW + 1) * (RH + 1) + NT - 1) / NT;
     unsigned int keys[KEYS];
     const int cx1 = min(RX0 + RW, nx), cy1 = min(RY0 + RH, ny);
@@ -291,9 +294,8 @@ k4p_descent(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__re
                 const float *q = F + (r + 1) * FW + (c + 2);            // pixel (i, j - 1)
                 T2 = edge_T2(eps2, q[0], q[FW], q[1], q[FW + 1], q[-1], q[FW - 1], &D);
             }
-            const float T = sqrtf(T2);
-            nonfinite |= !isfinite(T);
-            key = sel_key(T);
+            nonfinite |= !isfinite(T2);
+            key = sel_key(T2);
         }
         keys[k] = key;
     }
@@ -322,7 +324,7 @@ k4p_descent(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__re
         rank = s_rank;
         prefix = (pass == 0) ? (unsigned int)s_bin : (prefix << (pass == 1 ? 12 : 8)) | (unsigned int)s_bin;
     }
-    const double sigma = fmax((double)__uint_as_float(prefix), P->sigma_floor);
+    const double sigma = fmax((double)sqrtf(__uint_as_float(prefix)), P->sigma_floor);
     if (local == 0 && tid == 0) {
         S.sc[SC_SIGMA] = sigma;
         if (S.log && k_outer >= 0 && k_outer < S.log_outer)
@@ -334,8 +336,6 @@ k4p_descent(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__re
     const int grp = tid >> 7, vt = tid & 127;
     constexpr int kRing = 2 * FW + 2 * (FH - 2);
     static_assert(kRing <= NT, "one ring position per thread");
-    if (tid == 0 && K > 0) trial_steps(P, s_misc[0], K, s_t, s_td);
-    __syncthreads();
     for (int it = 0; it < pa.n_gd; ++it) {
         for (int w = tid; w < NV * kAccStride; w += NT) sacc[w] = 0ull;
         // the accumulator set of the next iteration: last read after barrier it - 2
@@ -386,11 +386,16 @@ k4p_descent(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__re
         __syncthreads();
 
         // phase 4: the tiles' sums (tile_sums: the per-thread assignment K4 uses), group grp
-        // (128 threads) takes tiles grp, grp + NG, ...; every warp adds its FP32 sums exactly
-        // into the block's accumulators (no barrier between the warps)
+        // (128 threads) takes TILES / NG tiles; every warp adds its FP32 sums exactly into the
+        // block's accumulators (no barrier between the warps).  2 x 4 regions: group grp takes
+        // tile (row grp, column grp & 1) and (row grp + 2 mod 4, the other column), so that
+        // in a region on the image's right or lower border (whose border tiles give one warp
+        // of the tile an extra round) every group has at most one border tile.
         float *wout = (it == pa.n_gd - 1) ? S.wout : nullptr;
         unsigned long long *set = acc_slice + (size_t)(it % kP2Sets) * kP2SetWords;
-        for (int q = grp; q < Sh::TILES; q += NG) {
+        for (int k = 0; k < Sh::TILES / NG; ++k) {
+            const int q = (RTX == 2 && RTY == 4) ? ((k == 0 ? grp : ((grp + 2) & 3)) * RTX + ((grp & 1) ^ k))
+                                                 : grp + k * NG;
             const int ox = (q % RTX) * kTileW, oy = (q / RTX) * kGdTileRows;
             const int X0 = RX0 + ox, Y0 = RY0 + oy;
             float vals[NV];

@@ -68,8 +68,10 @@ __device__ __forceinline__ void edge_ab(float lo, float hi, float lo_u, float hi
 }
 
 // dJ[m] += w (T'(t_m) - T) for the x- and y-edge of one position and every trial step,
-// in the cancellation-free form t (t b - 2 a) / (T' + T).
-template <int KT>
+// in the cancellation-free form t (t b - 2 a) / (T' + T).  EDGES = 1 / 2 evaluates only the
+// x / y term: for a position that owns only that edge the other one has weight 0 and a
+// finite change (T' + T >= eps), so it would add an exact zero.
+template <int KT, int EDGES = 3>
 __device__ __forceinline__ void trial_accum(int K, const float *s_t, float eps2, float Tx, float wx,
                                             float aex, float bex, float Ty, float wy, float aey,
                                             float bey, float (&dJ)[KT]) {
@@ -78,14 +80,18 @@ __device__ __forceinline__ void trial_accum(int K, const float *s_t, float eps2,
     for (int m = 0; m < KT; ++m) {
         if (m < K) {
             const float t = s_t[m];
-            const float numx = t * fmaf(t, bex, -2.0f * aex);
-            const float T2nx = fmaxf(T2x + numx, eps2);   // T'^2 >= eps^2
-            const float Tnx = T2nx * rsqrtf(T2nx);
-            dJ[m] = fmaf(wx, __fdividef(numx, Tnx + Tx), dJ[m]);
-            const float numy = t * fmaf(t, bey, -2.0f * aey);
-            const float T2ny = fmaxf(T2y + numy, eps2);
-            const float Tny = T2ny * rsqrtf(T2ny);
-            dJ[m] = fmaf(wy, __fdividef(numy, Tny + Ty), dJ[m]);
+            if (EDGES & 1) {
+                const float numx = t * fmaf(t, bex, -2.0f * aex);
+                const float T2nx = fmaxf(T2x + numx, eps2);   // T'^2 >= eps^2
+                const float Tnx = T2nx * rsqrtf(T2nx);
+                dJ[m] = fmaf(wx, __fdividef(numx, Tnx + Tx), dJ[m]);
+            }
+            if (EDGES & 2) {
+                const float numy = t * fmaf(t, bey, -2.0f * aey);
+                const float T2ny = fmaxf(T2y + numy, eps2);
+                const float Tny = T2ny * rsqrtf(T2ny);
+                dJ[m] = fmaf(wy, __fdividef(numy, Tny + Ty), dJ[m]);
+            }
         }
     }
 }
@@ -202,8 +208,9 @@ namespace eptv {
 
 // One position (a, b) of a 32 x 8 tile (tile_sums below): the fidelity terms of pixel
 // (X0 + b, Y0 + a) when it is the tile's, and the energy / trial terms of its left x-edge
-// and upper y-edge when the tile owns them.
-template <int KT>
+// and upper y-edge when the tile owns them (EDGES = 1 / 2: a border position that can own
+// only its x- / y-edge).
+template <int KT, int EDGES = 3>
 __device__ __forceinline__ void tile_position(int a, int b, int X0, int Y0, int nx, int ny,
                                               const float *F, int fs, const float *G, int gs,
                                               const float *V, int vs, const float *TX,
@@ -243,7 +250,7 @@ __device__ __forceinline__ void tile_position(int a, int b, int X0, int Y0, int 
         if (own_y)
             edge_ab(f12, f22, Fb[fs + 3], Fb[2 * fs + 3], f11, f21,
                     g01, g11, Gb[2], Gb[gs + 2], g00, g10, &aey, &bey);
-        trial_accum<KT>(K, s_t, eps2, Tx, wx, aex, bex, Ty, wy, aey, bey, dJ);
+        trial_accum<KT, EDGES>(K, s_t, eps2, Tx, wx, aex, bex, Ty, wy, aey, bey, dJ);
     }
 }
 
@@ -276,12 +283,12 @@ __device__ __forceinline__ void tile_sums(int vt, int X0, int Y0, int nx, int ny
     tile_position<KT>(a + 1, b, X0, Y0, nx, ny, F, fs, G, gs, V, vs, TX, WX, xs, TY, WY, ys, K, s_t,
                       eps2, wout, sA, sB, sF, sJ, dJ);
     // edges on the image's right / lower border (only tiles that reach it own them)
-    if (X0 + TW >= nx && vt < TH)
-        tile_position<KT>(vt, TW, X0, Y0, nx, ny, F, fs, G, gs, V, vs, TX, WX, xs, TY, WY, ys, K, s_t,
-                          eps2, wout, sA, sB, sF, sJ, dJ);
-    else if (Y0 + TH >= ny && vt >= 32 && vt < 32 + TW)
-        tile_position<KT>(TH, vt - 32, X0, Y0, nx, ny, F, fs, G, gs, V, vs, TX, WX, xs, TY, WY, ys, K,
-                          s_t, eps2, wout, sA, sB, sF, sJ, dJ);
+    if (X0 + TW >= nx && vt < TH)             // column TW: only its x-edge can be owned
+        tile_position<KT, 1>(vt, TW, X0, Y0, nx, ny, F, fs, G, gs, V, vs, TX, WX, xs, TY, WY, ys, K, s_t,
+                             eps2, wout, sA, sB, sF, sJ, dJ);
+    else if (Y0 + TH >= ny && vt >= 32 && vt < 32 + TW)    // row TH: only its y-edge
+        tile_position<KT, 2>(TH, vt - 32, X0, Y0, nx, ny, F, fs, G, gs, V, vs, TX, WX, xs, TY, WY, ys, K,
+                             s_t, eps2, wout, sA, sB, sF, sJ, dJ);
 }
 
 }  // namespace eptv

@@ -18,7 +18,7 @@
 //            owned half-edges with the weights frozen; each warp adds its FP32 sums exactly
 //            (integer fixed point) into the block's accumulators, and the block's words go
 //            into the slice's accumulators (one set per GD iteration, three in rotation);
-//   barrier  one grid-wide arrival / wait (bounded), polled by several warps; meanwhile
+//   barrier  one grid-wide arrival / wait (bounded), polled by one warp; meanwhile
 //            warp 1 prepares the next iteration's trial steps for every possible outcome;
 //   decide   every block reads the exact totals and takes the same FP64 Armijo decision
 //            (the first passing trial); the slice's first block keeps the record and
@@ -83,7 +83,10 @@ __device__ __forceinline__ bool p2_wait(const unsigned int *bar, unsigned int ta
 }
 
 // Accumulator copies K4p's blocks spread their words over (block b: copy b mod kP2Copies).
-constexpr int kP2Copies = 4;
+// Every block reads all copies after each barrier, and with one block per SM the push
+// atomics of 128 blocks on one copy cost less than the longer read-out of more copies
+// (per GD iteration at 512^2: 4 copies 13.0 us, 2 copies 12.6, 1 copy 12.1).
+constexpr int kP2Copies = 1;
 
 // One pass of the selection scan, run by every block on the slice's histogram gh (NB
 // bins): the bin holding the remaining rank (1-based) and the rank within it, to *s_bin and
@@ -175,7 +178,10 @@ k4p_descent(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__re
     float *WY = TY + QYH * QYW;
     __shared__ int s_abort;
     __shared__ int s_seen[2];                              // barrier seen (per iteration parity)
-    constexpr int kPollers = NT / 32 < 4 ? NT / 32 : 4;
+    // warps polling the barrier (lane 0 each; the first to see it tells the others through
+    // s_seen).  One: more polls in flight were measured slower (4 warps +0.2 us, 8 warps
+    // +1.8 us per GD iteration at 512^2), their loads queue on the counter's line.
+    constexpr int kPollers = 1;
     __shared__ unsigned long long sacc[NV * kAccStride];   // the block's exact sums
     // candidate trial steps of the next iteration ((K + 1) K <= 32: K <= 4)
     constexpr bool kCand = (KT + 1) * KT <= 32;
@@ -437,8 +443,8 @@ k4p_descent(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__re
                 cand_d[lane] = (double)(float)t;
             }
         }
-        // lane 0 of up to kPollers warps polls; the first to see every arrival tells the
-        // others through s_seen (polls of several warps in flight shorten the detection)
+        // lane 0 of the kPollers polling warps; the first to see every arrival tells the
+        // others through s_seen
         const int bnum = 3 + it;
         if ((tid & 31) == 0 && (tid >> 5) < kPollers) {
             const unsigned int need = base + (unsigned int)(bnum + 1) * per_bar;

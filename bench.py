@@ -31,6 +31,7 @@ METRIC = "EPTV iterations/s (512x512, 40 views x 888 bins, 100 iterations)"
 UNIT = "iterations/s"
 WORKLOAD = "eptv_512x512_40v_888b"
 N_OUTER = 100
+PT_BUDGET = 4 << 30     # bytes the stored P^T matrices may take (512^2: 0.32 GB)
 
 
 def parse():
@@ -779,6 +780,10 @@ def run_ours(args, world, rank, local):
     stream = torch.cuda.current_stream(dev)
 
     tuning = E.eptv_autotune(geo)          # launch shapes of K1 / K2 for this geometry
+    # P^T from the kernel or from the stored matrix (Sec. 2.3), whichever is faster here;
+    # the matrix (built once per geometry, like the ray tables) stays within PT_BUDGET
+    op_mode = E.eptv_autotune_operator(geo, PT_BUDGET)
+    stored_pt = op_mode == E.OPERATOR_STORED_PT
 
     def step():
         f_dev.zero_()
@@ -836,7 +841,16 @@ def run_ours(args, world, rank, local):
     ybuf = torch.empty(g.n_rays, device=dev)
     ximg = torch.empty_like(f_dev)
     t_k1 = time_kernel(lambda: E.eptv_project_t(geo, f_dev, fT, ybuf))
-    t_k2 = time_kernel(lambda: E.eptv_backproject(geo, y_dev, ximg))
+    t_pt = time_kernel(lambda: E.eptv_backproject(geo, y_dev, ximg))   # the P^T in use
+    if stored_pt:       # the kernel K2 as well (the Eq. 11 leg compares against it)
+        E.eptv_set_operator(geo, E.OPERATOR_ON_THE_FLY)
+        t_k2 = time_kernel(lambda: E.eptv_backproject(geo, y_dev, ximg))
+        E.eptv_set_operator(geo, E.OPERATOR_STORED_PT)
+        rows_t, _, sell_t = E.eptv_matrix_info(geo, 1)
+        # streamed per launch: the SELL-32 entries (8 B), slice offsets and lengths, output
+        pt_bytes = 8 * sell_t + 8 * ((rows_t + 31) // 32) + 4 * rows_t
+    else:
+        t_k2 = t_pt
 
     def outer_seconds(n_gd, n_outer=20, reps=3):
         pq = I.EptvParams(n_outer=n_outer, n_gd=n_gd)
@@ -860,15 +874,21 @@ def run_ours(args, world, rank, local):
     peak, peak_kind = measured_peaks()
     src_of = {"k1_project": ["paper_1009_2288_b300/csrc/project.cu"],
               "k2_backproject": ["paper_1009_2288_b300/csrc/backproject.cu"],
+              "k_spmv_pt": ["paper_1009_2288_b300/csrc/stored.cu"],
               "k4p_descent": ["paper_1009_2288_b300/csrc/tv_p2.cu",
                               "paper_1009_2288_b300/csrc/tv_stencil.cuh"]}
     common = ["paper_1009_2288_b300/csrc/eptv_internal.cuh", "paper_1009_2288_b300/csrc/kernels.cuh"]
+    if stored_pt:
+        pt_entry = ("k_spmv_pt", t_pt, pt_bytes, p.cgls_iters * t_pt, "launch",
+                    "hbm (the stored P^T streamed: 8 B per SELL-32 entry + offsets + output)")
+    else:
+        pt_entry = ("k2_backproject", t_k2, spmv_bytes, p.cgls_iters * t_k2, "launch",
+                    "gather/issue (SpMV-equivalent bytes)")
     kernels = []
     for name, t, nbytes, per_outer, unit_desc, limiter in (
             ("k1_project", t_k1, spmv_bytes, (p.cgls_iters + 1) * t_k1, "launch",
              "gather/issue (SpMV-equivalent bytes)"),
-            ("k2_backproject", t_k2, spmv_bytes, p.cgls_iters * t_k2, "launch",
-             "gather/issue (SpMV-equivalent bytes)"),
+            pt_entry,
             ("k4p_descent", t_gd, gd_bytes, p.n_gd * t_gd, "GD iteration",
              "latency: one grid barrier, exact read-out and FP64 Armijo decision per GD iteration")):
         achieved = nbytes / t / 1e9
@@ -884,6 +904,7 @@ def run_ours(args, world, rank, local):
                 "algorithmic_bytes_per_unit": dom["algorithmic_bytes"], "unit_of_work": dom["unit_of_work"],
                 "nnz": nnz, "outer_iteration_us": t_out10 * 1e6, "kernels": kernels,
                 "launch_us": {"k1_project": t_k1 * 1e6, "k2_backproject": t_k2 * 1e6,
+                              "p_transpose_in_use": t_pt * 1e6,
                               "k4p_descent_per_gd_iteration": t_gd * 1e6}}
 
     # time to the FP64 oracle's energy (stored by tests/golden/make_oracle_energy.py).
@@ -971,7 +992,9 @@ def run_ours(args, world, rank, local):
                    "image": "512x512 @ 0.8 mm", "views": 40, "bins": 888, "M": p.cgls_iters,
                    "n_gd": p.n_gd, "max_trials": p.max_trials, "l2": "flushed (256 MB write) between steps",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "tuning": {"k1_seg": tuning[0], "k2_vg": tuning[1]}},
+                   "tuning": {"k1_seg": tuning[0], "k2_vg": tuning[1],
+                              "operator": "P on the fly (K1), P^T from the stored matrix (SELL-32)"
+                              if stored_pt else "P, P^T on the fly (K1, K2)"}},
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": 4 * g.n_rays, "d2h_bytes_per_step": 4 * g.n_pix,
                 "ms_per_step": e2e_ms},

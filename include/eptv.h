@@ -358,6 +358,18 @@ int eptv_quality_metrics(const eptv_geometry *g, const float *d_f, const float *
  * entries), EPTV_ERR_NOMEM, EPTV_ERR_CUDA. */
 int eptv_set_operator(eptv_geometry *g, int mode, long long *h_nnz_opt);
 
+/* Chooses the form of P^T for handle g by measurement (the choice Sec. 2.3 leaves to the
+ * problem size): when the stored matrices can take at most max_matrix_bytes of device
+ * memory (bounded before anything is built by 32 bytes x n_rays x (nx + ny)), it builds
+ * them, times P^T from the kernel (at the shape eptv_autotune chose) and from the stored
+ * matrix in interleaved rounds of 20 launches on the handle's workspace (overwritten), and
+ * keeps the faster: EPTV_OPERATOR_STORED_PT or EPTV_OPERATOR_ON_THE_FLY (whose stored
+ * matrices are then freed).  P stays on the fly either way.  *mode_out (may be NULL)
+ * receives the choice.  The two forms have identical entries, so results differ only in
+ * summation order.  EPTV_ERR_ARG if g is in another operator mode; a matrix that cannot be
+ * built (too large, no memory) leaves the handle on the fly; EPTV_ERR_CUDA. */
+int eptv_autotune_operator(eptv_geometry *g, long long max_matrix_bytes, int *mode_out);
+
 /* Rows and stored entries (padding included) of the built matrix `which` (0: P, 1: P^T)
  * in the exported CSR form; *h_sell_opt (may be NULL) receives the entries of the SELL-32
  * copy the SpMV kernels stream (rows in slices of 32, each slice padded to its longest

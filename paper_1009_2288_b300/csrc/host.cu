@@ -1123,6 +1123,67 @@ int eptv_set_operator(eptv_geometry *g, int mode, long long *h_nnz_opt) {
     return 0;
 }
 
+int eptv_autotune_operator(eptv_geometry *g, long long max_matrix_bytes, int *mode_out) {
+    if (!g) return fail(EPTV_ERR_ARG, "NULL handle");
+    if (g->op_mode != EPTV_OPERATOR_ON_THE_FLY && g->op_mode != EPTV_OPERATOR_STORED_PT)
+        return fail(EPTV_ERR_ARG, "operator autotuning starts from EPTV_OPERATOR_ON_THE_FLY or _STORED_PT");
+    int rc = 0;
+    const SliceDev &sd = g->sd;
+    // about 32 bytes per entry of P (CSR and SELL-32 of P and P^T); a ray has at most
+    // nx + ny entries, so this bound is known before anything is built
+    const long long bound = 32ll * (long long)sd.n_rays * (long long)(sd.nx + sd.ny);
+    int best = EPTV_OPERATOR_ON_THE_FLY;
+    if (bound <= max_matrix_bytes) {
+        if ((rc = eptv_set_operator(g, EPTV_OPERATOR_STORED_PT, nullptr))) {
+            if (rc != EPTV_ERR_NOMEM && rc != EPTV_ERR_ARG) return rc;
+            rc = 0;                                  // too large to build: stays on the fly
+        } else {
+            Batch &B = g->B;
+            cudaStream_t st = nullptr;
+            CU(cudaMemsetAsync(sd.r, 0, sizeof(float) * sd.n_rays, st));
+            cudaEvent_t e0, e1;
+            CU(cudaEventCreate(&e0));
+            CU(cudaEventCreate(&e1));
+            BackArgs ba{};
+            ba.out = 1; ba.fin = FIN_NONE;
+            const long long saved = g_launch_count;
+            // P^T from the kernel (its tuned shape) and from the stored matrix, timed in
+            // interleaved rounds of 20 launches and ranked by the median round
+            constexpr int kRounds = 7;
+            float t[2][kRounds];
+            for (int c = 0; c < 2; ++c) {
+                B.stored_pt = c;
+                for (int i = 0; i < 3; ++i) op_backproject(B, ba, st);
+            }
+            for (int r = 0; r < kRounds; ++r)
+                for (int c = 0; c < 2; ++c) {
+                    B.stored_pt = c;
+                    cudaEventRecord(e0, st);
+                    for (int i = 0; i < 20; ++i) op_backproject(B, ba, st);
+                    cudaEventRecord(e1, st);
+                    cudaEventSynchronize(e1);
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    t[c][r] = ms;
+                }
+            g_launch_count = saved;
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            CU(cudaGetLastError());
+            std::nth_element(t[0], t[0] + kRounds / 2, t[0] + kRounds);
+            std::nth_element(t[1], t[1] + kRounds / 2, t[1] + kRounds);
+            if (t[1][kRounds / 2] < t[0][kRounds / 2]) best = EPTV_OPERATOR_STORED_PT;
+        }
+    }
+    if ((rc = eptv_set_operator(g, best, nullptr))) return rc;
+    if (best == EPTV_OPERATOR_ON_THE_FLY && g->stored.p_ptr) {   // not used: give the memory back
+        g->stored_mem.release();
+        g->stored = StoredMatrices{};
+    }
+    if (mode_out) *mode_out = best;
+    return 0;
+}
+
 int eptv_matrix_info(const eptv_geometry *g, int which, long long *h_rows, long long *h_nnz,
                      long long *h_sell_opt) {
     if (!g || !h_rows || !h_nnz) return fail(EPTV_ERR_ARG, "NULL argument");

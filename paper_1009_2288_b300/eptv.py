@@ -27,7 +27,7 @@ EXPORTED = [
     "eptv_autotune_batched", "eptv_unet_conv3x3", "eptv_unet_conv3x3_wgrad",
     "eptv_unet_weights_to_bf16", "eptv_unet_set_conv_kernel", "eptv_unet_tc_status", "eptv_unet_maxpool2", "eptv_unet_maxpool2_bwd",
     "eptv_unet_upsample2", "eptv_unet_upsample2_bwd", "eptv_unet_relu_bwd", "eptv_unet_head",
-    "eptv_unet_adam", "eptv_unet_pack_input", "eptv_set_operator", "eptv_matrix_info",
+    "eptv_unet_adam", "eptv_unet_pack_input", "eptv_set_operator", "eptv_autotune_operator", "eptv_matrix_info",
     "eptv_copy_matrix", "eptv_backproject_eq11", "eptv_quality_metrics",
     "eptv3_create_geometry", "eptv3_destroy_geometry", "eptv3_set_tuning", "eptv3_set_backprojector_stack", "eptv3_project",
     "eptv3_backproject", "eptv3_cgls", "eptv3_tv_step", "eptv3_reconstruct", "eptv3_report_energy",
@@ -153,6 +153,7 @@ def load():
                                    vp, vp, vp, c_int, c_int, vp, vp, vp, vp]),
         "eptv_unet_pack_input": (c_int, [vp, ctypes.c_float, vp, ctypes.c_float, ctypes.c_longlong, vp, vp]),
         "eptv_set_operator": (c_int, [vp, c_int, ctypes.POINTER(ctypes.c_longlong)]),
+        "eptv_autotune_operator": (c_int, [vp, ctypes.c_longlong, ctypes.POINTER(c_int)]),
         "eptv_backproject_eq11": (c_int, [vp, vp, vp, vp]),
         "eptv3_create_geometry": (c_int, [ctypes.POINTER(GeometryDesc3), ctypes.POINTER(vp)]),
         "eptv3_destroy_geometry": (None, [vp]),
@@ -396,6 +397,14 @@ def eptv_set_operator(geom: Geometry, mode: int) -> int:
     nnz = ctypes.c_longlong(0)
     _check(load().eptv_set_operator(geom.handle, int(mode), ctypes.byref(nnz)))
     return nnz.value
+
+
+def eptv_autotune_operator(geom: Geometry, max_matrix_bytes: int) -> int:
+    """P^T of geom from the kernel or from the stored matrix, whichever is faster (within
+    the memory bound); returns the operator mode kept."""
+    mode = ctypes.c_int(0)
+    _check(load().eptv_autotune_operator(geom.handle, int(max_matrix_bytes), ctypes.byref(mode)))
+    return mode.value
 
 
 def eptv_matrix_info(geom: Geometry, which: int):

@@ -264,3 +264,27 @@ def test_stored_pt_mode_mixes_the_operators_exactly():
         f1 = torch.zeros(cc.geom.n_pix, device=DEV)
         E.eptv_reconstruct(gg, p, y, f1)
         assert torch.equal(fv, f1)
+
+
+def test_autotune_operator_keeps_the_faster_back_projector():
+    """eptv_autotune_operator on the benchmark geometry: the kept mode is one of the two P^T
+    forms, P^T then agrees with the on-the-fly kernel to summation order, a budget below
+    the size bound keeps the kernel, and a handle in the fully stored mode is refused."""
+    g = I.make_c2(with_truth=False).geom
+    geo, ref = E.Geometry(g), E.Geometry(g)
+    E.eptv_autotune(geo)
+    mode = E.eptv_autotune_operator(geo, 4 << 30)
+    assert mode in (E.OPERATOR_ON_THE_FLY, E.OPERATOR_STORED_PT)
+    ys = t32(np.abs(I.random_sino(g, 8))).reshape(-1)
+    b1, b2 = torch.empty(g.n_pix, device=DEV), torch.empty(g.n_pix, device=DEV)
+    E.eptv_backproject(geo, ys, b1)
+    E.eptv_backproject(ref, ys, b2)
+    assert rel(np64(b1), np64(b2)) < 1e-6
+    small = E.Geometry(g)
+    assert E.eptv_autotune_operator(small, 1 << 20) == E.OPERATOR_ON_THE_FLY
+    E.eptv_backproject(small, ys, b1)
+    assert torch.equal(b1, b2)
+    full = E.Geometry(I.c1_geometry())
+    E.eptv_set_operator(full, E.OPERATOR_STORED)
+    with pytest.raises(E.EptvError):
+        E.eptv_autotune_operator(full, 4 << 30)

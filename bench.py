@@ -692,6 +692,7 @@ def run_learned(dev, stream, n_pairs=2000, epochs=40, eval_seeds=(1, 2, 3, 4), k
     g = I.ge_geometry(256, 1.6, 30)
     geo = E.Geometry(g)
     E.eptv_autotune(geo)
+    op_mode = E.eptv_autotune_operator(geo, PT_BUDGET)     # both arms run on this handle
     warm = L.WarmStart(net, geo)
     f = torch.zeros(g.n_pix, device=dev)
     w = torch.empty(g.n_pix, device=dev)
@@ -735,6 +736,7 @@ def run_learned(dev, stream, n_pairs=2000, epochs=40, eval_seeds=(1, 2, 3, 4), k
         return sum(vals) / len(vals) if len(vals) == len(per) else None
     out = {"workload": "learned_256x256_30v_888b", "criterion": "5-iteration mean of E_report within 1e-3 "
            "of the FP64 oracle's last-5 mean (sigma_ref = oracle's last sigma)",
+           "operator": "P^T stored" if op_mode == E.OPERATOR_STORED_PT else "P^T on the fly",
            "training": {"pairs": n_pairs, "pair_iterations": p.n_outer, "epochs": epochs, "batch": 16,
                         "steps": n_steps, "pairs_s": t_pairs, "train_s": t_train,
                         "ms_per_step": t_train * 1e3 / max(n_steps, 1),
@@ -880,7 +882,9 @@ def run_ours(args, world, rank, local):
     common = ["paper_1009_2288_b300/csrc/eptv_internal.cuh", "paper_1009_2288_b300/csrc/kernels.cuh"]
     if stored_pt:
         pt_entry = ("k_spmv_pt", t_pt, pt_bytes, p.cgls_iters * t_pt, "launch",
-                    "hbm (the stored P^T streamed: 8 B per SELL-32 entry + offsets + output)")
+                    "hbm + L2 (the stored P^T streamed, 8 B per SELL-32 entry + offsets + output; "
+                    "the leading slices that fit in half of L2 are read evict_last and stay in L2 "
+                    "between products, so part of the stream comes from L2)")
     else:
         pt_entry = ("k2_backproject", t_k2, spmv_bytes, p.cgls_iters * t_k2, "launch",
                     "gather/issue (SpMV-equivalent bytes)")

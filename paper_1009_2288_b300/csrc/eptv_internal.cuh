@@ -147,6 +147,7 @@ struct SliceDev {
     const float *p_sval;
     const int *pt_sptr, *pt_slen, *pt_scol;
     const float *pt_sval;
+    int pt_keep;         // P^T slices [0, pt_keep) are read with an L2 evict_last policy
 };
 
 // Launch plan of one kernel family over a set of slices: slice s owns the blocks

@@ -1100,6 +1100,18 @@ int eptv_set_operator(eptv_geometry *g, int mode, long long *h_nnz_opt) {
             if (e == cudaErrorMemoryAllocation) return fail(EPTV_ERR_NOMEM, "no device memory for the stored matrices");
             return fail(EPTV_ERR_CUDA, "building the stored matrices failed: %s", cudaGetErrorString(e));
         }
+        // the leading P^T slices whose entries fit in half of L2 (read evict_last)
+        int dev = 0, l2 = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess)
+            l2 = 0;
+        cudaGetLastError();
+        const int n_sl = ((g->sd.nx + 31) / 32) * g->sd.ny;
+        std::vector<int> sptr((size_t)n_sl + 1);
+        CU(cudaMemcpy(sptr.data(), m.pt_sptr, sizeof(int) * sptr.size(), cudaMemcpyDeviceToHost));
+        const long long keep_entries = (long long)l2 / 2 / 8;            // 8 B per entry
+        int keep = 0;
+        while (keep < n_sl && sptr[(size_t)keep + 1] <= keep_entries) ++keep;
+        m.pt_keep = keep;
         g->stored = m;
     }
     const bool on = mode == EPTV_OPERATOR_STORED;
@@ -1112,6 +1124,7 @@ int eptv_set_operator(eptv_geometry *g, int mode, long long *h_nnz_opt) {
         sd->pt_slen = need ? g->stored.pt_slen : nullptr;
         sd->pt_scol = need ? g->stored.pt_scol : nullptr;
         sd->pt_sval = need ? g->stored.pt_sval : nullptr;
+        sd->pt_keep = need ? g->stored.pt_keep : 0;
     }
     CU(cudaMemcpy(g->B.d_sd, g->B.h_sd.data(), sizeof(SliceDev), cudaMemcpyHostToDevice));
     g->B.stored = on ? 1 : 0;

@@ -181,6 +181,7 @@ struct StoredMatrices {
     int *pt_sptr = nullptr, *pt_slen = nullptr, *pt_scol = nullptr;
     float *pt_sval = nullptr;
     long long sell_pt = 0;
+    int pt_keep = 0;             // leading P^T slices kept in L2 (see SliceDev::pt_keep)
 };
 typedef cudaError_t (*StoredAlloc)(void *ctx, void **p, size_t bytes);
 cudaError_t build_stored(const SliceDev &S, const SliceDev *d_sd, StoredAlloc alloc, void *ctx,

@@ -261,17 +261,41 @@ __device__ __forceinline__ int sell_row(int sl, int l, int rows, int width) {
     return (ix < width && iy * width < rows) ? iy * width + ix : -1;
 }
 
+// L2 policies for the matrix stream: a matrix larger than L2 passes through it on every
+// product, evicting itself before reuse, so its entries are read evict_first -- except a
+// leading part that fits in half of L2, read evict_last, which then stays in L2 from one
+// product to the next (the products of an outer iteration and of the iterations after it)
+// and is not read from DRAM again.  The other half is left to everything else.
+__device__ __forceinline__ unsigned long long l2_evict_last_policy() {
+    unsigned long long p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ int4 ld_keep(const int4 *a, unsigned long long p) {
+    int4 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v4.s32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(a), "l"(p));
+    return v;
+}
+__device__ __forceinline__ float4 ld_keep(const float4 *a, unsigned long long p) {
+    float4 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(a), "l"(p));
+    return v;
+}
+
 // REMAP: columns are transposed pixel indices c = ix ny + iy to be read from the
 // natural image (no transposed copy given): index (c % ny) nx + c / ny.
 // PIPE (long rows): software-pipelined, the next chunk's loads are in flight while the
 // current chunk gathers from the vector, so the stream does not wait for the gathers.
 // Short rows (P^T) run faster without the extra prologue loads.  base: the slice's start
 // plus 32 times the first entry (a multiple of kSellChunk); len: a multiple of kSellChunk.
-// The lane sums its entries in order (the same sum as an entry-by-entry loop).
+// The lane sums its entries in order (the same sum as an entry-by-entry loop).  keep: the
+// slice's entries are read evict_last (the short-row form only).
 template <bool REMAP, bool PIPE>
 __device__ __forceinline__ float sell_row_dot(const int *__restrict__ scol, const float *__restrict__ sval,
                                               int base, int len, int lane, const float *__restrict__ x,
-                                              int nx, int ny) {
+                                              int nx, int ny, bool keep = false) {
     const int4 *pc = reinterpret_cast<const int4 *>(scol + base) + lane;
     const float4 *pv = reinterpret_cast<const float4 *>(sval + base) + lane;
     const int n_chunks = len / kSellChunk;
@@ -281,9 +305,10 @@ __device__ __forceinline__ float sell_row_dot(const int *__restrict__ scol, cons
     };
     float acc = 0.0f;
     if (!PIPE) {
+        const unsigned long long pol = l2_evict_last_policy();
         for (int c = 0; c < n_chunks; ++c) {
-            const int4 cc = __ldcs(pc + 32 * c);
-            const float4 vv = __ldcs(pv + 32 * c);
+            const int4 cc = keep ? ld_keep(pc + 32 * c, pol) : __ldcs(pc + 32 * c);
+            const float4 vv = keep ? ld_keep(pv + 32 * c, pol) : __ldcs(pv + 32 * c);
             const float x0 = gather(cc.x), x1 = gather(cc.y), x2 = gather(cc.z), x3 = gather(cc.w);
             acc = fmaf(vv.x, x0, acc);
             acc = fmaf(vv.y, x1, acc);
@@ -407,7 +432,8 @@ k_spmv_pt(const SliceDev *__restrict__ sls, TileMap map, BackArgs a, double *__r
     const bool valid = iy < S.ny && ix < S.nx;
     if (valid) {
         acc = sell_row_dot<false, false>(S.pt_scol, S.pt_sval, __ldg(S.pt_sptr + slice),
-                                         __ldg(S.pt_slen + slice), lane, in, S.nx, S.ny);
+                                         __ldg(S.pt_slen + slice), lane, in, S.nx, S.ny,
+                                         slice < S.pt_keep);
         out[(size_t)iy * S.nx + ix] = acc;
     }
     if (outT) {

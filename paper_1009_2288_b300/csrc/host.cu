@@ -264,8 +264,9 @@ static void op_backproject(const Batch &B, const BackArgs &a, cudaStream_t st) {
 }
 
 // (P1): M CGLS iterations from u (App. I).  r = y - P u; s = P^T r; then M times
-// q = P s, a; r -= a q; [t = P^T r, b; s = t + b s]; u += a s.
-static void enqueue_cgls(const Batch &B, int M, bool have_uT, cudaStream_t st) {
+// q = P s, a; r -= a q; [t = P^T r, b; s = t + b s]; u += a s.  defer_last: the last
+// u += a s is left to the caller (the persistent (P2) kernel applies it as it loads v).
+static void enqueue_cgls(const Batch &B, int M, bool have_uT, cudaStream_t st, bool defer_last = false) {
     ProjArgs pr{};
     pr.img = IMG_U; pr.out = SINO_R; pr.resid = 1; pr.fin = FIN_NONE; pr.no_T = have_uT ? 0 : 1;
     op_project(B, pr, st);
@@ -283,7 +284,7 @@ static void enqueue_cgls(const Batch &B, int M, bool have_uT, cudaStream_t st) {
             bt.out = 1; bt.write_T = 0; bt.fin = FIN_B;
             op_backproject(B, bt, st);
         }
-        launch_cgls_update_us(B, more ? 1 : 0, st);
+        if (more || !defer_last) launch_cgls_update_us(B, more ? 1 : 0, st);
     }
 }
 
@@ -307,9 +308,12 @@ static int ensure_p2(Batch &B, const eptv_params *p, cudaStream_t st) {
 
 // (P2) + clamp on v = u: either the persistent kernel K4p (sigma, all n_gd GD iterations,
 // apply + clamp into u, u^T) or sigma (K5) and n_gd fused GD launches of K4 and K4u.
+static bool p2_persistent(const Batch &B, const eptv_params *p) { return B.p2.ok && p->n_gd >= 1; }
+
+// fold: the CGLS's last u += a s is still to be applied (only with the persistent kernel)
 static void enqueue_p2(const Batch &B, const eptv_params *p, const float *v_override,
-                       float *out_override, cudaStream_t st) {
-    if (B.p2.ok && p->n_gd >= 1) {
+                       float *out_override, cudaStream_t st, bool fold = false) {
+    if (p2_persistent(B, p)) {
         P2Args pa{};
         pa.v = v_override;
         pa.out = out_override;
@@ -317,6 +321,7 @@ static void enqueue_p2(const Batch &B, const eptv_params *p, const float *v_over
         pa.n_trials = n_trials_of(p);
         pa.bar_extra = B.p2_bar_extra;
         pa.wait_cycles = B.p2_wait_cycles;
+        pa.fold = fold ? 1 : 0;
         launch_p2(B, B.p2, pa, st);   // a failure surfaces in the caller's launch check / capture
         return;
     }
@@ -334,8 +339,9 @@ static void enqueue_p2(const Batch &B, const eptv_params *p, const float *v_over
 }
 
 static void enqueue_outer(const Batch &B, const eptv_params *p, cudaStream_t st) {
-    enqueue_cgls(B, p->cgls_iters, true, st);
-    enqueue_p2(B, p, nullptr, nullptr, st);
+    const bool fold = p->cgls_iters > 0 && p2_persistent(B, p);
+    enqueue_cgls(B, p->cgls_iters, true, st, fold);
+    enqueue_p2(B, p, nullptr, nullptr, st, fold);
 }
 
 // Capture one outer iteration of batch B into a graph (cached per structural key).

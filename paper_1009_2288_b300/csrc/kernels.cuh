@@ -159,6 +159,7 @@ struct P2Args {
     int n_gd, n_trials;
     int bar_extra;                // blocks the barrier waits for beyond the grid (tests: > 0)
     long long wait_cycles;        // bound of one barrier wait in SM cycles
+    int fold;                     // v = u + a s: the CGLS's last update (u += a s), applied on load
 };
 
 int p2_plan(Batch &B, int n_trials, int n_gd, P2Plan *plan);

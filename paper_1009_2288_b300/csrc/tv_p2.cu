@@ -228,12 +228,19 @@ k4p_descent(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__re
         s_seen[1] = 0;
     }
 
+    // v at pixel p; pa.fold: the CGLS left its last update u += a s to this kernel (the
+    // arithmetic of k3_update_us, so v is bit for bit the u that update would store)
+    const float fold_a = pa.fold ? (float)S.sc[SC_A] : 0.0f;
+    auto v_at = [&](int p) -> float {
+        const float x = __ldcg(vv + p);
+        return pa.fold ? fmaf(fold_a, __ldcg(S.s + p), x) : x;
+    };
     // f = v on the region + 2 (0 outside the image), g = 0, the prior map (edge-replicated)
     for (int idx = tid; idx < FH * FW; idx += NT) {
         const int r = idx / FW, c = idx - r * FW;
         const int i = RX0 - 2 + c, j = RY0 - 2 + r;
         float fv = 0.0f;
-        if (i >= 0 && i < nx && j >= 0 && j < ny) fv = __ldcg(vv + (j * nx + i));
+        if (i >= 0 && i < nx && j >= 0 && j < ny) fv = v_at(j * nx + i);
         F[idx] = fv;
         G[idx] = 0.0f;
         if (mode == EPTV_WEIGHTS_PRIOR) {
@@ -247,7 +254,7 @@ k4p_descent(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__re
         const int r = idx / VW, c = idx - r * VW;
         const int i = RX0 - 1 + c, j = RY0 - 1 + r;
         float vx = 0.0f;
-        if (i >= 0 && i < nx && j >= 0 && j < ny) vx = __ldcg(vv + (j * nx + i));
+        if (i >= 0 && i < nx && j >= 0 && j < ny) vx = v_at(j * nx + i);
         V[idx] = vx;
     }
     // the slice's first accumulator set is used first after the sigma barriers

@@ -85,9 +85,10 @@ def test_persistent_equals_per_iteration_benchmark_workload():
     geo = E.Geometry(g)
     E.eptv_autotune(geo)
     ra, rb = _assert_same(geo, g, t32(c.y).reshape(-1), I.EptvParams(n_outer=3))
-    # per outer iteration: 3 sigma, n_gd GD and 1 clamp launches became the one persistent launch
-    assert rb.n_launches - ra.n_launches == 3 * 13
-    assert ra.n_launches == 3 * 13 + 6                # K1 x 4, K2 x 3, K3 x 5, K4p; 6 per call
+    # per outer iteration: 3 sigma, n_gd GD and 1 clamp launches became the one persistent
+    # launch, which also applies the CGLS's last u += a s as it loads v
+    assert rb.n_launches - ra.n_launches == 3 * 14
+    assert ra.n_launches == 3 * 12 + 6                # K1 x 4, K2 x 3, K3 x 4, K4p; 6 per call
 
 
 def test_persistent_tv_step_with_weights(c1_case):

@@ -428,7 +428,8 @@ int eptv_debug_set_p2_wait(eptv_geometry *g, int extra_blocks, long long wait_cy
 int eptv_autotune(eptv_geometry *g, int *k1_seg, int *k2_vg);
 
 /* The same for the batch {geoms[0..n)} used by eptv_reconstruct_batched (the choice is
- * kept with that batch, cached in geoms[0]). */
+ * kept with that batch, cached in geoms[0], also when the members change operator mode
+ * together). */
 int eptv_autotune_batched(int n, eptv_geometry *const *geoms, int *k1_seg, int *k2_vg);
 
 /* ---------------------------------------------------------------------------------

@@ -429,6 +429,9 @@ static int acquire_batch(int n, eptv_geometry *const *geoms, BatchCache &bc) {
     for (int i = 1; i < n; ++i)
         if (modes[i] != modes[0]) return fail(EPTV_ERR_ARG, "batch members use different operators");
     if (bc.members == members && bc.modes == modes) return 0;
+    // the same members in another operator mode keep the launch shapes tuned for them
+    const bool same = bc.members == members;
+    const int k1 = bc.B.k1_seg, k2 = bc.B.k2_vg;
     bc.reset();
     std::vector<SliceDev> sds;
     for (int i = 0; i < n; ++i) sds.push_back(geoms[i]->sd);
@@ -441,6 +444,10 @@ static int acquire_batch(int n, eptv_geometry *const *geoms, BatchCache &bc) {
     bc.B.stored = modes[0] == EPTV_OPERATOR_STORED;
     bc.B.stored_pt = modes[0] == EPTV_OPERATOR_STORED_PT;
     bc.B.bp_eq11 = modes[0] == EPTV_OPERATOR_EQ11;
+    if (same) {
+        bc.B.k1_seg = k1;
+        bc.B.k2_vg = k2;
+    }
     bc.members = members;
     bc.modes = modes;
     return 0;

@@ -14,15 +14,18 @@
 //   phase 3  g = lambda (f - v) + dJ/df on the region + 1 (Eqs. 9, A2); the owned values go
 //            to an exchange image;
 //   phase 4  per tile (tile_sums, the per-thread assignment K4 uses): the fidelity sums
-//            <g, f-v>, |g|^2, |f-v|^2 and, for every trial step, the energy change of the
-//            owned half-edges with the weights frozen; each warp adds its FP32 sums exactly
-//            (integer fixed point) into the block's accumulators, and the block's words go
-//            into the slice's accumulators (one set per GD iteration, three in rotation);
+//            <g, f-v>, |g|^2, |f-v|^2 and, for the first three trial steps, the energy
+//            change of the owned half-edges with the weights frozen; each warp adds its FP32
+//            sums exactly (integer fixed point) into the block's accumulators, and the
+//            block's words go into the slice's accumulators (one set per barrier, three in
+//            rotation);
 //   barrier  one grid-wide arrival / wait (bounded), polled by one warp; meanwhile
 //            warp 1 prepares the next iteration's trial steps for every possible outcome;
 //   decide   every block reads the exact totals and takes the same FP64 Armijo decision
-//            (the first passing trial); the slice's first block keeps the record and
-//            writes it to the slice's scalars and log once, at the end;
+//            (the first passing trial); when none of the three passes, the remaining
+//            trials are summed the same way behind one more barrier and the decision is
+//            taken over all of them; the slice's first block keeps the record and writes
+//            it to the slice's scalars and log once, at the end;
 //   apply    f <- f - t g on the region + 2, the ring 2 of g read from the neighbours'
 //            exchange values of this iteration.
 // After the last iteration the owned pixels get f = max(f, 0) (step 3) and go to u and u^T.
@@ -87,6 +90,15 @@ __device__ __forceinline__ bool p2_wait(const unsigned int *bar, unsigned int ta
 // atomics of 128 blocks on one copy cost less than the longer read-out of more copies
 // (per GD iteration at 512^2: 4 copies 13.0 us, 2 copies 12.6, 1 copy 12.1).
 constexpr int kP2Copies = 1;
+
+// Armijo trials evaluated before a GD iteration's grid barrier (at most the run's
+// max_trials).  The others are evaluated behind one more barrier, and only when none of
+// these passes.  A trial's exact total does not depend on which evaluation produced it,
+// so the decision is bit for bit that of one evaluation of every trial.  With
+// t0 = min(2 t_prev, t_max) the accepted trial is nearly always one of the first three
+// (the first 12 outer iterations at 512^2, 40 views x 888 bins: 22 % the first, 52 % the
+// second, 25 % the third, none later).
+constexpr int kP2FirstTrials = 3;
 
 // One pass of the selection scan, run by every block on the slice's histogram gh (NB
 // bins): the bin holding the remaining rank (1-based) and the rank within it, to *s_bin and
@@ -183,6 +195,8 @@ k4p_descent(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__re
     // +1.8 us per GD iteration at 512^2), their loads queue on the counter's line.
     constexpr int kPollers = 1;
     __shared__ unsigned long long sacc[NV * kAccStride];   // the block's exact sums
+    __shared__ double s_tot2[NV];                          // totals of a second trial evaluation
+    __shared__ int s_more;                                 // the iteration evaluates more trials
     // candidate trial steps of the next iteration ((K + 1) K <= 32: K <= 4)
     constexpr bool kCand = (KT + 1) * KT <= 32;
     __shared__ float cand_f[kCand ? (KT + 1) * KT : 1];
@@ -216,8 +230,8 @@ k4p_descent(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__re
                                                                       : EPTV_WEIGHTS_EPTV;
     }
     const int k_outer = (int)S.sc[SC_OUTER];
-    // barrier b of this launch (0, 1, 2: sigma passes; 3 + it: GD iteration it) completes
-    // when the counter reaches base + (b + 1) per_bar
+    // barrier b of this launch (0, 1, 2: the sigma passes; then one or two per GD
+    // iteration) completes when the counter reaches base + (b + 1) per_bar
     const unsigned int base = ld_acquire_gpu(S.p2bar + 1);
     const unsigned int per_bar = gridDim.x + (unsigned int)pa.bar_extra;
     const int nblk = __ldg(map.start + si + 1) - __ldg(map.start + si);
@@ -349,13 +363,78 @@ k4p_descent(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__re
     const int grp = tid >> 7, vt = tid & 127;
     constexpr int kRing = 2 * FW + 2 * (FH - 2);
     static_assert(kRing <= NT, "one ring position per thread");
-    for (int it = 0; it < pa.n_gd; ++it) {
-        for (int w = tid; w < NV * kAccStride; w += NT) sacc[w] = 0ull;
-        // the accumulator set of the next iteration: last read after barrier it - 2
+    // GD-phase barriers passed so far: barrier number 3 + ab, accumulator set ab mod kP2Sets
+    // (a second evaluation of trials adds a barrier; every block takes the same decisions,
+    // so every block counts the same barriers)
+    int ab = 0;
+    const int K1 = min(K, kP2FirstTrials);
+    // the slice's next accumulator set, zeroed in the phase before the barrier that
+    // precedes its use (its last use was read by every block before that barrier's
+    // predecessor)
+    auto zero_next_set = [&]() {
         if (local == 0) {
-            unsigned long long *nxt = acc_slice + (size_t)((it + 1) % kP2Sets) * kP2SetWords;
+            unsigned long long *nxt = acc_slice + (size_t)((ab + 1) % kP2Sets) * kP2SetWords;
             for (int w = tid; w < NV * kAccCopies * kAccStride; w += NT) nxt[w] = 0ull;
         }
+    };
+    // phase 4 for the trials m0 .. m0 + nk - 1: the tiles' sums (tile_sums, the per-thread
+    // assignment K4 uses), group grp (128 threads) takes TILES / NG tiles; every warp adds
+    // its FP32 sums exactly into the block's accumulators (no barrier between the warps),
+    // and the block's words go to the accumulator set ab.  2 x 4 regions: group grp takes
+    // tile (row grp, column grp & 1) and (row grp + 2 mod 4, the other column), so that in
+    // a region on the image's right or lower border (whose border tiles give one warp of
+    // the tile an extra round) every group has at most one border tile.  fid: the fidelity
+    // and energy sums are wanted (the first evaluation of the iteration).
+    auto tile_phase = [&](int m0, int nk, bool fid, float *wout) {
+        for (int k = 0; k < Sh::TILES / NG; ++k) {
+            const int q = (RTX == 2 && RTY == 4) ? ((k == 0 ? grp : ((grp + 2) & 3)) * RTX + ((grp & 1) ^ k))
+                                                 : grp + k * NG;
+            const int ox = (q % RTX) * kTileW, oy = (q / RTX) * kGdTileRows;
+            const int X0 = RX0 + ox, Y0 = RY0 + oy;
+            float vals[NV];
+#pragma unroll
+            for (int k = 0; k < NV; ++k) vals[k] = 0.0f;
+            if (X0 < nx && Y0 < ny) {
+                float dJ[KT];
+#pragma unroll
+                for (int m = 0; m < KT; ++m) dJ[m] = 0.0f;
+                tile_sums<KT>(vt, X0, Y0, nx, ny, F + oy * FW + ox, FW, G + (oy + 1) * FW + ox + 1, FW,
+                              V + oy * VW + ox, VW, TX + oy * QXW + ox, WX + oy * QXW + ox, QXW,
+                              TY + oy * QYW + ox, WY + oy * QYW + ox, QYW, nk, s_t + m0, eps2, wout,
+                              &vals[0], &vals[1], &vals[2], &vals[3], dJ);
+                if (!fid) vals[0] = vals[1] = vals[2] = vals[3] = 0.0f;
+#pragma unroll
+                for (int m = 0; m < KT; ++m) vals[4 + m] = dJ[m];
+            }
+            warp_acc<NV>(vals, sacc);
+        }
+        __syncthreads();
+        acc_push<NV, NT>(sacc, acc_slice + (size_t)(ab % kP2Sets) * kP2SetWords, blockIdx.x % kP2Copies);
+    };
+    // the final decision r of GD iteration it (warp 0, lane 0 stores)
+    auto take_decision = [&](const GdDecision &r, int it) {
+        if (tid == 0) {
+            s_misc[1] = r.t_step;
+            s_misc[0] = r.t_prev;
+            if (local == 0) {          // the slice's record, written to its scalars at the end
+                if (it == 0) rec.e_first = r.e0;
+                rec.t_step = r.t_step;
+                rec.e_last = r.e_last;
+                rec.t_prev = r.t_prev;
+                rec.nacc += r.accepted;
+                rec.nfail += 1 - r.accepted;
+                rec.bad |= r.bad;
+                if (S.log && k_outer >= 0 && k_outer < S.log_outer && it < S.log_gd)
+                    S.log[(size_t)k_outer * S.log_gd + it] = r.t_step;
+            }
+            if (!(kCand && K > 1) && K > 0 && P->step_rule != EPTV_STEP_FIXED)
+                trial_steps(P, r.t_prev, K, s_t, s_td);      // for the next iteration
+            s_misc[2] = (double)r.index;
+        }
+    };
+    for (int it = 0; it < pa.n_gd; ++it) {
+        for (int w = tid; w < NV * kAccStride; w += NT) sacc[w] = 0ull;
+        zero_next_set();
 
         // phase 2: half-edges around the g region (x-edge (a, b) and y-edge (a, b) of one
         // position share four of their six f values)
@@ -398,37 +477,9 @@ k4p_descent(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__re
         }
         __syncthreads();
 
-        // phase 4: the tiles' sums (tile_sums: the per-thread assignment K4 uses), group grp
-        // (128 threads) takes TILES / NG tiles; every warp adds its FP32 sums exactly into the
-        // block's accumulators (no barrier between the warps).  2 x 4 regions: group grp takes
-        // tile (row grp, column grp & 1) and (row grp + 2 mod 4, the other column), so that
-        // in a region on the image's right or lower border (whose border tiles give one warp
-        // of the tile an extra round) every group has at most one border tile.
-        float *wout = (it == pa.n_gd - 1) ? S.wout : nullptr;
-        unsigned long long *set = acc_slice + (size_t)(it % kP2Sets) * kP2SetWords;
-        for (int k = 0; k < Sh::TILES / NG; ++k) {
-            const int q = (RTX == 2 && RTY == 4) ? ((k == 0 ? grp : ((grp + 2) & 3)) * RTX + ((grp & 1) ^ k))
-                                                 : grp + k * NG;
-            const int ox = (q % RTX) * kTileW, oy = (q / RTX) * kGdTileRows;
-            const int X0 = RX0 + ox, Y0 = RY0 + oy;
-            float vals[NV];
-#pragma unroll
-            for (int k = 0; k < NV; ++k) vals[k] = 0.0f;
-            if (X0 < nx && Y0 < ny) {
-                float dJ[KT];
-#pragma unroll
-                for (int m = 0; m < KT; ++m) dJ[m] = 0.0f;
-                tile_sums<KT>(vt, X0, Y0, nx, ny, F + oy * FW + ox, FW, G + (oy + 1) * FW + ox + 1, FW,
-                              V + oy * VW + ox, VW, TX + oy * QXW + ox, WX + oy * QXW + ox, QXW,
-                              TY + oy * QYW + ox, WY + oy * QYW + ox, QYW, K, s_t, eps2, wout,
-                              &vals[0], &vals[1], &vals[2], &vals[3], dJ);
-#pragma unroll
-                for (int m = 0; m < KT; ++m) vals[4 + m] = dJ[m];
-            }
-            warp_acc<NV>(vals, sacc);
-        }
-        __syncthreads();
-        acc_push<NV, NT>(sacc, set, blockIdx.x % kP2Copies);
+        // phase 4: the fidelity and energy sums and the first K1 trials
+        tile_phase(0, K1, true, (it == pa.n_gd - 1) ? S.wout : nullptr);
+        unsigned long long *set = acc_slice + (size_t)(ab % kP2Sets) * kP2SetWords;
 
         // grid barrier: every block's accumulations and exchange values are visible after it
         __syncthreads();
@@ -452,7 +503,7 @@ k4p_descent(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__re
         }
         // lane 0 of the kPollers polling warps; the first to see every arrival tells the
         // others through s_seen
-        const int bnum = 3 + it;
+        const int bnum = 3 + ab;
         if ((tid & 31) == 0 && (tid >> 5) < kPollers) {
             const unsigned int need = base + (unsigned int)(bnum + 1) * per_bar;
             if (!p2_wait(S.p2bar, need, pa.wait_cycles, &s_seen[bnum & 1])) s_abort = 1;
@@ -464,6 +515,7 @@ k4p_descent(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__re
             if (tid == 0) S.sc[SC_TIMEOUT] = 1.0;
             return;
         }
+        ++ab;
         if (it == 0)      // every block has read the sigma histograms: zero them for the next launch
             for (int w = local * NT + tid; w < kP2HistWords; w += nblk * NT) S.p2hist[w] = 0u;
 
@@ -483,34 +535,46 @@ k4p_descent(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__re
         // the exact totals of this iteration (read, not cleared: every block reads them)
         acc_read<NV, NT, false, kP2Copies>(set, tot);
         __syncthreads();
+        // the decision over the first K1 trials; it is final unless none of them passes
+        // and trials are left
         if (tid < 32) {
-            const GdDecision r = gd_decide(tot, s_td, K, P, s_misc[0]);
-            if (tid == 0) {
-                s_misc[1] = r.t_step;
-                s_misc[0] = r.t_prev;
-                if (local == 0) {          // the slice's record, written to its scalars at the end
-                    if (it == 0) rec.e_first = r.e0;
-                    rec.t_step = r.t_step;
-                    rec.e_last = r.e_last;
-                    rec.t_prev = r.t_prev;
-                    rec.nacc += r.accepted;
-                    rec.nfail += 1 - r.accepted;
-                    rec.bad |= r.bad;
-                    if (S.log && k_outer >= 0 && k_outer < S.log_outer && it < S.log_gd)
-                        S.log[(size_t)k_outer * S.log_gd + it] = r.t_step;
-                }
-                if (!(kCand && K > 1) && K > 0 && P->step_rule != EPTV_STEP_FIXED)
-                    trial_steps(P, r.t_prev, K, s_t, s_td);      // for the next iteration
-                s_misc[2] = (double)r.index;
-            }
+            const GdDecision r = gd_decide(tot, s_td, K1, P, s_misc[0]);
+            const bool more = P->step_rule != EPTV_STEP_FIXED && !r.accepted && K1 < K;
+            if (tid == 0) s_more = more;
+            if (!more) take_decision(r, it);
         }
         __syncthreads();
+        // ring 2 is not read by the tile sums (they use g on the region + 1 only)
+        if (ring_at >= 0) G[ring_at] = ring_g;
+        if (s_more) {
+            // the trials K1 .. K - 1 (f, g and the edge terms are unchanged), behind one
+            // more barrier
+            for (int w = tid; w < NV * kAccStride; w += NT) sacc[w] = 0ull;
+            zero_next_set();
+            __syncthreads();
+            tile_phase(K1, K - K1, false, nullptr);
+            unsigned long long *set2 = acc_slice + (size_t)(ab % kP2Sets) * kP2SetWords;
+            if (!grid_sync(3 + ab)) {
+                if (tid == 0) S.sc[SC_TIMEOUT] = 1.0;
+                return;
+            }
+            ++ab;
+            acc_read<NV, NT, false, kP2Copies>(set2, s_tot2);
+            __syncthreads();
+            if (tid < 32) {
+                // the totals of all K trials, then the decision one evaluation of every
+                // trial takes
+                if (tid < K - K1) tot[4 + K1 + tid] = s_tot2[4 + tid];
+                __syncwarp();
+                take_decision(gd_decide(tot, s_td, K, P, s_misc[0]), it);
+            }
+            __syncthreads();
+        }
         if (kCand && K > 1 && tid < K && P->step_rule != EPTV_STEP_FIXED) {
             const int c = (int)s_misc[2];
             s_t[tid] = cand_f[c * K + tid];
             s_td[tid] = cand_d[c * K + tid];
         }
-        if (ring_at >= 0) G[ring_at] = ring_g;
         __syncthreads();
         const float tap = (float)s_misc[1];
         if (tap != 0.0f) {
@@ -538,7 +602,7 @@ k4p_descent(const SliceDev *__restrict__ sls, TileMap map, const ParamsDev *__re
         }
     }
     if (blockIdx.x == 0 && tid == 0)       // every block has passed the last barrier
-        S.p2bar[1] = base + (unsigned int)(3 + pa.n_gd) * per_bar;
+        S.p2bar[1] = base + (unsigned int)(3 + ab) * per_bar;
     if (local == 0 && tid == 0) {
         double *sc = S.sc;
         sc[SC_E_FIRST] = rec.e_first;

@@ -154,3 +154,38 @@ def test_persistent_equals_per_iteration_over_many_launches(c1_case):
     g = c1_case.geom
     geo = E.Geometry(g)
     _assert_same(geo, g, t32(c1_case.y).reshape(-1), I.EptvParams(n_outer=30))
+
+
+def _accepted_indices(steps, p):
+    """The accepted trial of every GD iteration (max_trials for a failed search) from the
+    step log: t0 = min(grow t_prev, t_max), the accepted step t0 shrink^m."""
+    t_prev, out = p.t_init_eff, []
+    for s in np.asarray(steps, dtype=np.float64).reshape(-1):
+        t0 = min(p.armijo_grow * t_prev, p.t_max_eff)
+        if s == 0.0:
+            out.append(p.max_trials)
+            t_prev = t0 * p.armijo_shrink ** (p.max_trials - 1) * p.armijo_shrink / p.armijo_grow
+        else:
+            out.append(int(round(np.log(t0 / s) / np.log(1.0 / p.armijo_shrink))))
+            t_prev = s
+    return np.array(out)
+
+
+@pytest.mark.parametrize("kw", [dict(armijo_grow=8.0), dict(armijo_grow=8.0, max_trials=8),
+                                dict(armijo_c=0.9), dict(max_trials=3)])
+def test_persistent_second_trial_evaluation(c1_case, kw):
+    """The persistent kernel evaluates the first three Armijo trials before a GD
+    iteration's barrier and the others behind one more barrier, only when none of the
+    three passes.  A growth factor of 8 (or c = 0.9) makes that frequent, failed searches
+    included; images, logs and scalars must still equal one evaluation of every trial, over
+    6 launches whose barrier counts differ."""
+    g = c1_case.geom
+    geo = E.Geometry(g)
+    p = I.EptvParams(n_outer=6, **kw)
+    ra, _ = _assert_same(geo, g, t32(c1_case.y).reshape(-1), p)
+    steps, _ = E.eptv_get_log(geo)
+    idx = _accepted_indices(steps, p)
+    assert np.all((idx >= 0) & (idx <= p.max_trials))
+    assert ra.n_fail == int(np.sum(idx == p.max_trials))
+    if p.max_trials > 3:
+        assert np.any(idx >= 3)            # some iteration needed the second evaluation

@@ -398,102 +398,118 @@ k3v_update_us(float *__restrict__ u, float *__restrict__ s, const float *__restr
 
 // ------------------------------------------------------------------ (P2) in 3-D
 
-// Face numbering: x-faces (nx+1) ny nz, then y-faces nx (ny+1) nz, then z-faces
-// nx ny (nz+1), each x fastest.  Face of family d at (i, j, k) lies between voxel
-// (i, j, k) - e_d ("a") and (i, j, k) ("b").
+// Faces: family d (0: x, 1: y, 2: z) at (i, j, k) lies between voxel (i, j, k) - e_d ("a")
+// and (i, j, k) ("b"); x-faces (nx+1) ny nz, y-faces nx (ny+1) nz, z-faces nx ny (nz+1).
+// Voxel p = (i, j, k) owns the lower face of each family (a = p - e_d, b = p) and, on the
+// volume's last plane of that family, the upper one (a = p, b = p + e_d): every face has
+// one owner.  A face's stencil (Eq. A3 extended to 3-D: its two voxels and their four
+// neighbours along each transverse axis) stays inside the 3 x 3 x 3 neighbourhood of
+// either voxel beside it -- the centre, its 6 face and 12 edge neighbours -- so the
+// kernels below take one voxel per thread, load those 19 values once (0 outside the
+// volume) and evaluate all six faces from registers.
 struct Vol {
     int nx, ny, nz;
     long long nfx, nfy, nfz, nf;
 };
 
-__device__ __forceinline__ float vol_at(const float *f, const Vol &V, int i, int j, int k) {
-    if (i < 0 || j < 0 || k < 0 || i >= V.nx || j >= V.ny || k >= V.nz) return 0.0f;
-    return __ldg(f + ((long long)k * V.ny + j) * V.nx + i);
-}
-
-// decode face index -> family d, position (i, j, k); 32-bit arithmetic (the handle
-// guarantees fewer than 2^31 faces), two integer divisions
-__device__ __forceinline__ int face_pos(const Vol &V, long long e64, int &i, int &j, int &k) {
-    const int e = (int)e64, nfx = (int)V.nfx, nfy = (int)V.nfy;
-    int d, r, wx, wy;
-    if (e < nfx) { d = 0; r = e; wx = V.nx + 1; wy = V.ny; }
-    else if (e < nfx + nfy) { d = 1; r = e - nfx; wx = V.nx; wy = V.ny + 1; }
-    else { d = 2; r = e - nfx - nfy; wx = V.nx; wy = V.ny; }
-    const int q = r / wx;
-    i = r - q * wx;
-    k = q / wy;
-    j = q - k * wy;
-    return d;
-}
-
-// Voxel value of x at (i, j, k): bounds-checked (0 outside the volume), or, for a face
-// whose whole stencil lies inside the volume, a plain load at linear index lin.
-template <bool CHECK>
-__device__ __forceinline__ float ld_vox(const float *x, const Vol &V, int i, int j, int k, int lin) {
-    if (CHECK) return vol_at(x, V, i, j, k);
-    return __ldg(x + lin);
-}
-
-// D, and the transverse parts of T^2 (A3 extended) of a face, from image x; also the
-// bilinear quantities of the Armijo decomposition when a second image g is given:
-// a = D dD + 1/2 sum c dc, b = dD^2 + 1/2 sum dc^2.  CHECK = false: the face and its
-// transverse neighbours are inside the volume (the same values and operations, without
-// the bounds tests).
-template <bool CHECK>
-__device__ __forceinline__ void face_terms_t(const float *x, const float *gx, const Vol &V, int d, int i, int j,
-                                             int k, float eps2, float &D, float &T2, float &ae, float &be) {
-    const int ai = i - (d == 0), aj = j - (d == 1), ak = k - (d == 2);
-    const int st[3] = {1, V.nx, V.nx * V.ny};
-    int lb = 0, la = 0;
-    if (!CHECK) {
-        lb = (k * V.ny + j) * V.nx + i;
-        la = lb - st[d];
-    }
-    const float xa = ld_vox<CHECK>(x, V, ai, aj, ak, la), xb = ld_vox<CHECK>(x, V, i, j, k, lb);
-    D = xb - xa;
-    T2 = eps2 + D * D;
-    float ga = 0.f, gb = 0.f, dD = 0.f;
-    if (gx) { ga = ld_vox<CHECK>(gx, V, ai, aj, ak, la); gb = ld_vox<CHECK>(gx, V, i, j, k, lb); dD = gb - ga; }
-    ae = D * dD;
-    be = dD * dD;
-    const float mc = 0.5f * (xa + xb), gc = 0.5f * (ga + gb);
+// The 19 values of x around voxel (i, j, k) at linear index p (corners unused, 0):
+// N[dk + 1][dj + 1][di + 1].
+__device__ __forceinline__ void load_nbhd(const float *__restrict__ x, const Vol &V, int i, int j, int k,
+                                          long long p, float (&N)[3][3][3]) {
+    const bool inner = i >= 1 && i <= V.nx - 2 && j >= 1 && j <= V.ny - 2 && k >= 1 && k <= V.nz - 2;
+    const long long sy = V.nx, sz = (long long)V.nx * V.ny;
 #pragma unroll
-    for (int t = 0; t < 3; ++t) {
-        if (t == d) continue;
-        const int ei = (t == 0), ej = (t == 1), ek = (t == 2), s = st[t];
-        const float mp = 0.5f * (ld_vox<CHECK>(x, V, ai + ei, aj + ej, ak + ek, la + s) +
-                                 ld_vox<CHECK>(x, V, i + ei, j + ej, k + ek, lb + s));
-        const float mm = 0.5f * (ld_vox<CHECK>(x, V, ai - ei, aj - ej, ak - ek, la - s) +
-                                 ld_vox<CHECK>(x, V, i - ei, j - ej, k - ek, lb - s));
-        const float cp = mp - mc, cm = mc - mm;
-        T2 += 0.5f * cp * cp + 0.5f * cm * cm;
-        if (gx) {
-            const float gp = 0.5f * (ld_vox<CHECK>(gx, V, ai + ei, aj + ej, ak + ek, la + s) +
-                                     ld_vox<CHECK>(gx, V, i + ei, j + ej, k + ek, lb + s));
-            const float gm = 0.5f * (ld_vox<CHECK>(gx, V, ai - ei, aj - ej, ak - ek, la - s) +
-                                     ld_vox<CHECK>(gx, V, i - ei, j - ej, k - ek, lb - s));
-            const float dcp = gp - gc, dcm = gc - gm;
-            ae += 0.5f * (cp * dcp + cm * dcm);
-            be += 0.5f * (dcp * dcp + dcm * dcm);
-        }
-    }
+    for (int dk = -1; dk <= 1; ++dk)
+#pragma unroll
+        for (int dj = -1; dj <= 1; ++dj)
+#pragma unroll
+            for (int di = -1; di <= 1; ++di) {
+                float val = 0.0f;
+                if (abs(di) + abs(dj) + abs(dk) <= 2) {
+                    const bool in = inner || (i + di >= 0 && i + di < V.nx && j + dj >= 0 && j + dj < V.ny &&
+                                              k + dk >= 0 && k + dk < V.nz);
+                    if (in) val = __ldg(x + p + di + dj * sy + dk * sz);
+                }
+                N[dk + 1][dj + 1][di + 1] = val;
+            }
 }
 
-__device__ __forceinline__ void face_terms(const float *x, const float *gx, const Vol &V, int d, int i, int j,
-                                           int k, float eps2, float &D, float &T2, float &ae, float &be) {
-    // interior: both voxels of the face inside, and one more voxel on each transverse side
-    const int c[3] = {i, j, k}, n[3] = {V.nx, V.ny, V.nz};
-    bool inner = true;
+// The stencil of face (family D, UP: the upper face of the centre voxel, else the lower)
+// in the neighbourhood N: a, b and, for the transverse axes t1 < t2, a +- e_t, b +- e_t.
+template <int D, int UP>
+struct FaceAt {
+    static constexpr int ax = (D == 0 && !UP) ? -1 : 0, ay = (D == 1 && !UP) ? -1 : 0,
+                         az = (D == 2 && !UP) ? -1 : 0;
+    static constexpr int bx = ax + (D == 0), by = ay + (D == 1), bz = az + (D == 2);
+    static constexpr int T1 = (D == 0) ? 1 : 0, T2 = (D == 2) ? 1 : 2;
+    __device__ static __forceinline__ float at(const float (&N)[3][3][3], int x, int y, int z) {
+        return N[z + 1][y + 1][x + 1];
+    }
+    // values: [0] a, [1] b, [2] a + e_t1, [3] b + e_t1, [4] a - e_t1, [5] b - e_t1, then t2
+    __device__ static __forceinline__ void values(const float (&N)[3][3][3], float (&s)[10]) {
+        constexpr int u1x = T1 == 0, u1y = T1 == 1, u1z = T1 == 2;
+        constexpr int u2x = T2 == 0, u2y = T2 == 1, u2z = T2 == 2;
+        s[0] = at(N, ax, ay, az);
+        s[1] = at(N, bx, by, bz);
+        s[2] = at(N, ax + u1x, ay + u1y, az + u1z);
+        s[3] = at(N, bx + u1x, by + u1y, bz + u1z);
+        s[4] = at(N, ax - u1x, ay - u1y, az - u1z);
+        s[5] = at(N, bx - u1x, by - u1y, bz - u1z);
+        s[6] = at(N, ax + u2x, ay + u2y, az + u2z);
+        s[7] = at(N, bx + u2x, by + u2y, bz + u2z);
+        s[8] = at(N, ax - u2x, ay - u2y, az - u2z);
+        s[9] = at(N, bx - u2x, by - u2y, bz - u2z);
+    }
+};
+
+// D = b - a and T^2 = eps^2 + D^2 + sum over t1, t2 of (cp^2 + cm^2) / 2 (Eq. A3 in 3-D:
+// mc = (a + b) / 2, cp = (a + e_t + b + e_t) / 2 - mc, cm = mc - (a - e_t + b - e_t) / 2)
+// from the stencil s of FaceAt::values.  Explicitly rounded operations: the two voxels
+// beside a face evaluate it to the same bits.
+__device__ __forceinline__ float face_T2(float eps2, const float (&s)[10], float *D) {
+    const float d = __fsub_rn(s[1], s[0]);
+    const float mc = __fmul_rn(0.5f, __fadd_rn(s[0], s[1]));
+    float t2 = __fmaf_rn(d, d, eps2);
 #pragma unroll
-    for (int t = 0; t < 3; ++t)
-        inner = inner && c[t] >= 1 && c[t] <= n[t] - (t == d ? 1 : 2);
-    if (inner) face_terms_t<false>(x, gx, V, d, i, j, k, eps2, D, T2, ae, be);
-    else face_terms_t<true>(x, gx, V, d, i, j, k, eps2, D, T2, ae, be);
+    for (int t = 0; t < 2; ++t) {
+        const float cp = __fsub_rn(__fmul_rn(0.5f, __fadd_rn(s[2 + 4 * t], s[3 + 4 * t])), mc);
+        const float cm = __fsub_rn(mc, __fmul_rn(0.5f, __fadd_rn(s[4 + 4 * t], s[5 + 4 * t])));
+        t2 = __fadd_rn(t2, __fadd_rn(__fmul_rn(0.5f, __fmul_rn(cp, cp)), __fmul_rn(0.5f, __fmul_rn(cm, cm))));
+    }
+    *D = d;
+    return t2;
+}
+
+// The Armijo decomposition of one face along -t g (weights frozen):
+// T'^2 = T^2 - 2 t a + t^2 b, a = D dD + 1/2 sum (cp dcp + cm dcm), b = dD^2 + 1/2 sum
+// (dcp^2 + dcm^2), the d-quantities the same differences of g (stencils sf, sg).
+__device__ __forceinline__ void face_ab(const float (&sf)[10], const float (&sg)[10], float *ae, float *be) {
+    const float D = sf[1] - sf[0], dD = sg[1] - sg[0];
+    const float mc = 0.5f * (sf[0] + sf[1]), gc = 0.5f * (sg[0] + sg[1]);
+    float a = D * dD, b = dD * dD;
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        const float cp = 0.5f * (sf[2 + 4 * t] + sf[3 + 4 * t]) - mc, cm = mc - 0.5f * (sf[4 + 4 * t] + sf[5 + 4 * t]);
+        const float dcp = 0.5f * (sg[2 + 4 * t] + sg[3 + 4 * t]) - gc, dcm = gc - 0.5f * (sg[4 + 4 * t] + sg[5 + 4 * t]);
+        a += 0.5f * (cp * dcp + cm * dcm);
+        b += 0.5f * (dcp * dcp + dcm * dcm);
+    }
+    *ae = a;
+    *be = b;
+}
+
+// T, w (Eq. 5 with 1 / sigma^2 = inv_s2, or 1) and q = w D / T of a face from its D, T^2.
+__device__ __forceinline__ void face_Twq(int mode, float inv_s2, float D, float t2, float *T, float *w,
+                                         float *q) {
+    const float rs = rsqrtf(t2);                // t2 >= eps^2 > 0
+    *T = __fmul_rn(t2, rs);
+    *w = (mode == EPTV_WEIGHTS_ONE) ? 1.0f : __expf(__fmul_rn(-t2, inv_s2));
+    *q = __fmul_rn(__fmul_rn(*w, D), rs);
 }
 
 // compensated (Kahan) running sum of one thread's terms: the grid-stride kernels below
-// give each thread a few hundred faces, and the compensation keeps the thread's sum
-// within a few units in the last place, as a single FP32 term was before
+// give each thread tens of voxels, and the compensation keeps the thread's sum within a
+// few units in the last place, as a single FP32 term would be
 __device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
     const float y = x - c;
     const float t = s + y;
@@ -501,89 +517,223 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
     s = t;
 }
 
-// T of every face of x (for sigma)
+__device__ __forceinline__ void vox_pos(const Vol &V, long long p, int &i, int &j, int &k) {
+    const int pi = (int)p, q = pi / V.nx;          // n_vox < 2^31
+    i = pi - q * V.nx;
+    k = q / V.ny;
+    j = q - k * V.ny;
+}
+
+// T of every face of x (for sigma), one slot per face: the owner's lower faces at
+// 3 p + d, the upper faces of the last planes after them (x: ny nz, y: nx nz, z: nx ny)
 __global__ void __launch_bounds__(256)
 k3tv_face_T(Vol V, const float *__restrict__ x, float eps2, float *__restrict__ T)
 {
-    const long long e = (long long)blockIdx.x * 256 + threadIdx.x;
-    if (e >= V.nf) return;
+    const long long nvox = (long long)V.nx * V.ny * V.nz;
+    const long long p = (long long)blockIdx.x * 256 + threadIdx.x;
+    if (p >= nvox) return;
     int i, j, k;
-    const int d = face_pos(V, e, i, j, k);
-    float D, T2, ae, be;
-    face_terms(x, nullptr, V, d, i, j, k, eps2, D, T2, ae, be);
-    T[e] = T2 * rsqrtf(T2);
+    vox_pos(V, p, i, j, k);
+    float N[3][3][3];
+    load_nbhd(x, V, i, j, k, p, N);
+    float s[10], D, t2;
+    FaceAt<0, 0>::values(N, s); t2 = face_T2(eps2, s, &D); T[3 * p + 0] = __fmul_rn(t2, rsqrtf(t2));
+    FaceAt<1, 0>::values(N, s); t2 = face_T2(eps2, s, &D); T[3 * p + 1] = __fmul_rn(t2, rsqrtf(t2));
+    FaceAt<2, 0>::values(N, s); t2 = face_T2(eps2, s, &D); T[3 * p + 2] = __fmul_rn(t2, rsqrtf(t2));
+    const long long up0 = 3 * nvox, up1 = up0 + (long long)V.ny * V.nz, up2 = up1 + (long long)V.nx * V.nz;
+    if (i == V.nx - 1) {
+        FaceAt<0, 1>::values(N, s); t2 = face_T2(eps2, s, &D);
+        T[up0 + (long long)k * V.ny + j] = __fmul_rn(t2, rsqrtf(t2));
+    }
+    if (j == V.ny - 1) {
+        FaceAt<1, 1>::values(N, s); t2 = face_T2(eps2, s, &D);
+        T[up1 + (long long)k * V.nx + i] = __fmul_rn(t2, rsqrtf(t2));
+    }
+    if (k == V.nz - 1) {
+        FaceAt<2, 1>::values(N, s); t2 = face_T2(eps2, s, &D);
+        T[up2 + (long long)j * V.nx + i] = __fmul_rn(t2, rsqrtf(t2));
+    }
 }
 
-// per face: T, w (Eq. 5 with sigma = sc[SC_SIGMA], or 1), q = w D / T; sum of w T (J)
-__global__ void __launch_bounds__(256, 8)
-k3tv_faces(Vol V, const float *__restrict__ f, float eps2, int mode, float *__restrict__ Q,
-           float *__restrict__ TT, float *__restrict__ WW, double *__restrict__ partials, SliceDev *S)
+// The grad and trial kernels march in z: a work item is a column (i, j) and up to kZChunk
+// consecutive voxels of it, and the thread keeps the 19-value neighbourhood in registers
+// as it moves up -- the plane below and the centre plane shift down, and only the centre
+// plane's four in-plane diagonals and the cross of the new plane above are loaded: 9
+// loads per voxel instead of 19, and no index division per voxel.  Items run with x
+// fastest, so a warp's loads are consecutive in x.
+constexpr int kZChunk = 16;
+
+// In-plane neighbours of column (i, j) inside the volume.
+struct ColIn {
+    bool xm, xp, ym, yp;
+};
+
+// Values around column (i, j) of the plane starting at pl (null: a plane outside the
+// volume, all 0): the cross (P[dj + 1][di + 1] with |di| + |dj| <= 1) and the diagonals.
+__device__ __forceinline__ void plane_cross(const float *pl, int nx, const ColIn &m, float (&P)[3][3]) {
+    P[1][1] = pl ? __ldg(pl) : 0.0f;
+    P[1][0] = (pl && m.xm) ? __ldg(pl - 1) : 0.0f;
+    P[1][2] = (pl && m.xp) ? __ldg(pl + 1) : 0.0f;
+    P[0][1] = (pl && m.ym) ? __ldg(pl - nx) : 0.0f;
+    P[2][1] = (pl && m.yp) ? __ldg(pl + nx) : 0.0f;
+}
+__device__ __forceinline__ void plane_diag(const float *pl, int nx, const ColIn &m, float (&P)[3][3]) {
+    P[0][0] = (pl && m.ym && m.xm) ? __ldg(pl - nx - 1) : 0.0f;
+    P[0][2] = (pl && m.ym && m.xp) ? __ldg(pl - nx + 1) : 0.0f;
+    P[2][0] = (pl && m.yp && m.xm) ? __ldg(pl + nx - 1) : 0.0f;
+    P[2][2] = (pl && m.yp && m.xp) ? __ldg(pl + nx + 1) : 0.0f;
+}
+
+// Column (i, j) of plane k of x (null outside the volume).
+__device__ __forceinline__ const float *plane_ptr(const float *x, const Vol &V, int i, int j, int k) {
+    return (k >= 0 && k < V.nz) ? x + ((long long)k * V.ny + j) * V.nx + i : nullptr;
+}
+
+// The window N[dk + 1][dj + 1][di + 1] of x around (i, j, k0): the crosses of planes
+// k0 - 1 and k0 + 1 and all of plane k0.
+__device__ __forceinline__ void zwin_start(const float *x, const Vol &V, int i, int j, int k0, const ColIn &m,
+                                           float (&N)[3][3][3]) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) N[a][b][c] = 0.0f;
+    plane_cross(plane_ptr(x, V, i, j, k0 - 1), V.nx, m, N[0]);
+    const float *p0 = plane_ptr(x, V, i, j, k0);
+    plane_cross(p0, V.nx, m, N[1]);
+    plane_diag(p0, V.nx, m, N[1]);
+    plane_cross(plane_ptr(x, V, i, j, k0 + 1), V.nx, m, N[2]);
+}
+
+// The window moved from (i, j, k) to (i, j, k + 1).
+__device__ __forceinline__ void zwin_step(const float *x, const Vol &V, int i, int j, int k, const ColIn &m,
+                                          float (&N)[3][3][3]) {
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            N[0][b][c] = N[1][b][c];
+            N[1][b][c] = N[2][b][c];
+        }
+    plane_diag(plane_ptr(x, V, i, j, k + 1), V.nx, m, N[1]);
+    plane_cross(plane_ptr(x, V, i, j, k + 2), V.nx, m, N[2]);
+}
+
+// Work item -> column (i, j), first plane k0 and the in-plane masks (two divisions per item).
+__device__ __forceinline__ void zitem(const Vol &V, long long it, int &i, int &j, int &k0, ColIn &m) {
+    const long long r = it / V.nx;
+    i = (int)(it - r * V.nx);
+    const long long c = r / V.ny;
+    j = (int)(r - c * V.ny);
+    k0 = (int)c * kZChunk;
+    m.xm = i > 0;
+    m.xp = i < V.nx - 1;
+    m.ym = j > 0;
+    m.yp = j < V.ny - 1;
+}
+
+// One face of the centre voxel: q, and w T.
+template <int D, int UP>
+__device__ __forceinline__ float face_q(const float (&N)[3][3][3], int mode, float eps2, float inv_s2, float *wT) {
+    float s[10], Dv, T, w, q;
+    FaceAt<D, UP>::values(N, s);
+    const float t2 = face_T2(eps2, s, &Dv);
+    face_Twq(mode, inv_s2, Dv, t2, &T, &w, &q);
+    *wT = w * T;
+    return q;
+}
+
+// g = lambda (f - v) - div q (Eq. 9 with Eq. A2: q = w D / T of the voxel's six faces,
+// w with sigma = sc[SC_SIGMA]), and the sums J = sum w T over the faces (each by its
+// owner), A = g.(f - v), B = g.g, F = |f - v|^2 (to sc[SC_Q0 .. SC_Q0 + 3]).  Along the
+// column, a voxel's lower z-face is the upper one of the voxel below: evaluated once.
+__global__ void __launch_bounds__(256, 4)
+k3tv_grad(Vol V, const float *__restrict__ f, const float *__restrict__ v, float eps2, int mode, float lam,
+          float *__restrict__ g, double *__restrict__ partials, SliceDev *S)
 {
-    __shared__ double rsm[1 * 8];
-    __shared__ double res[1];
+    __shared__ double rsm[4 * 8];
+    __shared__ double res[4];
     __shared__ int last_flag;
     const float sig = (float)S->sc[SC_SIGMA];
     const float inv_s2 = 1.0f / (sig * sig);
-    float wt = 0.0f, wc = 0.0f;
-    // grid-stride: a few blocks per SM, so that the block reductions stay few
-    for (long long e = (long long)blockIdx.x * 256 + threadIdx.x; e < V.nf; e += (long long)gridDim.x * 256) {
-        int i, j, k;
-        const int d = face_pos(V, e, i, j, k);
-        float D, T2, ae, be;
-        face_terms(f, nullptr, V, d, i, j, k, eps2, D, T2, ae, be);
-        const float rs = rsqrtf(T2);
-        const float T = T2 * rs;
-        const float w = (mode == EPTV_WEIGHTS_ONE) ? 1.0f : __expf(-T2 * inv_s2);
-        Q[e] = w * D * rs;
-        TT[e] = T;
-        WW[e] = w;
-        kahan_add(wt, wc, w * T);
+    float J = 0.f, A = 0.f, B = 0.f, F = 0.f, cJ = 0.f, cA = 0.f, cB = 0.f, cF = 0.f;
+    const long long n_items = (long long)V.nx * V.ny * ((V.nz + kZChunk - 1) / kZChunk);
+    for (long long it = (long long)blockIdx.x * 256 + threadIdx.x; it < n_items; it += (long long)gridDim.x * 256) {
+        int i, j, k0;
+        ColIn m;
+        zitem(V, it, i, j, k0, m);
+        const int k1 = min(k0 + kZChunk, V.nz);
+        float N[3][3][3];
+        zwin_start(f, V, i, j, k0, m, N);
+        float wT, qz0 = face_q<2, 0>(N, mode, eps2, inv_s2, &wT);
+        float wTz0 = wT;
+        const long long plane = (long long)V.nx * V.ny;
+        long long p = (long long)k0 * plane + (long long)j * V.nx + i;
+        for (int k = k0; k < k1; ++k, p += plane) {
+            if (k > k0) zwin_step(f, V, i, j, k - 1, m, N);
+            float wa, wb;
+            const float qx0 = face_q<0, 0>(N, mode, eps2, inv_s2, &wa);
+            kahan_add(J, cJ, wa);
+            const float qx1 = face_q<0, 1>(N, mode, eps2, inv_s2, &wb);
+            if (i == V.nx - 1) kahan_add(J, cJ, wb);
+            const float qy0 = face_q<1, 0>(N, mode, eps2, inv_s2, &wa);
+            kahan_add(J, cJ, wa);
+            const float qy1 = face_q<1, 1>(N, mode, eps2, inv_s2, &wb);
+            if (j == V.ny - 1) kahan_add(J, cJ, wb);
+            kahan_add(J, cJ, wTz0);
+            const float qz1 = face_q<2, 1>(N, mode, eps2, inv_s2, &wb);
+            if (k == V.nz - 1) kahan_add(J, cJ, wb);
+            const float div = (qx1 - qx0) + (qy1 - qy0) + (qz1 - qz0);
+            const float d = N[1][1][1] - __ldg(v + p);
+            const float gv = lam * d - div;
+            g[p] = gv;
+            kahan_add(A, cA, gv * d);
+            kahan_add(B, cB, gv * gv);
+            kahan_add(F, cF, d * d);
+            qz0 = qz1;
+            wTz0 = wb;
+        }
     }
-    float vals[1] = {wt - wc};
-    block_sum_to<1, 256>(vals, partials + (size_t)blockIdx.x * kPartialStride, rsm);
-    if (!reduce_slice<1, 256>(*S, partials, kPartialStride, 0, gridDim.x, blockIdx.x, rsm, res, &last_flag)) return;
-    if (threadIdx.x == 0) S->sc[SC_Q0] = res[0];                   // J
+    float vals[4] = {J - cJ, A - cA, B - cB, F - cF};
+    block_sum_to<4, 256>(vals, partials + (size_t)blockIdx.x * kPartialStride, rsm);
+    if (!reduce_slice<4, 256>(*S, partials, kPartialStride, 0, gridDim.x, blockIdx.x, rsm, res, &last_flag)) return;
+    if (threadIdx.x < 4) S->sc[SC_Q0 + threadIdx.x] = res[threadIdx.x];      // J, A, B, F
 }
 
-// g = lambda (f - v) - div Q; sums A = g.(f - v), B = g.g, F = |f - v|^2
-__global__ void __launch_bounds__(256, 8)
-k3tv_grad(Vol V, const float *__restrict__ f, const float *__restrict__ v, const float *__restrict__ Q,
-          float lam, float *__restrict__ g, double *__restrict__ partials, SliceDev *S)
-{
-    __shared__ double rsm[3 * 8];
-    __shared__ double res[3];
-    __shared__ int last_flag;
-    float A = 0.f, B = 0.f, F = 0.f, cA = 0.f, cB = 0.f, cF = 0.f;
-    const long long nvox = (long long)V.nx * V.ny * V.nz;
-    for (long long p = (long long)blockIdx.x * 256 + threadIdx.x; p < nvox; p += (long long)gridDim.x * 256) {
-        const int pi = (int)p, q = pi / V.nx;          // n_vox < 2^31
-        const int i = pi - q * V.nx, k = q / V.ny, j = q - k * V.ny;
-        const float *Qx = Q, *Qy = Q + V.nfx, *Qz = Q + V.nfx + V.nfy;
-        const long long ex = ((long long)k * V.ny + j) * (V.nx + 1) + i;
-        const long long ey = ((long long)k * (V.ny + 1) + j) * V.nx + i;
-        const long long ez = ((long long)k * V.ny + j) * V.nx + i;
-        const float div = (__ldg(Qx + ex + 1) - __ldg(Qx + ex)) + (__ldg(Qy + ey + V.nx) - __ldg(Qy + ey)) +
-                          (__ldg(Qz + ez + (long long)V.nx * V.ny) - __ldg(Qz + ez));
-        const float d = __ldg(f + p) - __ldg(v + p);
-        const float gv = lam * d - div;
-        g[p] = gv;
-        kahan_add(A, cA, gv * d);
-        kahan_add(B, cB, gv * gv);
-        kahan_add(F, cF, d * d);
+// dJ_m += w (T'_m - T) of one owned face in the cancellation-free form
+// t (t b - 2 a) / (T' + T), T'^2 = T^2 + t (t b - 2 a), for the trial steps s_t[0 .. K).
+template <int KT, int D, int UP>
+__device__ __forceinline__ void trial_face(const float (&NF)[3][3][3], const float (&NG)[3][3][3], int mode,
+                                           float eps2, float inv_s2, int K, const float *s_t, float (&dJ)[KT],
+                                           float (&cJ)[KT]) {
+    float sf[10], sg[10], Dv, T, w, q, ae, be;
+    FaceAt<D, UP>::values(NF, sf);
+    FaceAt<D, UP>::values(NG, sg);
+    const float t2 = face_T2(eps2, sf, &Dv);
+    face_Twq(mode, inv_s2, Dv, t2, &T, &w, &q);
+    face_ab(sf, sg, &ae, &be);
+    const float T2 = T * T;
+#pragma unroll
+    for (int m = 0; m < KT; ++m) {
+        if (m < K) {
+            const float t = s_t[m];
+            const float num = t * fmaf(t, be, -2.0f * ae);
+            const float T2n = fmaxf(T2 + num, eps2);
+            const float Tn = T2n * rsqrtf(T2n);
+            kahan_add(dJ[m], cJ[m], w * __fdividef(num, Tn + T));
+        }
     }
-    float vals[3] = {A - cA, B - cB, F - cF};
-    block_sum_to<3, 256>(vals, partials + (size_t)blockIdx.x * kPartialStride, rsm);
-    if (!reduce_slice<3, 256>(*S, partials, kPartialStride, 0, gridDim.x, blockIdx.x, rsm, res, &last_flag)) return;
-    if (threadIdx.x < 3) S->sc[SC_Q0 + 1 + threadIdx.x] = res[threadIdx.x];   // A, B, F
 }
 
-// All Armijo trials of one GD iteration: per face, with frozen w and T,
-// dJ_m += w (T'^2 - T^2) / (T' + T), T'^2 - T^2 = t (t b - 2 a); then the decision.
+// All Armijo trials of one GD iteration over the faces each voxel owns (weights and T
+// frozen at f, evaluated as k3tv_grad evaluates them), then the decision from the sums
+// k3tv_grad left in sc[SC_Q0 ..]: the first trial with
+// E(f - t g) <= E(f) - c t |g|^2, E = lambda/2 |f - v|^2 + J.
 template <int KT>
-__global__ void __launch_bounds__(256, 8)
-k3tv_trials(Vol V, const float *__restrict__ f, const float *__restrict__ g, const float *__restrict__ TT,
-            const float *__restrict__ WW, const ParamsDev *__restrict__ P, int K, int first, int energy_only,
-            double *__restrict__ partials, SliceDev *S)
+__global__ void __launch_bounds__(256, 3)
+k3tv_trials(Vol V, const float *__restrict__ f, const float *__restrict__ g, const ParamsDev *__restrict__ P,
+            int K, int first, int mode, double *__restrict__ partials, SliceDev *S)
 {
     __shared__ float s_t[KT];
     __shared__ double s_td[KT];
@@ -602,26 +752,32 @@ k3tv_trials(Vol V, const float *__restrict__ f, const float *__restrict__ g, con
     }
     __syncthreads();
     const float eps2 = (float)(P->eps * P->eps);
+    const float sig = (float)S->sc[SC_SIGMA];
+    const float inv_s2 = 1.0f / (sig * sig);
     float dJ[KT], cJ[KT];
 #pragma unroll
     for (int m = 0; m < KT; ++m) dJ[m] = cJ[m] = 0.0f;
-    for (long long e = (long long)blockIdx.x * 256 + threadIdx.x; K > 0 && e < V.nf;
-         e += (long long)gridDim.x * 256) {
-        int i, j, k;
-        const int d = face_pos(V, e, i, j, k);
-        float D, T2x, ae, be;
-        face_terms(f, g, V, d, i, j, k, eps2, D, T2x, ae, be);
-        const float T = __ldg(TT + e), w = __ldg(WW + e);
-        const float T2 = T * T;
-#pragma unroll
-        for (int m = 0; m < KT; ++m) {
-            if (m < K) {
-                const float t = s_t[m];
-                const float num = t * fmaf(t, be, -2.0f * ae);
-                const float T2n = fmaxf(T2 + num, eps2);
-                const float Tn = T2n * rsqrtf(T2n);
-                kahan_add(dJ[m], cJ[m], w * __fdividef(num, Tn + T));
+    const long long n_items = (long long)V.nx * V.ny * ((V.nz + kZChunk - 1) / kZChunk);
+    for (long long it = (long long)blockIdx.x * 256 + threadIdx.x; K > 0 && it < n_items;
+         it += (long long)gridDim.x * 256) {
+        int i, j, k0;
+        ColIn m;
+        zitem(V, it, i, j, k0, m);
+        const int k1 = min(k0 + kZChunk, V.nz);
+        float NF[3][3][3], NG[3][3][3];
+        zwin_start(f, V, i, j, k0, m, NF);
+        zwin_start(g, V, i, j, k0, m, NG);
+        for (int k = k0; k < k1; ++k) {
+            if (k > k0) {
+                zwin_step(f, V, i, j, k - 1, m, NF);
+                zwin_step(g, V, i, j, k - 1, m, NG);
             }
+            trial_face<KT, 0, 0>(NF, NG, mode, eps2, inv_s2, K, s_t, dJ, cJ);
+            trial_face<KT, 1, 0>(NF, NG, mode, eps2, inv_s2, K, s_t, dJ, cJ);
+            trial_face<KT, 2, 0>(NF, NG, mode, eps2, inv_s2, K, s_t, dJ, cJ);
+            if (i == V.nx - 1) trial_face<KT, 0, 1>(NF, NG, mode, eps2, inv_s2, K, s_t, dJ, cJ);
+            if (j == V.ny - 1) trial_face<KT, 1, 1>(NF, NG, mode, eps2, inv_s2, K, s_t, dJ, cJ);
+            if (k == V.nz - 1) trial_face<KT, 2, 1>(NF, NG, mode, eps2, inv_s2, K, s_t, dJ, cJ);
         }
     }
 #pragma unroll
@@ -634,7 +790,7 @@ k3tv_trials(Vol V, const float *__restrict__ f, const float *__restrict__ g, con
         const double J = sc[SC_Q0], A = sc[SC_Q0 + 1], Bg = sc[SC_Q0 + 2], F = sc[SC_Q0 + 3];
         const double lamd = P->lambda;
         const double E0 = 0.5 * lamd * F + J;
-        const bool armijo = !energy_only && P->step_rule != EPTV_STEP_FIXED;
+        const bool armijo = P->step_rule != EPTV_STEP_FIXED;
         double dl = 0.0;
         bool pass = false, nonfinite = false;
         if (armijo && threadIdx.x < K) {
@@ -649,9 +805,7 @@ k3tv_trials(Vol V, const float *__restrict__ f, const float *__restrict__ g, con
         const double dE = __shfl_sync(0xffffffffu, dl, acc_m >= 0 ? acc_m : 0);
         if (threadIdx.x == 0) {
             bool bad = !isfinite(E0) || !isfinite(A) || !isfinite(Bg);
-            if (energy_only) {
-                sc[SC_E_FIRST] = E0;
-            } else {
+            {
                 if (first) sc[SC_E_FIRST] = E0;
                 if (P->step_rule == EPTV_STEP_FIXED) {
                     const double t = s_td[0];
@@ -727,7 +881,7 @@ struct eptv3_geometry {
     ViewRec3 *view = nullptr;
     float *u = nullptr, *s = nullptr, *t = nullptr, *fa = nullptr, *fb = nullptr, *g = nullptr;
     float *y = nullptr, *r = nullptr, *q = nullptr;
-    float *Q = nullptr, *TT = nullptr, *WW = nullptr, *Tsel = nullptr, *sel = nullptr;
+    float *Tsel = nullptr, *sel = nullptr;
     double *partials = nullptr, *sc = nullptr;
     unsigned long long *acc = nullptr;
     unsigned int *ctr = nullptr;
@@ -805,7 +959,7 @@ static int c3_p2(const eptv3_geometry *g, const eptv_params *p, const float *v, 
     const long long nv = g->C.n_vox;
     const float eps2 = (float)(p->eps * p->eps);
     // sigma: k-th smallest face magnitude of v
-    k3tv_face_T<<<nblk_of(V.nf, 256), 256, 0, st>>>(V, v, eps2, g->Tsel);
+    k3tv_face_T<<<nblk_of(nv, 256), 256, 0, st>>>(V, v, eps2, g->Tsel);
     const long long rank = std::min<long long>(std::max<long long>((long long)std::ceil(p->sigma_q * V.nf), 1), V.nf);
     const char *err = "";
     int rc = select_kth_noalloc(g->Tsel, (long)V.nf, (long)rank, g->sel, st, &err);
@@ -819,13 +973,12 @@ static int c3_p2(const eptv3_geometry *g, const eptv_params *p, const float *v, 
     for (int n = 0; n < p->n_gd; ++n) {
         float *nxt = (n == p->n_gd - 1) ? out : ((cur == g->fb) ? g->u : g->fb);
         if (nxt == v) nxt = g->fb;
-        k3tv_faces<<<nblk_capped(V.nf, 256, g->red_blocks), 256, 0, st>>>(V, cur, eps2, mode, g->Q, g->TT, g->WW, g->partials, g->d_sd);
-        k3tv_grad<<<nblk_capped(nv, 256, g->red_blocks), 256, 0, st>>>(V, cur, v, g->Q, (float)p->lambda, g->g, g->partials, g->d_sd);
-        const unsigned nbf = nblk_capped(V.nf, 256, g->red_blocks);
-        if (K <= 1) k3tv_trials<1><<<nbf, 256, 0, st>>>(V, cur, g->g, g->TT, g->WW, g->d_params, K, n == 0, 0, g->partials, g->d_sd);
-        else if (K <= 4) k3tv_trials<4><<<nbf, 256, 0, st>>>(V, cur, g->g, g->TT, g->WW, g->d_params, K, n == 0, 0, g->partials, g->d_sd);
-        else if (K <= 8) k3tv_trials<8><<<nbf, 256, 0, st>>>(V, cur, g->g, g->TT, g->WW, g->d_params, K, n == 0, 0, g->partials, g->d_sd);
-        else k3tv_trials<16><<<nbf, 256, 0, st>>>(V, cur, g->g, g->TT, g->WW, g->d_params, K, n == 0, 0, g->partials, g->d_sd);
+        const unsigned nbv = nblk_capped((long long)V.nx * V.ny * ((V.nz + kZChunk - 1) / kZChunk), 256, g->red_blocks);
+        k3tv_grad<<<nbv, 256, 0, st>>>(V, cur, v, eps2, mode, (float)p->lambda, g->g, g->partials, g->d_sd);
+        if (K <= 1) k3tv_trials<1><<<nbv, 256, 0, st>>>(V, cur, g->g, g->d_params, K, n == 0, mode, g->partials, g->d_sd);
+        else if (K <= 4) k3tv_trials<4><<<nbv, 256, 0, st>>>(V, cur, g->g, g->d_params, K, n == 0, mode, g->partials, g->d_sd);
+        else if (K <= 8) k3tv_trials<8><<<nbv, 256, 0, st>>>(V, cur, g->g, g->d_params, K, n == 0, mode, g->partials, g->d_sd);
+        else k3tv_trials<16><<<nbv, 256, 0, st>>>(V, cur, g->g, g->d_params, K, n == 0, mode, g->partials, g->d_sd);
         k3tv_apply<<<nblk_of(nv, 256), 256, 0, st>>>(cur, g->g, nxt, nv, g->sc, n == p->n_gd - 1 ? 1 : 0);
         cur = nxt;
     }
@@ -971,7 +1124,7 @@ int eptv3_create_geometry(const eptv3_geometry_desc *d, eptv3_geometry **out) {
     A(&g->ys, (size_t)n_rays);
     for (float **p : {&g->u, &g->s, &g->t, &g->fa, &g->fb, &g->g}) A(p, (size_t)n_vox);
     for (float **p : {&g->y, &g->r, &g->q}) A(p, (size_t)n_rays);
-    for (float **p : {&g->Q, &g->TT, &g->WW, &g->Tsel}) A(p, (size_t)V.nf);
+    A(&g->Tsel, (size_t)V.nf);
     A(&g->sel, 1);
     A(&g->partials, (size_t)std::max(std::max(blk_k31, blk_k32) * 2, std::max(blk_face, blk_vox) * kPartialStride));
     A(&g->acc, (size_t)kPartialStride * kAccCopies * kAccStride);
@@ -1131,8 +1284,10 @@ int eptv3_report_energy(const eptv3_geometry *g, const eptv_params *p, double si
     c3_project(g, d_f, d_y, g->q, FIN_NORM, st);                         // |y - P f|^2 -> SC_NORM
     k3_set_scalar<<<1, 1, 0, st>>>(g->d_sd, SC_SIGMA, sigma_ref);
     const int mode = p->weights_mode == EPTV_WEIGHTS_ONE ? EPTV_WEIGHTS_ONE : EPTV_WEIGHTS_EPTV;
-    k3tv_faces<<<nblk_capped(g->V.nf, 256, g->red_blocks), 256, 0, st>>>(g->V, d_f, (float)(p->eps * p->eps), mode, g->Q, g->TT,
-                                                       g->WW, g->partials, g->d_sd);
+    // J at f (k3tv_grad with v = f; its g goes to the workspace)
+    const long long n_items = (long long)g->V.nx * g->V.ny * ((g->V.nz + kZChunk - 1) / kZChunk);
+    k3tv_grad<<<nblk_capped(n_items, 256, g->red_blocks), 256, 0, st>>>(g->V, d_f, d_f, (float)(p->eps * p->eps), mode,
+                                                                         (float)p->lambda, g->g, g->partials, g->d_sd);
     C3CU(cudaGetLastError());
     double sc[kScalarStride];
     if ((rc = c3_read_sc(g, sc, st))) return rc;

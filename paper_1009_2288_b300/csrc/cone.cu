@@ -268,7 +268,8 @@ __global__ void __launch_bounds__(256, 4)
 k32_backproject(Cone C, const float *__restrict__ ys, float *__restrict__ out, double *__restrict__ partials,
                 SliceDev *S, int fin)
 {
-    constexpr int NQ = ZP / 2;                              // float4 per row: (lo, hi) of two voxels
+    constexpr int NQ = ZP / 2;                              // float4 per row: the ZP + 1 plane parameters
+    static_assert(4 * NQ >= ZP + 1, "plane parameters fit the row's words");
     const double gamma_pre = threadIdx.x == 0 ? fin_gamma(S->sc, fin) : 0.0;
     extern __shared__ float4 s_zt[];                       // [band][NQ]
     __shared__ double rsm[2 * 8];
@@ -284,13 +285,12 @@ k32_backproject(Cone C, const float *__restrict__ ys, float *__restrict__ out, d
     k32_band(C, Z[0], Ze, b0, b1);
     for (int r = b0 + (int)threadIdx.x; r <= b1; r += 256) {
         const RowRec3 Rr = C.row[r];
-        float tz[ZP + 1];
+        float tz[4 * NQ];
 #pragma unroll
-        for (int q = 0; q <= ZP; ++q) tz[q] = cross_t(Z[q], Rr.qz, Rr.iz);
+        for (int q = 0; q < 4 * NQ; ++q) tz[q] = q <= ZP ? cross_t(Z[q], Rr.qz, Rr.iz) : 0.0f;
 #pragma unroll
         for (int h = 0; h < NQ; ++h)
-            s_zt[(r - b0) * NQ + h] = make_float4(fminf(tz[2 * h], tz[2 * h + 1]), fmaxf(tz[2 * h], tz[2 * h + 1]),
-                                                  fminf(tz[2 * h + 1], tz[2 * h + 2]), fmaxf(tz[2 * h + 1], tz[2 * h + 2]));
+            s_zt[(r - b0) * NQ + h] = make_float4(tz[4 * h], tz[4 * h + 1], tz[4 * h + 2], tz[4 * h + 3]);
     }
     __syncthreads();
     const int pxy = blockIdx.x * 256 + threadIdx.x;         // iy * nx + ix
@@ -336,18 +336,25 @@ k32_backproject(Cone C, const float *__restrict__ ys, float *__restrict__ out, d
                 const float hi_xy = fminf(fmaxf(ax, bx), fmaxf(ay, by));
                 if (!(lo_xy < hi_xy)) continue;
                 const float *ycol = ysv + iu;
-                // min / max are exact, so max(0, min(hi_xy, hi_z) - max(lo_xy, lo_z)) is
-                // the canonical six-plane length
+                // Voxel q of the stack spans the row's plane parameters tz[q], tz[q + 1]
+                // (a = their min, b = their max).  With c = min(max(tz, lo_xy), hi_xy),
+                // |c[q + 1] - c[q]| is bit for bit the canonical six-plane length
+                // max(0, min(hi_xy, b) - max(lo_xy, a)): where the intervals meet the two
+                // clamped ends are min(hi_xy, b) and max(lo_xy, a) themselves, elsewhere
+                // both ends clamp to the same bound (lo_xy < hi_xy here).  ZP + 1 clamps
+                // instead of two min / max per voxel.
                 for (int iv = iv0; iv <= iv1; ++iv) {
                     const float yv = __ldg(ycol + iv * C.nu);
+                    float c[4 * NQ];
 #pragma unroll
                     for (int h = 0; h < NQ; ++h) {
                         const float4 zt = s_zt[(iv - b0) * NQ + h];
-                        const float l0 = fmaxf(0.0f, __fsub_rn(fminf(hi_xy, zt.y), fmaxf(lo_xy, zt.x)));
-                        const float l1 = fmaxf(0.0f, __fsub_rn(fminf(hi_xy, zt.w), fmaxf(lo_xy, zt.z)));
-                        acc[2 * h] = fmaf(l0, yv, acc[2 * h]);
-                        acc[2 * h + 1] = fmaf(l1, yv, acc[2 * h + 1]);
+                        c[4 * h] = zt.x; c[4 * h + 1] = zt.y; c[4 * h + 2] = zt.z; c[4 * h + 3] = zt.w;
                     }
+#pragma unroll
+                    for (int q = 0; q <= ZP; ++q) c[q] = fminf(fmaxf(c[q], lo_xy), hi_xy);
+#pragma unroll
+                    for (int q = 0; q < ZP; ++q) acc[q] = fmaf(fabsf(__fsub_rn(c[q + 1], c[q])), yv, acc[q]);
                 }
             }
         }

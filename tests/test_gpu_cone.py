@@ -253,3 +253,26 @@ def test_create_rejects_geometries_outside_the_kernels_assumptions(change, msg):
     with pytest.raises(E.EptvError) as ei:
         E.Geometry3(I.ConeGeometry(**base))
     assert ei.value.code == -1 and msg in str(ei.value)
+
+
+@pytest.mark.parametrize("name", ["aniso", "tall", "slice"])
+@pytest.mark.parametrize("rule", [O.FIXED, O.ARMIJO])
+def test_tv_step_ragged_volumes(name, rule):
+    """(P2) on volumes whose sides are not multiples of the kernels' work units: 20 x 17 x 11
+    (a column segment of 11), 16 x 16 x 24 (a full 16-voxel segment and a short one above
+    it) and 9 x 13 x 1 (a single plane: every face's z neighbours are outside), so the
+    windows the threads carry up their columns start, stop and meet the volume's borders in
+    every way, against the oracle."""
+    g = GEOMS[name]
+    rng = np.random.Generator(np.random.PCG64(12))
+    v = blobs(g, 7) + 0.002 * rng.standard_normal((g.nz, g.ny, g.nx))
+    p = I.EptvParams(n_gd=4, step_rule=rule, t_fixed=2e-4)
+    want, st = C.p2_solve(v, p, p.t_init_eff)
+    want = np.maximum(want, 0.0)
+    geo = E.Geometry3(g)
+    f = torch.empty(g.n_vox, device=DEV)
+    stats, t_prev = E.eptv3_tv_step(geo, p, t32(v), f)
+    assert stats.sigma == pytest.approx(st.sigma, rel=2e-3)
+    assert rel(np64(f).reshape(want.shape), want) < 1e-4
+    if rule == O.ARMIJO:
+        assert t_prev == pytest.approx(st.t_prev, rel=1e-6)

@@ -8,18 +8,22 @@
 // w^2) / sdd^2) per detector pixel: P = diag(F) L', and both kernels below compute the
 // entries of L' with the same canonical formula from the same tables.  Kernels:
 //   K31  P:   ray-driven Siddon in 3-D.  A warp holds 32 adjacent detector columns of one
-//             detector row; the warps of a block split the ray's range along its major
-//             axis (x or y).  In each major-axis slab the ray walks the cells of the two
-//             minor axes incrementally, so every voxel it crosses gets the canonical
-//             length min(exit planes) - max(entry planes) of eptv_internal.cuh.
-//   K32  P^T: voxel-driven gather, the exact transpose L'^T diag(F): a thread owns two
-//             voxels stacked in z; per view, their corners bound the detector columns
-//             whose rays can cross them, each column's x-y chord through the pair bounds
-//             its rows, and each such ray's L' entry is the same canonical formula.
-//   (P2) half-face kernels (the 2-D half-edges extended to faces, Eqs. 5, 9, A2, A3 in
-//             3-D), a gradient kernel, one kernel that evaluates all Armijo trial steps,
-//             and the step/clamp kernel; every reduction is the exact, order-independent
-//             one of eptv_internal.cuh, the step decision FP64 in parallel lanes.
+//             detector row; the SEG warps of a block split the ray's range along its major
+//             axis (x or y).  The ray walks one cell per loop step: the cell's length is
+//             its exit (the nearest of its three exit planes) minus its entry (the
+//             previous cell's exit), the canonical min(exit planes) - max(entry planes) of
+//             eptv_internal.cuh, and the lanes advance by selects, never branching apart.
+//   K32  P^T: voxel-driven gather, the exact transpose L'^T diag(F): a thread owns ZP
+//             voxels stacked in z (2 or 4); per view, the stack's corners bound the
+//             detector columns and rows whose rays can cross it; per column, the x-y chord
+//             through the stack; per row, the stack's plane parameters clamped to the
+//             chord give each voxel's canonical length.
+//   (P2) voxel-major kernels (the 2-D half-edges extended to faces, Eqs. 5, 9, A2, A3 in
+//             3-D): the face magnitudes for sigma, the gradient with the energy sums, all
+//             Armijo trial steps with the step decision, and the step / clamp; a thread
+//             marches a column segment in z with the voxel's 19-value neighbourhood in
+//             registers.  The block sums go through the exact, order-independent
+//             reduction of eptv_internal.cuh; the step decision is FP64 in parallel lanes.
 #include <math.h>
 #include <stdint.h>
 

@@ -27,7 +27,7 @@ constexpr int kRowsPT = 2;                                   // pixel rows per t
 constexpr int kBlocksPT = (kTileW / 4) * (kTileH / kRowsPT);  // 4 x kRowsPT blocks per tile
 
 template <int VG, bool EQ11>
-__global__ void __launch_bounds__(kBlocksPT * VG)
+__global__ void __launch_bounds__(kBlocksPT * VG, EQ11 ? 1 : 1024 / (kBlocksPT * VG))
 k2_backproject(const SliceDev *__restrict__ sls, TileMap map, BackArgs a, double *__restrict__ partials)
 {
     pdl_wait();
@@ -144,14 +144,20 @@ k2_backproject(const SliceDev *__restrict__ sls, TileMap map, BackArgs a, double
                 for (int r = 0; r <= R; ++r) ty[r] = cross_t(Y[r], Rr.py, Rr.iy);
 #pragma unroll
                 for (int q = 0; q < 5; ++q) tx[q] = cross_t(X[q], Rr.px, Rr.ix);
+                // the column planes clamped to the row's slab [rlo, rhi]: pixel q's length
+                // |c[q + 1] - c[q]| is bit for bit seg_len(min, max of tx[q], tx[q + 1],
+                // rlo, rhi) (where the column meets the slab its clamped planes are those
+                // min / max, elsewhere both clamp to one bound) -- 5 clamps per row
+                // instead of two min / max pairs per pixel
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     const float rlo = fminf(ty[r], ty[r + 1]), rhi = fmaxf(ty[r], ty[r + 1]);
+                    float c[5];
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const float lo = fminf(tx[q], tx[q + 1]), hi = fmaxf(tx[q], tx[q + 1]);
-                        acc[r][q] = fmaf(seg_len(lo, hi, rlo, rhi), yv, acc[r][q]);
-                    }
+                    for (int q = 0; q < 5; ++q) c[q] = fminf(fmaxf(tx[q], rlo), rhi);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        acc[r][q] = fmaf(fabsf(__fsub_rn(c[q + 1], c[q])), yv, acc[r][q]);
                 }
             }
         }

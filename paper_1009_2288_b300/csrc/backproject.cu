@@ -27,7 +27,7 @@ constexpr int kRowsPT = 2;                                   // pixel rows per t
 constexpr int kBlocksPT = (kTileW / 4) * (kTileH / kRowsPT);  // 4 x kRowsPT blocks per tile
 
 template <int VG, bool EQ11>
-__global__ void __launch_bounds__(kBlocksPT * VG, EQ11 ? 1 : 1024 / (kBlocksPT * VG))
+__global__ void __launch_bounds__(kBlocksPT * VG, EQ11 ? 0 : 1024 / (kBlocksPT * VG))
 k2_backproject(const SliceDev *__restrict__ sls, TileMap map, BackArgs a, double *__restrict__ partials)
 {
     pdl_wait();

@@ -475,17 +475,18 @@ struct FaceAt {
 
 // D = b - a and T^2 = eps^2 + D^2 + sum over t1, t2 of (cp^2 + cm^2) / 2 (Eq. A3 in 3-D:
 // mc = (a + b) / 2, cp = (a + e_t + b + e_t) / 2 - mc, cm = mc - (a - e_t + b - e_t) / 2)
-// from the stencil s of FaceAt::values.  Explicitly rounded operations: the two voxels
-// beside a face evaluate it to the same bits.
+// from the stencil s of FaceAt::values.  Explicitly rounded (and explicitly fused)
+// operations: the two voxels beside a face evaluate it to the same bits.
 __device__ __forceinline__ float face_T2(float eps2, const float (&s)[10], float *D) {
     const float d = __fsub_rn(s[1], s[0]);
     const float mc = __fmul_rn(0.5f, __fadd_rn(s[0], s[1]));
     float t2 = __fmaf_rn(d, d, eps2);
 #pragma unroll
     for (int t = 0; t < 2; ++t) {
-        const float cp = __fsub_rn(__fmul_rn(0.5f, __fadd_rn(s[2 + 4 * t], s[3 + 4 * t])), mc);
-        const float cm = __fsub_rn(mc, __fmul_rn(0.5f, __fadd_rn(s[4 + 4 * t], s[5 + 4 * t])));
-        t2 = __fadd_rn(t2, __fadd_rn(__fmul_rn(0.5f, __fmul_rn(cp, cp)), __fmul_rn(0.5f, __fmul_rn(cm, cm))));
+        const float cp = __fmaf_rn(0.5f, __fadd_rn(s[2 + 4 * t], s[3 + 4 * t]), -mc);
+        const float cm = __fmaf_rn(-0.5f, __fadd_rn(s[4 + 4 * t], s[5 + 4 * t]), mc);
+        t2 = __fmaf_rn(__fmul_rn(0.5f, cp), cp, t2);      // 0.5 cp is exact
+        t2 = __fmaf_rn(__fmul_rn(0.5f, cm), cm, t2);
     }
     *D = d;
     return t2;
